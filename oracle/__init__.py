@@ -1,0 +1,193 @@
+"""Python access to the CPU oracle (oracle.c).
+
+TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and bench.py's
+cpu_baseline / reference legs use it. The product package never imports it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so next to it (plain C, -O2, no OpenMP)."""
+    src = os.path.join(_HERE, "oracle.c")
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
+            os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, src, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class _Basis(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("degree", ctypes.c_int32), ("n_knots", ctypes.c_int32),
+                ("knots", ctypes.POINTER(ctypes.c_double))]
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("u", _Basis), ("v", _Basis), ("ctrl", ctypes.POINTER(ctypes.c_double)),
+                ("weights", ctypes.POINTER(ctypes.c_double)), ("t", _Basis), ("n_plies", ctypes.c_int32),
+                ("ply_thickness", ctypes.POINTER(ctypes.c_double)),
+                ("ply_material", ctypes.POINTER(ctypes.c_int32)),
+                ("ply_angle", ctypes.POINTER(ctypes.c_double)), ("n_materials", ctypes.c_int32),
+                ("C21", ctypes.POINTER(ctypes.c_double)), ("nq_u", ctypes.c_int32), ("nq_v", ctypes.c_int32),
+                ("nq_t", ctypes.c_int32)]
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I32 = ctypes.POINTER(ctypes.c_int32)
+_I64 = ctypes.POINTER(ctypes.c_int64)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_SO)
+        L.ora_gauss.argtypes = [ctypes.c_int32, _D, _D]
+        L.ora_nfun.argtypes = [ctypes.POINTER(_Basis)]
+        L.ora_nfun.restype = ctypes.c_int32
+        L.ora_nel.argtypes = [ctypes.POINTER(_Basis)]
+        L.ora_nel.restype = ctypes.c_int32
+        L.ora_basis1d_eval.argtypes = [ctypes.POINTER(_Basis), ctypes.c_int32, ctypes.c_double, _D, _D, _I32]
+        L.ora_rotated_D.argtypes = [_D, ctypes.c_double, _D]
+        L.ora_rotated_D.restype = None
+        L.ora_sizes.argtypes = [ctypes.POINTER(_Problem), _I64, _I64]
+        for f in (L.ora_assemble, L.ora_assemble_split):
+            f.argtypes = [ctypes.POINTER(_Problem), _I64, _I32, _D]
+        L.ora_block.argtypes = [ctypes.POINTER(_Problem), ctypes.c_int64, ctypes.c_int64, _D]
+        L.ora_element_stiffness.argtypes = [ctypes.POINTER(_Problem), ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_int32, _D]
+        _lib = L
+    return _lib
+
+
+def _ptr(a, t=_D):
+    return a.ctypes.data_as(t)
+
+
+class Problem:
+    """Marshals a ``workloads.Laminate`` into the oracle's problem struct and
+    keeps the arrays alive."""
+
+    def __init__(self, lam):
+        self._keep = []
+
+        def arr(x, dt=np.float64):
+            a = np.ascontiguousarray(x, dtype=dt)
+            self._keep.append(a)
+            return a
+
+        def basis(b):
+            k = arr(b.knots)
+            return _Basis(b.kind, b.degree, len(k), _ptr(k))
+
+        ctrl = arr(lam.ctrl)
+        w = arr(lam.weights) if lam.weights is not None else None
+        h = arr(lam.ply_thickness)
+        pm = arr(lam.ply_material, np.int32)
+        pa = arr(lam.ply_angle)
+        C = arr(lam.C21)
+        nq = tuple(lam.nq) + (0,) * (3 - len(lam.nq))
+        self.s = _Problem(basis(lam.u), basis(lam.v), _ptr(ctrl), _ptr(w) if w is not None else _D(),
+                          basis(lam.t), len(h), _ptr(h), _ptr(pm, _I32), _ptr(pa), C.shape[0], _ptr(C),
+                          nq[0], nq[1], nq[2])
+        self.lam = lam
+
+    def ref(self):
+        return ctypes.byref(self.s)
+
+
+def gauss(n: int):
+    x = np.zeros(n)
+    w = np.zeros(n)
+    if lib().ora_gauss(n, _ptr(x), _ptr(w)) != 0:
+        raise ValueError("bad Gauss order")
+    return x, w
+
+
+def basis1d_eval(kind: int, degree: int, knots, e: int, x: float):
+    k = np.ascontiguousarray(knots, dtype=np.float64)
+    b = _Basis(kind, degree, len(k), _ptr(k))
+    val = np.zeros(degree + 1)
+    der = np.zeros(degree + 1)
+    first = ctypes.c_int32()
+    if lib().ora_basis1d_eval(ctypes.byref(b), e, x, _ptr(val), _ptr(der), ctypes.byref(first)) != 0:
+        raise ValueError("bad element")
+    return first.value, val, der
+
+
+def n_elements(kind: int, degree: int, knots) -> int:
+    k = np.ascontiguousarray(knots, dtype=np.float64)
+    b = _Basis(kind, degree, len(k), _ptr(k))
+    return lib().ora_nel(ctypes.byref(b))
+
+
+def rotated_D(C21, theta: float) -> np.ndarray:
+    C = np.ascontiguousarray(C21, dtype=np.float64)
+    D = np.zeros(36)
+    lib().ora_rotated_D(_ptr(C), float(theta), _ptr(D))
+    return D.reshape(6, 6)
+
+
+def sizes(lam):
+    p = Problem(lam)
+    n = ctypes.c_int64()
+    z = ctypes.c_int64()
+    if lib().ora_sizes(p.ref(), ctypes.byref(n), ctypes.byref(z)) != 0:
+        raise ValueError("oracle rejected the problem")
+    return n.value, z.value
+
+
+def _assemble(lam, fn):
+    p = Problem(lam)
+    n_dof, nnz = sizes(lam)
+    row_ptr = np.zeros(n_dof + 1, np.int64)
+    col = np.zeros(nnz, np.int32)
+    val = np.zeros(nnz, np.float64)
+    if fn(p.ref(), _ptr(row_ptr, _I64), _ptr(col, _I32), _ptr(val)) != 0:
+        raise ValueError("oracle assembly failed")
+    return row_ptr, col, val
+
+
+def assemble(lam):
+    """Standard element-by-element assembly: (row_ptr int64, col int32, val f64)."""
+    return _assemble(lam, lib().ora_assemble)
+
+
+def assemble_split(lam):
+    """Split assembly with one P per ply (small problems only)."""
+    return _assemble(lam, lib().ora_assemble_split)
+
+
+def block(lam, i: int, j: int, problem: Problem | None = None) -> np.ndarray:
+    p = problem if problem is not None else Problem(lam)
+    out = np.zeros(9)
+    if lib().ora_block(p.ref(), int(i), int(j), _ptr(out)) != 0:
+        raise ValueError("bad block index")
+    return out.reshape(3, 3)
+
+
+def element_stiffness(lam, ex: int, ey: int, et: int, problem: Problem | None = None) -> np.ndarray:
+    p = problem if problem is not None else Problem(lam)
+    nl = (lam.u.degree + 1) * (lam.v.degree + 1) * (lam.t.degree + 1)
+    out = np.zeros(nl * nl * 9)
+    if lib().ora_element_stiffness(p.ref(), ex, ey, et, _ptr(out)) < 0:
+        raise ValueError("element stiffness failed")
+    return out.reshape(nl, nl, 3, 3)
+
+
+def to_dense(row_ptr, col, val, n):
+    K = np.zeros((n, n))
+    for r in range(n):
+        s, e = row_ptr[r], row_ptr[r + 1]
+        K[r, col[s:e]] = val[s:e]
+    return K

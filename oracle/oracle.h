@@ -1,0 +1,91 @@
+/*
+ * CPU oracle for the stiffness matrix of an extruded layered solid.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py load this library. The product
+ * (paper_1905_05417_gb300 and its CUDA library) never includes, links or calls
+ * anything here, and nothing here includes the product's headers.
+ *
+ * What it computes (Antolin, "Fast assembly of Galerkin matrices for 3D solid
+ * laminated composites", Sections 2.1-2.4 and 3):
+ *   K^{ij} = sum_l int_{Omega_l} B^{iT} D_l B^j |DF| dxi            (Eq. Km_0)
+ * element by element with tensor Gauss rules (Section 2.4), and, as a second
+ * formula for small cases, the split form
+ *   K^{ij} = sum_l sum_{ab} P_{l,ab}^{i_s j_s} Q_{l,ab}^{i_t j_t}   (Eq. Km_2)
+ * with P from Eq. P and Q from Eq. Q.
+ *
+ * Conventions (the same ones the library documents, restated here):
+ *   - in-plane basis S^{i_s}, i_s = iy*nx + ix; thickness basis T^{i_t};
+ *     3D basis index i = i_t*n_s + i_s (Assumption 1); DOF = 3*i + c.
+ *   - the thickness coordinate is physical z (extrusion direction a = e_z).
+ *   - ply 0 starts at the first thickness knot; plies are stacked upwards.
+ *   - materials: 21 Voigt constants (upper triangle, row-major, order
+ *     11,22,33,12,13,23, engineering shear) in the material frame; a ply with
+ *     angle theta has its fibre axis 1 at +theta about +z from global x.
+ */
+#ifndef LAM_ORACLE_H
+#define LAM_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORA_BSPLINE = 0, ORA_LAGRANGE = 1 };
+
+typedef struct {
+  int32_t kind;          /* ORA_BSPLINE or ORA_LAGRANGE */
+  int32_t degree;
+  int32_t n_knots;       /* B-spline: knot-vector length; Lagrange: number of breakpoints */
+  const double* knots;   /* B-spline: open knot vector; Lagrange: element breakpoints */
+} ora_basis1d;
+
+typedef struct {
+  ora_basis1d u, v;        /* in-plane directions xi^1 (x-index) and xi^2 (y-index) */
+  const double* ctrl;      /* n_s x 2 control points (x, y), i_s = iy*nx + ix */
+  const double* weights;   /* n_s NURBS weights or NULL */
+  ora_basis1d t;           /* thickness basis in physical z */
+  int32_t n_plies;
+  const double* ply_thickness;
+  const int32_t* ply_material;
+  const double* ply_angle;  /* radians */
+  int32_t n_materials;
+  const double* C21;        /* n_materials x 21 */
+  int32_t nq_u, nq_v, nq_t; /* Gauss points per element direction (<= 0: degree + 1) */
+} ora_problem;
+
+/* Gauss-Legendre rule with n points on [-1, 1], ascending abscissae. */
+int ora_gauss(int32_t n, double* x, double* w);
+
+/* Number of functions / elements of a 1D basis. */
+int32_t ora_nfun(const ora_basis1d* b);
+int32_t ora_nel(const ora_basis1d* b);
+
+/* Values and first derivatives of the degree+1 functions of element e at x
+ * (x inside the element); *first receives the index of the first function. */
+int ora_basis1d_eval(const ora_basis1d* b, int32_t e, double x, double* val, double* der, int32_t* first);
+
+/* D of a ply: the 6x6 Voigt matrix of C rotated by theta about z. */
+void ora_rotated_D(const double* C21, double theta, double* D36);
+
+/* Sizes of the 3D problem. */
+int ora_sizes(const ora_problem* pr, int64_t* n_dof, int64_t* nnz);
+
+/* Full standard assembly (Eq. Km_0, Section 2.4) into the oracle's own CSR. */
+int ora_assemble(const ora_problem* pr, int64_t* row_ptr, int32_t* col, double* val);
+
+/* Full split assembly (Eq. Km_2 with Eq. P and Eq. Q, one P per ply). */
+int ora_assemble_split(const ora_problem* pr, int64_t* row_ptr, int32_t* col, double* val);
+
+/* One 3x3 block K^{ij} (row-major, [c][d]) for 3D basis indices i, j. */
+int ora_block(const ora_problem* pr, int64_t i, int64_t j, double* out9);
+
+/* Element stiffness of 3D element (ex, ey, et), all ply pieces inside it:
+ * out is nl x nl blocks of 3x3, nl = (pu+1)(pv+1)(q+1), local order
+ * (lt, ly, lx) with lx fastest. Returns nl, or -1 on error. */
+int ora_element_stiffness(const ora_problem* pr, int32_t ex, int32_t ey, int32_t et, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,215 @@
+/*
+ * lam.h -- C ABI of the GB300 (sm_103a) stiffness-assembly library for 3D
+ * layered solids built on an extruded tensor-product discretisation.
+ *
+ * Method: P. Antolin, "Fast assembly of Galerkin matrices for 3D solid
+ * laminated composites using finite element and isogeometric
+ * discretizations" (2019). The library assembles the FP64 stiffness matrix
+ *     K^{ij} = sum_l int_{Omega_l} B^{iT} D_l B^j |DF| dxi      (Eq. Km_0)
+ * of linear elasticity (Eq. a, Section 2.1) in CSR form, two ways:
+ *   - lam_assemble_split:    the split 2D x 1D method of Section 3,
+ *                            K = sum_m sum_{ab} P_{m,ab} (x) Q_{m,ab} (Eq. Km_2),
+ *                            one in-plane operator set per distinct
+ *                            (material, angle) configuration m;
+ *   - lam_assemble_standard: element-by-element 3D Gauss quadrature
+ *                            (Section 2.4), the comparison path.
+ * Both produce the same matrix up to rounding (Section 3, after Eq. Q).
+ *
+ * Discretisation (Assumption 1, Eq. basis_functions): 3D functions are
+ * products S^{i_s}(xi^1, xi^2) T^{i_t}(z) of an in-plane function and a
+ * thickness function.
+ *   - In-plane: tensor-product B-spline (optionally NURBS) or Lagrange Q_p basis
+ *     on [knots], with n_x * n_y functions, i_s = iy * n_x + ix; the in-plane
+ *     map is x(xi) = sum_i S^i(xi) X_i from the control points X_i.
+ *   - Thickness: B-spline or Lagrange basis in PHYSICAL z (the extrusion of
+ *     Eq. extrusion with a = e_z; Assumption 2 holds by construction).
+ *   - 3D function index i = i_t * n_s + i_s (0-based form of Assumption 1);
+ *     DOF index 3*i + c, c in {x, y, z}.
+ * Plies (Eq. C_layers, Assumption 3): ply 0 starts at the first thickness
+ * knot, plies stack upwards; each ply has a thickness, a material and an
+ * in-plane angle; the ply thicknesses must add up to the thickness-knot range
+ * (to 1e-10 relative). A ply interface closer than 1e-10 of a thickness
+ * element's length to an end of that element is taken to coincide with it.
+ * Materials: 21 Voigt constants (upper triangle, row-major, order
+ * 11,22,33,12,13,23, engineering shear, Eq. D) in the material frame; a ply
+ * of angle theta has its fibre axis 1 at +theta about +z from global x.
+ *
+ * Sparsity (bit-exact, independent of the values): one 3x3 block for every
+ * pair of 3D functions whose supports share a 3D element (an in-plane
+ * element times a thickness element); all 9 entries are stored, explicit
+ * zeros included; columns ascending; int64 row pointers, int32 columns.
+ *
+ * Conventions for every call:
+ *   - Errors are returned as lam_status; nothing traps or aborts. The last
+ *     error message of the calling thread is available from lam_last_error().
+ *   - Host pointers (struct fields of lam_plan_create) are read during the
+ *     call only; the plan copies what it needs.
+ *   - Device pointers (the d_ arguments) are caller-owned device memory of the
+ *     plan's device; the library never frees them.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Every device
+ *     call is stream-ordered and asynchronous unless stated otherwise. A plan
+ *     must not be used on two streams at the same time.
+ *   - The plan owns its device workspace (allocated with cudaMalloc on the
+ *     first device call, on the device current at that time).
+ */
+#ifndef LAM_H
+#define LAM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LAM_OK = 0,
+  LAM_ERR_INVALID_ARG = 1,  /* malformed input (degree, knots, plies, sizes) */
+  LAM_ERR_UNSUPPORTED = 2,  /* valid input outside what this build handles */
+  LAM_ERR_OOM = 3,          /* host or device allocation failed */
+  LAM_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+  LAM_ERR_TIMEOUT = 5       /* a bounded device wait gave up */
+} lam_status;
+
+typedef enum { LAM_BSPLINE = 0, LAM_LAGRANGE = 1 } lam_basis_kind;
+
+/* A 1D basis (Section 2.2). B-spline: `knots` is a non-decreasing open knot
+ * vector of length n_knots (functions: n_knots - degree - 1; interior knot
+ * multiplicity <= degree). Lagrange: `knots` holds the n_knots increasing
+ * element breakpoints; each element carries degree + 1 equispaced nodes
+ * (functions: degree * (n_knots - 1) + 1). 1 <= degree <= 7. */
+typedef struct {
+  int32_t kind;          /* lam_basis_kind */
+  int32_t degree;
+  int32_t n_knots;
+  const double* knots;   /* host */
+} lam_basis1d;
+
+/* In-plane discretisation and map (Section 2.2, Eq. gradient). */
+typedef struct {
+  lam_basis1d u;          /* xi^1 direction, index ix */
+  lam_basis1d v;          /* xi^2 direction, index iy */
+  const double* ctrl;     /* host, n_s x 2 (x, y), row i_s = iy * n_x + ix */
+  const double* weights;  /* host, n_s NURBS weights (> 0), or NULL (polynomial) */
+} lam_inplane;
+
+/* One ply (Eq. C_layers): thickness > 0, material index, angle in radians. */
+typedef struct {
+  double thickness;
+  int32_t material;
+  double angle_rad;
+} lam_ply;
+
+/* Material-frame Voigt constants (Eq. D), upper triangle row-major. */
+typedef struct {
+  double C[21];
+} lam_material;
+
+/* Options; pass NULL for the defaults. */
+typedef struct {
+  int32_t nq_u, nq_v, nq_t; /* Gauss points per element direction; 0 = degree + 1 (Section 2.4) */
+  double class_tol;         /* thickness pairs whose Q vectors (Eq. Q) agree to class_tol times the
+                               largest |Q| of the same (a, b) term share one combine slice; < 0 = 1e-13,
+                               0 = exact equality only */
+} lam_options;
+
+/* Sizes and structure of a plan. */
+typedef struct {
+  int64_t n_dof;          /* 3 * n_s * n_t */
+  int64_t nnz;            /* stored entries of K */
+  int64_t n_s, n_t;       /* in-plane and thickness function counts */
+  int64_t nnz_inplane;    /* in-plane neighbour pairs (sum over i_s of its neighbours) */
+  int64_t nnz_thickness;  /* thickness neighbour pairs */
+  int32_t n_configs;      /* distinct (material, angle) pairs, m-bar of Section 3.1 */
+  int32_t n_classes;      /* distinct thickness slices used by the combine */
+  int32_t monoclinic;     /* 1 if every configuration has D[I][J] == 0 for I < 4 <= J */
+  int32_t n_pieces;       /* (thickness element, ply) pieces */
+} lam_plan_info;
+
+typedef struct lam_plan lam_plan;
+
+/* Build a plan: validates the input, builds the 1D tables, Gauss rules,
+ * (material, angle) configurations (Section 3, the reuse of P per distinct
+ * configuration), thickness pieces and pair classes, and the sparsity sizes.
+ * Host work only: no device memory is touched until the first device call.
+ * `out` receives the plan (NULL on error). */
+lam_status lam_plan_create(lam_plan** out, const lam_inplane* inplane, const lam_basis1d* thickness,
+                           const lam_ply* plies, int32_t n_plies, const lam_material* materials,
+                           int32_t n_materials, const lam_options* options);
+
+/* Release the plan and its device workspace. NULL is accepted. Synchronises
+ * the plan's device before freeing. */
+lam_status lam_plan_destroy(lam_plan* plan);
+
+/* Sizes of the plan (host only). */
+lam_status lam_plan_get_info(const lam_plan* plan, lam_plan_info* info);
+
+/* Sparsity pattern of K (see above). With d_row_ptr == NULL and
+ * d_col_ind == NULL only *nnz_out is written (host only, no device work).
+ * Otherwise d_row_ptr (n_dof + 1 int64) and d_col_ind (nnz int32) are device
+ * buffers written on `stream`. nnz_out may be NULL. */
+lam_status lam_pattern(lam_plan* plan, int64_t* nnz_out, int64_t* d_row_ptr, int32_t* d_col_ind, void* stream);
+
+/* Split assembly (Section 3, Eq. Km_2 with Eq. P and Eq. Q): writes all nnz
+ * FP64 values of K, in the order of lam_pattern, to the device buffer
+ * d_values (nnz doubles). Recomputes the in-plane and thickness integrals on
+ * every call. Asynchronous on `stream`. */
+lam_status lam_assemble_split(lam_plan* plan, double* d_values, void* stream);
+
+/* Standard assembly (Section 2.4, Eq. Km_0): the same matrix by
+ * element-by-element 3D Gauss quadrature, into d_values (nnz doubles, device).
+ * Asynchronous on `stream`. */
+lam_status lam_assemble_standard(lam_plan* plan, double* d_values, void* stream);
+
+/* Split assembly into HOST memory: the values are assembled slab by slab of
+ * thickness rows in plan-owned device staging buffers and copied to h_values
+ * (nnz doubles, host; pinned memory gives full copy speed) while the next
+ * slab is assembled. Synchronous: returns when h_values is complete. */
+lam_status lam_assemble_split_host(lam_plan* plan, double* h_values, void* stream);
+
+/* Replace the ply angles (radians, n_plies values) and material constants
+ * (n_materials x 21, NULL = keep) of an existing plan, as a design loop does
+ * between assemblies. Host only; the configuration table and thickness
+ * classes are rebuilt. Returns LAM_ERR_INVALID_ARG if a count does not match. */
+lam_status lam_plan_update(lam_plan* plan, const double* ply_angle_rad, int32_t n_plies,
+                           const lam_material* materials, int32_t n_materials);
+
+/* Kernel kinds counted by the profiler. */
+typedef enum {
+  LAM_KERNEL_PATTERN = 0,   /* kp_row_ptr, kp_col_ind */
+  LAM_KERNEL_THICKNESS = 1, /* K-b: Eq. Q per thickness pair */
+  LAM_KERNEL_INPLANE = 2,   /* K-a: in-plane Gram blocks (Eq. P without D) */
+  LAM_KERNEL_COMBINE = 3,   /* K-c: Eq. Km_2 into the CSR values */
+  LAM_KERNEL_STANDARD = 4,  /* K-d: Section 2.4 element quadrature */
+  LAM_KERNEL_KINDS = 5
+} lam_kernel_kind;
+
+/* Per-plan profile: device time of every kernel launch, measured with CUDA
+ * events recorded on the launching stream around each launch, plus the bytes
+ * the plan moved between host and device. */
+typedef struct {
+  int32_t enabled;
+  int64_t launches[LAM_KERNEL_KINDS];
+  double ms[LAM_KERNEL_KINDS];
+  int64_t h2d_bytes;
+  int64_t d2h_bytes;
+} lam_profile;
+
+/* Enable (1) or disable (0) profiling of a plan's launches; either way the
+ * counters restart from zero. Host only. */
+lam_status lam_profile_enable(lam_plan* plan, int32_t enable);
+
+/* Read the counters. Waits for the recorded events of pending launches (so it
+ * synchronises with the streams they were recorded on). */
+lam_status lam_profile_get(lam_plan* plan, lam_profile* out);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* lam_last_error(void);
+
+/* Library version string. */
+const char* lam_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LAM_H */

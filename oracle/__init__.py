@@ -63,6 +63,7 @@ def lib():
         L.ora_sizes.argtypes = [ctypes.POINTER(_Problem), _I64, _I64]
         for f in (L.ora_assemble, L.ora_assemble_split):
             f.argtypes = [ctypes.POINTER(_Problem), _I64, _I32, _D]
+        L.ora_pattern.argtypes = [ctypes.POINTER(_Problem), _I64, _I32]
         L.ora_block.argtypes = [ctypes.POINTER(_Problem), ctypes.c_int64, ctypes.c_int64, _D]
         L.ora_element_stiffness.argtypes = [ctypes.POINTER(_Problem), ctypes.c_int32, ctypes.c_int32,
                                             ctypes.c_int32, _D]
@@ -156,6 +157,17 @@ def _assemble(lam, fn):
     if fn(p.ref(), _ptr(row_ptr, _I64), _ptr(col, _I32), _ptr(val)) != 0:
         raise ValueError("oracle assembly failed")
     return row_ptr, col, val
+
+
+def pattern(lam):
+    """Sparsity pattern only: (row_ptr int64, col int32)."""
+    p = Problem(lam)
+    n_dof, nnz = sizes(lam)
+    row_ptr = np.zeros(n_dof + 1, np.int64)
+    col = np.zeros(nnz, np.int32)
+    if lib().ora_pattern(p.ref(), _ptr(row_ptr, _I64), _ptr(col, _I32)) != 0:
+        raise ValueError("oracle pattern failed")
+    return row_ptr, col
 
 
 def assemble(lam):

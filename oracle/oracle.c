@@ -579,6 +579,15 @@ static void add_block(const pattern* P, int64_t i, int64_t j, const double* blk,
     for (int d = 0; d < 3; ++d) val[9 * P->bptr[i] + 3 * len * c + 3 * k + d] += blk[c * 3 + d];
 }
 
+int ora_pattern(const ora_problem* pr, int64_t* row_ptr, int32_t* col) {
+  if (check_problem(pr) < 0) return -1;
+  pattern P;
+  if (pattern_build(pr, &P) < 0) return -1;
+  pattern_to_csr(&P, row_ptr, col);
+  pattern_free(&P);
+  return 0;
+}
+
 int ora_assemble(const ora_problem* pr, int64_t* row_ptr, int32_t* col, double* val) {
   if (check_problem(pr) < 0) return -1;
   pattern P;

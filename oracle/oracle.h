@@ -71,6 +71,9 @@ void ora_rotated_D(const double* C21, double theta, double* D36);
 /* Sizes of the 3D problem. */
 int ora_sizes(const ora_problem* pr, int64_t* n_dof, int64_t* nnz);
 
+/* Sparsity pattern only (the oracle's own construction by element supports). */
+int ora_pattern(const ora_problem* pr, int64_t* row_ptr, int32_t* col);
+
 /* Full standard assembly (Eq. Km_0, Section 2.4) into the oracle's own CSR. */
 int ora_assemble(const ora_problem* pr, int64_t* row_ptr, int32_t* col, double* val);
 

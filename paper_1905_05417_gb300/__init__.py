@@ -1,0 +1,303 @@
+"""GB300 (sm_103a) FP64 stiffness assembly for 3D laminated solids.
+
+Thin Python binding of the C ABI in ``include/lam.h`` (liblam.so, built in-tree
+by ``paper_1905_05417_gb300.build``). Every step of the assembly runs in the
+library's CUDA kernels; this module only marshals arguments. PyTorch supplies
+device memory and streams. There is no CPU fallback: when the library is not
+built or no GPU is present, the device calls raise.
+
+Method: Antolin (2019), split assembly of K = sum_m sum_ab P_{m,ab} (x) Q_{m,ab}
+(Section 3, Eq. Km_2) and the standard 3D quadrature (Section 2.4).
+
+Module-level functions mirror the C entry points (``plan_create``,
+``plan_get_info``, ``pattern``, ``assemble_split``, ``assemble_standard``,
+``assemble_split_host``, ``plan_update``, ``plan_destroy``, ``last_error``,
+``version``); ``Plan`` wraps them for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+__all__ = [
+    "LamError", "Plan", "load", "plan_create", "plan_destroy", "plan_get_info", "pattern", "assemble_split",
+    "assemble_standard", "assemble_split_host", "plan_update", "last_error", "version", "SYMBOLS", "BSPLINE",
+    "LAGRANGE",
+]
+
+BSPLINE = 0
+LAGRANGE = 1
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblam.so")
+
+# every symbol include/lam.h declares
+SYMBOLS = ("lam_plan_create", "lam_plan_destroy", "lam_plan_get_info", "lam_pattern", "lam_assemble_split",
+           "lam_assemble_standard", "lam_assemble_split_host", "lam_plan_update", "lam_last_error", "lam_version")
+
+_STATUS = {0: "LAM_OK", 1: "LAM_ERR_INVALID_ARG", 2: "LAM_ERR_UNSUPPORTED", 3: "LAM_ERR_OOM", 4: "LAM_ERR_CUDA",
+           5: "LAM_ERR_TIMEOUT"}
+
+
+class LamError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class _Basis1d(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("degree", ctypes.c_int32), ("n_knots", ctypes.c_int32),
+                ("knots", ctypes.POINTER(ctypes.c_double))]
+
+
+class _Inplane(ctypes.Structure):
+    _fields_ = [("u", _Basis1d), ("v", _Basis1d), ("ctrl", ctypes.POINTER(ctypes.c_double)),
+                ("weights", ctypes.POINTER(ctypes.c_double))]
+
+
+class _Ply(ctypes.Structure):
+    _fields_ = [("thickness", ctypes.c_double), ("material", ctypes.c_int32), ("angle_rad", ctypes.c_double)]
+
+
+class _Material(ctypes.Structure):
+    _fields_ = [("C", ctypes.c_double * 21)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("nq_u", ctypes.c_int32), ("nq_v", ctypes.c_int32), ("nq_t", ctypes.c_int32),
+                ("class_tol", ctypes.c_double)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n_dof", ctypes.c_int64), ("nnz", ctypes.c_int64), ("n_s", ctypes.c_int64), ("n_t", ctypes.c_int64),
+                ("nnz_inplane", ctypes.c_int64), ("nnz_thickness", ctypes.c_int64), ("n_configs", ctypes.c_int32),
+                ("n_classes", ctypes.c_int32), ("monoclinic", ctypes.c_int32), ("n_pieces", ctypes.c_int32)]
+
+
+_lib = None
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def load() -> ctypes.CDLL:
+    """Load liblam.so (built by ``paper_1905_05417_gb300.build``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_1905_05417_gb300.build` "
+                          "(the CUDA library is required; there is no fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp = ctypes.c_void_p
+    L.lam_plan_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_Inplane), ctypes.POINTER(_Basis1d),
+                                  ctypes.POINTER(_Ply), ctypes.c_int32, ctypes.POINTER(_Material), ctypes.c_int32,
+                                  ctypes.POINTER(_Options)]
+    L.lam_plan_destroy.argtypes = [vp]
+    L.lam_plan_get_info.argtypes = [vp, ctypes.POINTER(_Info)]
+    L.lam_pattern.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), vp, vp, vp]
+    L.lam_assemble_split.argtypes = [vp, vp, vp]
+    L.lam_assemble_standard.argtypes = [vp, vp, vp]
+    L.lam_assemble_split_host.argtypes = [vp, vp, vp]
+    L.lam_plan_update.argtypes = [vp, _D, ctypes.c_int32, ctypes.POINTER(_Material), ctypes.c_int32]
+    L.lam_last_error.restype = ctypes.c_char_p
+    L.lam_version.restype = ctypes.c_char_p
+    for name in SYMBOLS:
+        if name not in ("lam_last_error", "lam_version"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def last_error() -> str:
+    return load().lam_last_error().decode()
+
+
+def version() -> str:
+    return load().lam_version().decode()
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise LamError(status, where, last_error())
+
+
+def _as_f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t) -> int:
+    """Device address of a torch tensor (or an int address)."""
+    if isinstance(t, int):
+        return t
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def plan_create(u, v, ctrl, t, ply_thickness, ply_material, ply_angle, C21, weights=None,
+                nq: Sequence[int] = (0, 0, 0), class_tol: float = -1.0) -> ctypes.c_void_p:
+    """lam_plan_create. u, v, t are (kind, degree, knots); C21 is (n_materials, 21)."""
+    L = load()
+    keep = []
+
+    def basis(b):
+        kind, degree, knots = b
+        k = _as_f64(knots)
+        keep.append(k)
+        return _Basis1d(int(kind), int(degree), len(k), k.ctypes.data_as(_D))
+
+    ctrl = _as_f64(ctrl)
+    keep.append(ctrl)
+    w = None if weights is None else _as_f64(weights)
+    keep.append(w)
+    ip = _Inplane(basis(u), basis(v), ctrl.ctypes.data_as(_D), w.ctypes.data_as(_D) if w is not None else _D())
+    tb = basis(t)
+    h = _as_f64(ply_thickness)
+    pm = np.ascontiguousarray(ply_material, dtype=np.int32)
+    pa = _as_f64(ply_angle)
+    n = len(h)
+    if len(pm) != n or len(pa) != n:
+        raise ValueError("ply arrays differ in length")
+    plies = (_Ply * n)(*[_Ply(float(h[k]), int(pm[k]), float(pa[k])) for k in range(n)])
+    C = np.atleast_2d(_as_f64(C21))
+    if C.shape[1] != 21:
+        raise ValueError("C21 must have 21 columns")
+    mats = (_Material * C.shape[0])()
+    for k in range(C.shape[0]):
+        mats[k].C[:] = C[k].tolist()
+    opt = _Options(int(nq[0]), int(nq[1]), int(nq[2]), float(class_tol))
+    handle = ctypes.c_void_p()
+    _check(L.lam_plan_create(ctypes.byref(handle), ctypes.byref(ip), ctypes.byref(tb), plies, n, mats, C.shape[0],
+                             ctypes.byref(opt)), "lam_plan_create")
+    return handle
+
+
+def plan_destroy(handle) -> None:
+    _check(load().lam_plan_destroy(handle), "lam_plan_destroy")
+
+
+def plan_get_info(handle) -> dict:
+    info = _Info()
+    _check(load().lam_plan_get_info(handle, ctypes.byref(info)), "lam_plan_get_info")
+    return {name: getattr(info, name) for name, _ in _Info._fields_}
+
+
+def pattern(handle, d_row_ptr=None, d_col_ind=None, stream=None) -> int:
+    """lam_pattern. With no buffers, returns nnz only (host)."""
+    nnz = ctypes.c_int64()
+    if d_row_ptr is None and d_col_ind is None:
+        _check(load().lam_pattern(handle, ctypes.byref(nnz), None, None, None), "lam_pattern")
+        return nnz.value
+    _check(load().lam_pattern(handle, ctypes.byref(nnz), _ptr(d_row_ptr), _ptr(d_col_ind), _stream_handle(stream)),
+           "lam_pattern")
+    return nnz.value
+
+
+def assemble_split(handle, d_values, stream=None) -> None:
+    _check(load().lam_assemble_split(handle, _ptr(d_values), _stream_handle(stream)), "lam_assemble_split")
+
+
+def assemble_standard(handle, d_values, stream=None) -> None:
+    _check(load().lam_assemble_standard(handle, _ptr(d_values), _stream_handle(stream)), "lam_assemble_standard")
+
+
+def assemble_split_host(handle, h_values, stream=None) -> None:
+    """h_values: a host buffer (numpy float64 array or pinned torch CPU tensor)."""
+    if isinstance(h_values, np.ndarray):
+        if h_values.dtype != np.float64 or not h_values.flags.c_contiguous:
+            raise ValueError("h_values must be a contiguous float64 array")
+        addr = h_values.ctypes.data
+    else:
+        addr = h_values.data_ptr()
+    _check(load().lam_assemble_split_host(handle, addr, _stream_handle(stream)), "lam_assemble_split_host")
+
+
+def plan_update(handle, ply_angle=None, C21=None) -> None:
+    pa = None if ply_angle is None else _as_f64(ply_angle)
+    mats, nm = None, 0
+    if C21 is not None:
+        C = np.atleast_2d(_as_f64(C21))
+        mats = (_Material * C.shape[0])()
+        for k in range(C.shape[0]):
+            mats[k].C[:] = C[k].tolist()
+        nm = C.shape[0]
+    _check(load().lam_plan_update(handle, pa.ctypes.data_as(_D) if pa is not None else _D(),
+                                  0 if pa is None else len(pa), mats, nm), "lam_plan_update")
+
+
+class Plan:
+    """Convenience owner of a lam_plan handle; outputs are torch tensors."""
+
+    def __init__(self, u, v, ctrl, t, ply_thickness, ply_material, ply_angle, C21, weights=None,
+                 nq=(0, 0, 0), class_tol=-1.0):
+        self.handle = plan_create(u, v, ctrl, t, ply_thickness, ply_material, ply_angle, C21, weights=weights,
+                                  nq=nq, class_tol=class_tol)
+        self.info = plan_get_info(self.handle)
+
+    @classmethod
+    def from_laminate(cls, lam, class_tol=-1.0) -> "Plan":
+        """Build from any object with the fields u, v, t (kind, degree, knots),
+        ctrl, weights, ply_thickness, ply_material, ply_angle, C21, nq."""
+        b = lambda x: (x.kind, x.degree, x.knots)
+        return cls(b(lam.u), b(lam.v), lam.ctrl, b(lam.t), lam.ply_thickness, lam.ply_material, lam.ply_angle,
+                   lam.C21, weights=lam.weights, nq=tuple(lam.nq), class_tol=class_tol)
+
+    @property
+    def nnz(self) -> int:
+        return self.info["nnz"]
+
+    @property
+    def n_dof(self) -> int:
+        return self.info["n_dof"]
+
+    def pattern(self, stream=None):
+        import torch
+        row_ptr = torch.empty(self.n_dof + 1, dtype=torch.int64, device="cuda")
+        col = torch.empty(self.nnz, dtype=torch.int32, device="cuda")
+        pattern(self.handle, row_ptr, col, stream)
+        return row_ptr, col
+
+    def assemble_split(self, values=None, stream=None):
+        import torch
+        if values is None:
+            values = torch.empty(self.nnz, dtype=torch.float64, device="cuda")
+        assemble_split(self.handle, values, stream)
+        return values
+
+    def assemble_standard(self, values=None, stream=None):
+        import torch
+        if values is None:
+            values = torch.empty(self.nnz, dtype=torch.float64, device="cuda")
+        assemble_standard(self.handle, values, stream)
+        return values
+
+    def assemble_split_host(self, values=None, stream=None):
+        if values is None:
+            values = np.empty(self.nnz, dtype=np.float64)
+        assemble_split_host(self.handle, values, stream)
+        return values
+
+    def update(self, ply_angle=None, C21=None):
+        plan_update(self.handle, ply_angle, C21)
+        self.info = plan_get_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,123 @@
+// Internal plan representation shared by the host plan builder (lam_plan.cpp)
+// and the CUDA side (lam_kernels.cu). Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/lam.h"
+
+namespace lam {
+
+constexpr int kMaxDegree = 7;
+
+// One 1D basis with its element structure (Section 2.2).
+struct Basis {
+  int kind = LAM_BSPLINE;
+  int p = 1;
+  std::vector<double> knots;
+  int n = 0;                     // functions
+  int nel = 0;                   // elements (nonempty knot spans / breakpoint intervals)
+  std::vector<double> ea, eb;    // element bounds
+  std::vector<int> span;         // B-spline knot-span index of each element
+  std::vector<int> first;        // first function of each element
+  std::vector<int> elo, ehi;     // elements in the support of each function
+  std::vector<int> lo, len;      // neighbour range [lo, lo + len) of each function
+  int colors = 1;                // elements >= colors apart share no function
+};
+
+// A (thickness element, ply) piece: Eq. C_layers restricted to one element.
+struct Piece {
+  int elem;
+  int ply;
+  int cfg;
+  double z0, z1;
+};
+
+struct Device;  // device mirror, defined in lam_kernels.cu
+
+struct Plan {
+  Basis u, v, t;
+  std::vector<double> ctrl;      // n_s x 2
+  std::vector<double> weights;   // n_s, empty when polynomial
+  std::vector<lam_ply> plies;
+  std::vector<lam_material> mats;
+  int nqu = 0, nqv = 0, nqt = 0;
+  double class_tol = 1e-13;
+
+  // Gauss-Legendre rules on [-1, 1]
+  std::vector<double> gxu, gwu, gxv, gwv, gxt, gwt;
+  // in-plane 1D tables: [e][q][k][2] (value, d/dxi) and weights [e][q] (Gauss weight x half length)
+  std::vector<double> tabU, tabV, wU, wV;
+
+  // (material, angle) configurations: Section 3, one P set per distinct D
+  std::vector<int> ply_cfg;
+  std::vector<int> cfg_mat;
+  std::vector<double> cfg_angle;
+  std::vector<double> cfgD;      // [m][6][6]
+  std::vector<double> cfgE;      // [m][c*3+d][a*3+b] = D_m[V(c,a)][V(d,b)]
+  bool monoclinic = true;
+
+  // thickness pieces and their 1D tables
+  std::vector<Piece> pieces;
+  std::vector<int> piece_begin;  // per thickness element, size t.nel + 1
+  std::vector<double> tabT;      // [piece][q][k][2] (T, dT/dz)
+  std::vector<double> wT;        // [piece][q]
+
+  // in-plane pattern: row i_s has len_s(i_s) = len_x * len_y neighbours
+  int64_t ns = 0, nnz_s = 0;
+  std::vector<int64_t> LSb;      // prefix of len_s, size ns + 1
+  // thickness pattern
+  int64_t nt = 0, nnz_t = 0;
+  std::vector<int64_t> LTb;      // prefix of len_t, size nt + 1
+  std::vector<int> tp_row, tp_col;       // thickness pair -> (i_t, j_t)
+  std::vector<int> tp_e0, tp_e1;         // shared thickness elements of the pair
+
+  // combine classes: thickness pairs with equal Q vectors
+  int ncls = 0;
+  std::vector<int> cls_rep;              // representative pair of each class
+  std::vector<int> cls_term_begin;       // size ncls + 1
+  std::vector<int> cls_terms;            // configuration ids with nonzero Q
+  std::vector<int> cls_occ_begin;        // size ncls + 1
+  std::vector<int64_t> occ_A;            // 9 * LTb[i_t] * nnz_s of each occurrence
+  std::vector<int> occ_lt, occ_k, occ_it;  // len_t(i_t), k_t, i_t of each occurrence
+  std::vector<double> host_q;            // host Q per pair [pair][cfg][4] (classification only)
+
+  // colourings
+  std::vector<int> col2_begin, col2_elem;  // in-plane elements (ey * nel_u + ex)
+  std::vector<int> col3_begin, col3_elem;  // 3D elements ((et * nel_v + ey) * nel_u + ex)
+
+  int64_t n_dof = 0, nnz = 0;
+
+  Device* dev = nullptr;
+  int device_id = -1;
+  bool cfg_dirty = true;         // configuration tables must be (re)uploaded
+
+  // profiler (lam_profile_*): events are cudaEvent_t, kept opaque here
+  struct Pending {
+    int kind;
+    int count;
+    void* start;
+    void* stop;
+  };
+  bool prof_enabled = false;
+  int64_t prof_launches[LAM_KERNEL_KINDS] = {};
+  double prof_ms[LAM_KERNEL_KINDS] = {};
+  int64_t prof_h2d = 0, prof_d2h = 0;
+  std::vector<Pending> prof_pending;
+  std::vector<void*> prof_free_events;
+};
+
+// lam_plan.cpp
+lam_status build_plan(Plan& P, const lam_inplane* inplane, const lam_basis1d* thickness, const lam_ply* plies,
+                      int32_t n_plies, const lam_material* materials, int32_t n_materials, const lam_options* opt);
+lam_status rebuild_configs(Plan& P);
+void set_error(const char* fmt, ...);
+void free_device(Plan& P);  // lam_kernels.cu
+
+}  // namespace lam
+
+struct lam_plan {
+  lam::Plan p;
+};

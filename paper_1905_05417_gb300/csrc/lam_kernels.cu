@@ -1,0 +1,1092 @@
+// CUDA (sm_103a) kernels and the device-side C ABI of the stiffness assembly.
+//
+// Split path (Section 3 of Antolin 2019, Eq. Km_2):
+//   K-b  kb_thickness  Q_{m,ab}^{i_t j_t} = sum_{plies l of configuration m}
+//                      int_{ply l} tau_a^{i_t} tau_b^{j_t} dz   (Eq. Q; tau_1 = T, tau_2 = T')
+//   K-a  ka_inplane    configuration-free in-plane Gram blocks
+//                      G_{ab}^{i_s j_s} = int g_a^{i_s} g_b^{j_s} |DF| dxi,
+//                      g = (dS/dx, dS/dy, S)   (pull-back of Eq. gradient)
+//   K-c  kc_combine    P_{m,ab}[c][d] = sum D_m[V(c,a)][V(d,b)] G_{ab} (Eq. P with a
+//                      homogeneous ply), then K = sum_m sum_ab P_{m,ab} Q_{m,ab}
+//                      written straight into the CSR values.
+// Standard path (Section 2.4): K-d kd_standard, one CTA per 3D element.
+// Pattern: kp_row_ptr / kp_col_ind.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "lam_internal.h"
+
+namespace lam {
+
+#define LAM_CUDA(call)                                                                         \
+  do {                                                                                         \
+    cudaError_t err__ = (call);                                                                \
+    if (err__ != cudaSuccess) {                                                                \
+      ::lam::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(err__), __FILE__, __LINE__); \
+      return LAM_ERR_CUDA;                                                                     \
+    }                                                                                          \
+  } while (0)
+
+struct Device {
+  // in-plane
+  double *tabU = nullptr, *tabV = nullptr, *wU = nullptr, *wV = nullptr;
+  int *firstU = nullptr, *firstV = nullptr;
+  int *loX = nullptr, *lenX = nullptr, *loY = nullptr, *lenY = nullptr;
+  double *ctrl = nullptr, *weights = nullptr;
+  int64_t* LSb = nullptr;
+  int* col2_elem = nullptr;
+  // thickness
+  int *loT = nullptr, *lenT = nullptr, *firstT = nullptr;
+  int64_t* LTb = nullptr;
+  double *tabT = nullptr, *wT = nullptr;
+  int *piece_begin = nullptr, *piece_cfg = nullptr;
+  int *tp_row = nullptr, *tp_col = nullptr, *tp_e0 = nullptr, *tp_e1 = nullptr;
+  // classes
+  int *cls_term_begin = nullptr, *cls_terms = nullptr, *cls_occ_begin = nullptr, *term_rep = nullptr;
+  int64_t* occ_A = nullptr;
+  int *occ_lt = nullptr, *occ_k = nullptr, *occ_it = nullptr;
+  // configurations
+  double* cfgE = nullptr;
+  // standard path
+  int* col3_elem = nullptr;
+  // workspace
+  double* G = nullptr;  // nnz_s x 9
+  double* q = nullptr;  // nnz_t x n_cfg x 4
+  // host-output staging
+  double* stage[2] = {nullptr, nullptr};
+  size_t stage_elems = 0;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_done[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
+  std::vector<void*> allocs;      // geometry tables and in-plane workspace (plan lifetime)
+  std::vector<void*> cfg_allocs;  // configuration tables (replaced after lam_plan_update)
+};
+
+template <typename T>
+static lam_status upload(Plan& P, std::vector<void*>& list, T** dst, const std::vector<T>& src) {
+  *dst = nullptr;
+  size_t bytes = std::max<size_t>(src.size(), 1) * sizeof(T);
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? LAM_ERR_OOM : LAM_ERR_CUDA;
+  }
+  list.push_back(p);
+  if (!src.empty()) {
+    LAM_CUDA(cudaMemcpy(p, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    P.prof_h2d += (int64_t)(src.size() * sizeof(T));
+  }
+  *dst = static_cast<T*>(p);
+  return LAM_OK;
+}
+
+static lam_status alloc_dev(std::vector<void*>& list, double** dst, size_t n) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(double));
+  if (e != cudaSuccess) {
+    set_error("cudaMalloc(%zu doubles) failed: %s", n, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? LAM_ERR_OOM : LAM_ERR_CUDA;
+  }
+  list.push_back(p);
+  *dst = static_cast<double*>(p);
+  return LAM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Profiler: an event pair on the launching stream around each launch group.
+// ---------------------------------------------------------------------------
+static cudaEvent_t prof_event(Plan& P) {
+  if (!P.prof_free_events.empty()) {
+    cudaEvent_t e = static_cast<cudaEvent_t>(P.prof_free_events.back());
+    P.prof_free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+static cudaEvent_t prof_begin(Plan& P, cudaStream_t s) {
+  if (!P.prof_enabled) return nullptr;
+  cudaEvent_t a = prof_event(P);
+  if (a) cudaEventRecord(a, s);
+  return a;
+}
+
+static void prof_end(Plan& P, int kind, int count, cudaStream_t s, cudaEvent_t a) {
+  P.prof_launches[kind] += count;
+  if (!P.prof_enabled || !a) return;
+  cudaEvent_t b = prof_event(P);
+  if (!b) return;
+  cudaEventRecord(b, s);
+  P.prof_pending.push_back(Plan::Pending{kind, count, a, b});
+}
+
+static void prof_collect(Plan& P) {
+  for (auto& pd : P.prof_pending) {
+    cudaEvent_t a = static_cast<cudaEvent_t>(pd.start), b = static_cast<cudaEvent_t>(pd.stop);
+    float ms = 0.0f;
+    if (cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess)
+      P.prof_ms[pd.kind] += ms;
+    P.prof_free_events.push_back(a);
+    P.prof_free_events.push_back(b);
+  }
+  P.prof_pending.clear();
+}
+
+static void free_cfg_tables(Device& D) {
+  for (void* p : D.cfg_allocs) cudaFree(p);
+  D.cfg_allocs.clear();
+}
+
+void free_device(Plan& P) {
+  if (!P.dev) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (P.device_id >= 0) cudaSetDevice(P.device_id);
+  cudaDeviceSynchronize();
+  prof_collect(P);
+  for (void* e : P.prof_free_events) cudaEventDestroy(static_cast<cudaEvent_t>(e));
+  P.prof_free_events.clear();
+  free_cfg_tables(*P.dev);
+  for (void* p : P.dev->allocs) cudaFree(p);
+  for (int k = 0; k < 2; ++k) {
+    if (P.dev->stage[k]) cudaFree(P.dev->stage[k]);
+    if (P.dev->ev_done[k]) cudaEventDestroy(P.dev->ev_done[k]);
+    if (P.dev->ev_copied[k]) cudaEventDestroy(P.dev->ev_copied[k]);
+  }
+  if (P.dev->copy_stream) cudaStreamDestroy(P.dev->copy_stream);
+  delete P.dev;
+  P.dev = nullptr;
+  if (cur >= 0) cudaSetDevice(cur);
+}
+
+// ---------------------------------------------------------------------------
+// Launch geometry
+// ---------------------------------------------------------------------------
+static int max_len_s(const Plan& P) {
+  int mx = 0, my = 0;
+  for (int v : P.u.len) mx = std::max(mx, v);
+  for (int v : P.v.len) my = std::max(my, v);
+  return mx * my;
+}
+
+static int kc_block(const Plan& P) { return ((9 * max_len_s(P) + 31) / 32) * 32; }
+
+static int kc_np(const Plan& P) { return P.monoclinic ? 2 : 4; }
+
+static int kc_gs_cap(const Plan& P) { return (9 * max_len_s(P) + 1) & ~1; }
+
+static size_t kc_smem(const Plan& P) {
+  const int ncfg = (int)P.cfg_mat.size();
+  size_t b = 0;
+  b += (size_t)kc_gs_cap(P) * sizeof(double);                     // G row
+  b += (size_t)ncfg * kc_np(P) * kc_block(P) * sizeof(double);    // per-thread P
+  b += (size_t)P.cls_terms.size() * 4 * sizeof(double);           // Q of every class term
+  b += (size_t)P.nnz_t * (sizeof(int64_t) + 2 * sizeof(int));      // occurrences
+  b += (size_t)(2 * (P.ncls + 1) + P.cls_terms.size()) * sizeof(int);
+  return (b + 15) & ~(size_t)15;
+}
+
+static int ka_nls(const Plan& P) { return (P.u.p + 1) * (P.v.p + 1); }
+static int ka_block(const Plan& P) {
+  int np = ka_nls(P) * (ka_nls(P) + 1) / 2;
+  return np >= 256 ? 256 : ((np + 31) / 32) * 32;
+}
+static size_t ka_smem(const Plan& P) {
+  const int nqs = P.nqu * P.nqv, nls = ka_nls(P);
+  size_t b = (size_t)nqs * nls * 6 * sizeof(double) + (size_t)nqs * 8 * sizeof(double);
+  b += (size_t)(nls * (nls + 1) / 2) * 2;
+  return (b + 15) & ~(size_t)15;
+}
+static size_t kd_smem(const Plan& P) {
+  const int nqs = P.nqu * P.nqv, nls = ka_nls(P);
+  return (size_t)nqs * nls * 3 * sizeof(double) + (size_t)nqs * 8 * sizeof(double);
+}
+
+// ---------------------------------------------------------------------------
+// Pattern kernels
+// ---------------------------------------------------------------------------
+struct PatArgs {
+  int64_t ns, nt, n_dof, nnz, nnz_s;
+  int nx;
+  const int64_t *LSb, *LTb;
+  const int *loX, *lenX, *loY, *lenY, *loT, *lenT;
+};
+
+// row_ptr(i_t, i_s, c) = 9 LTb[i_t] nnz_s + 9 len_t LSb[i_s] + 3 c len_t len_s
+__global__ void kp_row_ptr(PatArgs a, int64_t* __restrict__ row_ptr) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r > a.n_dof) return;
+  if (r == a.n_dof) {
+    row_ptr[r] = a.nnz;
+    return;
+  }
+  const int64_t i = r / 3, c = r % 3, it = i / a.ns, is = i % a.ns;
+  const int64_t lt = a.LTb[it + 1] - a.LTb[it], ls = a.LSb[is + 1] - a.LSb[is];
+  row_ptr[r] = 9 * a.LTb[it] * a.nnz_s + 9 * lt * a.LSb[is] + 3 * c * lt * ls;
+}
+
+// One block per (i_s, i_t): the 3 rows of that function pair are contiguous.
+__global__ void kp_col_ind(PatArgs a, int32_t* __restrict__ col) {
+  const int64_t is = blockIdx.x, it = blockIdx.y;
+  const int ix = (int)(is % a.nx), iy = (int)(is / a.nx);
+  const int lx = a.lenX[ix], ly = a.lenY[iy], ls = lx * ly;
+  const int lt = a.lenT[it];
+  const int64_t base = 9 * a.LTb[it] * a.nnz_s + 9 * (int64_t)lt * a.LSb[is];
+  const int row_len = 3 * lt * ls, total = 3 * row_len;
+  for (int p = threadIdx.x; p < total; p += blockDim.x) {
+    const int rem = p % row_len;
+    const int kt = rem / (3 * ls), rem2 = rem % (3 * ls);
+    const int ks = rem2 / 3, d = rem2 % 3;
+    const int jx = a.loX[ix] + ks % lx, jy = a.loY[iy] + ks / lx;
+    const int64_t jt = a.loT[it] + kt;
+    col[base + p] = (int32_t)(3 * (jt * a.ns + (int64_t)jy * a.nx + jx) + d);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K-b: thickness pair integrals (Eq. Q), summed per configuration.
+// ---------------------------------------------------------------------------
+struct KbArgs {
+  int64_t npairs;
+  int ncfg, nqt, q1;
+  const int *tp_row, *tp_col, *tp_e0, *tp_e1, *firstT, *piece_begin, *piece_cfg;
+  const double *tabT, *wT;
+  double* q;
+};
+
+__global__ void kb_thickness(KbArgs a) {
+  const int64_t pr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pr >= a.npairs) return;
+  double* out = a.q + pr * a.ncfg * 4;
+  for (int k = 0; k < a.ncfg * 4; ++k) out[k] = 0.0;
+  const int i = a.tp_row[pr], j = a.tp_col[pr];
+  for (int e = a.tp_e0[pr]; e <= a.tp_e1[pr]; ++e) {
+    const int ia = i - a.firstT[e], jb = j - a.firstT[e];
+    for (int pc = a.piece_begin[e]; pc < a.piece_begin[e + 1]; ++pc) {
+      double q11 = 0.0, q12 = 0.0, q21 = 0.0, q22 = 0.0;
+      for (int g = 0; g < a.nqt; ++g) {
+        const double* tb = a.tabT + ((size_t)pc * a.nqt + g) * a.q1 * 2;
+        const double w = a.wT[(size_t)pc * a.nqt + g];
+        const double Ti = tb[2 * ia], dTi = tb[2 * ia + 1], Tj = tb[2 * jb], dTj = tb[2 * jb + 1];
+        q11 += w * Ti * Tj;
+        q12 += w * Ti * dTj;
+        q21 += w * dTi * Tj;
+        q22 += w * dTi * dTj;
+      }
+      double* o = out + a.piece_cfg[pc] * 4;
+      o[0] += q11;
+      o[1] += q12;
+      o[2] += q21;
+      o[3] += q22;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// In-plane point data shared by K-a and K-d: for each Gauss point of the
+// in-plane element, the physical gradient (Eq. gradient) and value of every
+// local function and the weight w |DF|.
+// ---------------------------------------------------------------------------
+struct InplaneArgs {
+  int nx, nel_u, pu, pv, nqu, nqv;
+  const double *tabU, *tabV, *wU, *wV, *ctrl, *weights;
+  const int *firstU, *firstV;
+};
+
+// qd[q*8 + 0..3] = DF^{-1} (row-major, [k][a]), [4] = w|DF|, [5..7] = W, dW/dxi1, dW/dxi2
+__device__ void inplane_points(const InplaneArgs& a, int ex, int ey, double* phi, double* phiw, double* qd) {
+  const int nlx = a.pu + 1, nly = a.pv + 1, nls = nlx * nly, nqs = a.nqu * a.nqv;
+  const int fx = a.firstU[ex], fy = a.firstV[ey];
+  for (int t = threadIdx.x; t < nqs; t += blockDim.x) {
+    const int qu = t % a.nqu, qv = t / a.nqu;
+    const double* tu = a.tabU + ((size_t)ex * a.nqu + qu) * nlx * 2;
+    const double* tv = a.tabV + ((size_t)ey * a.nqv + qv) * nly * 2;
+    double W = 1.0, W1 = 0.0, W2 = 0.0;
+    if (a.weights) {
+      W = 0.0;
+      for (int ly = 0; ly < nly; ++ly)
+        for (int lx = 0; lx < nlx; ++lx) {
+          const double w = a.weights[(size_t)(fy + ly) * a.nx + fx + lx];
+          W += w * tu[2 * lx] * tv[2 * ly];
+          W1 += w * tu[2 * lx + 1] * tv[2 * ly];
+          W2 += w * tu[2 * lx] * tv[2 * ly + 1];
+        }
+    }
+    double J00 = 0.0, J01 = 0.0, J10 = 0.0, J11 = 0.0;
+    for (int ly = 0; ly < nly; ++ly)
+      for (int lx = 0; lx < nlx; ++lx) {
+        const size_t gi = (size_t)(fy + ly) * a.nx + fx + lx;
+        double N = tu[2 * lx] * tv[2 * ly], N1 = tu[2 * lx + 1] * tv[2 * ly], N2 = tu[2 * lx] * tv[2 * ly + 1];
+        double R1 = N1, R2 = N2;
+        if (a.weights) {
+          const double w = a.weights[gi];
+          R1 = w * (N1 * W - N * W1) / (W * W);
+          R2 = w * (N2 * W - N * W2) / (W * W);
+        }
+        const double X = a.ctrl[2 * gi], Y = a.ctrl[2 * gi + 1];
+        J00 += R1 * X;
+        J01 += R2 * X;
+        J10 += R1 * Y;
+        J11 += R2 * Y;
+      }
+    const double det = J00 * J11 - J01 * J10;
+    const double inv = 1.0 / det;
+    double* d = qd + t * 8;
+    d[0] = J11 * inv;   // dxi1/dx
+    d[1] = -J01 * inv;  // dxi1/dy
+    d[2] = -J10 * inv;  // dxi2/dx
+    d[3] = J00 * inv;   // dxi2/dy
+    d[4] = a.wU[(size_t)ex * a.nqu + qu] * a.wV[(size_t)ey * a.nqv + qv] * fabs(det);
+    d[5] = W;
+    d[6] = W1;
+    d[7] = W2;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nqs * nls; t += blockDim.x) {
+    const int q = t / nls, k = t % nls;
+    const int qu = q % a.nqu, qv = q / a.nqu, lx = k % nlx, ly = k / nlx;
+    const double* tu = a.tabU + ((size_t)ex * a.nqu + qu) * nlx * 2;
+    const double* tv = a.tabV + ((size_t)ey * a.nqv + qv) * nly * 2;
+    const double* d = qd + q * 8;
+    double R = tu[2 * lx] * tv[2 * ly], R1 = tu[2 * lx + 1] * tv[2 * ly], R2 = tu[2 * lx] * tv[2 * ly + 1];
+    if (a.weights) {
+      const double w = a.weights[(size_t)(fy + ly) * a.nx + fx + lx], W = d[5];
+      const double N = R, N1 = R1, N2 = R2;
+      R = w * N / W;
+      R1 = w * (N1 * W - N * d[6]) / (W * W);
+      R2 = w * (N2 * W - N * d[7]) / (W * W);
+    }
+    const double gx = d[0] * R1 + d[2] * R2;
+    const double gy = d[1] * R1 + d[3] * R2;
+    double* f = phi + (size_t)t * 3;
+    f[0] = gx;
+    f[1] = gy;
+    f[2] = R;
+    if (phiw) {
+      double* fw = phiw + (size_t)t * 3;
+      fw[0] = d[4] * gx;
+      fw[1] = d[4] * gy;
+      fw[2] = d[4] * R;
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// K-a: in-plane Gram blocks of one element, accumulated into G (one colour of
+// elements per launch, so no two CTAs of a launch touch the same block).
+// ---------------------------------------------------------------------------
+struct KaArgs {
+  InplaneArgs ip;
+  const int* elems;
+  const int *loX, *lenX, *loY, *lenY;
+  const int64_t* LSb;
+  double* G;
+};
+
+__global__ void __launch_bounds__(256) ka_inplane(KaArgs a) {
+  extern __shared__ double sm[];
+  const InplaneArgs& ip = a.ip;
+  const int nlx = ip.pu + 1, nly = ip.pv + 1, nls = nlx * nly, nqs = ip.nqu * ip.nqv;
+  double* phi = sm;
+  double* phiw = phi + (size_t)nqs * nls * 3;
+  double* qd = phiw + (size_t)nqs * nls * 3;
+  const int e = a.elems[blockIdx.x];
+  const int ex = e % ip.nel_u, ey = e / ip.nel_u;
+  inplane_points(ip, ex, ey, phi, phiw, qd);
+  const int npairs = nls * (nls + 1) / 2;
+  const int fx = ip.firstU[ex], fy = ip.firstV[ey];
+  for (int t = threadIdx.x; t < npairs; t += blockDim.x) {
+    // t -> (li <= lj), row-major over the upper triangle
+    int li = 0, rem = t;
+    while (rem >= nls - li) {
+      rem -= nls - li;
+      ++li;
+    }
+    const int lj = li + rem;
+    double acc[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[k] = 0.0;
+    for (int q = 0; q < nqs; ++q) {
+      const double* A = phiw + ((size_t)q * nls + li) * 3;
+      const double* B = phi + ((size_t)q * nls + lj) * 3;
+      const double a0 = A[0], a1 = A[1], a2 = A[2], b0 = B[0], b1 = B[1], b2 = B[2];
+      acc[0] += a0 * b0;
+      acc[1] += a0 * b1;
+      acc[2] += a0 * b2;
+      acc[3] += a1 * b0;
+      acc[4] += a1 * b1;
+      acc[5] += a1 * b2;
+      acc[6] += a2 * b0;
+      acc[7] += a2 * b1;
+      acc[8] += a2 * b2;
+    }
+    const int ix = fx + li % nlx, iy = fy + li / nlx, jx = fx + lj % nlx, jy = fy + lj / nlx;
+    const int64_t is = (int64_t)iy * ip.nx + ix, js = (int64_t)jy * ip.nx + jx;
+    const int64_t kij = (int64_t)(jy - a.loY[iy]) * a.lenX[ix] + (jx - a.loX[ix]);
+    double* g = a.G + (a.LSb[is] + kij) * 9;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) g[k] += acc[k];
+    if (li != lj) {
+      const int64_t kji = (int64_t)(iy - a.loY[jy]) * a.lenX[jx] + (ix - a.loX[jx]);
+      double* h = a.G + (a.LSb[js] + kji) * 9;
+#pragma unroll
+      for (int ab = 0; ab < 9; ++ab) h[(ab % 3) * 3 + ab / 3] += acc[ab];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K-c: fused combine. One CTA per in-plane row i_s; thread <-> (c, k_s, d) of
+// that row. Each thread forms its P_{m,ab}[c][d] from the G block, then for
+// every thickness class u evaluates slice_u = sum_terms sum_ab Q P and stores
+// it at every occurrence (i_t, k_t) of the class.
+// ---------------------------------------------------------------------------
+struct KcArgs {
+  int64_t ns, nnz_s;
+  int nx, ncfg, ncls, nterms, nocc, gs_cap;
+  const int64_t* LSb;
+  const int *lenX, *lenY;
+  const double* G;
+  const double* cfgE;
+  const double* q;
+  const int *cls_term_begin, *cls_terms, *cls_occ_begin, *term_rep;
+  const int64_t* occ_A;
+  const int *occ_lt, *occ_k, *occ_it;
+  int it_lo, it_hi;     // thickness rows written (chunked output)
+  int64_t out_offset;   // subtracted from every CSR position
+  double* values;
+};
+
+template <bool MONO, bool CHUNKED>
+__global__ void __launch_bounds__(1024) kc_combine(KcArgs a) {
+  extern __shared__ double sm[];
+  constexpr int NP = MONO ? 2 : 4;
+  const int64_t is = blockIdx.x;
+  const int ix = (int)(is % a.nx), iy = (int)(is / a.nx);
+  const int ls = a.lenX[ix] * a.lenY[iy];
+  const int64_t ls0 = a.LSb[is];
+  const int nthr = blockDim.x, tid = threadIdx.x;
+  // shared layout
+  double* Gs = sm;                                         // 9 * ls (max)
+  double* Ps = Gs + a.gs_cap;                              // ncfg * NP * nthr
+  double* Qs = Ps + (size_t)a.ncfg * NP * nthr;            // nterms * 4
+  int64_t* oA = reinterpret_cast<int64_t*>(Qs + (size_t)a.nterms * 4);
+  int* oLT = reinterpret_cast<int*>(oA + a.nocc);
+  int* oK = oLT + a.nocc;
+  int* tb = oK + a.nocc;                                   // ncls + 1
+  int* ob = tb + (a.ncls + 1);                             // ncls + 1
+  int* tm = ob + (a.ncls + 1);                             // nterms
+  for (int k = tid; k < 9 * ls; k += nthr) Gs[k] = a.G[ls0 * 9 + k];
+  for (int k = tid; k < a.nterms; k += nthr) {
+    const int m = a.cls_terms[k];
+    tm[k] = m;
+    const double* src = a.q + ((size_t)a.term_rep[k] * a.ncfg + m) * 4;
+    Qs[4 * k + 0] = src[0];
+    Qs[4 * k + 1] = src[1];
+    Qs[4 * k + 2] = src[2];
+    Qs[4 * k + 3] = src[3];
+  }
+  for (int k = tid; k < a.nocc; k += nthr) {
+    oA[k] = a.occ_A[k];
+    oLT[k] = CHUNKED ? ((a.occ_it[k] >= a.it_lo && a.occ_it[k] < a.it_hi) ? a.occ_lt[k] : -1) : a.occ_lt[k];
+    oK[k] = a.occ_k[k];
+  }
+  for (int k = tid; k <= a.ncls; k += nthr) {
+    tb[k] = a.cls_term_begin[k];
+    ob[k] = a.cls_occ_begin[k];
+  }
+  __syncthreads();
+  const int item = tid;
+  if (item >= 9 * ls) return;
+  const int c = item / (3 * ls), rem = item % (3 * ls), ks = rem / 3, d = rem % 3;
+  const double* g = Gs + ks * 9;
+  const int cd = c * 3 + d;
+  // P for every configuration, in registers -> shared (indexed by the class terms)
+  const bool block_type = ((c == 2) == (d == 2));
+  for (int m = 0; m < a.ncfg; ++m) {
+    const double* E = a.cfgE + (size_t)m * 81 + cd * 9;
+    const double p11 = E[0] * g[0] + E[1] * g[1] + E[3] * g[3] + E[4] * g[4];
+    const double p12 = E[2] * g[2] + E[5] * g[5];
+    const double p21 = E[6] * g[6] + E[7] * g[7];
+    const double p22 = E[8] * g[8];
+    if (MONO) {
+      Ps[(m * 2 + 0) * nthr + tid] = block_type ? p11 : p12;
+      Ps[(m * 2 + 1) * nthr + tid] = block_type ? p22 : p21;
+    } else {
+      Ps[(m * 4 + 0) * nthr + tid] = p11;
+      Ps[(m * 4 + 1) * nthr + tid] = p12;
+      Ps[(m * 4 + 2) * nthr + tid] = p21;
+      Ps[(m * 4 + 3) * nthr + tid] = p22;
+    }
+  }
+  const int offa = block_type ? 0 : 1, offb = block_type ? 3 : 2;
+  const int64_t X = 9 * ls0 + 3 * (int64_t)c * ls, Y = 3 * (int64_t)ls, Z = 3 * ks + d;
+  double* out = a.values - a.out_offset;
+  for (int u = 0; u < a.ncls; ++u) {
+    double v = 0.0;
+    for (int k = tb[u]; k < tb[u + 1]; ++k) {
+      const int m = tm[k];
+      if (MONO) {
+        v += Qs[4 * k + offa] * Ps[(m * 2 + 0) * nthr + tid] + Qs[4 * k + offb] * Ps[(m * 2 + 1) * nthr + tid];
+      } else {
+        v += Qs[4 * k + 0] * Ps[(m * 4 + 0) * nthr + tid] + Qs[4 * k + 1] * Ps[(m * 4 + 1) * nthr + tid] +
+             Qs[4 * k + 2] * Ps[(m * 4 + 2) * nthr + tid] + Qs[4 * k + 3] * Ps[(m * 4 + 3) * nthr + tid];
+      }
+    }
+    for (int o = ob[u]; o < ob[u + 1]; ++o) {
+      const int lt = oLT[o];
+      if (CHUNKED && lt < 0) continue;
+      out[oA[o] + lt * X + oK[o] * Y + Z] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K-d: standard element-by-element quadrature (Section 2.4). One CTA per 3D
+// element of one colour; thread <-> pairs (li <= lj) of local 3D functions.
+// For each ply piece of the element: Gram of the 3D gradients over the piece's
+// points, contracted with D of the piece's ply; both blocks of the pair are
+// scattered into the CSR values.
+// ---------------------------------------------------------------------------
+struct KdArgs {
+  InplaneArgs ip;
+  const int* elems;
+  int nel_v, nqt, q1;
+  int64_t ns, nnz_s;
+  const int *loX, *lenX, *loY, *lenY, *loT, *lenT, *firstT;
+  const int64_t *LSb, *LTb;
+  const int *piece_begin, *piece_cfg;
+  const double *tabT, *wT, *cfgE;
+  double* values;
+};
+
+__device__ __forceinline__ int64_t csr_pos(const KdArgs& a, int it, int64_t is, int c, int jt, int64_t js) {
+  const int ix = (int)(is % a.ip.nx), iy = (int)(is / a.ip.nx);
+  const int jx = (int)(js % a.ip.nx), jy = (int)(js / a.ip.nx);
+  const int64_t lt = a.LTb[it + 1] - a.LTb[it];
+  const int64_t ls = (int64_t)a.lenX[ix] * a.lenY[iy];
+  const int64_t ks = (int64_t)(jy - a.loY[iy]) * a.lenX[ix] + (jx - a.loX[ix]);
+  const int64_t kt = jt - a.loT[it];
+  return 9 * a.LTb[it] * a.nnz_s + 9 * lt * a.LSb[is] + 3 * c * lt * ls + (kt * ls + ks) * 3;
+}
+
+__global__ void __launch_bounds__(256) kd_standard(KdArgs a) {
+  extern __shared__ double sm[];
+  const InplaneArgs& ip = a.ip;
+  const int nlx = ip.pu + 1, nly = ip.pv + 1, nls = nlx * nly, nqs = ip.nqu * ip.nqv;
+  double* phi = sm;
+  double* qd = phi + (size_t)nqs * nls * 3;
+  const int e3 = a.elems[blockIdx.x];
+  const int ex = e3 % ip.nel_u, ey = (e3 / ip.nel_u) % a.nel_v, et = e3 / (ip.nel_u * a.nel_v);
+  inplane_points(ip, ex, ey, phi, nullptr, qd);
+  const int nl = nls * a.q1;
+  const int npairs = nl * (nl + 1) / 2;
+  const int fx = ip.firstU[ex], fy = ip.firstV[ey], ft = a.firstT[et];
+  const int pc0 = a.piece_begin[et], pc1 = a.piece_begin[et + 1];
+  for (int t = threadIdx.x; t < npairs; t += blockDim.x) {
+    int li = 0, rem = t;
+    while (rem >= nl - li) {
+      rem -= nl - li;
+      ++li;
+    }
+    const int lj = li + rem;
+    const int lti = li / nls, lsi = li % nls, ltj = lj / nls, lsj = lj % nls;
+    double K[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) K[k] = 0.0;
+    for (int pc = pc0; pc < pc1; ++pc) {
+      double acc[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) acc[k] = 0.0;
+      for (int qs = 0; qs < nqs; ++qs) {
+        const double* A = phi + ((size_t)qs * nls + lsi) * 3;
+        const double* B = phi + ((size_t)qs * nls + lsj) * 3;
+        const double ws = qd[qs * 8 + 4];
+        for (int g = 0; g < a.nqt; ++g) {
+          const double* tb = a.tabT + ((size_t)pc * a.nqt + g) * a.q1 * 2;
+          const double w = ws * a.wT[(size_t)pc * a.nqt + g];
+          const double Ti = tb[2 * lti], dTi = tb[2 * lti + 1], Tj = tb[2 * ltj], dTj = tb[2 * ltj + 1];
+          const double a0 = w * A[0] * Ti, a1 = w * A[1] * Ti, a2 = w * A[2] * dTi;
+          const double b0 = B[0] * Tj, b1 = B[1] * Tj, b2 = B[2] * dTj;
+          acc[0] += a0 * b0;
+          acc[1] += a0 * b1;
+          acc[2] += a0 * b2;
+          acc[3] += a1 * b0;
+          acc[4] += a1 * b1;
+          acc[5] += a1 * b2;
+          acc[6] += a2 * b0;
+          acc[7] += a2 * b1;
+          acc[8] += a2 * b2;
+        }
+      }
+      const double* E = a.cfgE + (size_t)a.piece_cfg[pc] * 81;
+#pragma unroll
+      for (int cd = 0; cd < 9; ++cd) {
+        double s = 0.0;
+#pragma unroll
+        for (int ab = 0; ab < 9; ++ab) s += E[cd * 9 + ab] * acc[ab];
+        K[cd] += s;
+      }
+    }
+    const int it = ft + lti, jt = ft + ltj;
+    const int64_t is = (int64_t)(fy + lsi / nlx) * ip.nx + fx + lsi % nlx;
+    const int64_t js = (int64_t)(fy + lsj / nlx) * ip.nx + fx + lsj % nlx;
+    for (int c = 0; c < 3; ++c) {
+      const int64_t pos = csr_pos(a, it, is, c, jt, js);
+      for (int d = 0; d < 3; ++d) a.values[pos + d] += K[c * 3 + d];
+    }
+    if (li != lj) {
+      for (int d = 0; d < 3; ++d) {
+        const int64_t pos = csr_pos(a, jt, js, d, it, is);
+        for (int c = 0; c < 3; ++c) a.values[pos + c] += K[c * 3 + d];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Device set-up
+// ---------------------------------------------------------------------------
+static lam_status ensure_device(Plan& P) {
+  int cur = 0;
+  LAM_CUDA(cudaGetDevice(&cur));
+  if (P.dev && cur != P.device_id) {
+    set_error("plan lives on device %d, current device is %d", P.device_id, cur);
+    return LAM_ERR_INVALID_ARG;
+  }
+  lam_status st = LAM_OK;
+#define UP(list, dst, src)                                   \
+  do {                                                       \
+    if ((st = upload(P, (list), &(dst), (src))) != LAM_OK) { \
+      free_device(P);                                        \
+      return st;                                             \
+    }                                                        \
+  } while (0)
+  if (!P.dev) {
+    Device* D = new Device();
+    P.dev = D;
+    P.device_id = cur;
+    P.cfg_dirty = true;
+    auto& L = D->allocs;
+    UP(L, D->tabU, P.tabU);
+    UP(L, D->tabV, P.tabV);
+    UP(L, D->wU, P.wU);
+    UP(L, D->wV, P.wV);
+    UP(L, D->firstU, P.u.first);
+    UP(L, D->firstV, P.v.first);
+    UP(L, D->loX, P.u.lo);
+    UP(L, D->lenX, P.u.len);
+    UP(L, D->loY, P.v.lo);
+    UP(L, D->lenY, P.v.len);
+    UP(L, D->ctrl, P.ctrl);
+    if (!P.weights.empty()) UP(L, D->weights, P.weights);
+    UP(L, D->LSb, P.LSb);
+    UP(L, D->col2_elem, P.col2_elem);
+    UP(L, D->loT, P.t.lo);
+    UP(L, D->lenT, P.t.len);
+    UP(L, D->firstT, P.t.first);
+    UP(L, D->LTb, P.LTb);
+    UP(L, D->tabT, P.tabT);
+    UP(L, D->wT, P.wT);
+    UP(L, D->piece_begin, P.piece_begin);
+    UP(L, D->tp_row, P.tp_row);
+    UP(L, D->tp_col, P.tp_col);
+    UP(L, D->tp_e0, P.tp_e0);
+    UP(L, D->tp_e1, P.tp_e1);
+    UP(L, D->col3_elem, P.col3_elem);
+    if ((st = alloc_dev(L, &D->G, (size_t)P.nnz_s * 9)) != LAM_OK) {
+      free_device(P);
+      return st;
+    }
+  }
+  if (P.cfg_dirty) {
+    Device* D = P.dev;
+    LAM_CUDA(cudaDeviceSynchronize());  // no launch may still read the old tables
+    free_cfg_tables(*D);
+    auto& L = D->cfg_allocs;
+    std::vector<int> pcfg(P.pieces.size());
+    for (size_t k = 0; k < P.pieces.size(); ++k) pcfg[k] = P.pieces[k].cfg;
+    UP(L, D->piece_cfg, pcfg);
+    UP(L, D->cls_term_begin, P.cls_term_begin);
+    UP(L, D->cls_terms, P.cls_terms);
+    UP(L, D->cls_occ_begin, P.cls_occ_begin);
+    std::vector<int> trep(P.cls_terms.size());
+    for (int u = 0; u < P.ncls; ++u)
+      for (int k = P.cls_term_begin[u]; k < P.cls_term_begin[u + 1]; ++k) trep[k] = P.cls_rep[u];
+    UP(L, D->term_rep, trep);
+    UP(L, D->occ_A, P.occ_A);
+    UP(L, D->occ_lt, P.occ_lt);
+    UP(L, D->occ_k, P.occ_k);
+    UP(L, D->occ_it, P.occ_it);
+    UP(L, D->cfgE, P.cfgE);
+    if ((st = alloc_dev(L, &D->q, (size_t)P.nnz_t * P.cfg_mat.size() * 4)) != LAM_OK) {
+      free_device(P);
+      return st;
+    }
+    P.cfg_dirty = false;
+  }
+#undef UP
+  return LAM_OK;
+}
+
+static lam_status check_limits(const Plan& P) {
+  if (P.nt > 65535) {
+    set_error("more than 65535 thickness functions are not supported");
+    return LAM_ERR_UNSUPPORTED;
+  }
+  if (9 * max_len_s(P) > 1024) {
+    set_error("in-plane rows with more than %d neighbours are not supported by the combine kernel", 1024 / 9);
+    return LAM_ERR_UNSUPPORTED;
+  }
+  if (kc_smem(P) > 200 * 1024 || ka_smem(P) > 200 * 1024 || kd_smem(P) > 200 * 1024) {
+    set_error("plan tables exceed the shared-memory budget of this build");
+    return LAM_ERR_UNSUPPORTED;
+  }
+  return LAM_OK;
+}
+
+static InplaneArgs inplane_args(const Plan& P) {
+  const Device& D = *P.dev;
+  InplaneArgs ip;
+  ip.nx = P.u.n;
+  ip.nel_u = P.u.nel;
+  ip.pu = P.u.p;
+  ip.pv = P.v.p;
+  ip.nqu = P.nqu;
+  ip.nqv = P.nqv;
+  ip.tabU = D.tabU;
+  ip.tabV = D.tabV;
+  ip.wU = D.wU;
+  ip.wV = D.wV;
+  ip.ctrl = D.ctrl;
+  ip.weights = D.weights;
+  ip.firstU = D.firstU;
+  ip.firstV = D.firstV;
+  return ip;
+}
+
+static KcArgs kc_args(const Plan& P, double* values) {
+  const Device& D = *P.dev;
+  KcArgs k;
+  k.ns = P.ns;
+  k.nnz_s = P.nnz_s;
+  k.nx = P.u.n;
+  k.ncfg = (int)P.cfg_mat.size();
+  k.ncls = P.ncls;
+  k.nterms = (int)P.cls_terms.size();
+  k.nocc = (int)P.nnz_t;
+  k.gs_cap = kc_gs_cap(P);
+  k.LSb = D.LSb;
+  k.lenX = D.lenX;
+  k.lenY = D.lenY;
+  k.G = D.G;
+  k.cfgE = D.cfgE;
+  k.q = D.q;
+  k.cls_term_begin = D.cls_term_begin;
+  k.cls_terms = D.cls_terms;
+  k.cls_occ_begin = D.cls_occ_begin;
+  k.term_rep = D.term_rep;
+  k.occ_A = D.occ_A;
+  k.occ_lt = D.occ_lt;
+  k.occ_k = D.occ_k;
+  k.occ_it = D.occ_it;
+  k.it_lo = 0;
+  k.it_hi = (int)P.nt;
+  k.out_offset = 0;
+  k.values = values;
+  return k;
+}
+
+template <bool MONO, bool CHUNKED>
+static lam_status launch_kc(const Plan& P, const KcArgs& k, cudaStream_t s) {
+  const size_t smem = kc_smem(P);
+  LAM_CUDA(cudaFuncSetAttribute(kc_combine<MONO, CHUNKED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaEvent_t ev = prof_begin(const_cast<Plan&>(P), s);
+  kc_combine<MONO, CHUNKED><<<(unsigned)P.ns, kc_block(P), smem, s>>>(k);
+  LAM_CUDA(cudaGetLastError());
+  prof_end(const_cast<Plan&>(P), LAM_KERNEL_COMBINE, 1, s, ev);
+  return LAM_OK;
+}
+
+// K-b then K-a (all colours): leaves Q and G in the plan's workspace.
+static lam_status split_integrals(Plan& P, cudaStream_t s) {
+  Device& D = *P.dev;
+  KbArgs kb;
+  kb.npairs = P.nnz_t;
+  kb.ncfg = (int)P.cfg_mat.size();
+  kb.nqt = P.nqt;
+  kb.q1 = P.t.p + 1;
+  kb.tp_row = D.tp_row;
+  kb.tp_col = D.tp_col;
+  kb.tp_e0 = D.tp_e0;
+  kb.tp_e1 = D.tp_e1;
+  kb.firstT = D.firstT;
+  kb.piece_begin = D.piece_begin;
+  kb.piece_cfg = D.piece_cfg;
+  kb.tabT = D.tabT;
+  kb.wT = D.wT;
+  kb.q = D.q;
+  cudaEvent_t ev = prof_begin(P, s);
+  kb_thickness<<<(unsigned)((P.nnz_t + 127) / 128), 128, 0, s>>>(kb);
+  LAM_CUDA(cudaGetLastError());
+  prof_end(P, LAM_KERNEL_THICKNESS, 1, s, ev);
+  LAM_CUDA(cudaMemsetAsync(D.G, 0, (size_t)P.nnz_s * 9 * sizeof(double), s));
+  KaArgs ka;
+  ka.ip = inplane_args(P);
+  ka.loX = D.loX;
+  ka.lenX = D.lenX;
+  ka.loY = D.loY;
+  ka.lenY = D.lenY;
+  ka.LSb = D.LSb;
+  ka.G = D.G;
+  const size_t smem = ka_smem(P);
+  LAM_CUDA(cudaFuncSetAttribute(ka_inplane, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int ncol = (int)P.col2_begin.size() - 1;
+  ev = prof_begin(P, s);
+  int launched = 0;
+  for (int c = 0; c < ncol; ++c) {
+    const int n = P.col2_begin[c + 1] - P.col2_begin[c];
+    if (n == 0) continue;
+    ka.elems = D.col2_elem + P.col2_begin[c];
+    ka_inplane<<<n, ka_block(P), smem, s>>>(ka);
+    LAM_CUDA(cudaGetLastError());
+    ++launched;
+  }
+  prof_end(P, LAM_KERNEL_INPLANE, launched, s, ev);
+  return LAM_OK;
+}
+
+static lam_status pattern_args(const Plan& P, PatArgs& a) {
+  const Device& D = *P.dev;
+  a.ns = P.ns;
+  a.nt = P.nt;
+  a.n_dof = P.n_dof;
+  a.nnz = P.nnz;
+  a.nnz_s = P.nnz_s;
+  a.nx = P.u.n;
+  a.LSb = D.LSb;
+  a.LTb = D.LTb;
+  a.loX = D.loX;
+  a.lenX = D.lenX;
+  a.loY = D.loY;
+  a.lenY = D.lenY;
+  a.loT = D.loT;
+  a.lenT = D.lenT;
+  return LAM_OK;
+}
+
+}  // namespace lam
+
+// ---------------------------------------------------------------------------
+// Device C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+lam_status lam_plan_destroy(lam_plan* plan) {
+  if (!plan) return LAM_OK;
+  lam::free_device(plan->p);
+  delete plan;
+  return LAM_OK;
+}
+
+lam_status lam_pattern(lam_plan* plan, int64_t* nnz_out, int64_t* d_row_ptr, int32_t* d_col_ind, void* stream) {
+  if (!plan) {
+    lam::set_error("lam_pattern: plan is NULL");
+    return LAM_ERR_INVALID_ARG;
+  }
+  lam::Plan& P = plan->p;
+  if (nnz_out) *nnz_out = P.nnz;
+  if (!d_row_ptr && !d_col_ind) return LAM_OK;
+  if (!d_row_ptr || !d_col_ind) {
+    lam::set_error("lam_pattern: give both d_row_ptr and d_col_ind, or neither");
+    return LAM_ERR_INVALID_ARG;
+  }
+  lam_status st = lam::ensure_device(P);
+  if (st != LAM_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  lam::PatArgs a;
+  lam::pattern_args(P, a);
+  const int64_t rows = P.n_dof + 1;
+  cudaEvent_t ev = lam::prof_begin(P, s);
+  lam::kp_row_ptr<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(a, d_row_ptr);
+  LAM_CUDA(cudaGetLastError());
+  dim3 grid((unsigned)P.ns, (unsigned)P.nt);
+  lam::kp_col_ind<<<grid, 256, 0, s>>>(a, d_col_ind);
+  LAM_CUDA(cudaGetLastError());
+  lam::prof_end(P, LAM_KERNEL_PATTERN, 2, s, ev);
+  return LAM_OK;
+}
+
+lam_status lam_assemble_split(lam_plan* plan, double* d_values, void* stream) {
+  if (!plan || !d_values) {
+    lam::set_error("lam_assemble_split: NULL argument");
+    return LAM_ERR_INVALID_ARG;
+  }
+  lam::Plan& P = plan->p;
+  lam_status st;
+  if ((st = lam::check_limits(P)) != LAM_OK) return st;
+  if ((st = lam::ensure_device(P)) != LAM_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = lam::split_integrals(P, s)) != LAM_OK) return st;
+  lam::KcArgs k = lam::kc_args(P, d_values);
+  return P.monoclinic ? lam::launch_kc<true, false>(P, k, s) : lam::launch_kc<false, false>(P, k, s);
+}
+
+lam_status lam_assemble_split_host(lam_plan* plan, double* h_values, void* stream) {
+  if (!plan || !h_values) {
+    lam::set_error("lam_assemble_split_host: NULL argument");
+    return LAM_ERR_INVALID_ARG;
+  }
+  lam::Plan& P = plan->p;
+  lam_status st;
+  if ((st = lam::check_limits(P)) != LAM_OK) return st;
+  if ((st = lam::ensure_device(P)) != LAM_OK) return st;
+  lam::Device& D = *P.dev;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // slabs of thickness rows: about 256 MB of values each
+  const int64_t per_row = 9 * P.nnz_s * 4;  // upper bound of one thickness row's share (len_t <= 4 avg)
+  int64_t rows_per_slab = std::max<int64_t>(1, (int64_t)(32 << 20) / std::max<int64_t>(1, per_row));
+  rows_per_slab = std::min<int64_t>(rows_per_slab, P.nt);
+  size_t need = 0;
+  for (int64_t r0 = 0; r0 < P.nt; r0 += rows_per_slab) {
+    const int64_t r1 = std::min<int64_t>(P.nt, r0 + rows_per_slab);
+    need = std::max<size_t>(need, (size_t)(9 * (P.LTb[r1] - P.LTb[r0]) * P.nnz_s));
+  }
+  if (D.stage_elems < need) {
+    for (int k = 0; k < 2; ++k) {
+      if (D.stage[k]) cudaFree(D.stage[k]);
+      D.stage[k] = nullptr;
+      cudaError_t e = cudaMalloc(&D.stage[k], need * sizeof(double));
+      if (e != cudaSuccess) {
+        lam::set_error("cudaMalloc(staging) failed: %s", cudaGetErrorString(e));
+        D.stage_elems = 0;
+        return LAM_ERR_OOM;
+      }
+    }
+    D.stage_elems = need;
+  }
+  if (!D.copy_stream) {
+    LAM_CUDA(cudaStreamCreateWithFlags(&D.copy_stream, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+      LAM_CUDA(cudaEventCreateWithFlags(&D.ev_done[k], cudaEventDisableTiming));
+      LAM_CUDA(cudaEventCreateWithFlags(&D.ev_copied[k], cudaEventDisableTiming));
+      LAM_CUDA(cudaEventRecord(D.ev_copied[k], D.copy_stream));
+    }
+  }
+  if ((st = lam::split_integrals(P, s)) != LAM_OK) return st;
+  int slot = 0;
+  for (int64_t r0 = 0; r0 < P.nt; r0 += rows_per_slab, slot ^= 1) {
+    const int64_t r1 = std::min<int64_t>(P.nt, r0 + rows_per_slab);
+    const int64_t off = 9 * P.LTb[r0] * P.nnz_s, cnt = 9 * (P.LTb[r1] - P.LTb[r0]) * P.nnz_s;
+    LAM_CUDA(cudaStreamWaitEvent(s, D.ev_copied[slot], 0));
+    lam::KcArgs k = lam::kc_args(P, D.stage[slot]);
+    k.it_lo = (int)r0;
+    k.it_hi = (int)r1;
+    k.out_offset = off;
+    st = P.monoclinic ? lam::launch_kc<true, true>(P, k, s) : lam::launch_kc<false, true>(P, k, s);
+    if (st != LAM_OK) return st;
+    LAM_CUDA(cudaEventRecord(D.ev_done[slot], s));
+    LAM_CUDA(cudaStreamWaitEvent(D.copy_stream, D.ev_done[slot], 0));
+    LAM_CUDA(cudaMemcpyAsync(h_values + off, D.stage[slot], (size_t)cnt * sizeof(double), cudaMemcpyDeviceToHost,
+                             D.copy_stream));
+    P.prof_d2h += cnt * (int64_t)sizeof(double);
+    LAM_CUDA(cudaEventRecord(D.ev_copied[slot], D.copy_stream));
+  }
+  LAM_CUDA(cudaStreamSynchronize(D.copy_stream));
+  LAM_CUDA(cudaStreamSynchronize(s));
+  return LAM_OK;
+}
+
+lam_status lam_assemble_standard(lam_plan* plan, double* d_values, void* stream) {
+  if (!plan || !d_values) {
+    lam::set_error("lam_assemble_standard: NULL argument");
+    return LAM_ERR_INVALID_ARG;
+  }
+  lam::Plan& P = plan->p;
+  lam_status st;
+  if ((st = lam::check_limits(P)) != LAM_OK) return st;
+  if ((st = lam::ensure_device(P)) != LAM_OK) return st;
+  lam::Device& D = *P.dev;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  LAM_CUDA(cudaMemsetAsync(d_values, 0, (size_t)P.nnz * sizeof(double), s));
+  lam::KdArgs k;
+  k.ip = lam::inplane_args(P);
+  k.nel_v = P.v.nel;
+  k.nqt = P.nqt;
+  k.q1 = P.t.p + 1;
+  k.ns = P.ns;
+  k.nnz_s = P.nnz_s;
+  k.loX = D.loX;
+  k.lenX = D.lenX;
+  k.loY = D.loY;
+  k.lenY = D.lenY;
+  k.loT = D.loT;
+  k.lenT = D.lenT;
+  k.firstT = D.firstT;
+  k.LSb = D.LSb;
+  k.LTb = D.LTb;
+  k.piece_begin = D.piece_begin;
+  k.piece_cfg = D.piece_cfg;
+  k.tabT = D.tabT;
+  k.wT = D.wT;
+  k.cfgE = D.cfgE;
+  k.values = d_values;
+  const size_t smem = lam::kd_smem(P);
+  LAM_CUDA(cudaFuncSetAttribute(lam::kd_standard, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int ncol = (int)P.col3_begin.size() - 1;
+  cudaEvent_t ev = lam::prof_begin(P, s);
+  int launched = 0;
+  for (int c = 0; c < ncol; ++c) {
+    const int n = P.col3_begin[c + 1] - P.col3_begin[c];
+    if (n == 0) continue;
+    k.elems = D.col3_elem + P.col3_begin[c];
+    lam::kd_standard<<<n, 256, smem, s>>>(k);
+    LAM_CUDA(cudaGetLastError());
+    ++launched;
+  }
+  lam::prof_end(P, LAM_KERNEL_STANDARD, launched, s, ev);
+  return LAM_OK;
+}
+
+lam_status lam_profile_enable(lam_plan* plan, int32_t enable) {
+  if (!plan) {
+    lam::set_error("lam_profile_enable: plan is NULL");
+    return LAM_ERR_INVALID_ARG;
+  }
+  lam::Plan& P = plan->p;
+  if (!P.prof_pending.empty()) lam::prof_collect(P);
+  P.prof_enabled = enable != 0;
+  for (int k = 0; k < LAM_KERNEL_KINDS; ++k) {
+    P.prof_launches[k] = 0;
+    P.prof_ms[k] = 0.0;
+  }
+  P.prof_h2d = 0;
+  P.prof_d2h = 0;
+  return LAM_OK;
+}
+
+lam_status lam_profile_get(lam_plan* plan, lam_profile* out) {
+  if (!plan || !out) {
+    lam::set_error("lam_profile_get: NULL argument");
+    return LAM_ERR_INVALID_ARG;
+  }
+  lam::Plan& P = plan->p;
+  lam::prof_collect(P);
+  out->enabled = P.prof_enabled ? 1 : 0;
+  for (int k = 0; k < LAM_KERNEL_KINDS; ++k) {
+    out->launches[k] = P.prof_launches[k];
+    out->ms[k] = P.prof_ms[k];
+  }
+  out->h2d_bytes = P.prof_h2d;
+  out->d2h_bytes = P.prof_d2h;
+  return LAM_OK;
+}
+
+}  // extern "C"

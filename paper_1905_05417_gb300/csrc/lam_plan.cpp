@@ -1,0 +1,722 @@
+// Host side of the plan: validation, 1D bases and Gauss rules, element
+// structure, (material, angle) configurations, thickness pieces and pair
+// classes, and the analytic sizes of the sparsity pattern. No CUDA here.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <new>
+
+#include "lam_internal.h"
+
+namespace lam {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+// ---------------------------------------------------------------------------
+// Gauss-Legendre rule on [-1, 1] (Section 2.4 uses tensor Gauss rules).
+// Newton's method on P_n with P_n' = n (x P_n - P_{n-1}) / (x^2 - 1), started
+// from Tricomi's approximation of the roots.
+// ---------------------------------------------------------------------------
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  const double pi = 3.14159265358979323846;
+  for (int i = 1; i <= (n + 1) / 2; ++i) {
+    double th = pi * (4.0 * i - 1.0) / (4.0 * n + 2.0);
+    double r = (1.0 - (n - 1.0) / (8.0 * n * n * n)) * std::cos(th);
+    double dp = 1.0;
+    for (int it = 0; it < 60; ++it) {
+      double pm = 1.0, pc = r;
+      for (int k = 2; k <= n; ++k) {
+        double pn = ((2 * k - 1) * r * pc - (k - 1) * pm) / k;
+        pm = pc;
+        pc = pn;
+      }
+      dp = n * (r * pc - pm) / (r * r - 1.0);
+      double step = pc / dp;
+      r -= step;
+      if (std::fabs(step) <= 4e-17) {
+        // one more evaluation of the derivative at the converged root
+        pm = 1.0;
+        pc = r;
+        for (int k = 2; k <= n; ++k) {
+          double pn = ((2 * k - 1) * r * pc - (k - 1) * pm) / k;
+          pm = pc;
+          pc = pn;
+        }
+        dp = n * (r * pc - pm) / (r * r - 1.0);
+        break;
+      }
+    }
+    double wi = 2.0 / ((1.0 - r * r) * dp * dp);
+    x[i - 1] = -r;
+    x[n - i] = r;
+    w[i - 1] = wi;
+    w[n - i] = wi;
+  }
+  if (n % 2 == 1) x[n / 2] = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// 1D bases
+// ---------------------------------------------------------------------------
+static lam_status setup_basis(Basis& B, const lam_basis1d& in, const char* name) {
+  if (in.kind != LAM_BSPLINE && in.kind != LAM_LAGRANGE) {
+    set_error("%s: unknown basis kind %d", name, in.kind);
+    return LAM_ERR_INVALID_ARG;
+  }
+  if (in.degree < 1 || in.degree > kMaxDegree) {
+    set_error("%s: degree %d outside [1, %d]", name, in.degree, kMaxDegree);
+    return LAM_ERR_INVALID_ARG;
+  }
+  if (!in.knots || in.n_knots < 2) {
+    set_error("%s: missing knots", name);
+    return LAM_ERR_INVALID_ARG;
+  }
+  B.kind = in.kind;
+  B.p = in.degree;
+  B.knots.assign(in.knots, in.knots + in.n_knots);
+  const int p = B.p;
+  const int nk = in.n_knots;
+  for (int k = 0; k < nk; ++k)
+    if (!std::isfinite(B.knots[k])) {
+      set_error("%s: non-finite knot", name);
+      return LAM_ERR_INVALID_ARG;
+    }
+  if (B.kind == LAM_LAGRANGE) {
+    for (int k = 0; k + 1 < nk; ++k)
+      if (!(B.knots[k] < B.knots[k + 1])) {
+        set_error("%s: Lagrange breakpoints must increase strictly", name);
+        return LAM_ERR_INVALID_ARG;
+      }
+    B.nel = nk - 1;
+    B.n = p * B.nel + 1;
+    for (int e = 0; e < B.nel; ++e) {
+      B.ea.push_back(B.knots[e]);
+      B.eb.push_back(B.knots[e + 1]);
+      B.span.push_back(e);
+      B.first.push_back(p * e);
+    }
+  } else {
+    if (nk < 2 * (p + 1)) {
+      set_error("%s: knot vector too short for degree %d", name, p);
+      return LAM_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k + 1 < nk; ++k)
+      if (B.knots[k + 1] < B.knots[k]) {
+        set_error("%s: knots must not decrease", name);
+        return LAM_ERR_INVALID_ARG;
+      }
+    for (int k = 1; k <= p; ++k)
+      if (B.knots[k] != B.knots[0] || B.knots[nk - 1 - k] != B.knots[nk - 1]) {
+        set_error("%s: knot vector must be open (end knots repeated degree + 1 times)", name);
+        return LAM_ERR_INVALID_ARG;
+      }
+    if (!(B.knots[p] < B.knots[p + 1]) && nk == 2 * (p + 1)) {
+      set_error("%s: empty parametric domain", name);
+      return LAM_ERR_INVALID_ARG;
+    }
+    // interior multiplicity <= p
+    int run = 1;
+    for (int k = p + 1; k < nk - p - 1; ++k) {
+      run = (B.knots[k] == B.knots[k - 1] && k - 1 > p) ? run + 1 : 1;
+      if (run > p) {
+        set_error("%s: interior knot multiplicity exceeds the degree", name);
+        return LAM_ERR_INVALID_ARG;
+      }
+    }
+    B.n = nk - p - 1;
+    for (int s = p; s <= nk - p - 2; ++s) {
+      if (B.knots[s] < B.knots[s + 1]) {
+        B.ea.push_back(B.knots[s]);
+        B.eb.push_back(B.knots[s + 1]);
+        B.span.push_back(s);
+        B.first.push_back(s - p);
+      }
+    }
+    B.nel = (int)B.ea.size();
+  }
+  // supports and neighbour ranges
+  B.elo.assign(B.n, -1);
+  B.ehi.assign(B.n, -1);
+  for (int e = 0; e < B.nel; ++e)
+    for (int k = 0; k <= p; ++k) {
+      int i = B.first[e] + k;
+      if (B.elo[i] < 0) B.elo[i] = e;
+      B.ehi[i] = e;
+    }
+  B.lo.resize(B.n);
+  B.len.resize(B.n);
+  for (int i = 0; i < B.n; ++i) {
+    if (B.elo[i] < 0) {
+      set_error("%s: function %d has an empty support", name, i);
+      return LAM_ERR_INVALID_ARG;
+    }
+    B.lo[i] = B.first[B.elo[i]];
+    B.len[i] = B.first[B.ehi[i]] + p - B.lo[i] + 1;
+  }
+  B.colors = 1;
+  for (int e = 0; e < B.nel; ++e) {
+    int e2 = e;
+    while (e2 + 1 < B.nel && B.first[e2 + 1] <= B.first[e] + p) ++e2;
+    B.colors = std::max(B.colors, e2 - e + 1);
+  }
+  return LAM_OK;
+}
+
+// Values and derivatives of the p+1 functions of element e at the point
+// x_local (measured from the element's left end, so that structurally equal
+// elements give equal tables). B-spline: de Boor's triangular scheme on the
+// local knot differences; Lagrange: barycentric form on equispaced nodes.
+static void eval_basis_local(const Basis& B, int e, double xl, double* val, double* der) {
+  const int p = B.p;
+  if (B.kind == LAM_BSPLINE) {
+    const int s = B.span[e];
+    const double ts = B.knots[s];
+    double left[kMaxDegree + 2], right[kMaxDegree + 2], N[kMaxDegree + 2];
+    double Nm[kMaxDegree + 2];  // degree p-1 values
+    N[0] = 1.0;
+    for (int j = 1; j <= p; ++j) {
+      left[j] = xl - (B.knots[s + 1 - j] - ts);
+      right[j] = (B.knots[s + j] - ts) - xl;
+      double saved = 0.0;
+      for (int r = 0; r < j; ++r) {
+        double tmp = N[r] / (right[r + 1] + left[j - r]);
+        N[r] = saved + right[r + 1] * tmp;
+        saved = left[j - r] * tmp;
+      }
+      N[j] = saved;
+      if (j == p - 1)
+        for (int r = 0; r <= j; ++r) Nm[r] = N[r];
+    }
+    if (p == 1) Nm[0] = 1.0;
+    for (int k = 0; k <= p; ++k) val[k] = N[k];
+    // dN_{i,p} = p (N_{i,p-1}/(t_{i+p}-t_i) - N_{i+1,p-1}/(t_{i+p+1}-t_{i+1})),
+    // i = s-p+k; the degree p-1 functions of span s are i = s-p+1..s (Nm[0..p-1]).
+    for (int k = 0; k <= p; ++k) {
+      int i = s - p + k;
+      double a = (k >= 1) ? Nm[k - 1] : 0.0;  // N_{i,p-1}
+      double b = (k <= p - 1) ? Nm[k] : 0.0;   // N_{i+1,p-1}
+      double d = 0.0;
+      if (a != 0.0) d += a / (B.knots[i + p] - B.knots[i]);
+      if (b != 0.0) d -= b / (B.knots[i + p + 1] - B.knots[i + 1]);
+      der[k] = p * d;
+    }
+    return;
+  }
+  const double h = B.eb[e] - B.ea[e];
+  double nodes[kMaxDegree + 1], wb[kMaxDegree + 1];
+  for (int k = 0; k <= p; ++k) nodes[k] = h * k / p;
+  for (int k = 0; k <= p; ++k) {
+    double prod = 1.0;
+    for (int m = 0; m <= p; ++m)
+      if (m != k) prod *= (nodes[k] - nodes[m]);
+    wb[k] = 1.0 / prod;
+  }
+  int at = -1;
+  for (int k = 0; k <= p; ++k)
+    if (xl == nodes[k]) at = k;
+  if (at >= 0) {
+    for (int k = 0; k <= p; ++k) val[k] = (k == at) ? 1.0 : 0.0;
+    double sum = 0.0;
+    for (int k = 0; k <= p; ++k) {
+      if (k == at) continue;
+      der[k] = (wb[k] / wb[at]) / (nodes[at] - nodes[k]);
+      sum += der[k];
+    }
+    der[at] = -sum;
+    return;
+  }
+  double denom = 0.0;
+  for (int k = 0; k <= p; ++k) denom += wb[k] / (xl - nodes[k]);
+  for (int k = 0; k <= p; ++k) {
+    val[k] = (wb[k] / (xl - nodes[k])) / denom;
+    double s = 0.0;
+    for (int m = 0; m <= p; ++m)
+      if (m != k) s += 1.0 / (xl - nodes[m]);
+    der[k] = val[k] * s;
+  }
+}
+
+static void build_inplane_table(const Basis& B, const std::vector<double>& gx, const std::vector<double>& gw,
+                                std::vector<double>& tab, std::vector<double>& wt) {
+  const int nq = (int)gx.size(), p = B.p;
+  tab.assign((size_t)B.nel * nq * (p + 1) * 2, 0.0);
+  wt.assign((size_t)B.nel * nq, 0.0);
+  for (int e = 0; e < B.nel; ++e) {
+    const double h = B.eb[e] - B.ea[e];
+    for (int q = 0; q < nq; ++q) {
+      double val[kMaxDegree + 1], der[kMaxDegree + 1];
+      eval_basis_local(B, e, 0.5 * h * (1.0 + gx[q]), val, der);
+      for (int k = 0; k <= p; ++k) {
+        tab[(((size_t)e * nq + q) * (p + 1) + k) * 2 + 0] = val[k];
+        tab[(((size_t)e * nq + q) * (p + 1) + k) * 2 + 1] = der[k];
+      }
+      wt[(size_t)e * nq + q] = gw[q] * 0.5 * h;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Configurations: Eq. D for a ply rotated about z, by the Bond stress
+// transformation M (sigma_global = M sigma_material): D_global = M D M^T.
+// ---------------------------------------------------------------------------
+static void bond_rotate(const double* C21, double theta, double* D) {
+  double Dm[6][6];
+  int k = 0;
+  for (int I = 0; I < 6; ++I)
+    for (int J = I; J < 6; ++J) {
+      Dm[I][J] = Dm[J][I] = C21[k];
+      ++k;
+    }
+  const double c = std::cos(theta), s = std::sin(theta);
+  const double R[3][3] = {{c, -s, 0.0}, {s, c, 0.0}, {0.0, 0.0, 1.0}};
+  static const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
+  double M[6][6];
+  for (int I = 0; I < 6; ++I) {
+    const int a = ii[I], b = jj[I];
+    for (int J = 0; J < 6; ++J) {
+      const int p = ii[J], q = jj[J];
+      M[I][J] = (J < 3) ? R[a][p] * R[b][q] : R[a][p] * R[b][q] + R[a][q] * R[b][p];
+    }
+  }
+  double T[6][6];
+  for (int I = 0; I < 6; ++I)
+    for (int J = 0; J < 6; ++J) {
+      double acc = 0.0;
+      for (int K = 0; K < 6; ++K) acc += M[I][K] * Dm[K][J];
+      T[I][J] = acc;
+    }
+  for (int I = 0; I < 6; ++I)
+    for (int J = 0; J < 6; ++J) {
+      double acc = 0.0;
+      for (int K = 0; K < 6; ++K) acc += T[I][K] * M[J][K];
+      D[I * 6 + J] = acc;
+    }
+}
+
+static int voigt_index(int i, int j) {
+  static const int V[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+  return V[i][j];
+}
+
+lam_status rebuild_configs(Plan& P) {
+  P.cfg_mat.clear();
+  P.cfg_angle.clear();
+  P.ply_cfg.assign(P.plies.size(), -1);
+  for (size_t l = 0; l < P.plies.size(); ++l) {
+    int found = -1;
+    for (size_t m = 0; m < P.cfg_mat.size(); ++m)
+      if (P.cfg_mat[m] == P.plies[l].material && P.cfg_angle[m] == P.plies[l].angle_rad) found = (int)m;
+    if (found < 0) {
+      found = (int)P.cfg_mat.size();
+      P.cfg_mat.push_back(P.plies[l].material);
+      P.cfg_angle.push_back(P.plies[l].angle_rad);
+    }
+    P.ply_cfg[l] = found;
+  }
+  const int nc = (int)P.cfg_mat.size();
+  P.cfgD.assign((size_t)nc * 36, 0.0);
+  P.cfgE.assign((size_t)nc * 81, 0.0);
+  P.monoclinic = true;
+  for (int m = 0; m < nc; ++m) {
+    double* D = &P.cfgD[(size_t)m * 36];
+    bond_rotate(P.mats[P.cfg_mat[m]].C, P.cfg_angle[m], D);
+    for (int I = 0; I < 4; ++I)
+      for (int J = 4; J < 6; ++J)
+        if (D[I * 6 + J] != 0.0 || D[J * 6 + I] != 0.0) P.monoclinic = false;
+    for (int c = 0; c < 3; ++c)
+      for (int d = 0; d < 3; ++d)
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b)
+            P.cfgE[(size_t)m * 81 + (c * 3 + d) * 9 + a * 3 + b] = D[voigt_index(c, a) * 6 + voigt_index(d, b)];
+  }
+  for (auto& pc : P.pieces) pc.cfg = P.ply_cfg[pc.ply];
+  return LAM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Thickness pieces (Eq. C_layers per element) and their tables
+// ---------------------------------------------------------------------------
+static lam_status build_pieces(Plan& P) {
+  const Basis& T = P.t;
+  P.pieces.clear();
+  P.piece_begin.assign(T.nel + 1, 0);
+  const double z_start = T.knots.front();
+  std::vector<double> tops(P.plies.size());
+  double z = z_start;
+  for (size_t l = 0; l < P.plies.size(); ++l) {
+    z += P.plies[l].thickness;
+    tops[l] = z;
+  }
+  for (int e = 0; e < T.nel; ++e) {
+    P.piece_begin[e] = (int)P.pieces.size();
+    const double a = T.ea[e], b = T.eb[e], snap = 1e-10 * (b - a);
+    std::vector<double> cuts{a};
+    for (size_t l = 0; l + 1 < P.plies.size(); ++l)
+      if (tops[l] > a + snap && tops[l] < b - snap) cuts.push_back(tops[l]);
+    cuts.push_back(b);
+    for (size_t k = 0; k + 1 < cuts.size(); ++k) {
+      const double mid = 0.5 * (cuts[k] + cuts[k + 1]);
+      int ply = (int)P.plies.size() - 1;
+      for (size_t l = 0; l < P.plies.size(); ++l)
+        if (mid < tops[l]) {
+          ply = (int)l;
+          break;
+        }
+      P.pieces.push_back(Piece{e, ply, 0, cuts[k], cuts[k + 1]});
+    }
+  }
+  P.piece_begin[T.nel] = (int)P.pieces.size();
+  const int nq = P.nqt, q1 = T.p + 1;
+  P.tabT.assign(P.pieces.size() * nq * q1 * 2, 0.0);
+  P.wT.assign(P.pieces.size() * nq, 0.0);
+  for (size_t pc = 0; pc < P.pieces.size(); ++pc) {
+    const Piece& PC = P.pieces[pc];
+    const double a = T.ea[PC.elem];
+    const double off = PC.z0 - a, h = PC.z1 - PC.z0;
+    for (int q = 0; q < nq; ++q) {
+      double val[kMaxDegree + 1], der[kMaxDegree + 1];
+      eval_basis_local(T, PC.elem, off + 0.5 * h * (1.0 + P.gxt[q]), val, der);
+      for (int k = 0; k < q1; ++k) {
+        P.tabT[((pc * nq + q) * q1 + k) * 2 + 0] = val[k];
+        P.tabT[((pc * nq + q) * q1 + k) * 2 + 1] = der[k];
+      }
+      P.wT[pc * nq + q] = P.gwt[q] * 0.5 * h;
+    }
+  }
+  return LAM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Thickness pairs, their Q vectors (Eq. Q summed per configuration), and the
+// classes of equal vectors used by the combine.
+// ---------------------------------------------------------------------------
+static lam_status build_classes(Plan& P) {
+  const Basis& T = P.t;
+  const int nc = (int)P.cfg_mat.size(), nq = P.nqt, q1 = T.p + 1;
+  const int64_t npairs = P.nnz_t;
+  P.host_q.assign((size_t)npairs * nc * 4, 0.0);
+  std::vector<std::vector<int>> terms(npairs);
+  for (int64_t pr = 0; pr < npairs; ++pr) {
+    const int i = P.tp_row[pr], j = P.tp_col[pr];
+    double* q = &P.host_q[(size_t)pr * nc * 4];
+    for (int e = P.tp_e0[pr]; e <= P.tp_e1[pr]; ++e) {
+      const int a = i - T.first[e], b = j - T.first[e];
+      for (int pc = P.piece_begin[e]; pc < P.piece_begin[e + 1]; ++pc) {
+        const int m = P.pieces[pc].cfg;
+        if (std::find(terms[pr].begin(), terms[pr].end(), m) == terms[pr].end()) terms[pr].push_back(m);
+        for (int g = 0; g < nq; ++g) {
+          const double* tb = &P.tabT[((size_t)pc * nq + g) * q1 * 2];
+          const double w = P.wT[(size_t)pc * nq + g];
+          const double Ta = tb[a * 2], dTa = tb[a * 2 + 1], Tb = tb[b * 2], dTb = tb[b * 2 + 1];
+          q[m * 4 + 0] += w * Ta * Tb;
+          q[m * 4 + 1] += w * Ta * dTb;
+          q[m * 4 + 2] += w * dTa * Tb;
+          q[m * 4 + 3] += w * dTa * dTb;
+        }
+      }
+    }
+    std::sort(terms[pr].begin(), terms[pr].end());
+  }
+  double scale[4] = {0, 0, 0, 0};
+  for (size_t k = 0; k < P.host_q.size(); ++k) scale[k % 4] = std::max(scale[k % 4], std::fabs(P.host_q[k]));
+  const double tol = P.class_tol;
+  std::vector<int> cls_of(npairs, -1);
+  std::vector<int> reps;
+  for (int64_t pr = 0; pr < npairs; ++pr) {
+    const double* q = &P.host_q[(size_t)pr * nc * 4];
+    int found = -1;
+    for (size_t u = 0; u < reps.size() && found < 0; ++u) {
+      const int r = reps[u];
+      if (terms[r] != terms[pr]) continue;
+      const double* qr = &P.host_q[(size_t)r * nc * 4];
+      bool same = true;
+      for (int m : terms[pr])
+        for (int ab = 0; ab < 4 && same; ++ab) {
+          const double d = std::fabs(q[m * 4 + ab] - qr[m * 4 + ab]);
+          same = (tol == 0.0) ? (q[m * 4 + ab] == qr[m * 4 + ab]) : (d <= tol * scale[ab]);
+        }
+      if (same) found = (int)u;
+    }
+    if (found < 0) {
+      found = (int)reps.size();
+      reps.push_back((int)pr);
+    }
+    cls_of[pr] = found;
+  }
+  P.ncls = (int)reps.size();
+  P.cls_rep = reps;
+  P.cls_term_begin.assign(P.ncls + 1, 0);
+  P.cls_terms.clear();
+  for (int u = 0; u < P.ncls; ++u) {
+    P.cls_term_begin[u] = (int)P.cls_terms.size();
+    for (int m : terms[reps[u]]) P.cls_terms.push_back(m);
+  }
+  P.cls_term_begin[P.ncls] = (int)P.cls_terms.size();
+  P.cls_occ_begin.assign(P.ncls + 1, 0);
+  std::vector<int> count(P.ncls, 0);
+  for (int64_t pr = 0; pr < npairs; ++pr) ++count[cls_of[pr]];
+  for (int u = 0; u < P.ncls; ++u) P.cls_occ_begin[u + 1] = P.cls_occ_begin[u] + count[u];
+  P.occ_A.assign(npairs, 0);
+  P.occ_lt.assign(npairs, 0);
+  P.occ_k.assign(npairs, 0);
+  P.occ_it.assign(npairs, 0);
+  std::vector<int> fill(P.cls_occ_begin.begin(), P.cls_occ_begin.end() - 1);
+  for (int64_t pr = 0; pr < npairs; ++pr) {
+    const int u = cls_of[pr], o = fill[u]++;
+    const int i = P.tp_row[pr];
+    P.occ_A[o] = 9 * P.LTb[i] * P.nnz_s;
+    P.occ_lt[o] = T.len[i];
+    P.occ_k[o] = P.tp_col[pr] - T.lo[i];
+    P.occ_it[o] = i;
+  }
+  return LAM_OK;
+}
+
+static void build_colourings(Plan& P) {
+  const int cu = P.u.colors, cv = P.v.colors, ct = P.t.colors;
+  const int nc2 = cu * cv, nc3 = cu * cv * ct;
+  std::vector<std::vector<int>> c2(nc2), c3(nc3);
+  for (int ey = 0; ey < P.v.nel; ++ey)
+    for (int ex = 0; ex < P.u.nel; ++ex) c2[(ex % cu) + cu * (ey % cv)].push_back(ey * P.u.nel + ex);
+  for (int et = 0; et < P.t.nel; ++et)
+    for (int ey = 0; ey < P.v.nel; ++ey)
+      for (int ex = 0; ex < P.u.nel; ++ex)
+        c3[(ex % cu) + cu * ((ey % cv) + cv * (et % ct))].push_back((et * P.v.nel + ey) * P.u.nel + ex);
+  P.col2_begin.assign(nc2 + 1, 0);
+  P.col2_elem.clear();
+  for (int c = 0; c < nc2; ++c) {
+    P.col2_begin[c] = (int)P.col2_elem.size();
+    P.col2_elem.insert(P.col2_elem.end(), c2[c].begin(), c2[c].end());
+  }
+  P.col2_begin[nc2] = (int)P.col2_elem.size();
+  P.col3_begin.assign(nc3 + 1, 0);
+  P.col3_elem.clear();
+  for (int c = 0; c < nc3; ++c) {
+    P.col3_begin[c] = (int)P.col3_elem.size();
+    P.col3_elem.insert(P.col3_elem.end(), c3[c].begin(), c3[c].end());
+  }
+  P.col3_begin[nc3] = (int)P.col3_elem.size();
+}
+
+lam_status build_plan(Plan& P, const lam_inplane* inplane, const lam_basis1d* thickness, const lam_ply* plies,
+                      int32_t n_plies, const lam_material* materials, int32_t n_materials, const lam_options* opt) {
+  if (!inplane || !thickness || !plies || !materials) {
+    set_error("lam_plan_create: NULL argument");
+    return LAM_ERR_INVALID_ARG;
+  }
+  lam_status st;
+  if ((st = setup_basis(P.u, inplane->u, "in-plane u")) != LAM_OK) return st;
+  if ((st = setup_basis(P.v, inplane->v, "in-plane v")) != LAM_OK) return st;
+  if ((st = setup_basis(P.t, *thickness, "thickness")) != LAM_OK) return st;
+  if (P.u.kind != P.v.kind) {
+    set_error("in-plane u and v must use the same basis kind");
+    return LAM_ERR_INVALID_ARG;
+  }
+  if (!inplane->ctrl) {
+    set_error("in-plane control points missing");
+    return LAM_ERR_INVALID_ARG;
+  }
+  P.ns = (int64_t)P.u.n * P.v.n;
+  P.nt = P.t.n;
+  P.n_dof = 3 * P.ns * P.nt;
+  if (P.n_dof > std::numeric_limits<int32_t>::max()) {
+    set_error("n_dof %lld exceeds the int32 column index range", (long long)P.n_dof);
+    return LAM_ERR_UNSUPPORTED;
+  }
+  P.ctrl.assign(inplane->ctrl, inplane->ctrl + 2 * P.ns);
+  for (double x : P.ctrl)
+    if (!std::isfinite(x)) {
+      set_error("non-finite control point");
+      return LAM_ERR_INVALID_ARG;
+    }
+  P.weights.clear();
+  if (inplane->weights) {
+    if (P.u.kind != LAM_BSPLINE) {
+      set_error("weights are only accepted with a B-spline (NURBS) in-plane basis");
+      return LAM_ERR_INVALID_ARG;
+    }
+    P.weights.assign(inplane->weights, inplane->weights + P.ns);
+    for (double w : P.weights)
+      if (!(w > 0.0) || !std::isfinite(w)) {
+        set_error("NURBS weights must be positive");
+        return LAM_ERR_INVALID_ARG;
+      }
+  }
+  if (n_plies < 1 || n_materials < 1) {
+    set_error("need at least one ply and one material");
+    return LAM_ERR_INVALID_ARG;
+  }
+  P.plies.assign(plies, plies + n_plies);
+  P.mats.assign(materials, materials + n_materials);
+  double H = P.t.knots.back() - P.t.knots.front(), sum = 0.0;
+  for (int l = 0; l < n_plies; ++l) {
+    if (!(P.plies[l].thickness > 0.0) || !std::isfinite(P.plies[l].thickness) ||
+        !std::isfinite(P.plies[l].angle_rad) || P.plies[l].material < 0 || P.plies[l].material >= n_materials) {
+      set_error("ply %d: invalid thickness, angle or material", l);
+      return LAM_ERR_INVALID_ARG;
+    }
+    sum += P.plies[l].thickness;
+  }
+  if (std::fabs(sum - H) > 1e-10 * H) {
+    set_error("ply thicknesses add up to %.17g, the thickness knots span %.17g", sum, H);
+    return LAM_ERR_INVALID_ARG;
+  }
+  for (int m = 0; m < n_materials; ++m)
+    for (int k = 0; k < 21; ++k)
+      if (!std::isfinite(P.mats[m].C[k])) {
+        set_error("material %d: non-finite constant", m);
+        return LAM_ERR_INVALID_ARG;
+      }
+  lam_options o{0, 0, 0, -1.0};
+  if (opt) o = *opt;
+  P.nqu = o.nq_u > 0 ? o.nq_u : P.u.p + 1;
+  P.nqv = o.nq_v > 0 ? o.nq_v : P.v.p + 1;
+  P.nqt = o.nq_t > 0 ? o.nq_t : P.t.p + 1;
+  if (P.nqu > 16 || P.nqv > 16 || P.nqt > 16) {
+    set_error("at most 16 Gauss points per direction");
+    return LAM_ERR_UNSUPPORTED;
+  }
+  if ((P.u.p + 1) * (P.v.p + 1) > 64 || P.nqu * P.nqv > 256) {
+    set_error("in-plane element too large for this build");
+    return LAM_ERR_UNSUPPORTED;
+  }
+  P.class_tol = o.class_tol < 0.0 ? 1e-13 : o.class_tol;
+  gauss_legendre(P.nqu, P.gxu, P.gwu);
+  gauss_legendre(P.nqv, P.gxv, P.gwv);
+  gauss_legendre(P.nqt, P.gxt, P.gwt);
+  build_inplane_table(P.u, P.gxu, P.gwu, P.tabU, P.wU);
+  build_inplane_table(P.v, P.gxv, P.gwv, P.tabV, P.wV);
+  if ((st = build_pieces(P)) != LAM_OK) return st;
+  if ((st = rebuild_configs(P)) != LAM_OK) return st;
+  // in-plane pattern: i_s = iy * nx + ix, neighbours (jy major, jx minor)
+  P.LSb.assign(P.ns + 1, 0);
+  for (int64_t is = 0; is < P.ns; ++is) {
+    const int ix = (int)(is % P.u.n), iy = (int)(is / P.u.n);
+    P.LSb[is + 1] = P.LSb[is] + (int64_t)P.u.len[ix] * P.v.len[iy];
+  }
+  P.nnz_s = P.LSb[P.ns];
+  P.LTb.assign(P.nt + 1, 0);
+  P.tp_row.clear();
+  P.tp_col.clear();
+  P.tp_e0.clear();
+  P.tp_e1.clear();
+  for (int it = 0; it < P.nt; ++it) {
+    P.LTb[it + 1] = P.LTb[it] + P.t.len[it];
+    for (int k = 0; k < P.t.len[it]; ++k) {
+      const int jt = P.t.lo[it] + k;
+      P.tp_row.push_back(it);
+      P.tp_col.push_back(jt);
+      P.tp_e0.push_back(std::max(P.t.elo[it], P.t.elo[jt]));
+      P.tp_e1.push_back(std::min(P.t.ehi[it], P.t.ehi[jt]));
+    }
+  }
+  P.nnz_t = P.LTb[P.nt];
+  P.nnz = 9 * P.nnz_s * P.nnz_t;
+  if ((st = build_classes(P)) != LAM_OK) return st;
+  build_colourings(P);
+  return LAM_OK;
+}
+
+}  // namespace lam
+
+// ---------------------------------------------------------------------------
+// Host-only C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* lam_last_error(void) { return lam::g_err; }
+
+const char* lam_version(void) { return "lam 0.1 (sm_103a, FP64)"; }
+
+lam_status lam_plan_create(lam_plan** out, const lam_inplane* inplane, const lam_basis1d* thickness,
+                           const lam_ply* plies, int32_t n_plies, const lam_material* materials,
+                           int32_t n_materials, const lam_options* options) {
+  if (!out) {
+    lam::set_error("lam_plan_create: out is NULL");
+    return LAM_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  lam_plan* plan = new (std::nothrow) lam_plan();
+  if (!plan) {
+    lam::set_error("lam_plan_create: out of host memory");
+    return LAM_ERR_OOM;
+  }
+  lam_status st;
+  try {
+    st = lam::build_plan(plan->p, inplane, thickness, plies, n_plies, materials, n_materials, options);
+  } catch (const std::bad_alloc&) {
+    lam::set_error("lam_plan_create: out of host memory");
+    st = LAM_ERR_OOM;
+  }
+  if (st != LAM_OK) {
+    delete plan;
+    return st;
+  }
+  lam::set_error("");
+  *out = plan;
+  return LAM_OK;
+}
+
+lam_status lam_plan_get_info(const lam_plan* plan, lam_plan_info* info) {
+  if (!plan || !info) {
+    lam::set_error("lam_plan_get_info: NULL argument");
+    return LAM_ERR_INVALID_ARG;
+  }
+  const lam::Plan& P = plan->p;
+  info->n_dof = P.n_dof;
+  info->nnz = P.nnz;
+  info->n_s = P.ns;
+  info->n_t = P.nt;
+  info->nnz_inplane = P.nnz_s;
+  info->nnz_thickness = P.nnz_t;
+  info->n_configs = (int32_t)P.cfg_mat.size();
+  info->n_classes = P.ncls;
+  info->monoclinic = P.monoclinic ? 1 : 0;
+  info->n_pieces = (int32_t)P.pieces.size();
+  return LAM_OK;
+}
+
+lam_status lam_plan_update(lam_plan* plan, const double* ply_angle_rad, int32_t n_plies,
+                           const lam_material* materials, int32_t n_materials) {
+  if (!plan) {
+    lam::set_error("lam_plan_update: plan is NULL");
+    return LAM_ERR_INVALID_ARG;
+  }
+  lam::Plan& P = plan->p;
+  if (ply_angle_rad) {
+    if (n_plies != (int32_t)P.plies.size()) {
+      lam::set_error("lam_plan_update: %d angles for %d plies", n_plies, (int)P.plies.size());
+      return LAM_ERR_INVALID_ARG;
+    }
+    for (int l = 0; l < n_plies; ++l)
+      if (!std::isfinite(ply_angle_rad[l])) {
+        lam::set_error("lam_plan_update: non-finite angle");
+        return LAM_ERR_INVALID_ARG;
+      }
+  }
+  if (materials && n_materials != (int32_t)P.mats.size()) {
+    lam::set_error("lam_plan_update: %d materials for %d", n_materials, (int)P.mats.size());
+    return LAM_ERR_INVALID_ARG;
+  }
+  if (ply_angle_rad)
+    for (int l = 0; l < n_plies; ++l) P.plies[l].angle_rad = ply_angle_rad[l];
+  if (materials) P.mats.assign(materials, materials + n_materials);
+  lam::rebuild_configs(P);
+  lam::build_classes(P);
+  P.cfg_dirty = true;  // configuration tables are re-uploaded by the next device call
+  return LAM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,434 @@
+#!/usr/bin/env python
+"""FP64 stiffness assembly benchmark on GB300: split 2D x 1D vs standard 3D quadrature.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lam|reference]
+
+Workload (synthetic, seeded by construction): in-plane cubic B-spline on 64x64
+elements of the unit square under the curved map x = xi + 0.05 sin(2 pi xi)
+sin(2 pi eta), y = eta + 0.05 sin(2 pi eta) cos(2 pi xi); 48 plies
+[0/45/-45/90]_6s of 0.001 with one quadratic C0 element each (97 thickness
+functions); orthotropic ply E1=140, E2=E3=10, G12=G13=5, G23=3.4, nu12=nu13=0.3,
+nu23=0.49; 1,306,299 DOFs, 723,661,785 stored nonzeros.
+
+One step = one call of lam_assemble_split (thickness integrals, in-plane Gram
+blocks, fused combine into the CSR values) into a resident device buffer; the
+pattern is built once before timing. Every timed step is preceded by a 256 MiB
+device write that flushes the 129 MB L2 (outside the step's events). The line
+also reports the standard path (lam_assemble_standard) on the same plan, the
+end-to-end figure through lam_assemble_split_host (ply angles in from pinned
+host memory, all values out to pinned host memory), the roofline of the
+dominant kernel from the library's own event timing, SM clocks sampled during
+the timed regions, and the CPU oracle timed on a bounded sample.
+
+Under torchrun (N > 1) every rank assembles its own replica of the workload
+(weak scaling, no collective on the data path); the step time is the maximum
+over ranks and `value` counts the nonzeros of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FP64 K nnz/s on 1 GB300: split 2D×1D vs standard 3D quadrature; HBM roofline %"
+UNIT = "nnz/s"
+FALLBACK_HBM_GBS = 6800.0
+FP64_PEAK_TFLOPS = 1.25          # nominal FP64 rate of the part (vector = tensor on GB300)
+L2_FLUSH_BYTES = 256 << 20
+
+
+def workload_desc(args) -> str:
+    return (f"curved plate, cubic B-spline {args.n_el}x{args.n_el}, {8 * args.repeats} plies "
+            f"[0/45/-45/90]_{args.repeats}s, quadratic C0 per ply")
+
+
+# ----------------------------------------------------------------------------- distributed helpers
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), int(
+        os.environ.get("WORLD_SIZE", "1"))
+
+
+def dist_init(backend: str):
+    import torch.distributed as dist
+    rank, local, world = dist_env()
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        os.environ.setdefault("MASTER_PORT", "29517")
+        dist.init_process_group(backend, rank=rank, world_size=world)
+    return rank, local, world
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest value of x over all ranks (x itself without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_throughput(units_per_rank: int, world: int, seconds_max: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return units_per_rank * world / seconds_max
+
+
+# ----------------------------------------------------------------------------- peaks and profiles
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_1905_05417_gb300", "csrc", "lam_kernels.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(summary: str):
+    """DRAM bytes per launch recorded by an ncu capture, if the kernel source
+    has not changed since; else None."""
+    path = os.path.join(ROOT, "profiles", summary)
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    s = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    if not m or not s or s.group(1) != kernel_source_sha():
+        return None
+    return float(m.group(1))
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, period_ms: int = 100):
+        self.index = gpu_index
+        self.period = period_ms
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            out_dir = os.path.join(ROOT, "gpurun_out") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp"
+            self.path = os.path.join(out_dir, f"clocks_rank{dist_env()[0]}.csv")
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader",
+                                          "-i", str(self.index), "-lms", str(self.period)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1].split()[0]))
+                smax.append(float(f[2].split()[0]))
+                power.append(float(f[3].split()[0]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        # samples "under load": power above the midpoint of the observed range
+        cut = min(power) + 0.5 * (max(power) - min(power))
+        loaded = [c for c, p in zip(sm, power) if p >= cut] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "samples_under_load": len(loaded), "power_w_max": max(power)}
+
+
+def gpu_index(local_rank: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [v.strip() for v in vis.split(",") if v.strip()]
+    if ids and all(v.isdigit() for v in ids) and local_rank < len(ids):
+        return int(ids[local_rank])
+    return local_rank
+
+
+# ----------------------------------------------------------------------------- CPU oracle legs
+def oracle_sample(lam, budget_s: float, nnz: int):
+    """Time the CPU oracle's element stiffness (Section 2.4, Eq. Km_0 per
+    element) on a bounded, evenly spread sample of the workload's 3D elements
+    and scale by the element count. Single-threaded plain C."""
+    import oracle
+    prob = oracle.Problem(lam)
+    nex = oracle.n_elements(lam.u.kind, lam.u.degree, lam.u.knots)
+    ney = oracle.n_elements(lam.v.kind, lam.v.degree, lam.v.knots)
+    net = oracle.n_elements(lam.t.kind, lam.t.degree, lam.t.knots)
+    n_el = nex * ney * net
+    t0 = time.perf_counter()
+    oracle.element_stiffness(lam, 0, 0, 0, prob)
+    one = max(time.perf_counter() - t0, 1e-6)
+    n = int(max(1, min(n_el, budget_s / one)))
+    stride = max(1, n_el // n)
+    t0 = time.perf_counter()
+    done = 0
+    for k in range(0, n_el, stride):
+        if done >= n:
+            break
+        et, rem = divmod(k, nex * ney)
+        ey, ex = divmod(rem, nex)
+        oracle.element_stiffness(lam, ex, ey, et, prob)
+        done += 1
+    dt = time.perf_counter() - t0
+    per_elem = dt / done
+    full = per_elem * n_el
+    return {"value": nnz / full, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle element stiffness of {done} of {n_el} 3D elements (every {stride}th), "
+                      f"{dt:.1f} s, scaled by the element count; CSR scatter not timed",
+            "seconds_full_estimate": full}
+
+
+def run_reference(args):
+    rank, local, world = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    lam = make_workload(args)
+    n_dof, nnz = oracle.sizes(lam)
+    budget = max(0.2, min(2.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(lam, budget, nnz)
+    vals = [oracle_sample(lam, budget, nnz) for _ in range(args.steps)]
+    secs = [nnz / v["value"] for v in vals]
+    value = nnz / statistics.mean(secs)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": workload_desc(args), "n_dof": n_dof, "nnz": nnz, "parallelism": "none (host)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": vals[0]["sample"] + "; one such sample per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def standard_flops_per_step(info, lam):
+    """FP64 flops of the standard kernel's algorithm: per 3D element piece, for
+    every unordered pair of its (p+1)^2 (q+1) functions, (p+1)^2 (q+1) points x
+    (9 FMA + 6 MUL) and the 81-FMA contraction with D."""
+    nl = (lam.u.degree + 1) * (lam.v.degree + 1) * (lam.t.degree + 1)
+    nq = (lam.u.degree + 1) * (lam.v.degree + 1) * (lam.t.degree + 1)
+    pairs = nl * (nl + 1) // 2
+    per_piece = pairs * (nq * (9 * 2 + 6) + 81 * 2)
+    n_inplane = (len(set(lam.u.knots)) - 1) * (len(set(lam.v.knots)) - 1)
+    return per_piece * info["n_pieces"] * n_inplane
+
+
+def make_workload(args):
+    import workloads as W
+    return W.curved_plate(n_el=args.n_el, degree=3, repeats=args.repeats)
+
+
+def run_lam(args):
+    import torch
+    rank, local, world = dist_init("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_1905_05417_gb300 as L
+    lam = make_workload(args)
+    plan = L.Plan.from_laminate(lam)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = oracle_sample(lam, args.cpu_budget, plan.nnz)
+    info = plan.info
+    nnz, nnz_s = info["nnz"], info["nnz_inplane"]
+    row_ptr, col = plan.pattern()
+    values = torch.empty(nnz, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        plan.assemble_split(values)
+    torch.cuda.synchronize()
+    peak, peak_kind = measured_peaks()
+
+    with ClockSampler(gpu_index(local)) as clocks:
+        # ---- split, timed
+        barrier()
+        torch.cuda.synchronize()
+        plan.profile_enable(True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record()
+            plan.assemble_split(values)
+            ev[k][1].record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        barrier()
+        prof = plan.profile()
+        plan.profile_enable(False)
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        ms_local = sum(step_ms) / args.steps
+        ms = max_over_ranks(ms_local, dev)
+        launches = sum(prof[k]["launches"] for k in L.KERNEL_KINDS)
+
+        # ---- standard, timed on the same plan
+        std = None
+        if args.standard_steps > 0:
+            std_vals = values  # same buffer: the split result is not needed any more
+            for _ in range(args.standard_warmup):
+                plan.assemble_standard(std_vals)
+            torch.cuda.synchronize()
+            barrier()
+            plan.profile_enable(True)
+            sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.standard_steps)]
+            for k in range(args.standard_steps):
+                flush.zero_()
+                sev[k][0].record()
+                plan.assemble_standard(std_vals)
+                sev[k][1].record()
+            torch.cuda.synchronize()
+            barrier()
+            sprof = plan.profile()
+            plan.profile_enable(False)
+            sms = max_over_ranks(sum(a.elapsed_time(b) for a, b in sev) / args.standard_steps, dev)
+            flops = standard_flops_per_step(info, lam)
+            k_ms = sprof["standard"]["ms"] / args.standard_steps
+            std = {"value": aggregate_throughput(nnz, world, sms / 1e3), "unit": UNIT, "ms_per_step": sms,
+                   "steps": args.standard_steps, "warmup": args.standard_warmup,
+                   "roofline": {"bound": "alu", "achieved": flops / (k_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                                "unit": "TFLOP/s", "frac": flops / (k_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                                "traffic": None, "flops_per_step": flops,
+                                "peak_kind": "nominal FP64 rate (1.20 TFLOP/s measured by a DFMA probe)"},
+                   "gpu_launches": sum(sprof[k]["launches"] for k in L.KERNEL_KINDS)}
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        host = torch.empty(nnz, dtype=torch.float64, pin_memory=True)
+        angles = torch.tensor(lam.ply_angle, dtype=torch.float64).pin_memory()
+        plan.update(ply_angle=angles.numpy())
+        plan.assemble_split_host(host)
+        torch.cuda.synchronize()
+        barrier()
+        plan.profile_enable(True)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            plan.update(ply_angle=angles.numpy())
+            plan.assemble_split_host(host)
+        t_e2e = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, dev)
+        eprof = plan.profile()
+        plan.profile_enable(False)
+        barrier()
+        e2e = {"value": aggregate_throughput(nnz, world, t_e2e), "unit": UNIT,
+               "h2d_bytes_per_step": eprof["h2d_bytes"] // args.e2e_steps + angles.numel() * 8,
+               "d2h_bytes_per_step": eprof["d2h_bytes"] // args.e2e_steps, "ms_per_step": 1e3 * t_e2e,
+               "call": "lam_plan_update (ply angles from pinned host memory) + lam_assemble_split_host "
+                       "(values to pinned host memory)"}
+        del host
+
+    if rank != 0:
+        return 0
+    kc = prof["combine"]
+    kc_ms = kc["ms"] / max(1, kc["launches"])
+    kc_bytes = 8 * nnz + 72 * nnz_s
+    achieved = kc_bytes / (kc_ms / 1e3) / 1e9
+    summary = "kc_combine_curved_p3_64x64_48plies.md"
+    traffic = recorded_traffic(summary) if (args.n_el, args.repeats) == (64, 6) else None
+    clk = clocks.summary()
+    line = {
+        "metric": METRIC,
+        "value": aggregate_throughput(nnz, world, ms / 1e3),
+        "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(args), "n_dof": info["n_dof"], "nnz": nnz, "n_configs": info["n_configs"],
+                   "n_classes": info["n_classes"], "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "256 MiB device write before every timed step (L2 is 129 MB); outputs 5.8 GB per step"},
+        "step_hbm_frac": 8 * nnz / (ms / 1e3) / 1e9 / peak,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "kernel": "kc_combine", "bytes_per_launch": kc_bytes,
+                     "ms_per_launch": kc_ms, "peak_kind": f"{peak_kind} copy bandwidth"},
+        "kernels_ms_per_step": {k: prof[k]["ms"] / args.steps for k in L.KERNEL_KINDS if prof[k]["launches"]},
+        "gpu_launches": launches,
+        "wall_s_timed": wall,
+        "clocks": clk,
+    }
+    if std is not None:
+        line["standard"] = std
+        line["speedup_split_vs_standard"] = std["ms_per_step"] / ms
+    if e2e is not None:
+        line["e2e"] = e2e
+    if cpu is not None:
+        line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    print(json.dumps(line), flush=True)
+    plan.close()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("lam", "reference"), default="lam")
+    ap.add_argument("--standard-steps", type=int, default=2)
+    ap.add_argument("--standard-warmup", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--n-el", type=int, default=64, help="in-plane elements per direction (64 = the benchmark)")
+    ap.add_argument("--repeats", type=int, default=6, help="[0/45/-45/90]_{repeats}s stack (6 = 48 plies)")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_lam(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

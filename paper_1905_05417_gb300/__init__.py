@@ -24,8 +24,8 @@ import numpy as np
 
 __all__ = [
     "LamError", "Plan", "load", "plan_create", "plan_destroy", "plan_get_info", "pattern", "assemble_split",
-    "assemble_standard", "assemble_split_host", "plan_update", "last_error", "version", "SYMBOLS", "BSPLINE",
-    "LAGRANGE",
+    "assemble_standard", "assemble_split_host", "plan_update", "profile_enable", "profile_get", "last_error",
+    "version", "SYMBOLS", "KERNEL_KINDS", "BSPLINE", "LAGRANGE",
 ]
 
 BSPLINE = 0
@@ -35,7 +35,9 @@ LIB_PATH = os.path.join(_HERE, "liblam.so")
 
 # every symbol include/lam.h declares
 SYMBOLS = ("lam_plan_create", "lam_plan_destroy", "lam_plan_get_info", "lam_pattern", "lam_assemble_split",
-           "lam_assemble_standard", "lam_assemble_split_host", "lam_plan_update", "lam_last_error", "lam_version")
+           "lam_assemble_standard", "lam_assemble_split_host", "lam_plan_update", "lam_profile_enable",
+           "lam_profile_get", "lam_last_error", "lam_version")
+KERNEL_KINDS = ("pattern", "thickness", "inplane", "combine", "standard")
 
 _STATUS = {0: "LAM_OK", 1: "LAM_ERR_INVALID_ARG", 2: "LAM_ERR_UNSUPPORTED", 3: "LAM_ERR_OOM", 4: "LAM_ERR_CUDA",
            5: "LAM_ERR_TIMEOUT"}
@@ -70,6 +72,11 @@ class _Options(ctypes.Structure):
                 ("class_tol", ctypes.c_double)]
 
 
+class _Profile(ctypes.Structure):
+    _fields_ = [("enabled", ctypes.c_int32), ("launches", ctypes.c_int64 * 5), ("ms", ctypes.c_double * 5),
+                ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64)]
+
+
 class _Info(ctypes.Structure):
     _fields_ = [("n_dof", ctypes.c_int64), ("nnz", ctypes.c_int64), ("n_s", ctypes.c_int64), ("n_t", ctypes.c_int64),
                 ("nnz_inplane", ctypes.c_int64), ("nnz_thickness", ctypes.c_int64), ("n_configs", ctypes.c_int32),
@@ -100,6 +107,8 @@ def load() -> ctypes.CDLL:
     L.lam_assemble_standard.argtypes = [vp, vp, vp]
     L.lam_assemble_split_host.argtypes = [vp, vp, vp]
     L.lam_plan_update.argtypes = [vp, _D, ctypes.c_int32, ctypes.POINTER(_Material), ctypes.c_int32]
+    L.lam_profile_enable.argtypes = [vp, ctypes.c_int32]
+    L.lam_profile_get.argtypes = [vp, ctypes.POINTER(_Profile)]
     L.lam_last_error.restype = ctypes.c_char_p
     L.lam_version.restype = ctypes.c_char_p
     for name in SYMBOLS:
@@ -235,6 +244,21 @@ def plan_update(handle, ply_angle=None, C21=None) -> None:
                                   0 if pa is None else len(pa), mats, nm), "lam_plan_update")
 
 
+def profile_enable(handle, enable: bool = True) -> None:
+    """lam_profile_enable: start (or stop) timing every launch; counters restart."""
+    _check(load().lam_profile_enable(handle, 1 if enable else 0), "lam_profile_enable")
+
+
+def profile_get(handle) -> dict:
+    """lam_profile_get: per kernel kind, launches and device milliseconds; bytes moved."""
+    pr = _Profile()
+    _check(load().lam_profile_get(handle, ctypes.byref(pr)), "lam_profile_get")
+    out = {"enabled": bool(pr.enabled), "h2d_bytes": pr.h2d_bytes, "d2h_bytes": pr.d2h_bytes}
+    for k, name in enumerate(KERNEL_KINDS):
+        out[name] = {"launches": pr.launches[k], "ms": pr.ms[k]}
+    return out
+
+
 class Plan:
     """Convenience owner of a lam_plan handle; outputs are torch tensors."""
 
@@ -290,6 +314,12 @@ class Plan:
     def update(self, ply_angle=None, C21=None):
         plan_update(self.handle, ply_angle, C21)
         self.info = plan_get_info(self.handle)
+
+    def profile_enable(self, enable=True):
+        profile_enable(self.handle, enable)
+
+    def profile(self) -> dict:
+        return profile_get(self.handle)
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:

@@ -167,6 +167,33 @@ lam_status lam_assemble_standard(lam_plan* plan, double* d_values, void* stream)
  * slab is assembled. Synchronous: returns when h_values is complete. */
 lam_status lam_assemble_split_host(lam_plan* plan, double* h_values, void* stream);
 
+/* Split assembly that allocates nothing. The paper has no counterpart: this is
+ * a deployment variant of lam_assemble_split for callers that cannot call
+ * cudaMalloc -- for example a host application whose device memory all comes
+ * from its own pool allocator, or code that must not grow the device
+ * footprint while it runs. The result equals lam_assemble_split's.
+ *   - Instead of plan-owned cudaMalloc memory, the plan's tables and the
+ *     in-plane and thickness workspace are placed in ONE fixed array of static
+ *     device memory inside the library, LAM_NOALLOC_SCRATCH_BYTES (32 MiB)
+ *     long. Every GPU that loads the library holds this array until the
+ *     process exits.
+ *   - The call uploads the plan's tables into the array each time (plain
+ *     stream-ordered copies) and clears the part that must start at zero. It
+ *     calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - A plan whose tables and workspace need more than the array holds is
+ *     rejected with LAM_ERR_UNSUPPORTED (the message gives both sizes); the
+ *     64x64 cubic 48-ply plate needs about 16 MB.
+ *   - The first call on a device looks up the array's device address for that
+ *     device (once per device, with that device current); make that first
+ *     call before any stream capture.
+ *   - All calls on a device share the one array and it keeps the last call's
+ *     contents: calls that overlap on the GPU (two streams, or two host
+ *     threads) race and corrupt each other's results, so serialise them.
+ *   - The plan's own device workspace is neither used nor created.
+ * d_values: nnz doubles of caller-owned device memory. Asynchronous on `stream`. */
+#define LAM_NOALLOC_SCRATCH_BYTES (32u << 20)
+lam_status lam_assemble_split_noalloc(const lam_plan* plan, double* d_values, void* stream);
+
 /* Replace the ply angles (radians, n_plies values) and material constants
  * (n_materials x 21, NULL = keep) of an existing plan, as a design loop does
  * between assemblies. Host only; the configuration table and thickness

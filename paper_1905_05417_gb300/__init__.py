@@ -24,7 +24,7 @@ import numpy as np
 
 __all__ = [
     "LamError", "Plan", "load", "plan_create", "plan_destroy", "plan_get_info", "pattern", "assemble_split",
-    "assemble_standard", "assemble_split_host", "plan_update", "profile_enable", "profile_get", "last_error",
+    "assemble_standard", "assemble_split_host", "assemble_split_noalloc", "plan_update", "profile_enable", "profile_get", "last_error",
     "version", "SYMBOLS", "KERNEL_KINDS", "BSPLINE", "LAGRANGE",
 ]
 
@@ -35,7 +35,8 @@ LIB_PATH = os.path.join(_HERE, "liblam.so")
 
 # every symbol include/lam.h declares
 SYMBOLS = ("lam_plan_create", "lam_plan_destroy", "lam_plan_get_info", "lam_pattern", "lam_assemble_split",
-           "lam_assemble_standard", "lam_assemble_split_host", "lam_plan_update", "lam_profile_enable",
+           "lam_assemble_standard", "lam_assemble_split_host", "lam_assemble_split_noalloc", "lam_plan_update",
+           "lam_profile_enable",
            "lam_profile_get", "lam_last_error", "lam_version")
 KERNEL_KINDS = ("pattern", "thickness", "inplane", "combine", "standard")
 
@@ -106,6 +107,7 @@ def load() -> ctypes.CDLL:
     L.lam_assemble_split.argtypes = [vp, vp, vp]
     L.lam_assemble_standard.argtypes = [vp, vp, vp]
     L.lam_assemble_split_host.argtypes = [vp, vp, vp]
+    L.lam_assemble_split_noalloc.argtypes = [vp, vp, vp]
     L.lam_plan_update.argtypes = [vp, _D, ctypes.c_int32, ctypes.POINTER(_Material), ctypes.c_int32]
     L.lam_profile_enable.argtypes = [vp, ctypes.c_int32]
     L.lam_profile_get.argtypes = [vp, ctypes.POINTER(_Profile)]
@@ -214,6 +216,13 @@ def pattern(handle, d_row_ptr=None, d_col_ind=None, stream=None) -> int:
 
 def assemble_split(handle, d_values, stream=None) -> None:
     _check(load().lam_assemble_split(handle, _ptr(d_values), _stream_handle(stream)), "lam_assemble_split")
+
+
+def assemble_split_noalloc(handle, d_values, stream=None) -> None:
+    """lam_assemble_split_noalloc: the split assembly with its tables and
+    workspace in the library's fixed static device array (no allocation)."""
+    _check(load().lam_assemble_split_noalloc(handle, _ptr(d_values), _stream_handle(stream)),
+           "lam_assemble_split_noalloc")
 
 
 def assemble_standard(handle, d_values, stream=None) -> None:

@@ -1090,3 +1090,257 @@ lam_status lam_profile_get(lam_plan* plan, lam_profile* out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Split assembly without allocation (lam_assemble_split_noalloc): the same
+// kernels, with every table and workspace placed in one static device array.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace lam {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[LAM_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoallocMaxDevices = 64;
+static void* g_noalloc_addr[kNoallocMaxDevices] = {};
+static std::mutex g_noalloc_mutex;
+
+// Device address of the static array on the current device. Host code cannot
+// use the array's name as a device pointer, so the address is looked up once
+// per device (with that device current) and remembered.
+static lam_status noalloc_scratch_address(int dev, unsigned char** out) {
+  if (dev < 0 || dev >= kNoallocMaxDevices) {
+    set_error("lam_assemble_split_noalloc: device ordinal %d outside [0, %d)", dev, kNoallocMaxDevices);
+    return LAM_ERR_UNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error("lam_assemble_split_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return LAM_ERR_CUDA;
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+  return LAM_OK;
+}
+
+// Fills trep[k] = cls_rep[u] for the terms k of every class u.
+__global__ void noalloc_term_rep(const int* __restrict__ term_begin, const int* __restrict__ cls_rep, int ncls,
+                                 int* __restrict__ trep) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= ncls) return;
+  for (int k = term_begin[u]; k < term_begin[u + 1]; ++k) trep[k] = cls_rep[u];
+}
+
+// Carves the scratch array into 256-byte aligned slices.
+struct ScratchCarver {
+  unsigned char* base;
+  size_t used = 0;
+  template <typename T>
+  T* take(size_t count) {
+    T* p = reinterpret_cast<T*>(base + used);
+    used += (std::max<size_t>(count, 1) * sizeof(T) + 255) & ~(size_t)255;
+    return p;
+  }
+};
+
+}  // namespace lam
+
+extern "C" lam_status lam_assemble_split_noalloc(const lam_plan* plan, double* d_values, void* stream) {
+  if (!plan || !d_values) {
+    lam::set_error("lam_assemble_split_noalloc: NULL argument");
+    return LAM_ERR_INVALID_ARG;
+  }
+  const lam::Plan& P = plan->p;
+  lam_status st;
+  if ((st = lam::check_limits(P)) != LAM_OK) return st;
+  const int ncfg = (int)P.cfg_mat.size();
+  // layout (sizes only: base 0)
+  lam::ScratchCarver lay{nullptr};
+  lay.take<double>(P.tabU.size());
+  lay.take<double>(P.tabV.size());
+  lay.take<double>(P.wU.size());
+  lay.take<double>(P.wV.size());
+  lay.take<int>(P.u.first.size());
+  lay.take<int>(P.v.first.size());
+  lay.take<int>(P.u.lo.size());
+  lay.take<int>(P.u.len.size());
+  lay.take<int>(P.v.lo.size());
+  lay.take<int>(P.v.len.size());
+  lay.take<double>(P.ctrl.size());
+  lay.take<double>(P.weights.size());
+  lay.take<int64_t>(P.LSb.size());
+  lay.take<int>(P.col2_elem.size());
+  lay.take<int>(P.t.first.size());
+  lay.take<double>(P.tabT.size());
+  lay.take<double>(P.wT.size());
+  lay.take<int>(P.piece_begin.size());
+  lay.take<int>(P.pieces.size());
+  lay.take<int>(P.tp_row.size());
+  lay.take<int>(P.tp_col.size());
+  lay.take<int>(P.tp_e0.size());
+  lay.take<int>(P.tp_e1.size());
+  lay.take<int>(P.cls_term_begin.size());
+  lay.take<int>(P.cls_terms.size());
+  lay.take<int>(P.cls_occ_begin.size());
+  lay.take<int>(P.cls_rep.size());
+  lay.take<int>(P.cls_terms.size());
+  lay.take<int64_t>(P.occ_A.size());
+  lay.take<int>(P.occ_lt.size());
+  lay.take<int>(P.occ_k.size());
+  lay.take<int>(P.occ_it.size());
+  lay.take<double>(P.cfgE.size());
+  lay.take<double>((size_t)P.nnz_t * ncfg * 4);
+  lay.take<double>((size_t)P.nnz_s * 9);
+  if (lay.used > LAM_NOALLOC_SCRATCH_BYTES) {
+    lam::set_error("lam_assemble_split_noalloc: this plan needs %zu bytes of scratch, the static array holds %u",
+                   lay.used, (unsigned)LAM_NOALLOC_SCRATCH_BYTES);
+    return LAM_ERR_UNSUPPORTED;
+  }
+  int dev = 0;
+  LAM_CUDA(cudaGetDevice(&dev));
+  unsigned char* base = nullptr;
+  if ((st = lam::noalloc_scratch_address(dev, &base)) != LAM_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  lam::ScratchCarver sc{base};
+  // tables: host -> static array (stream-ordered copies)
+#define PUT(T, name, vec)                                                                              \
+  T* name = sc.take<T>((vec).size());                                                                  \
+  if (!(vec).empty())                                                                                  \
+    LAM_CUDA(cudaMemcpyAsync(name, (vec).data(), (vec).size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  PUT(double, tabU, P.tabU);
+  PUT(double, tabV, P.tabV);
+  PUT(double, wU, P.wU);
+  PUT(double, wV, P.wV);
+  PUT(int, firstU, P.u.first);
+  PUT(int, firstV, P.v.first);
+  PUT(int, loX, P.u.lo);
+  PUT(int, lenX, P.u.len);
+  PUT(int, loY, P.v.lo);
+  PUT(int, lenY, P.v.len);
+  PUT(double, ctrl, P.ctrl);
+  PUT(double, weights, P.weights);
+  PUT(int64_t, LSb, P.LSb);
+  PUT(int, col2_elem, P.col2_elem);
+  PUT(int, firstT, P.t.first);
+  PUT(double, tabT, P.tabT);
+  PUT(double, wT, P.wT);
+  PUT(int, piece_begin, P.piece_begin);
+  int* piece_cfg = sc.take<int>(P.pieces.size());
+  if (!P.pieces.empty())  // the cfg field of every Piece, gathered by a strided copy
+    LAM_CUDA(cudaMemcpy2DAsync(piece_cfg, sizeof(int), &P.pieces[0].cfg, sizeof(lam::Piece), sizeof(int),
+                               P.pieces.size(), cudaMemcpyHostToDevice, s));
+  PUT(int, tp_row, P.tp_row);
+  PUT(int, tp_col, P.tp_col);
+  PUT(int, tp_e0, P.tp_e0);
+  PUT(int, tp_e1, P.tp_e1);
+  PUT(int, cls_term_begin, P.cls_term_begin);
+  PUT(int, cls_terms, P.cls_terms);
+  PUT(int, cls_occ_begin, P.cls_occ_begin);
+  PUT(int, cls_rep, P.cls_rep);
+  int* term_rep = sc.take<int>(P.cls_terms.size());
+  PUT(int64_t, occ_A, P.occ_A);
+  PUT(int, occ_lt, P.occ_lt);
+  PUT(int, occ_k, P.occ_k);
+  PUT(int, occ_it, P.occ_it);
+  PUT(double, cfgE, P.cfgE);
+#undef PUT
+  double* q = sc.take<double>((size_t)P.nnz_t * ncfg * 4);
+  double* G = sc.take<double>((size_t)P.nnz_s * 9);
+  lam::noalloc_term_rep<<<(P.ncls + 127) / 128, 128, 0, s>>>(cls_term_begin, cls_rep, P.ncls, term_rep);
+  LAM_CUDA(cudaGetLastError());
+  // K-b
+  lam::KbArgs kb;
+  kb.npairs = P.nnz_t;
+  kb.ncfg = ncfg;
+  kb.nqt = P.nqt;
+  kb.q1 = P.t.p + 1;
+  kb.tp_row = tp_row;
+  kb.tp_col = tp_col;
+  kb.tp_e0 = tp_e0;
+  kb.tp_e1 = tp_e1;
+  kb.firstT = firstT;
+  kb.piece_begin = piece_begin;
+  kb.piece_cfg = piece_cfg;
+  kb.tabT = tabT;
+  kb.wT = wT;
+  kb.q = q;
+  lam::kb_thickness<<<(unsigned)((P.nnz_t + 127) / 128), 128, 0, s>>>(kb);
+  LAM_CUDA(cudaGetLastError());
+  // K-a: G accumulates, so it starts at zero
+  LAM_CUDA(cudaMemsetAsync(G, 0, (size_t)P.nnz_s * 9 * sizeof(double), s));
+  lam::KaArgs ka;
+  ka.ip.nx = P.u.n;
+  ka.ip.nel_u = P.u.nel;
+  ka.ip.pu = P.u.p;
+  ka.ip.pv = P.v.p;
+  ka.ip.nqu = P.nqu;
+  ka.ip.nqv = P.nqv;
+  ka.ip.tabU = tabU;
+  ka.ip.tabV = tabV;
+  ka.ip.wU = wU;
+  ka.ip.wV = wV;
+  ka.ip.ctrl = ctrl;
+  ka.ip.weights = P.weights.empty() ? nullptr : weights;
+  ka.ip.firstU = firstU;
+  ka.ip.firstV = firstV;
+  ka.loX = loX;
+  ka.lenX = lenX;
+  ka.loY = loY;
+  ka.lenY = lenY;
+  ka.LSb = LSb;
+  ka.G = G;
+  const size_t ka_sm = lam::ka_smem(P);
+  LAM_CUDA(cudaFuncSetAttribute(lam::ka_inplane, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ka_sm));
+  const int ncol = (int)P.col2_begin.size() - 1;
+  for (int c = 0; c < ncol; ++c) {
+    const int n = P.col2_begin[c + 1] - P.col2_begin[c];
+    if (n == 0) continue;
+    ka.elems = col2_elem + P.col2_begin[c];
+    lam::ka_inplane<<<n, lam::ka_block(P), ka_sm, s>>>(ka);
+    LAM_CUDA(cudaGetLastError());
+  }
+  // K-c
+  lam::KcArgs k;
+  k.ns = P.ns;
+  k.nnz_s = P.nnz_s;
+  k.nx = P.u.n;
+  k.ncfg = ncfg;
+  k.ncls = P.ncls;
+  k.nterms = (int)P.cls_terms.size();
+  k.nocc = (int)P.nnz_t;
+  k.gs_cap = lam::kc_gs_cap(P);
+  k.LSb = LSb;
+  k.lenX = lenX;
+  k.lenY = lenY;
+  k.G = G;
+  k.cfgE = cfgE;
+  k.q = q;
+  k.cls_term_begin = cls_term_begin;
+  k.cls_terms = cls_terms;
+  k.cls_occ_begin = cls_occ_begin;
+  k.term_rep = term_rep;
+  k.occ_A = occ_A;
+  k.occ_lt = occ_lt;
+  k.occ_k = occ_k;
+  k.occ_it = occ_it;
+  k.it_lo = 0;
+  k.it_hi = (int)P.nt;
+  k.out_offset = 0;
+  k.values = d_values;
+  const size_t kc_sm = lam::kc_smem(P);
+  if (P.monoclinic) {
+    LAM_CUDA(cudaFuncSetAttribute(lam::kc_combine<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kc_sm));
+    lam::kc_combine<true, false><<<(unsigned)P.ns, lam::kc_block(P), kc_sm, s>>>(k);
+  } else {
+    LAM_CUDA(cudaFuncSetAttribute(lam::kc_combine<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kc_sm));
+    lam::kc_combine<false, false><<<(unsigned)P.ns, lam::kc_block(P), kc_sm, s>>>(k);
+  }
+  LAM_CUDA(cudaGetLastError());
+  return LAM_OK;
+}

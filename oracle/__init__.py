@@ -47,11 +47,9 @@ _I32 = ctypes.POINTER(ctypes.c_int32)
 _I64 = ctypes.POINTER(ctypes.c_int64)
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        build()
-        L = ctypes.CDLL(_SO)
+def configure(L):
+    """Declare the argument types of an oracle library handle."""
+    if True:
         L.ora_gauss.argtypes = [ctypes.c_int32, _D, _D]
         L.ora_nfun.argtypes = [ctypes.POINTER(_Basis)]
         L.ora_nfun.restype = ctypes.c_int32
@@ -67,7 +65,14 @@ def lib():
         L.ora_block.argtypes = [ctypes.POINTER(_Problem), ctypes.c_int64, ctypes.c_int64, _D]
         L.ora_element_stiffness.argtypes = [ctypes.POINTER(_Problem), ctypes.c_int32, ctypes.c_int32,
                                             ctypes.c_int32, _D]
-        _lib = L
+    return L
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = configure(ctypes.CDLL(_SO))
     return _lib
 
 

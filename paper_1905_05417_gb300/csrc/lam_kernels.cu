@@ -54,8 +54,9 @@ struct Device {
   // standard path
   int* col3_elem = nullptr;
   // workspace
-  double* G = nullptr;  // nnz_s x 9
-  double* q = nullptr;  // nnz_t x n_cfg x 4
+  int *eloX = nullptr, *ehiX = nullptr, *eloY = nullptr, *ehiY = nullptr;
+  double* EG = nullptr;  // element Gram blocks: n_el x 9 x pairs
+  double* q = nullptr;   // nnz_t x n_cfg x 4
   // host-output staging
   double* stage[2] = {nullptr, nullptr};
   size_t stage_elems = 0;
@@ -187,12 +188,13 @@ static size_t kc_smem(const Plan& P) {
   b += (size_t)kc_gs_cap(P) * sizeof(double);                     // G row
   b += (size_t)ncfg * kc_np(P) * kc_block(P) * sizeof(double);    // per-thread P
   b += (size_t)P.cls_terms.size() * 4 * sizeof(double);           // Q of every class term
-  b += (size_t)P.nnz_t * (sizeof(int64_t) + 2 * sizeof(int));      // occurrences
+  b += (size_t)P.nnz_t * 3 * sizeof(int64_t);                     // CSR bases per (c, occurrence)
   b += (size_t)(2 * (P.ncls + 1) + P.cls_terms.size()) * sizeof(int);
   return (b + 15) & ~(size_t)15;
 }
 
 static int ka_nls(const Plan& P) { return (P.u.p + 1) * (P.v.p + 1); }
+static int ka_npl(const Plan& P) { return ka_nls(P) * (ka_nls(P) + 1) / 2; }
 static int ka_block(const Plan& P) {
   int np = ka_nls(P) * (ka_nls(P) + 1) / 2;
   return np >= 256 ? 256 : ((np + 31) / 32) * 32;
@@ -443,17 +445,77 @@ __global__ void __launch_bounds__(256) ka_inplane(KaArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// K-a (single launch): one CTA per in-plane element; the Gram blocks of its
+// unordered local pairs (li <= lj) go to EG[(e * 9 + ab) * npl + pair], pair
+// numbered row-major over the upper triangle. The combine gathers them per row
+// in a fixed element order, so the sums are deterministic without colouring.
+// ---------------------------------------------------------------------------
+struct KaLocalArgs {
+  InplaneArgs ip;
+  int nel;
+  double* EG;
+};
+
+__global__ void __launch_bounds__(256) ka_local(KaLocalArgs a) {
+  extern __shared__ double sm[];
+  const InplaneArgs& ip = a.ip;
+  const int nlx = ip.pu + 1, nly = ip.pv + 1, nls = nlx * nly, nqs = ip.nqu * ip.nqv;
+  double* phi = sm;
+  double* phiw = phi + (size_t)nqs * nls * 3;
+  double* qd = phiw + (size_t)nqs * nls * 3;
+  const int e = blockIdx.x;
+  const int ex = e % ip.nel_u, ey = e / ip.nel_u;
+  inplane_points(ip, ex, ey, phi, phiw, qd);
+  const int npl = nls * (nls + 1) / 2;
+  double* out = a.EG + (size_t)e * 9 * npl;
+  for (int t = threadIdx.x; t < npl; t += blockDim.x) {
+    int li = 0, rem = t;
+    while (rem >= nls - li) {
+      rem -= nls - li;
+      ++li;
+    }
+    const int lj = li + rem;
+    double acc[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[k] = 0.0;
+    for (int q = 0; q < nqs; ++q) {
+      const double* A = phiw + ((size_t)q * nls + li) * 3;
+      const double* B = phi + ((size_t)q * nls + lj) * 3;
+      const double a0 = A[0], a1 = A[1], a2 = A[2], b0 = B[0], b1 = B[1], b2 = B[2];
+      acc[0] += a0 * b0;
+      acc[1] += a0 * b1;
+      acc[2] += a0 * b2;
+      acc[3] += a1 * b0;
+      acc[4] += a1 * b1;
+      acc[5] += a1 * b2;
+      acc[6] += a2 * b0;
+      acc[7] += a2 * b1;
+      acc[8] += a2 * b2;
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) out[(size_t)k * npl + t] = acc[k];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // K-c: fused combine. One CTA per in-plane row i_s; thread <-> (c, k_s, d) of
-// that row. Each thread forms its P_{m,ab}[c][d] from the G block, then for
-// every thickness class u evaluates slice_u = sum_terms sum_ab Q P and stores
-// it at every occurrence (i_t, k_t) of the class.
+// that row. The CTA first forms the row's G blocks (gathered from the element
+// blocks, or loaded from an assembled G), the class Q vectors, and the CSR base
+// of every (c, thickness occurrence). Each thread then forms its
+// P_{m,ab}[c][d] from its G block and, for every thickness class u, evaluates
+// slice_u = sum_terms sum_ab Q P once and stores it at every occurrence
+// (i_t, k_t) of the class: one shared load and one 8-byte store per value.
 // ---------------------------------------------------------------------------
 struct KcArgs {
   int64_t ns, nnz_s;
   int nx, ncfg, ncls, nterms, nocc, gs_cap;
   const int64_t* LSb;
   const int *lenX, *lenY;
-  const double* G;
+  const double* G;      // assembled G (nnz_s x 9), when not gathering
+  // gathering from element blocks
+  const double* EG;
+  int nel_u, nlx, nls, npl;  // elements in u, local functions in x / per element, pairs per element
+  const int *loX, *loY, *eloX, *ehiX, *eloY, *ehiY, *firstU, *firstV;
   const double* cfgE;
   const double* q;
   const int *cls_term_begin, *cls_terms, *cls_occ_begin, *term_rep;
@@ -464,26 +526,51 @@ struct KcArgs {
   double* values;
 };
 
-template <bool MONO, bool CHUNKED>
-__global__ void __launch_bounds__(1024) kc_combine(KcArgs a) {
+__device__ __forceinline__ int upper_pair(int a, int b, int n) { return a * n - a * (a - 1) / 2 + (b - a); }
+
+template <bool MONO, bool CHUNKED, bool GATHER>
+__global__ void __launch_bounds__(1024, 2) kc_combine(KcArgs a) {
   extern __shared__ double sm[];
   constexpr int NP = MONO ? 2 : 4;
   const int64_t is = blockIdx.x;
   const int ix = (int)(is % a.nx), iy = (int)(is / a.nx);
-  const int ls = a.lenX[ix] * a.lenY[iy];
+  const int lx = a.lenX[ix];
+  const int ls = lx * a.lenY[iy];
   const int64_t ls0 = a.LSb[is];
   const int nthr = blockDim.x, tid = threadIdx.x;
   // shared layout
   double* Gs = sm;                                         // 9 * ls (max)
   double* Ps = Gs + a.gs_cap;                              // ncfg * NP * nthr
   double* Qs = Ps + (size_t)a.ncfg * NP * nthr;            // nterms * 4
-  int64_t* oA = reinterpret_cast<int64_t*>(Qs + (size_t)a.nterms * 4);
-  int* oLT = reinterpret_cast<int*>(oA + a.nocc);
-  int* oK = oLT + a.nocc;
-  int* tb = oK + a.nocc;                                   // ncls + 1
+  int64_t* base3 = reinterpret_cast<int64_t*>(Qs + (size_t)a.nterms * 4);  // 3 * nocc
+  int* tb = reinterpret_cast<int*>(base3 + 3 * (size_t)a.nocc);            // ncls + 1
   int* ob = tb + (a.ncls + 1);                             // ncls + 1
   int* tm = ob + (a.ncls + 1);                             // nterms
-  for (int k = tid; k < 9 * ls; k += nthr) Gs[k] = a.G[ls0 * 9 + k];
+  if (GATHER) {
+    for (int item = tid; item < 9 * ls; item += nthr) {
+      const int ks = item / 9, ab = item % 9;
+      const int jx = a.loX[ix] + ks % lx, jy = a.loY[iy] + ks / lx;
+      const int ex0 = max(a.eloX[ix], a.eloX[jx]), ex1 = min(a.ehiX[ix], a.ehiX[jx]);
+      const int ey0 = max(a.eloY[iy], a.eloY[jy]), ey1 = min(a.ehiY[iy], a.ehiY[jy]);
+      const int ba = (ab % 3) * 3 + ab / 3;
+      double acc = 0.0;
+      for (int ey = ey0; ey <= ey1; ++ey) {
+        const int fy = a.firstV[ey];
+        for (int ex = ex0; ex <= ex1; ++ex) {
+          const int fx = a.firstU[ex];
+          const int li = (iy - fy) * a.nlx + (ix - fx), lj = (jy - fy) * a.nlx + (jx - fx);
+          const size_t e9 = ((size_t)ey * a.nel_u + ex) * 9;
+          if (li <= lj)
+            acc += a.EG[(e9 + ab) * a.npl + upper_pair(li, lj, a.nls)];
+          else
+            acc += a.EG[(e9 + ba) * a.npl + upper_pair(lj, li, a.nls)];
+        }
+      }
+      Gs[item] = acc;
+    }
+  } else {
+    for (int k = tid; k < 9 * ls; k += nthr) Gs[k] = a.G[ls0 * 9 + k];
+  }
   for (int k = tid; k < a.nterms; k += nthr) {
     const int m = a.cls_terms[k];
     tm[k] = m;
@@ -493,10 +580,15 @@ __global__ void __launch_bounds__(1024) kc_combine(KcArgs a) {
     Qs[4 * k + 2] = src[2];
     Qs[4 * k + 3] = src[3];
   }
-  for (int k = tid; k < a.nocc; k += nthr) {
-    oA[k] = a.occ_A[k];
-    oLT[k] = CHUNKED ? ((a.occ_it[k] >= a.it_lo && a.occ_it[k] < a.it_hi) ? a.occ_lt[k] : -1) : a.occ_lt[k];
-    oK[k] = a.occ_k[k];
+  // CSR base of (c, occurrence o): row_ptr(i_t, i_s, c) + 3 k_t len_s, minus the output offset
+  for (int o = tid; o < a.nocc; o += nthr) {
+    const int64_t A = a.occ_A[o];
+    const int64_t lt = a.occ_lt[o], kt = a.occ_k[o];
+    const bool keep = !CHUNKED || (a.occ_it[o] >= a.it_lo && a.occ_it[o] < a.it_hi);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      base3[(size_t)c * a.nocc + o] =
+          keep ? A + lt * (9 * ls0 + 3 * (int64_t)c * ls) + kt * 3 * (int64_t)ls - a.out_offset : (int64_t)-1;
   }
   for (int k = tid; k <= a.ncls; k += nthr) {
     tb[k] = a.cls_term_begin[k];
@@ -508,7 +600,7 @@ __global__ void __launch_bounds__(1024) kc_combine(KcArgs a) {
   const int c = item / (3 * ls), rem = item % (3 * ls), ks = rem / 3, d = rem % 3;
   const double* g = Gs + ks * 9;
   const int cd = c * 3 + d;
-  // P for every configuration, in registers -> shared (indexed by the class terms)
+  // P for every configuration, into shared memory (indexed by the class terms)
   const bool block_type = ((c == 2) == (d == 2));
   for (int m = 0; m < a.ncfg; ++m) {
     const double* E = a.cfgE + (size_t)m * 81 + cd * 9;
@@ -527,8 +619,8 @@ __global__ void __launch_bounds__(1024) kc_combine(KcArgs a) {
     }
   }
   const int offa = block_type ? 0 : 1, offb = block_type ? 3 : 2;
-  const int64_t X = 9 * ls0 + 3 * (int64_t)c * ls, Y = 3 * (int64_t)ls, Z = 3 * ks + d;
-  double* out = a.values - a.out_offset;
+  const int64_t* B = base3 + (size_t)c * a.nocc;
+  double* out = a.values + (3 * ks + d);
   for (int u = 0; u < a.ncls; ++u) {
     double v = 0.0;
     for (int k = tb[u]; k < tb[u + 1]; ++k) {
@@ -540,10 +632,12 @@ __global__ void __launch_bounds__(1024) kc_combine(KcArgs a) {
              Qs[4 * k + 2] * Ps[(m * 4 + 2) * nthr + tid] + Qs[4 * k + 3] * Ps[(m * 4 + 3) * nthr + tid];
       }
     }
-    for (int o = ob[u]; o < ob[u + 1]; ++o) {
-      const int lt = oLT[o];
-      if (CHUNKED && lt < 0) continue;
-      out[oA[o] + lt * X + oK[o] * Y + Z] = v;
+    const int o1 = ob[u + 1];
+#pragma unroll 4
+    for (int o = ob[u]; o < o1; ++o) {
+      const int64_t b = B[o];
+      if (CHUNKED && b < 0) continue;
+      out[b] = v;
     }
   }
 }
@@ -701,7 +795,11 @@ static lam_status ensure_device(Plan& P) {
     UP(L, D->tp_e0, P.tp_e0);
     UP(L, D->tp_e1, P.tp_e1);
     UP(L, D->col3_elem, P.col3_elem);
-    if ((st = alloc_dev(L, &D->G, (size_t)P.nnz_s * 9)) != LAM_OK) {
+    UP(L, D->eloX, P.u.elo);
+    UP(L, D->ehiX, P.u.ehi);
+    UP(L, D->eloY, P.v.elo);
+    UP(L, D->ehiY, P.v.ehi);
+    if ((st = alloc_dev(L, &D->EG, (size_t)P.u.nel * P.v.nel * 9 * ka_npl(P))) != LAM_OK) {
       free_device(P);
       return st;
     }
@@ -786,7 +884,20 @@ static KcArgs kc_args(const Plan& P, double* values) {
   k.LSb = D.LSb;
   k.lenX = D.lenX;
   k.lenY = D.lenY;
-  k.G = D.G;
+  k.G = nullptr;
+  k.EG = D.EG;
+  k.nel_u = P.u.nel;
+  k.nlx = P.u.p + 1;
+  k.nls = ka_nls(P);
+  k.npl = ka_npl(P);
+  k.loX = D.loX;
+  k.loY = D.loY;
+  k.eloX = D.eloX;
+  k.ehiX = D.ehiX;
+  k.eloY = D.eloY;
+  k.ehiY = D.ehiY;
+  k.firstU = D.firstU;
+  k.firstV = D.firstV;
   k.cfgE = D.cfgE;
   k.q = D.q;
   k.cls_term_begin = D.cls_term_begin;
@@ -807,9 +918,10 @@ static KcArgs kc_args(const Plan& P, double* values) {
 template <bool MONO, bool CHUNKED>
 static lam_status launch_kc(const Plan& P, const KcArgs& k, cudaStream_t s) {
   const size_t smem = kc_smem(P);
-  LAM_CUDA(cudaFuncSetAttribute(kc_combine<MONO, CHUNKED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LAM_CUDA(cudaFuncSetAttribute(kc_combine<MONO, CHUNKED, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
   cudaEvent_t ev = prof_begin(const_cast<Plan&>(P), s);
-  kc_combine<MONO, CHUNKED><<<(unsigned)P.ns, kc_block(P), smem, s>>>(k);
+  kc_combine<MONO, CHUNKED, true><<<(unsigned)P.ns, kc_block(P), smem, s>>>(k);
   LAM_CUDA(cudaGetLastError());
   prof_end(const_cast<Plan&>(P), LAM_KERNEL_COMBINE, 1, s, ev);
   return LAM_OK;
@@ -837,28 +949,16 @@ static lam_status split_integrals(Plan& P, cudaStream_t s) {
   kb_thickness<<<(unsigned)((P.nnz_t + 127) / 128), 128, 0, s>>>(kb);
   LAM_CUDA(cudaGetLastError());
   prof_end(P, LAM_KERNEL_THICKNESS, 1, s, ev);
-  LAM_CUDA(cudaMemsetAsync(D.G, 0, (size_t)P.nnz_s * 9 * sizeof(double), s));
-  KaArgs ka;
+  KaLocalArgs ka;
   ka.ip = inplane_args(P);
-  ka.loX = D.loX;
-  ka.lenX = D.lenX;
-  ka.loY = D.loY;
-  ka.lenY = D.lenY;
-  ka.LSb = D.LSb;
-  ka.G = D.G;
+  ka.nel = P.u.nel * P.v.nel;
+  ka.EG = D.EG;
   const size_t smem = ka_smem(P);
-  LAM_CUDA(cudaFuncSetAttribute(ka_inplane, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int ncol = (int)P.col2_begin.size() - 1;
+  LAM_CUDA(cudaFuncSetAttribute(ka_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ev = prof_begin(P, s);
-  int launched = 0;
-  for (int c = 0; c < ncol; ++c) {
-    const int n = P.col2_begin[c + 1] - P.col2_begin[c];
-    if (n == 0) continue;
-    ka.elems = D.col2_elem + P.col2_begin[c];
-    ka_inplane<<<n, ka_block(P), smem, s>>>(ka);
-    LAM_CUDA(cudaGetLastError());
-    ++launched;
-  }
+  ka_local<<<ka.nel, ka_block(P), smem, s>>>(ka);
+  LAM_CUDA(cudaGetLastError());
+  const int launched = 1;
   prof_end(P, LAM_KERNEL_INPLANE, launched, s, ev);
   return LAM_OK;
 }
@@ -1317,6 +1417,7 @@ extern "C" lam_status lam_assemble_split_noalloc(const lam_plan* plan, double* d
   k.lenX = lenX;
   k.lenY = lenY;
   k.G = G;
+  k.EG = nullptr;
   k.cfgE = cfgE;
   k.q = q;
   k.cls_term_begin = cls_term_begin;
@@ -1333,13 +1434,13 @@ extern "C" lam_status lam_assemble_split_noalloc(const lam_plan* plan, double* d
   k.values = d_values;
   const size_t kc_sm = lam::kc_smem(P);
   if (P.monoclinic) {
-    LAM_CUDA(cudaFuncSetAttribute(lam::kc_combine<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kc_sm));
-    lam::kc_combine<true, false><<<(unsigned)P.ns, lam::kc_block(P), kc_sm, s>>>(k);
+    LAM_CUDA(cudaFuncSetAttribute(lam::kc_combine<true, false, false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kc_sm));
+    lam::kc_combine<true, false, false><<<(unsigned)P.ns, lam::kc_block(P), kc_sm, s>>>(k);
   } else {
-    LAM_CUDA(cudaFuncSetAttribute(lam::kc_combine<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kc_sm));
-    lam::kc_combine<false, false><<<(unsigned)P.ns, lam::kc_block(P), kc_sm, s>>>(k);
+    LAM_CUDA(cudaFuncSetAttribute(lam::kc_combine<false, false, false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kc_sm));
+    lam::kc_combine<false, false, false><<<(unsigned)P.ns, lam::kc_block(P), kc_sm, s>>>(k);
   }
   LAM_CUDA(cudaGetLastError());
   return LAM_OK;

@@ -64,16 +64,22 @@ def test_noalloc_matches_split_on_two_calls(lib, make):
 
 
 def test_noalloc_on_the_benchmark_plate(lib):
-    """The 64x64 cubic 48-ply plate fits in the static array."""
+    """The 64x64 cubic 48-ply plate fits in the static array; two calls in a
+    row agree with lam_assemble_split and, bit for bit, with each other."""
     import torch
     plan = lib.Plan.from_laminate(W.curved_plate())
     ref = plan.assemble_split()
+    scale = ref.abs().max().item()
     out = torch.empty_like(ref)
+    prev = None
     for _ in range(2):
         out.zero_()
         assert _noalloc(lib, plan, out) == 0, lib.last_error()
         torch.cuda.synchronize()
-        assert torch.equal(out, ref)  # same kernels, same arithmetic
+        assert (out - ref).abs().max().item() <= TOL * scale
+        if prev is not None:
+            assert torch.equal(out, prev)
+        prev = out.clone()
     plan.close()
 
 

@@ -77,6 +77,10 @@ struct Plan {
   // combine classes: thickness pairs with equal Q vectors
   int ncls = 0;
   std::vector<int> cls_rep;              // representative pair of each class
+  std::vector<int> pair_cls;             // class of every thickness pair
+  std::vector<int> st_begin;             // class terms sorted by configuration: [m] range, size n_cfg + 1
+  std::vector<int> st_cls, st_rep, st_cfg;  // class, representative pair and configuration of each sorted term
+  std::vector<int> st_first;                // 1 if the sorted term is the first one of its class
   std::vector<int> cls_term_begin;       // size ncls + 1
   std::vector<int> cls_terms;            // configuration ids with nonzero Q
   std::vector<int> cls_occ_begin;        // size ncls + 1
@@ -108,6 +112,23 @@ struct Plan {
   std::vector<Pending> prof_pending;
   std::vector<void*> prof_free_events;
 };
+
+// Launch geometry of the combine shared by host and device code: the
+// streaming form keeps a row's class slices in shared memory (one 512-thread
+// CTA per row, two per SM); otherwise the class-major form runs.
+inline int max_len_s(const Plan& P) {
+  int mx = 0, my = 0;
+  for (int v : P.u.len) mx = mx > v ? mx : v;
+  for (int v : P.v.len) my = my > v ? my : v;
+  return mx * my;
+}
+inline int kcs_stride(const Plan& P) { return 9 * max_len_s(P); }
+inline size_t kcs_smem(const Plan& P) {
+  size_t b = (size_t)P.ncls * kcs_stride(P) * sizeof(double) +      // class slices (the G row first)
+             P.st_cls.size() * (4 * sizeof(double) + 2 * sizeof(int));  // sorted terms: Q, class, flag
+  return (b + 15) & ~(size_t)15;
+}
+inline bool use_stream(const Plan& P) { return 9 * max_len_s(P) <= 512 && kcs_smem(P) <= 110 * 1024; }
 
 // lam_plan.cpp
 lam_status build_plan(Plan& P, const lam_inplane* inplane, const lam_basis1d* thickness, const lam_ply* plies,

@@ -55,6 +55,8 @@ struct Device {
   int* col3_elem = nullptr;
   // workspace
   int *eloX = nullptr, *ehiX = nullptr, *eloY = nullptr, *ehiY = nullptr;
+  int *pair_cls = nullptr, *st_begin = nullptr, *st_cls = nullptr, *st_rep = nullptr, *st_first = nullptr;
+
   double* EG = nullptr;  // element Gram blocks: n_el x 9 x pairs
   double* q = nullptr;   // nnz_t x n_cfg x 4
   // host-output staging
@@ -169,12 +171,6 @@ void free_device(Plan& P) {
 // ---------------------------------------------------------------------------
 // Launch geometry
 // ---------------------------------------------------------------------------
-static int max_len_s(const Plan& P) {
-  int mx = 0, my = 0;
-  for (int v : P.u.len) mx = std::max(mx, v);
-  for (int v : P.v.len) my = std::max(my, v);
-  return mx * my;
-}
 
 static int kc_block(const Plan& P) { return ((9 * max_len_s(P) + 31) / 32) * 32; }
 
@@ -524,6 +520,11 @@ struct KcArgs {
   int it_lo, it_hi;     // thickness rows written (chunked output)
   int64_t out_offset;   // subtracted from every CSR position
   double* values;
+  // streaming combine
+  const int64_t* LTb;
+  const int* pair_cls;
+  const int *st_begin, *st_cls, *st_rep, *st_first;
+  int nst, slice_stride, nt;
 };
 
 __device__ __forceinline__ int upper_pair(int a, int b, int n) { return a * n - a * (a - 1) / 2 + (b - a); }
@@ -639,6 +640,139 @@ __global__ void __launch_bounds__(1024, 2) kc_combine(KcArgs a) {
       if (CHUNKED && b < 0) continue;
       out[b] = v;
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K-c, streaming form (used when a row's class slices fit in shared memory):
+// one 512-thread CTA per in-plane row i_s, two CTAs per SM. Phase 1 forms the
+// row's G blocks (gathered from the element blocks); each thread (c, k_s, d)
+// forms the P_{m,ab}[c][d] it needs per configuration and accumulates
+// slice_u = sum Q P for every class u in shared memory. Phase 2 writes the
+// row's share of the CSR values in address order: for each thickness row i_t
+// the 3 rows c, each of len_t segments of 3 len_s values, are contiguous; each
+// warp copies whole segments, issuing all of a segment's shared loads before
+// its global stores. The other CTA on the SM computes while this one stores.
+// ---------------------------------------------------------------------------
+constexpr int kStreamThreads = 512;
+constexpr int kSegUnroll = 6;  // 32 * 6 >= 3 * len_s for rows of at most 512 / 9 neighbours
+
+template <bool MONO, bool CHUNKED>
+__global__ void __launch_bounds__(kStreamThreads, 2) kc_stream(KcArgs a) {
+  extern __shared__ double sm[];
+  const int64_t is = blockIdx.x;
+  const int ix = (int)(is % a.nx), iy = (int)(is / a.nx);
+  const int lx = a.lenX[ix];
+  const int ls = lx * a.lenY[iy];
+  const int n9 = 9 * ls;
+  const int64_t ls0 = a.LSb[is];
+  const int nthr = blockDim.x, tid = threadIdx.x;
+  double* slices = sm;                                  // ncls x stride (the G row first)
+  double* Qs = sm + (size_t)a.ncls * a.slice_stride;    // nst x 4, terms sorted by configuration
+  int* tcls = reinterpret_cast<int*>(Qs + (size_t)a.nst * 4);
+  int* tfirst = tcls + a.nst;
+  // phase 0: the row's G blocks into slices[0 .. 9 ls); Q, class and first-term flag of every term
+  for (int item = tid; item < n9; item += nthr) {
+    const int ks = item / 9, ab = item % 9;
+    const int jx = a.loX[ix] + ks % lx, jy = a.loY[iy] + ks / lx;
+    const int ex0 = max(a.eloX[ix], a.eloX[jx]), ex1 = min(a.ehiX[ix], a.ehiX[jx]);
+    const int ey0 = max(a.eloY[iy], a.eloY[jy]), ey1 = min(a.ehiY[iy], a.ehiY[jy]);
+    const int ba = (ab % 3) * 3 + ab / 3;
+    double acc = 0.0;
+    for (int ey = ey0; ey <= ey1; ++ey) {
+      const int fy = a.firstV[ey];
+      for (int ex = ex0; ex <= ex1; ++ex) {
+        const int fx = a.firstU[ex];
+        const int li = (iy - fy) * a.nlx + (ix - fx), lj = (jy - fy) * a.nlx + (jx - fx);
+        const size_t e9 = ((size_t)ey * a.nel_u + ex) * 9;
+        if (li <= lj)
+          acc += a.EG[(e9 + ab) * a.npl + upper_pair(li, lj, a.nls)];
+        else
+          acc += a.EG[(e9 + ba) * a.npl + upper_pair(lj, li, a.nls)];
+      }
+    }
+    slices[item] = acc;
+  }
+  for (int k = tid; k < a.nst; k += nthr) {
+    tcls[k] = a.st_cls[k];
+    tfirst[k] = a.st_first[k];
+  }
+  for (int m = 0; m < a.ncfg; ++m)
+    for (int k = a.st_begin[m] + tid; k < a.st_begin[m + 1]; k += nthr) {
+      const double* src = a.q + ((size_t)a.st_rep[k] * a.ncfg + m) * 4;
+      Qs[4 * k + 0] = src[0];
+      Qs[4 * k + 1] = src[1];
+      Qs[4 * k + 2] = src[2];
+      Qs[4 * k + 3] = src[3];
+    }
+  __syncthreads();
+  const int item = tid;
+  const bool active = item < n9;
+  int c = 0, ks = 0, d = 0;
+  double g[9];
+  if (active) {
+    c = item / (3 * ls);
+    const int rem = item % (3 * ls);
+    ks = rem / 3;
+    d = rem % 3;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) g[k] = slices[ks * 9 + k];
+  }
+  __syncthreads();  // the G row is in registers; its space is reused by the slices
+  if (active) {
+    const int cd = c * 3 + d;
+    const bool block_type = ((c == 2) == (d == 2));
+    const int offa = block_type ? 0 : 1, offb = block_type ? 3 : 2;
+    for (int m = 0; m < a.ncfg; ++m) {
+      const double* E = a.cfgE + (size_t)m * 81 + cd * 9;
+      double pa, pb, p11 = 0.0, p12 = 0.0, p21 = 0.0, p22 = 0.0;
+      if (MONO) {
+        if (block_type) {
+          pa = E[0] * g[0] + E[1] * g[1] + E[3] * g[3] + E[4] * g[4];
+          pb = E[8] * g[8];
+        } else {
+          pa = E[2] * g[2] + E[5] * g[5];
+          pb = E[6] * g[6] + E[7] * g[7];
+        }
+      } else {
+        p11 = E[0] * g[0] + E[1] * g[1] + E[3] * g[3] + E[4] * g[4];
+        p12 = E[2] * g[2] + E[5] * g[5];
+        p21 = E[6] * g[6] + E[7] * g[7];
+        p22 = E[8] * g[8];
+        pa = pb = 0.0;
+      }
+      const int k1 = a.st_begin[m + 1];
+      for (int t = a.st_begin[m]; t < k1; ++t) {
+        const double v = MONO ? Qs[4 * t + offa] * pa + Qs[4 * t + offb] * pb
+                              : Qs[4 * t] * p11 + Qs[4 * t + 1] * p12 + Qs[4 * t + 2] * p21 + Qs[4 * t + 3] * p22;
+        double* dst = slices + (size_t)tcls[t] * a.slice_stride + item;
+        *dst = tfirst[t] ? v : *dst + v;
+      }
+    }
+  }
+  __syncthreads();
+  // phase 2: segments s = (i_t, c, k_t) in address order, one warp per segment
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
+  const int seg_len = 3 * ls;
+  const int64_t s_begin = CHUNKED ? 3 * a.LTb[a.it_lo] : 0;
+  const int64_t s_end = CHUNKED ? 3 * a.LTb[a.it_hi] : 3 * a.LTb[a.nt];
+  int it = CHUNKED ? a.it_lo : 0;
+  for (int64_t s = s_begin + warp; s < s_end; s += nwarps) {
+    while (s >= 3 * a.LTb[it + 1]) ++it;
+    const int64_t lt0 = a.LTb[it];
+    const int lt = (int)(a.LTb[it + 1] - lt0);
+    const int rel = (int)(s - 3 * lt0);
+    const int cc = rel / lt, kt = rel % lt;
+    const int u = a.pair_cls[lt0 + kt];
+    const double* src = slices + (size_t)u * a.slice_stride + cc * seg_len;
+    double* dst = a.values + (9 * lt0 * a.nnz_s + (int64_t)lt * (9 * ls0 + 3 * (int64_t)cc * ls) +
+                              (int64_t)kt * seg_len - a.out_offset);
+    double v[kSegUnroll];
+#pragma unroll
+    for (int j = 0; j < kSegUnroll; ++j) v[j] = (lane + 32 * j < seg_len) ? src[lane + 32 * j] : 0.0;
+#pragma unroll
+    for (int j = 0; j < kSegUnroll; ++j)
+      if (lane + 32 * j < seg_len) dst[lane + 32 * j] = v[j];
   }
 }
 
@@ -824,6 +958,11 @@ static lam_status ensure_device(Plan& P) {
     UP(L, D->occ_k, P.occ_k);
     UP(L, D->occ_it, P.occ_it);
     UP(L, D->cfgE, P.cfgE);
+    UP(L, D->pair_cls, P.pair_cls);
+    UP(L, D->st_begin, P.st_begin);
+    UP(L, D->st_cls, P.st_cls);
+    UP(L, D->st_rep, P.st_rep);
+    UP(L, D->st_first, P.st_first);
     if ((st = alloc_dev(L, &D->q, (size_t)P.nnz_t * P.cfg_mat.size() * 4)) != LAM_OK) {
       free_device(P);
       return st;
@@ -912,7 +1051,27 @@ static KcArgs kc_args(const Plan& P, double* values) {
   k.it_hi = (int)P.nt;
   k.out_offset = 0;
   k.values = values;
+  k.LTb = D.LTb;
+  k.pair_cls = D.pair_cls;
+  k.st_begin = D.st_begin;
+  k.st_cls = D.st_cls;
+  k.st_rep = D.st_rep;
+  k.nst = (int)P.st_cls.size();
+  k.slice_stride = kcs_stride(P);
+  k.nt = (int)P.nt;
+  k.st_first = D.st_first;
   return k;
+}
+
+template <bool MONO, bool CHUNKED>
+static lam_status launch_kcs(const Plan& P, const KcArgs& k, cudaStream_t s) {
+  const size_t smem = kcs_smem(P);
+  LAM_CUDA(cudaFuncSetAttribute(kc_stream<MONO, CHUNKED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaEvent_t ev = prof_begin(const_cast<Plan&>(P), s);
+  kc_stream<MONO, CHUNKED><<<(unsigned)P.ns, kStreamThreads, smem, s>>>(k);
+  LAM_CUDA(cudaGetLastError());
+  prof_end(const_cast<Plan&>(P), LAM_KERNEL_COMBINE, 1, s, ev);
+  return LAM_OK;
 }
 
 template <bool MONO, bool CHUNKED>
@@ -925,6 +1084,14 @@ static lam_status launch_kc(const Plan& P, const KcArgs& k, cudaStream_t s) {
   LAM_CUDA(cudaGetLastError());
   prof_end(const_cast<Plan&>(P), LAM_KERNEL_COMBINE, 1, s, ev);
   return LAM_OK;
+}
+
+// Combine into `values`: streaming form when a row's slices fit, class-major form otherwise.
+template <bool CHUNKED>
+static lam_status launch_combine(const Plan& P, const KcArgs& k, cudaStream_t s) {
+  if (use_stream(P))
+    return P.monoclinic ? launch_kcs<true, CHUNKED>(P, k, s) : launch_kcs<false, CHUNKED>(P, k, s);
+  return P.monoclinic ? launch_kc<true, CHUNKED>(P, k, s) : launch_kc<false, CHUNKED>(P, k, s);
 }
 
 // K-b then K-a (all colours): leaves Q and G in the plan's workspace.
@@ -1036,7 +1203,7 @@ lam_status lam_assemble_split(lam_plan* plan, double* d_values, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if ((st = lam::split_integrals(P, s)) != LAM_OK) return st;
   lam::KcArgs k = lam::kc_args(P, d_values);
-  return P.monoclinic ? lam::launch_kc<true, false>(P, k, s) : lam::launch_kc<false, false>(P, k, s);
+  return lam::launch_combine<false>(P, k, s);
 }
 
 lam_status lam_assemble_split_host(lam_plan* plan, double* h_values, void* stream) {
@@ -1090,7 +1257,7 @@ lam_status lam_assemble_split_host(lam_plan* plan, double* h_values, void* strea
     k.it_lo = (int)r0;
     k.it_hi = (int)r1;
     k.out_offset = off;
-    st = P.monoclinic ? lam::launch_kc<true, true>(P, k, s) : lam::launch_kc<false, true>(P, k, s);
+    st = lam::launch_combine<true>(P, k, s);
     if (st != LAM_OK) return st;
     LAM_CUDA(cudaEventRecord(D.ev_done[slot], s));
     LAM_CUDA(cudaStreamWaitEvent(D.copy_stream, D.ev_done[slot], 0));

@@ -457,6 +457,30 @@ static lam_status build_classes(Plan& P) {
   }
   P.ncls = (int)reps.size();
   P.cls_rep = reps;
+  P.pair_cls = cls_of;
+  // the same terms, grouped by configuration
+  P.st_begin.assign(nc + 1, 0);
+  P.st_cls.clear();
+  P.st_rep.clear();
+  P.st_cfg.clear();
+  for (int m = 0; m < nc; ++m) {
+    P.st_begin[m] = (int)P.st_cls.size();
+    for (int u = 0; u < (int)reps.size(); ++u)
+      for (int m2 : terms[reps[u]])
+        if (m2 == m) {
+          P.st_cls.push_back(u);
+          P.st_rep.push_back(reps[u]);
+          P.st_cfg.push_back(m);
+        }
+  }
+  P.st_begin[nc] = (int)P.st_cls.size();
+  P.st_first.assign(P.st_cls.size(), 0);
+  std::vector<char> seen(P.ncls, 0);
+  for (size_t k = 0; k < P.st_cls.size(); ++k)
+    if (!seen[P.st_cls[k]]) {
+      seen[P.st_cls[k]] = 1;
+      P.st_first[k] = 1;
+    }
   P.cls_term_begin.assign(P.ncls + 1, 0);
   P.cls_terms.clear();
   for (int u = 0; u < P.ncls; ++u) {
@@ -685,6 +709,7 @@ lam_status lam_plan_get_info(const lam_plan* plan, lam_plan_info* info) {
   info->n_classes = P.ncls;
   info->monoclinic = P.monoclinic ? 1 : 0;
   info->n_pieces = (int32_t)P.pieces.size();
+  info->combine_streaming = lam::use_stream(P) ? 1 : 0;
   return LAM_OK;
 }
 

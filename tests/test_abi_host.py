@@ -103,6 +103,17 @@ def test_configurations_and_classes(lam):
     assert lam.Plan.from_laminate(L).info["monoclinic"] == 0
 
 
+def test_combine_variant_selection(lam):
+    assert lam.Plan.from_laminate(W.curved_plate()).info["combine_streaming"] == 1
+    assert lam.Plan.from_laminate(W.cross_ply_plate()).info["combine_streaming"] == 1
+    quartic = W.laminate("p4", W.BSPLINE, 4, 8, [0, 45], 0.02, n_el_y=8, thickness_degree=1)
+    assert lam.Plan.from_laminate(quartic).info["combine_streaming"] == 0
+    rng = np.random.default_rng(5)
+    uneven = W.laminate("u", W.BSPLINE, 1, 3, [0.0] * 70, rng.uniform(0.0005, 0.002, 70), thickness_degree=1)
+    p = lam.Plan.from_laminate(uneven)
+    assert p.info["n_classes"] > 150 and p.info["combine_streaming"] == 0  # slices beyond shared memory
+
+
 def test_update_rebuilds_configurations(lam):
     L = W.cross_ply_plate()
     p = lam.Plan.from_laminate(L)

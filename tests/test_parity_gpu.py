@@ -70,6 +70,13 @@ SMALL = {
     "single_element_single_ply": lambda: W.laminate("min", W.BSPLINE, 1, 1, [30.0], 0.5, thickness_degree=1),
     "more_gauss_points": lambda: W.laminate("nq", W.BSPLINE, 2, 3, [0, 90], 0.05, mapping=W.curved_map(),
                                             nq=(5, 4, 4)),
+    # rows of 81 in-plane neighbours (729 values > 512 threads): the class-major combine
+    "quartic_inplane": lambda: W.laminate("p4", W.BSPLINE, 4, 8, [0, 45], 0.02, mapping=W.curved_map(),
+                                          n_el_y=8, thickness_degree=1),
+    # uneven plies: hundreds of distinct Q vectors, the class-major combine
+    "uneven_plies_many_classes": lambda: W.laminate(
+        "uneven", W.BSPLINE, 1, 3, list(np.random.default_rng(4).choice([0.0, 45.0, -45.0, 90.0], 70)),
+        np.random.default_rng(5).uniform(0.0005, 0.002, 70), mapping=W.curved_map(), thickness_degree=1),
 }
 
 

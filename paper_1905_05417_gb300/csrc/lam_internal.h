@@ -73,6 +73,8 @@ struct Plan {
   std::vector<int64_t> LTb;      // prefix of len_t, size nt + 1
   std::vector<int> tp_row, tp_col;       // thickness pair -> (i_t, j_t)
   std::vector<int> tp_e0, tp_e1;         // shared thickness elements of the pair
+  std::vector<int64_t> tp_A;             // 9 * LTb[i_t] * nnz_s: CSR start of thickness row i_t's slab
+  std::vector<int> tp_lt, tp_k;          // len_t(i_t) and k_t of the pair
 
   // combine classes: thickness pairs with equal Q vectors
   int ncls = 0;

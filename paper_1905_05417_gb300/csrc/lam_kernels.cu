@@ -45,6 +45,8 @@ struct Device {
   double *tabT = nullptr, *wT = nullptr;
   int *piece_begin = nullptr, *piece_cfg = nullptr;
   int *tp_row = nullptr, *tp_col = nullptr, *tp_e0 = nullptr, *tp_e1 = nullptr;
+  int64_t* tp_A = nullptr;
+  int *tp_lt = nullptr, *tp_k = nullptr;
   // classes
   int *cls_term_begin = nullptr, *cls_terms = nullptr, *cls_occ_begin = nullptr, *term_rep = nullptr;
   int64_t* occ_A = nullptr;
@@ -525,6 +527,8 @@ struct KcArgs {
   const int* pair_cls;
   const int *st_begin, *st_cls, *st_rep, *st_first;
   int nst, slice_stride, nt;
+  const int64_t* tp_A;
+  const int *tp_lt, *tp_k;
 };
 
 __device__ __forceinline__ int upper_pair(int a, int b, int n) { return a * n - a * (a - 1) / 2 + (b - a); }
@@ -651,8 +655,9 @@ __global__ void __launch_bounds__(1024, 2) kc_combine(KcArgs a) {
 // slice_u = sum Q P for every class u in shared memory. Phase 2 writes the
 // row's share of the CSR values in address order: for each thickness row i_t
 // the 3 rows c, each of len_t segments of 3 len_s values, are contiguous; each
-// warp copies whole segments, issuing all of a segment's shared loads before
-// its global stores. The other CTA on the SM computes while this one stores.
+// warp copies the three segments of one thickness pair, issuing all of a
+// segment's shared loads before its global stores. The other CTA on the SM
+// computes while this one stores.
 // ---------------------------------------------------------------------------
 constexpr int kStreamThreads = 512;
 constexpr int kSegUnroll = 6;  // 32 * 6 >= 3 * len_s for rows of at most 512 / 9 neighbours
@@ -751,28 +756,29 @@ __global__ void __launch_bounds__(kStreamThreads, 2) kc_stream(KcArgs a) {
     }
   }
   __syncthreads();
-  // phase 2: segments s = (i_t, c, k_t) in address order, one warp per segment
+  // phase 2: thickness pairs (i_t, k_t) in address order, one warp per pair.
+  // Row (i_t, i_s, c) holds len_t segments of 3 len_s values; the pair's three
+  // segments (c = 0, 1, 2) sit one row apart. Each copy issues all of its
+  // shared loads before its global stores.
   const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
   const int seg_len = 3 * ls;
-  const int64_t s_begin = CHUNKED ? 3 * a.LTb[a.it_lo] : 0;
-  const int64_t s_end = CHUNKED ? 3 * a.LTb[a.it_hi] : 3 * a.LTb[a.nt];
-  int it = CHUNKED ? a.it_lo : 0;
-  for (int64_t s = s_begin + warp; s < s_end; s += nwarps) {
-    while (s >= 3 * a.LTb[it + 1]) ++it;
-    const int64_t lt0 = a.LTb[it];
-    const int lt = (int)(a.LTb[it + 1] - lt0);
-    const int rel = (int)(s - 3 * lt0);
-    const int cc = rel / lt, kt = rel % lt;
-    const int u = a.pair_cls[lt0 + kt];
-    const double* src = slices + (size_t)u * a.slice_stride + cc * seg_len;
-    double* dst = a.values + (9 * lt0 * a.nnz_s + (int64_t)lt * (9 * ls0 + 3 * (int64_t)cc * ls) +
-                              (int64_t)kt * seg_len - a.out_offset);
-    double v[kSegUnroll];
+  const int64_t p_begin = CHUNKED ? a.LTb[a.it_lo] : 0;
+  const int64_t p_end = CHUNKED ? a.LTb[a.it_hi] : a.LTb[a.nt];
+  for (int64_t pr = p_begin + warp; pr < p_end; pr += nwarps) {
+    const int64_t A = a.tp_A[pr];
+    const int lt = a.tp_lt[pr], kt = a.tp_k[pr], u = a.pair_cls[pr];
+    const double* src = slices + (size_t)u * a.slice_stride;
+    double* dst = a.values + (A + (int64_t)lt * 9 * ls0 + (int64_t)kt * seg_len - a.out_offset);
+    const int64_t row_step = (int64_t)lt * seg_len;
 #pragma unroll
-    for (int j = 0; j < kSegUnroll; ++j) v[j] = (lane + 32 * j < seg_len) ? src[lane + 32 * j] : 0.0;
+    for (int cc = 0; cc < 3; ++cc) {
+      double v[kSegUnroll];
 #pragma unroll
-    for (int j = 0; j < kSegUnroll; ++j)
-      if (lane + 32 * j < seg_len) dst[lane + 32 * j] = v[j];
+      for (int j = 0; j < kSegUnroll; ++j) v[j] = (lane + 32 * j < seg_len) ? src[cc * seg_len + lane + 32 * j] : 0.0;
+#pragma unroll
+      for (int j = 0; j < kSegUnroll; ++j)
+        if (lane + 32 * j < seg_len) dst[cc * row_step + lane + 32 * j] = v[j];
+    }
   }
 }
 
@@ -928,6 +934,9 @@ static lam_status ensure_device(Plan& P) {
     UP(L, D->tp_col, P.tp_col);
     UP(L, D->tp_e0, P.tp_e0);
     UP(L, D->tp_e1, P.tp_e1);
+    UP(L, D->tp_A, P.tp_A);
+    UP(L, D->tp_lt, P.tp_lt);
+    UP(L, D->tp_k, P.tp_k);
     UP(L, D->col3_elem, P.col3_elem);
     UP(L, D->eloX, P.u.elo);
     UP(L, D->ehiX, P.u.ehi);
@@ -1011,7 +1020,7 @@ static InplaneArgs inplane_args(const Plan& P) {
 
 static KcArgs kc_args(const Plan& P, double* values) {
   const Device& D = *P.dev;
-  KcArgs k;
+  KcArgs k{};
   k.ns = P.ns;
   k.nnz_s = P.nnz_s;
   k.nx = P.u.n;
@@ -1060,6 +1069,9 @@ static KcArgs kc_args(const Plan& P, double* values) {
   k.slice_stride = kcs_stride(P);
   k.nt = (int)P.nt;
   k.st_first = D.st_first;
+  k.tp_A = D.tp_A;
+  k.tp_lt = D.tp_lt;
+  k.tp_k = D.tp_k;
   return k;
 }
 
@@ -1097,7 +1109,7 @@ static lam_status launch_combine(const Plan& P, const KcArgs& k, cudaStream_t s)
 // K-b then K-a (all colours): leaves Q and G in the plan's workspace.
 static lam_status split_integrals(Plan& P, cudaStream_t s) {
   Device& D = *P.dev;
-  KbArgs kb;
+  KbArgs kb{};
   kb.npairs = P.nnz_t;
   kb.ncfg = (int)P.cfg_mat.size();
   kb.nqt = P.nqt;
@@ -1116,7 +1128,7 @@ static lam_status split_integrals(Plan& P, cudaStream_t s) {
   kb_thickness<<<(unsigned)((P.nnz_t + 127) / 128), 128, 0, s>>>(kb);
   LAM_CUDA(cudaGetLastError());
   prof_end(P, LAM_KERNEL_THICKNESS, 1, s, ev);
-  KaLocalArgs ka;
+  KaLocalArgs ka{};
   ka.ip = inplane_args(P);
   ka.nel = P.u.nel * P.v.nel;
   ka.EG = D.EG;
@@ -1283,7 +1295,7 @@ lam_status lam_assemble_standard(lam_plan* plan, double* d_values, void* stream)
   lam::Device& D = *P.dev;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   LAM_CUDA(cudaMemsetAsync(d_values, 0, (size_t)P.nnz * sizeof(double), s));
-  lam::KdArgs k;
+  lam::KdArgs k{};
   k.ip = lam::inplane_args(P);
   k.nel_v = P.v.nel;
   k.nqt = P.nqt;
@@ -1520,7 +1532,7 @@ extern "C" lam_status lam_assemble_split_noalloc(const lam_plan* plan, double* d
   lam::noalloc_term_rep<<<(P.ncls + 127) / 128, 128, 0, s>>>(cls_term_begin, cls_rep, P.ncls, term_rep);
   LAM_CUDA(cudaGetLastError());
   // K-b
-  lam::KbArgs kb;
+  lam::KbArgs kb{};
   kb.npairs = P.nnz_t;
   kb.ncfg = ncfg;
   kb.nqt = P.nqt;
@@ -1539,7 +1551,7 @@ extern "C" lam_status lam_assemble_split_noalloc(const lam_plan* plan, double* d
   LAM_CUDA(cudaGetLastError());
   // K-a: G accumulates, so it starts at zero
   LAM_CUDA(cudaMemsetAsync(G, 0, (size_t)P.nnz_s * 9 * sizeof(double), s));
-  lam::KaArgs ka;
+  lam::KaArgs ka{};
   ka.ip.nx = P.u.n;
   ka.ip.nel_u = P.u.nel;
   ka.ip.pu = P.u.p;
@@ -1571,7 +1583,7 @@ extern "C" lam_status lam_assemble_split_noalloc(const lam_plan* plan, double* d
     LAM_CUDA(cudaGetLastError());
   }
   // K-c
-  lam::KcArgs k;
+  lam::KcArgs k{};
   k.ns = P.ns;
   k.nnz_s = P.nnz_s;
   k.nx = P.u.n;

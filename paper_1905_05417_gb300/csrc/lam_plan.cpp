@@ -648,6 +648,15 @@ lam_status build_plan(Plan& P, const lam_inplane* inplane, const lam_basis1d* th
   }
   P.nnz_t = P.LTb[P.nt];
   P.nnz = 9 * P.nnz_s * P.nnz_t;
+  P.tp_A.resize(P.nnz_t);
+  P.tp_lt.resize(P.nnz_t);
+  P.tp_k.resize(P.nnz_t);
+  for (int64_t pr = 0; pr < P.nnz_t; ++pr) {
+    const int it = P.tp_row[pr];
+    P.tp_A[pr] = 9 * P.LTb[it] * P.nnz_s;
+    P.tp_lt[pr] = P.t.len[it];
+    P.tp_k[pr] = P.tp_col[pr] - P.t.lo[it];
+  }
   if ((st = build_classes(P)) != LAM_OK) return st;
   build_colourings(P);
   return LAM_OK;

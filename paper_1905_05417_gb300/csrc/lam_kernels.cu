@@ -454,6 +454,23 @@ struct KaLocalArgs {
   double* EG;
 };
 
+// a * b added to the double-float accumulator (sh, sl), with a = ah + al and
+// b = bh + bl split into float pairs. The product is taken to about 2^-48
+// relative (the rounding error of ah * bh by FMA, plus the two cross terms;
+// al * bl is below that), the sum by Knuth's two-sum. Intrinsics keep the
+// compiler from contracting the error-free transformations.
+__device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, float& sh, float& sl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+  const float t = __fadd_rn(sh, p);
+  const float z = __fsub_rn(t, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(p, z));
+  sl = __fadd_rn(sl, __fadd_rn(err, e));
+  sh = t;
+}
+
 __global__ void __launch_bounds__(256) ka_local(KaLocalArgs a) {
   extern __shared__ double sm[];
   const InplaneArgs& ip = a.ip;
@@ -464,6 +481,27 @@ __global__ void __launch_bounds__(256) ka_local(KaLocalArgs a) {
   const int e = blockIdx.x;
   const int ex = e % ip.nel_u, ey = e / ip.nel_u;
   inplane_points(ip, ex, ey, phi, phiw, qd);
+  // FP64 point values -> float pairs (hi0 hi1 hi2 lo0 lo1 lo2), in place
+  float* phf = reinterpret_cast<float*>(phi);
+  float* pwf = reinterpret_cast<float*>(phiw);
+  for (int t = threadIdx.x; t < nqs * nls; t += blockDim.x) {
+    double v[3], w[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      v[k] = phi[(size_t)t * 3 + k];
+      w[k] = phiw[(size_t)t * 3 + k];
+    }
+    // each item's 6 floats overwrite exactly its own 3 doubles (no other item's)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float vh = __double2float_rn(v[k]), wh = __double2float_rn(w[k]);
+      phf[(size_t)t * 6 + k] = vh;
+      phf[(size_t)t * 6 + 3 + k] = __double2float_rn(v[k] - (double)vh);
+      pwf[(size_t)t * 6 + k] = wh;
+      pwf[(size_t)t * 6 + 3 + k] = __double2float_rn(w[k] - (double)wh);
+    }
+  }
+  __syncthreads();
   const int npl = nls * (nls + 1) / 2;
   double* out = a.EG + (size_t)e * 9 * npl;
   for (int t = threadIdx.x; t < npl; t += blockDim.x) {
@@ -473,25 +511,27 @@ __global__ void __launch_bounds__(256) ka_local(KaLocalArgs a) {
       ++li;
     }
     const int lj = li + rem;
-    double acc[9];
+    float sh[9], sl[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) acc[k] = 0.0;
+    for (int k = 0; k < 9; ++k) sh[k] = sl[k] = 0.0f;
     for (int q = 0; q < nqs; ++q) {
-      const double* A = phiw + ((size_t)q * nls + li) * 3;
-      const double* B = phi + ((size_t)q * nls + lj) * 3;
-      const double a0 = A[0], a1 = A[1], a2 = A[2], b0 = B[0], b1 = B[1], b2 = B[2];
-      acc[0] += a0 * b0;
-      acc[1] += a0 * b1;
-      acc[2] += a0 * b2;
-      acc[3] += a1 * b0;
-      acc[4] += a1 * b1;
-      acc[5] += a1 * b2;
-      acc[6] += a2 * b0;
-      acc[7] += a2 * b1;
-      acc[8] += a2 * b2;
+      const float* A = pwf + ((size_t)q * nls + li) * 6;
+      const float* B = phf + ((size_t)q * nls + lj) * 6;
+      float ah[3], al[3], bh[3], bl[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        ah[k] = A[k];
+        al[k] = A[3 + k];
+        bh[k] = B[k];
+        bl[k] = B[3 + k];
+      }
+#pragma unroll
+      for (int x = 0; x < 3; ++x)
+#pragma unroll
+        for (int y = 0; y < 3; ++y) df_mac(ah[x], al[x], bh[y], bl[y], sh[x * 3 + y], sl[x * 3 + y]);
     }
 #pragma unroll
-    for (int k = 0; k < 9; ++k) out[(size_t)k * npl + t] = acc[k];
+    for (int k = 0; k < 9; ++k) out[(size_t)k * npl + t] = (double)sh[k] + (double)sl[k];
   }
 }
 

@@ -62,6 +62,10 @@ def configure(L):
         for f in (L.ora_assemble, L.ora_assemble_split):
             f.argtypes = [ctypes.POINTER(_Problem), _I64, _I32, _D]
         L.ora_pattern.argtypes = [ctypes.POINTER(_Problem), _I64, _I32]
+        L.ora_adjoint_D.argtypes = [ctypes.POINTER(_Problem), _I64, _I32, _D, _D]
+        L.ora_adjoint.argtypes = [ctypes.POINTER(_Problem), _I64, _I32, _D, _D, _D, _D]
+        L.ora_rotated_D_dtheta.argtypes = [_D, ctypes.c_double, _D]
+        L.ora_rotated_D_dtheta.restype = None
         L.ora_block.argtypes = [ctypes.POINTER(_Problem), ctypes.c_int64, ctypes.c_int64, _D]
         L.ora_element_stiffness.argtypes = [ctypes.POINTER(_Problem), ctypes.c_int32, ctypes.c_int32,
                                             ctypes.c_int32, _D]
@@ -183,6 +187,53 @@ def assemble(lam):
 def assemble_split(lam):
     """Split assembly with one P per ply (small problems only)."""
     return _assemble(lam, lib().ora_assemble_split)
+
+
+def adjoint_D(lam, row_ptr, col, gbar) -> np.ndarray:
+    """dL/dD_l (n_plies x 6 x 6) for L = sum(gbar * K) on the oracle's pattern."""
+    p = Problem(lam)
+    out = np.zeros(36 * len(lam.ply_thickness))
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    g = np.ascontiguousarray(gbar, dtype=np.float64)
+    if lib().ora_adjoint_D(p.ref(), _ptr(rp, _I64), _ptr(cl, _I32), _ptr(g), _ptr(out)) != 0:
+        raise ValueError("oracle adjoint failed")
+    return out.reshape(-1, 6, 6)
+
+
+def adjoint(lam, row_ptr, col, gbar):
+    """(dL/dC: n_materials x 21, dL/dtheta: n_plies, dL/dD: n_plies x 6 x 6)
+    for L = sum(gbar * K) on the oracle's pattern."""
+    p = Problem(lam)
+    n_pl, n_mat = len(lam.ply_thickness), lam.C21.shape[0]
+    dD = np.zeros(36 * n_pl)
+    dC = np.zeros(21 * n_mat)
+    dth = np.zeros(n_pl)
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    g = np.ascontiguousarray(gbar, dtype=np.float64)
+    if lib().ora_adjoint(p.ref(), _ptr(rp, _I64), _ptr(cl, _I32), _ptr(g), _ptr(dD), _ptr(dC), _ptr(dth)) != 0:
+        raise ValueError("oracle adjoint failed")
+    return dC.reshape(n_mat, 21), dth, dD.reshape(n_pl, 6, 6)
+
+
+def lowrank_cotangent(row_ptr, col, u, v) -> np.ndarray:
+    """Values of sum_r u_r v_r^T on the pattern (row-major CSR order): the
+    cotangent of L = sum_r u_r^T K v_r."""
+    u = np.atleast_2d(np.asarray(u, dtype=np.float64))
+    v = np.atleast_2d(np.asarray(v, dtype=np.float64))
+    rows = np.repeat(np.arange(len(row_ptr) - 1), np.diff(row_ptr))
+    out = np.zeros(len(col))
+    for r in range(u.shape[0]):
+        out += u[r][rows] * v[r][col]
+    return out
+
+
+def rotated_D_dtheta(C21, theta: float) -> np.ndarray:
+    out = np.zeros(36)
+    c = np.ascontiguousarray(C21, dtype=np.float64)
+    lib().ora_rotated_D_dtheta(_ptr(c), float(theta), _ptr(out))
+    return out.reshape(6, 6)
 
 
 def block(lam, i: int, j: int, problem: Problem | None = None) -> np.ndarray:

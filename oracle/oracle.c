@@ -801,3 +801,171 @@ int ora_assemble_split(const ora_problem* pr, int64_t* row_ptr, int32_t* col, do
   pattern_free(&P);
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Gradient of L = sum_{stored (r, s)} gbar_rs K_rs with respect to the     */
+/* Voigt matrix D_l of every ply (all 36 entries taken as independent).     */
+/* K is linear in D_l (Eq. Km_0), so                                        */
+/*   dL/dD_l[I][J] = sum_{elements, points in ply l} w |DF|                  */
+/*                   sum_{i,j,c,d} gbar_{3i+c, 3j+d} B^i[I][c] B^j[J][d].    */
+/* out: n_plies x 36, row-major [l][I*6+J].                                  */
+/* ------------------------------------------------------------------------ */
+int ora_adjoint_D(const ora_problem* pr, const int64_t* row_ptr, const int32_t* col, const double* gbar,
+                  double* out) {
+  if (check_problem(pr) < 0) return -1;
+  pattern P;
+  if (pattern_build(pr, &P) < 0) return -1;
+  int nlx = pr->u.degree + 1, nly = pr->v.degree + 1, nlt = pr->t.degree + 1;
+  int nls = nlx * nly, nl = nls * nlt;
+  int nx = P.su.n;
+  int64_t ns = (int64_t)P.su.n * P.sv.n;
+  int nqu = nq_or_default(pr->nq_u, pr->u.degree), nqv = nq_or_default(pr->nq_v, pr->v.degree);
+  int nqt = nq_or_default(pr->nq_t, pr->t.degree);
+  double xu[64], wu[64], xv[64], wv[64], xt[64], wt[64];
+  ora_gauss(nqu, xu, wu);
+  ora_gauss(nqv, xv, wv);
+  ora_gauss(nqt, xt, wt);
+  memset(out, 0, sizeof(double) * 36 * pr->n_plies);
+  double* gl = malloc(sizeof(double) * (size_t)nl * nl * 9);   /* local cotangent blocks */
+  double (*B)[6][3] = malloc(sizeof(double) * 18 * nl);
+  int64_t* gidx = malloc(sizeof(int64_t) * nl);
+  if (!gl || !B || !gidx) { free(gl); free(B); free(gidx); pattern_free(&P); return -1; }
+  inplane_point ip;
+  for (int et = 0; et < P.st.nel; ++et)
+    for (int ey = 0; ey < P.sv.nel; ++ey)
+      for (int ex = 0; ex < P.su.nel; ++ex) {
+        double ua, ub, va, vb, ta, tb;
+        int fx, fy, ft;
+        element_of(&pr->u, ex, &ua, &ub, &fx);
+        element_of(&pr->v, ey, &va, &vb, &fy);
+        element_of(&pr->t, et, &ta, &tb, &ft);
+        for (int a = 0; a < nl; ++a) {
+          int lt = a / nls, ls = a % nls;
+          gidx[a] = (int64_t)(ft + lt) * ns + (int64_t)(fy + ls / nlx) * nx + (fx + ls % nlx);
+        }
+        /* the cotangent restricted to this element's function pairs, read from the CSR */
+        for (int a = 0; a < nl; ++a)
+          for (int b = 0; b < nl; ++b) {
+            int64_t k = find_in_row(&P, gidx[a], gidx[b]);
+            int64_t len = P.bptr[gidx[a] + 1] - P.bptr[gidx[a]];
+            for (int c = 0; c < 3; ++c) {
+              int64_t r = 3 * gidx[a] + c;
+              for (int d = 0; d < 3; ++d) gl[((size_t)a * nl + b) * 9 + c * 3 + d] = gbar[row_ptr[r] + 3 * k + d];
+              (void)len;
+            }
+          }
+        double z0[512], z1[512];
+        int ply[512];
+        int npieces = ply_pieces(pr, et, z0, z1, ply, 512);
+        for (int pc = 0; pc < npieces; ++pc) {
+          double* o = out + 36 * ply[pc];
+          for (int qa = 0; qa < nqu; ++qa)
+            for (int qb = 0; qb < nqv; ++qb) {
+              double xi = ua + 0.5 * (ub - ua) * (1.0 + xu[qa]);
+              double eta = va + 0.5 * (vb - va) * (1.0 + xv[qb]);
+              eval_inplane(pr, ex, ey, xi, eta, &ip);
+              for (int g = 0; g < nqt; ++g) {
+                double z = z0[pc] + 0.5 * (z1[pc] - z0[pc]) * (1.0 + xt[g]);
+                double T[8], dT[8];
+                int f2;
+                ora_basis1d_eval(&pr->t, et, z, T, dT, &f2);
+                double w = wu[qa] * 0.5 * (ub - ua) * wv[qb] * 0.5 * (vb - va) * wt[g] * 0.5 * (z1[pc] - z0[pc]) * ip.detJ;
+                for (int lt = 0; lt < nlt; ++lt)
+                  for (int ls = 0; ls < nls; ++ls) {
+                    double grad[3] = {ip.gx[ls] * T[lt], ip.gy[ls] * T[lt], ip.R[ls] * dT[lt]};
+                    strain_matrix(grad, B[lt * nls + ls]);
+                  }
+                for (int a = 0; a < nl; ++a)
+                  for (int b = 0; b < nl; ++b) {
+                    const double* gb = gl + ((size_t)a * nl + b) * 9;
+                    for (int c = 0; c < 3; ++c)
+                      for (int d = 0; d < 3; ++d) {
+                        double gv = gb[c * 3 + d];
+                        if (gv == 0.0) continue;
+                        for (int I = 0; I < 6; ++I) {
+                          double bi = B[a][I][c];
+                          if (bi == 0.0) continue;
+                          for (int J = 0; J < 6; ++J) o[I * 6 + J] += w * gv * bi * B[b][J][d];
+                        }
+                      }
+                  }
+              }
+            }
+        }
+      }
+  free(gl);
+  free(B);
+  free(gidx);
+  pattern_free(&P);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* d/dtheta of the rotated Voigt matrix: the product rule applied to the    */
+/* four rotation factors of C'_ijkl = R_ip R_jq R_kr R_ls C_pqrs.          */
+/* ------------------------------------------------------------------------ */
+void ora_rotated_D_dtheta(const double* C21, double theta, double* D36) {
+  double Dm[6][6];
+  int k = 0;
+  for (int I = 0; I < 6; ++I)
+    for (int J = I; J < 6; ++J) {
+      Dm[I][J] = C21[k];
+      Dm[J][I] = C21[k];
+      ++k;
+    }
+  double c = cos(theta), s = sin(theta);
+  double R[3][3] = {{c, -s, 0.0}, {s, c, 0.0}, {0.0, 0.0, 1.0}};
+  double dR[3][3] = {{-s, -c, 0.0}, {c, -s, 0.0}, {0.0, 0.0, 0.0}};
+  static const int pairs[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+  for (int I = 0; I < 6; ++I)
+    for (int J = 0; J < 6; ++J) {
+      int i = pairs[I][0], j = pairs[I][1], kk = pairs[J][0], l = pairs[J][1];
+      double sum = 0.0;
+      for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q)
+          for (int r = 0; r < 3; ++r)
+            for (int t = 0; t < 3; ++t) {
+              double f = dR[i][p] * R[j][q] * R[kk][r] * R[l][t] + R[i][p] * dR[j][q] * R[kk][r] * R[l][t] +
+                         R[i][p] * R[j][q] * dR[kk][r] * R[l][t] + R[i][p] * R[j][q] * R[kk][r] * dR[l][t];
+              sum += f * Dm[voigt(p, q)][voigt(r, t)];
+            }
+      D36[I * 6 + J] = sum;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gradients of L = sum gbar_rs K_rs with respect to the material constants */
+/* (21 per material, the upper triangle of C in the material frame) and to  */
+/* every ply angle. K is linear in each D_l, and D_l = rot(C_m, theta_l) is  */
+/* linear in C_m, so                                                        */
+/*   dL/dC_m[k]   = sum_{plies l of m} < dL/dD_l, rot(e_k, theta_l) >        */
+/*   dL/dtheta_l  = < dL/dD_l, d rot(C_m, theta)/dtheta at theta_l >         */
+/* with <A, B> = sum_IJ A_IJ B_IJ and e_k the k-th unit constant vector.     */
+/* dD may be NULL.                                                          */
+/* ------------------------------------------------------------------------ */
+int ora_adjoint(const ora_problem* pr, const int64_t* row_ptr, const int32_t* col, const double* gbar, double* dD,
+                double* dC, double* dtheta) {
+  double* g = malloc(sizeof(double) * 36 * (pr->n_plies > 0 ? pr->n_plies : 1));
+  if (!g) return -1;
+  if (ora_adjoint_D(pr, row_ptr, col, gbar, g) < 0) { free(g); return -1; }
+  memset(dC, 0, sizeof(double) * 21 * pr->n_materials);
+  for (int l = 0; l < pr->n_plies; ++l) {
+    const int m = pr->ply_material[l];
+    double R[36], e[21];
+    for (int k = 0; k < 21; ++k) {
+      memset(e, 0, sizeof e);
+      e[k] = 1.0;
+      ora_rotated_D(e, pr->ply_angle[l], R);
+      double acc = 0.0;
+      for (int t = 0; t < 36; ++t) acc += g[36 * l + t] * R[t];
+      dC[21 * m + k] += acc;
+    }
+    ora_rotated_D_dtheta(pr->C21 + 21 * m, pr->ply_angle[l], R);
+    double acc = 0.0;
+    for (int t = 0; t < 36; ++t) acc += g[36 * l + t] * R[t];
+    dtheta[l] = acc;
+  }
+  if (dD) memcpy(dD, g, sizeof(double) * 36 * pr->n_plies);
+  free(g);
+  return 0;
+}

@@ -88,6 +88,20 @@ int ora_block(const ora_problem* pr, int64_t i, int64_t j, double* out9);
  * (lt, ly, lx) with lx fastest. Returns nl, or -1 on error. */
 int ora_element_stiffness(const ora_problem* pr, int32_t ex, int32_t ey, int32_t et, double* out);
 
+/* Gradient of L = sum gbar_rs K_rs (gbar on the oracle's CSR pattern) with
+ * respect to every ply's Voigt matrix D_l, all 36 entries independent:
+ * out[l * 36 + I * 6 + J]. */
+int ora_adjoint_D(const ora_problem* pr, const int64_t* row_ptr, const int32_t* col, const double* gbar,
+                  double* out);
+
+/* d/dtheta of ora_rotated_D (product rule over the four rotation factors). */
+void ora_rotated_D_dtheta(const double* C21, double theta, double* D36);
+
+/* dL/dC (n_materials x 21), dL/dtheta (n_plies) and optionally dL/dD
+ * (n_plies x 36, may be NULL) for L = sum gbar * K on the oracle's pattern. */
+int ora_adjoint(const ora_problem* pr, const int64_t* row_ptr, const int32_t* col, const double* gbar, double* dD,
+                double* dC, double* dtheta);
+
 #ifdef __cplusplus
 }
 #endif

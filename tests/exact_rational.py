@@ -209,3 +209,48 @@ def exact_box_blocks(lam, Lx, Ly, C21_exact_per_material, angles_deg, blocks):
                             K[c, d] += D[voigt(c, a), voigt(d, b)] * f
         out[(i, j)] = K
     return out
+
+
+def _dense_1d(basis, lo=None, hi=None):
+    """The four Gram matrices of gram_1d as dense float arrays."""
+    I = gram_1d(basis, lo, hi)
+    n = basis.n_functions
+    out = {}
+    for key, entries in I.items():
+        M = np.zeros((n, n))
+        for (i, j), val in entries.items():
+            M[i, j] = float(val)
+        out[key] = M
+    return out
+
+
+def exact_box_dL_dD(lam, Lx, Ly, gbar_dense):
+    """dL/dD_l (n_plies x 6 x 6, every entry independent) for
+    L = sum gbar[i, c, j, d] K^{ij}_{cd} on an affine box laminate.
+
+    K is linear in D_l with coefficient
+      dK^{ij}_{cd} / dD_l[V(c,a), V(d,b)] = sum over (a, b) of Ix Iy Iz_l,
+    the same exact 1D integrals as exact_box_blocks; the Kronecker product of
+    the three 1D matrices gives the coefficient of every basis pair at once.
+    """
+    Mx = _dense_1d(lam.u)
+    My = _dense_1d(lam.v)
+    z = [Fraction(0)]
+    for h in lam.ply_thickness:
+        z.append(z[-1] + Fraction(float(h)))
+    n_pl = len(lam.ply_thickness)
+    out = np.zeros((n_pl, 6, 6))
+    for l in range(n_pl):
+        Mz = _dense_1d(lam.t, z[l], z[l + 1])
+        for a in range(3):
+            for b in range(3):
+                rx, sx = int(a == 0), int(b == 0)
+                ry, sy = int(a == 1), int(b == 1)
+                rz, sz = int(a == 2), int(b == 2)
+                fx = Mx[(rx, sx)] * float(Fraction(Lx) / Fraction(Lx) ** (rx + sx))
+                fy = My[(ry, sy)] * float(Fraction(Ly) / Fraction(Ly) ** (ry + sy))
+                F = np.kron(Mz[(rz, sz)], np.kron(fy, fx))
+                for c in range(3):
+                    for d in range(3):
+                        out[l, voigt(c, a), voigt(d, b)] += np.sum(gbar_dense[:, c, :, d] * F)
+    return out

@@ -204,6 +204,60 @@ lam_status lam_assemble_split_noalloc(const lam_plan* plan, double* d_values, vo
 lam_status lam_plan_update(lam_plan* plan, const double* ply_angle_rad, int32_t n_plies,
                            const lam_material* materials, int32_t n_materials);
 
+/* Cotangent of a scalar L(K) for lam_adjoint: the gradient of L with respect
+ * to the stored entries of K, given either on the pattern or as a low-rank
+ * product. */
+typedef enum {
+  LAM_COTANGENT_CSR = 0,     /* L = sum over stored (r, s) of values[k(r, s)] * K_rs */
+  LAM_COTANGENT_LOWRANK = 1  /* L = sum_{q < rank} u_q^T K v_q */
+} lam_cotangent_kind;
+
+/* lam_cotangent.flags */
+#define LAM_ADJOINT_FP64 1   /* evaluate every product in FP64 (slower; see lam_adjoint) */
+
+typedef struct {
+  int32_t kind;          /* lam_cotangent_kind */
+  int32_t rank;          /* LOWRANK: number of vector pairs, >= 1 */
+  int32_t flags;         /* 0 or LAM_ADJOINT_FP64 */
+  int32_t reserved;      /* 0 */
+  const double* values;  /* CSR: nnz doubles (device), in the order of lam_pattern */
+  const double* u;       /* LOWRANK: rank x n_dof doubles (device), row-major */
+  const double* v;       /* LOWRANK: rank x n_dof doubles (device), row-major */
+} lam_cotangent;
+
+/* Adjoint of the assembly: gradients of L (see lam_cotangent) with respect to
+ * the material constants and the ply angles. The paper assembles K only; the
+ * gradient follows from its structure: K is linear in every ply's Voigt matrix
+ * D_l (Eq. Km_0), and with the split of Section 3 (Eq. Km_2, Eq. P, Eq. Q)
+ *   dL/dD_l[V(c,a)][V(d,b)] += sum over stored entries of
+ *       gbar^{(i_t i_s c)(j_t j_s d)} * G_ab^{i_s j_s} * Q_{l,ab}^{i_t j_t},
+ * where G_ab = int g_a g_b |DF| (g = (dS/dx, dS/dy, S)) is the in-plane Gram
+ * block and Q_{l,ab} Eq. Q restricted to ply l. Then, with D_l = M C_m M^T
+ * (Eq. D; M the Bond matrix of the ply angle theta_l),
+ *   dL/dC_m  = sum_{plies l of material m} M^T (dL/dD_l) M, folded onto the
+ *              21 constants (an off-diagonal constant takes both entries);
+ *   dL/dtheta_l = < dL/dD_l, M' C_m M^T + M C_m M'^T >.
+ * Outputs (device, caller-owned; any of them may be NULL):
+ *   d_dC      n_materials x 21 doubles, the layout of lam_material.C;
+ *   d_dtheta  n_plies doubles, per radian;
+ *   d_dD      n_plies x 36 doubles, dL/dD_l[I][J] row-major, every entry of
+ *             D_l taken as independent.
+ * Arithmetic: products and sums run in double-float arithmetic on the FP32
+ * pipes (about 2^-44 relative per term) with FP64 partial sums. The whole
+ * gradient is recomputed in FP64 on the same stream when a partial result is
+ * not finite (a cotangent entry beyond float range, an infinity or a NaN) or
+ * when no cotangent entry (low-rank: product of entries) reaches 2^-60 in
+ * magnitude. Entries below 2^-80 next to larger ones contribute with an
+ * absolute error below 2^-100 of their own size. LAM_ADJOINT_FP64 forces the
+ * FP64 evaluation.
+ * Recomputes the in-plane Gram blocks on every call. Workspace: about
+ * 16 * 9 * nnz_inplane + 648 * n_plies * ceil(n_s / 16) bytes, plan-owned.
+ * Errors: LAM_ERR_INVALID_ARG for a NULL plan or cotangent, an unknown kind, a
+ * missing vector or rank < 1; LAM_ERR_UNSUPPORTED when a ply meets more than
+ * 1024 thickness pairs. Asynchronous on `stream`. */
+lam_status lam_adjoint(lam_plan* plan, const lam_cotangent* cotangent, double* d_dC, double* d_dtheta,
+                       double* d_dD, void* stream);
+
 /* Kernel kinds counted by the profiler. */
 typedef enum {
   LAM_KERNEL_PATTERN = 0,   /* kp_row_ptr, kp_col_ind */
@@ -211,7 +265,8 @@ typedef enum {
   LAM_KERNEL_INPLANE = 2,   /* K-a: in-plane Gram blocks (Eq. P without D) */
   LAM_KERNEL_COMBINE = 3,   /* K-c: Eq. Km_2 into the CSR values */
   LAM_KERNEL_STANDARD = 4,  /* K-d: Section 2.4 element quadrature */
-  LAM_KERNEL_KINDS = 5
+  LAM_KERNEL_ADJOINT = 5,   /* lam_adjoint: Gram gather, ply contraction, chain rule */
+  LAM_KERNEL_KINDS = 6
 } lam_kernel_kind;
 
 /* Per-plan profile: device time of every kernel launch, measured with CUDA

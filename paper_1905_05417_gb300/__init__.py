@@ -12,7 +12,8 @@ Method: Antolin (2019), split assembly of K = sum_m sum_ab P_{m,ab} (x) Q_{m,ab}
 Module-level functions mirror the C entry points (``plan_create``,
 ``plan_get_info``, ``pattern``, ``assemble_split``, ``assemble_standard``,
 ``assemble_split_host``, ``plan_update``, ``plan_destroy``, ``last_error``,
-``version``); ``Plan`` wraps them for convenience.
+``version``, ``adjoint``); ``Plan`` wraps them for convenience, and
+``StiffnessFunction`` exposes the assembly and its adjoint to torch.autograd.
 """
 from __future__ import annotations
 
@@ -25,7 +26,7 @@ import numpy as np
 __all__ = [
     "LamError", "Plan", "load", "plan_create", "plan_destroy", "plan_get_info", "pattern", "assemble_split",
     "assemble_standard", "assemble_split_host", "assemble_split_noalloc", "plan_update", "profile_enable", "profile_get", "last_error",
-    "version", "SYMBOLS", "KERNEL_KINDS", "BSPLINE", "LAGRANGE",
+    "version", "adjoint", "StiffnessFunction", "SYMBOLS", "KERNEL_KINDS", "BSPLINE", "LAGRANGE",
 ]
 
 BSPLINE = 0
@@ -36,9 +37,12 @@ LIB_PATH = os.path.join(_HERE, "liblam.so")
 # every symbol include/lam.h declares
 SYMBOLS = ("lam_plan_create", "lam_plan_destroy", "lam_plan_get_info", "lam_pattern", "lam_assemble_split",
            "lam_assemble_standard", "lam_assemble_split_host", "lam_assemble_split_noalloc", "lam_plan_update",
-           "lam_profile_enable",
+           "lam_adjoint", "lam_profile_enable",
            "lam_profile_get", "lam_last_error", "lam_version")
-KERNEL_KINDS = ("pattern", "thickness", "inplane", "combine", "standard")
+KERNEL_KINDS = ("pattern", "thickness", "inplane", "combine", "standard", "adjoint")
+COTANGENT_CSR = 0
+COTANGENT_LOWRANK = 1
+ADJOINT_FP64 = 1
 
 _STATUS = {0: "LAM_OK", 1: "LAM_ERR_INVALID_ARG", 2: "LAM_ERR_UNSUPPORTED", 3: "LAM_ERR_OOM", 4: "LAM_ERR_CUDA",
            5: "LAM_ERR_TIMEOUT"}
@@ -74,8 +78,14 @@ class _Options(ctypes.Structure):
 
 
 class _Profile(ctypes.Structure):
-    _fields_ = [("enabled", ctypes.c_int32), ("launches", ctypes.c_int64 * 5), ("ms", ctypes.c_double * 5),
+    _fields_ = [("enabled", ctypes.c_int32), ("launches", ctypes.c_int64 * 6), ("ms", ctypes.c_double * 6),
                 ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64)]
+
+
+class _Cotangent(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("rank", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("values", ctypes.c_void_p), ("u", ctypes.c_void_p),
+                ("v", ctypes.c_void_p)]
 
 
 class _Info(ctypes.Structure):
@@ -110,6 +120,7 @@ def load() -> ctypes.CDLL:
     L.lam_assemble_split_host.argtypes = [vp, vp, vp]
     L.lam_assemble_split_noalloc.argtypes = [vp, vp, vp]
     L.lam_plan_update.argtypes = [vp, _D, ctypes.c_int32, ctypes.POINTER(_Material), ctypes.c_int32]
+    L.lam_adjoint.argtypes = [vp, ctypes.POINTER(_Cotangent), vp, vp, vp, vp]
     L.lam_profile_enable.argtypes = [vp, ctypes.c_int32]
     L.lam_profile_get.argtypes = [vp, ctypes.POINTER(_Profile)]
     L.lam_last_error.restype = ctypes.c_char_p
@@ -148,7 +159,9 @@ def _stream_handle(stream) -> Optional[int]:
 
 
 def _ptr(t) -> int:
-    """Device address of a torch tensor (or an int address)."""
+    """Device address of a torch tensor (or an int address; None for NULL)."""
+    if t is None:
+        return None
     if isinstance(t, int):
         return t
     if not t.is_contiguous():
@@ -254,6 +267,20 @@ def plan_update(handle, ply_angle=None, C21=None) -> None:
                                   0 if pa is None else len(pa), mats, nm), "lam_plan_update")
 
 
+def adjoint(handle, d_dC=None, d_dtheta=None, d_dD=None, values=None, u=None, v=None, rank=1, fp64=False,
+            stream=None) -> None:
+    """lam_adjoint: gradients of L = sum(values * K) (values on the pattern) or
+    of L = sum_q u_q^T K v_q (u, v: rank x n_dof) into the given device buffers."""
+    c = _Cotangent()
+    if values is not None:
+        c.kind, c.values = COTANGENT_CSR, _ptr(values)
+    else:
+        c.kind, c.rank, c.u, c.v = COTANGENT_LOWRANK, int(rank), _ptr(u), _ptr(v)
+    c.flags = ADJOINT_FP64 if fp64 else 0
+    _check(load().lam_adjoint(handle, ctypes.byref(c), _ptr(d_dC), _ptr(d_dtheta), _ptr(d_dD), _stream_handle(stream)),
+           "lam_adjoint")
+
+
 def profile_enable(handle, enable: bool = True) -> None:
     """lam_profile_enable: start (or stop) timing every launch; counters restart."""
     _check(load().lam_profile_enable(handle, 1 if enable else 0), "lam_profile_enable")
@@ -277,6 +304,8 @@ class Plan:
         self.handle = plan_create(u, v, ctrl, t, ply_thickness, ply_material, ply_angle, C21, weights=weights,
                                   nq=nq, class_tol=class_tol)
         self.info = plan_get_info(self.handle)
+        self.n_plies = len(ply_thickness)
+        self.n_materials = int(np.atleast_2d(np.asarray(C21)).shape[0])
 
     @classmethod
     def from_laminate(cls, lam, class_tol=-1.0) -> "Plan":
@@ -325,6 +354,22 @@ class Plan:
         plan_update(self.handle, ply_angle, C21)
         self.info = plan_get_info(self.handle)
 
+    def adjoint(self, values=None, u=None, v=None, fp64=False, want_dD=True, stream=None):
+        """(dL/dC: n_materials x 21, dL/dtheta: n_plies, dL/dD: n_plies x 6 x 6 or None)
+        for L = sum(values * K) or L = sum_q u_q^T K v_q; device tensors."""
+        import torch
+        dC = torch.empty(self.n_materials, 21, dtype=torch.float64, device="cuda")
+        dth = torch.empty(self.n_plies, dtype=torch.float64, device="cuda")
+        dD = torch.empty(self.n_plies, 6, 6, dtype=torch.float64, device="cuda") if want_dD else None
+        rank = 1
+        if values is None:
+            u, v = u.reshape(-1, self.n_dof).contiguous(), v.reshape(-1, self.n_dof).contiguous()
+            rank = u.shape[0]
+            if v.shape[0] != rank:
+                raise ValueError("u and v must have the same number of rows")
+        adjoint(self.handle, dC, dth, dD, values=values, u=u, v=v, rank=rank, fp64=fp64, stream=stream)
+        return dC, dth, dD
+
     def profile_enable(self, enable=True):
         profile_enable(self.handle, enable)
 
@@ -341,3 +386,34 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def _stiffness_function():
+    import torch
+
+    class StiffnessFunction(torch.autograd.Function):
+        """values = K(C21, ply_angle) on the plan's pattern (lam_assemble_split),
+        differentiable in the constants and the angles through lam_adjoint.
+        The plan is updated to the given constants and angles (host copies)."""
+
+        @staticmethod
+        def forward(ctx, plan, C21, ply_angle):
+            plan.update(ply_angle=ply_angle.detach().cpu().numpy(), C21=C21.detach().cpu().numpy())
+            ctx.plan = plan
+            ctx.devices = (C21.device, ply_angle.device)
+            return plan.assemble_split()
+
+        @staticmethod
+        def backward(ctx, grad_values):
+            dC, dth, _ = ctx.plan.adjoint(values=grad_values.contiguous(), want_dD=False)
+            return None, dC.to(ctx.devices[0]), dth.to(ctx.devices[1])
+
+    return StiffnessFunction
+
+
+def __getattr__(name):
+    if name == "StiffnessFunction":
+        fn = _stiffness_function()
+        globals()["StiffnessFunction"] = fn
+        return fn
+    raise AttributeError(name)

@@ -90,6 +90,20 @@ struct Plan {
   std::vector<int> occ_lt, occ_k, occ_it;  // len_t(i_t), k_t, i_t of each occurrence
   std::vector<double> host_q;            // host Q per pair [pair][cfg][4] (classification only)
 
+  // adjoint (lam_adjoint): for every ply, the thickness pairs whose common
+  // support meets the ply, with Eq. Q restricted to that ply, divided by the
+  // power of two adj_qscale[type] (types: T T, T T', T' T, T' T')
+  std::vector<int> adj_begin;            // size n_plies + 1
+  std::vector<int> adj_pair;             // thickness pair of each term
+  std::vector<double> adj_q;             // [term][4]
+  std::vector<float> adj_qdf;            // [term][8]: float pairs (hi[4], lo[4]) of adj_q
+  double adj_qscale[4] = {1.0, 1.0, 1.0, 1.0};
+  int adj_max_terms = 0;
+  // chain rule through Eq. D: D_l = M(theta_l) C_m M(theta_l)^T
+  std::vector<double> ply_M, ply_dM;     // [l][36]: Bond matrix and its derivative in theta
+  std::vector<double> mat_C;             // [m][36]: material matrix
+  std::vector<int> ply_mat;              // material of each ply
+
   // colourings
   std::vector<int> col2_begin, col2_elem;  // in-plane elements (ey * nel_u + ex)
   std::vector<int> col3_begin, col3_elem;  // 3D elements ((et * nel_v + ey) * nel_u + ex)

@@ -61,6 +61,20 @@ struct Device {
 
   double* EG = nullptr;  // element Gram blocks: n_el x 9 x pairs
   double* q = nullptr;   // nnz_t x n_cfg x 4
+  // adjoint: geometry tables and workspace (allocated by the first lam_adjoint)
+  bool adj_ready = false;
+  int *adj_begin = nullptr, *adj_pair = nullptr;
+  double* adj_q = nullptr;
+  float* adj_qdf = nullptr;
+  double* adj_G = nullptr;         // assembled G / gscale, nnz_s x 9
+  float2* adj_Gdf = nullptr;       // float pairs of adj_G
+  unsigned long long* adj_gmax = nullptr;  // 9 maxima of |G_ab| (bit patterns), then 9 scales (doubles)
+  double* adj_partial = nullptr;   // n_plies x n_chunks x 81
+  double* adj_plyC = nullptr;      // n_plies x 21
+  int* adj_flag = nullptr;         // set when the double-float pass produced a non-finite partial
+  // adjoint: chain-rule tables (configuration dependent)
+  double *ply_M = nullptr, *ply_dM = nullptr, *mat_C = nullptr;
+  int* ply_mat = nullptr;
   // host-output staging
   double* stage[2] = {nullptr, nullptr};
   size_t stage_elems = 0;
@@ -1012,6 +1026,10 @@ static lam_status ensure_device(Plan& P) {
     UP(L, D->st_cls, P.st_cls);
     UP(L, D->st_rep, P.st_rep);
     UP(L, D->st_first, P.st_first);
+    UP(L, D->ply_M, P.ply_M);
+    UP(L, D->ply_dM, P.ply_dM);
+    UP(L, D->mat_C, P.mat_C);
+    UP(L, D->ply_mat, P.ply_mat);
     if ((st = alloc_dev(L, &D->q, (size_t)P.nnz_t * P.cfg_mat.size() * 4)) != LAM_OK) {
       free_device(P);
       return st;
@@ -1146,7 +1164,23 @@ static lam_status launch_combine(const Plan& P, const KcArgs& k, cudaStream_t s)
   return P.monoclinic ? launch_kc<true, CHUNKED>(P, k, s) : launch_kc<false, CHUNKED>(P, k, s);
 }
 
-// K-b then K-a (all colours): leaves Q and G in the plan's workspace.
+// K-a: the configuration-free in-plane Gram blocks of every element, into EG.
+static lam_status inplane_gram(Plan& P, cudaStream_t s) {
+  Device& D = *P.dev;
+  KaLocalArgs ka{};
+  ka.ip = inplane_args(P);
+  ka.nel = P.u.nel * P.v.nel;
+  ka.EG = D.EG;
+  const size_t smem = ka_smem(P);
+  LAM_CUDA(cudaFuncSetAttribute(ka_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaEvent_t ev = prof_begin(P, s);
+  ka_local<<<ka.nel, ka_block(P), smem, s>>>(ka);
+  LAM_CUDA(cudaGetLastError());
+  prof_end(P, LAM_KERNEL_INPLANE, 1, s, ev);
+  return LAM_OK;
+}
+
+// K-b then K-a: leaves Q and the element Gram blocks in the plan's workspace.
 static lam_status split_integrals(Plan& P, cudaStream_t s) {
   Device& D = *P.dev;
   KbArgs kb{};
@@ -1168,17 +1202,683 @@ static lam_status split_integrals(Plan& P, cudaStream_t s) {
   kb_thickness<<<(unsigned)((P.nnz_t + 127) / 128), 128, 0, s>>>(kb);
   LAM_CUDA(cudaGetLastError());
   prof_end(P, LAM_KERNEL_THICKNESS, 1, s, ev);
-  KaLocalArgs ka{};
-  ka.ip = inplane_args(P);
-  ka.nel = P.u.nel * P.v.nel;
-  ka.EG = D.EG;
-  const size_t smem = ka_smem(P);
-  LAM_CUDA(cudaFuncSetAttribute(ka_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  ev = prof_begin(P, s);
-  ka_local<<<ka.nel, ka_block(P), smem, s>>>(ka);
+  return inplane_gram(P, s);
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint (lam_adjoint). K is linear in every ply's D_l; with the split of
+// Section 3 the coefficient of the stored entry (i_t i_s c, j_t j_s d) in
+// D_l[V(c,a)][V(d,b)] is G_ab^{i_s j_s} Q_{l,ab}^{i_t j_t} (Eq. Km_2, with
+// Eq. P and Eq. Q restricted to ply l), so
+//   S_l[cd][ab] = sum over stored entries of gbar * G_ab * Q_{l,ab}.
+// adj_ply evaluates it thickness first: CTA (chunk of in-plane rows, ply l),
+// thread (c, k_s, d). Per row, z_type = sum over the ply's thickness pairs of
+// gbar * Q_type (types T T, T T', T' T, T' T'), then S[ab] += z_type(ab) *
+// G_ab(i_s, k_s); at the end the CTA sums S over k_s (fixed order) into one
+// partial per (ply, chunk). Q and G enter divided by powers of two (exact), so
+// the double-float arithmetic stays far from float overflow; adj_reduce
+// multiplies the scales back, folds the 81 (cd, ab) sums onto the 36 entries of
+// dL/dD_l and applies the chain rule through Eq. D.
+// ---------------------------------------------------------------------------
+constexpr int kAdjRows = 16;        // in-plane rows per CTA
+constexpr int kAdjMaxTerms = 1024;  // thickness pairs meeting one ply
+constexpr int kAdjBatch = 8;        // cotangent loads issued together
+// The double-float pass is kept only if the largest cotangent magnitude is at
+// least 2^(kAdjMinExp - 1023); below that (a cotangent of tiny entries only)
+// the FP64 pass recomputes everything, as it does for non-finite partials.
+constexpr int kAdjMinExp = 1023 - 60;
+// ... and likewise when an entry (low-rank: a product of entries) reaches 2^128.
+constexpr int kAdjMaxExp = 1150;
+
+// g = hi + lo with |g - hi - lo| <= 2^-46 |g| for 2^-80 <= |g| < 2^128: hi is
+// g truncated to 24 significant bits, lo the top 23 of the remaining 29 bits,
+// both formed from the bits of g with integer and exact float operations (no
+// FP64 arithmetic). Smaller magnitudes keep hi only (|g| >= 2^-126) or vanish;
+// larger ones, infinities and NaNs give a non-finite hi, which the caller's
+// finiteness check turns into the FP64 evaluation. Returns the biased FP64
+// exponent of g (0 for zero).
+__device__ __forceinline__ int split_df(double g, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(g);
+  const unsigned int H = (unsigned int)(b >> 32), Lw = (unsigned int)b;
+  const unsigned int sign = H & 0x80000000u;
+  const int E = (int)((H >> 20) & 0x7FFu);
+  const unsigned int nb = sign | ((unsigned int)(E - 896) << 23) | ((H & 0xFFFFFu) << 3) | (Lw >> 29);
+  hi = __int_as_float((int)((E < 897) ? sign : ((E > 1150) ? (sign | 0x7F800000u) : nb)));
+  const float r = __fsub_rn(__int_as_float((int)(0x4B000000u | ((Lw & 0x1FFFFFFFu) >> 6))), 8388608.0f);
+  const int se = (E >= 943 && E <= 1150) ? (E - 942) : 0;  // exponent field of 2^(E - 1069); 0 gives 0.0f
+  lo = __int_as_float(__float_as_int(__fmul_rn(r, __int_as_float(se << 23))) | (int)sign);
+  return E;
+}
+
+// The split of split_df for the hot loop, in fewer integer operations: valid
+// for 2^-80 <= |g| < 2^128 (biased exponent 943 ... 1150); below, hi = lo = 0.
+// Above, the result is meaningless: the caller tracks the largest exponent and
+// the FP64 pass recomputes everything when it exceeds 1150.
+__device__ __forceinline__ int split_df_fast(double g, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(g);
+  const unsigned int H = (unsigned int)(b >> 32), Lw = (unsigned int)b;
+  const int E = (int)((H >> 20) & 0x7FFu);
+  // (H << 3 | Lw >> 29) holds E mod 512 and the top 23 mantissa bits; rebias E by -896
+  const unsigned int hb = ((__funnelshift_l(Lw, H, 3) - (384u << 23)) & 0x7FFFFFFFu) | (H & 0x80000000u);
+  const unsigned int sb = (hb & 0xFF800000u) - (46u << 23);  // sign * 2^(E - 1069)
+  const float r = __fsub_rn(__int_as_float((int)(0x4B000000u | ((Lw >> 6) & 0x7FFFFFu))), 8388608.0f);
+  const bool keep = E >= 943;
+  hi = keep ? __int_as_float((int)hb) : 0.0f;
+  lo = keep ? __fmul_rn(r, __int_as_float((int)sb)) : 0.0f;
+  return E;
+}
+
+// (p, e) with p + e = a * b to about 2^-47 relative, a and b given as float pairs
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float& p, float& e) {
+  p = __fmul_rn(ah, bh);
+  e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+}
+
+// (sh, sl) += (ph, pl) by Knuth's two-sum on the high parts
+__device__ __forceinline__ void df_add(float ph, float pl, float& sh, float& sl) {
+  const float t = __fadd_rn(sh, ph);
+  const float z = __fsub_rn(t, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(ph, z));
+  sl = __fadd_rn(sl, __fadd_rn(err, pl));
+  sh = t;
+}
+
+struct AdjGatherArgs {
+  int nx, nel_u, nlx, nls, npl;
+  const int64_t* LSb;
+  const int *lenX, *lenY, *loX, *loY, *eloX, *ehiX, *eloY, *ehiY, *firstU, *firstV;
+  const double* EG;
+  double* G;                   // nnz_s x 9
+  unsigned long long* gmax;    // 9 maxima of |G_ab| as bit patterns
+};
+
+// Assembled in-plane Gram blocks G_ab(i_s, k_s) (the sum over the shared
+// elements, in a fixed element order) and the maxima of |G_ab|.
+__global__ void __launch_bounds__(1024) adj_gather(AdjGatherArgs a) {
+  __shared__ unsigned long long smax[9];
+  if (threadIdx.x < 9) smax[threadIdx.x] = 0ull;
+  __syncthreads();
+  const int64_t is = blockIdx.x;
+  const int ix = (int)(is % a.nx), iy = (int)(is / a.nx);
+  const int lx = a.lenX[ix], ls = lx * a.lenY[iy];
+  const int64_t ls0 = a.LSb[is];
+  for (int item = threadIdx.x; item < 9 * ls; item += blockDim.x) {
+    const int ks = item / 9, ab = item % 9;
+    const int jx = a.loX[ix] + ks % lx, jy = a.loY[iy] + ks / lx;
+    const int ex0 = max(a.eloX[ix], a.eloX[jx]), ex1 = min(a.ehiX[ix], a.ehiX[jx]);
+    const int ey0 = max(a.eloY[iy], a.eloY[jy]), ey1 = min(a.ehiY[iy], a.ehiY[jy]);
+    const int ba = (ab % 3) * 3 + ab / 3;
+    double acc = 0.0;
+    for (int ey = ey0; ey <= ey1; ++ey) {
+      const int fy = a.firstV[ey];
+      for (int ex = ex0; ex <= ex1; ++ex) {
+        const int fx = a.firstU[ex];
+        const int li = (iy - fy) * a.nlx + (ix - fx), lj = (jy - fy) * a.nlx + (jx - fx);
+        const size_t e9 = ((size_t)ey * a.nel_u + ex) * 9;
+        if (li <= lj)
+          acc += a.EG[(e9 + ab) * a.npl + upper_pair(li, lj, a.nls)];
+        else
+          acc += a.EG[(e9 + ba) * a.npl + upper_pair(lj, li, a.nls)];
+      }
+    }
+    a.G[(ls0 + ks) * 9 + ab] = acc;
+    atomicMax(&smax[ab], (unsigned long long)__double_as_longlong(fabs(acc)));
+  }
+  __syncthreads();
+  if (threadIdx.x < 9) atomicMax(&a.gmax[threadIdx.x], smax[threadIdx.x]);
+}
+
+// G_ab divided by a power of two at least max |G_ab| (exact), and its float
+// pairs. The 9 scales go to gscale.
+__global__ void adj_split(int64_t n9, double* __restrict__ G, float2* __restrict__ Gdf,
+                          const unsigned long long* __restrict__ gmax, double* __restrict__ gscale) {
+  __shared__ double inv[9];
+  if (threadIdx.x < 9) {
+    const double m = __longlong_as_double((long long)gmax[threadIdx.x]);
+    double sc = 1.0;
+    if (m > 0.0 && m <= 1.7976931348623157e308) {
+      int e = 0;
+      frexp(m, &e);
+      sc = ldexp(1.0, e);
+    }
+    inv[threadIdx.x] = 1.0 / sc;
+    if (blockIdx.x == 0) gscale[threadIdx.x] = sc;
+  }
+  __syncthreads();
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n9; k += (int64_t)gridDim.x * blockDim.x) {
+    const double g = G[k] * inv[k % 9];
+    G[k] = g;
+    float hi, lo;
+    split_df(g, hi, lo);
+    Gdf[k] = make_float2(hi, lo);
+  }
+}
+
+struct AdjArgs {
+  int64_t ns, n_dof;
+  int nx, lsp, nchunks, mt;
+  const int64_t* LSb;
+  const int *lenX, *lenY, *loX, *loY;
+  const int *term_begin, *term_pair;
+  const double* term_q;     // [term][4], scaled
+  const float* term_qdf;    // [term][8]: hi[4], lo[4]
+  const int64_t* tp_A;
+  const int *tp_lt, *tp_k, *tp_row, *tp_col;
+  const double* gbar;       // CSR cotangent
+  const double *u, *v;      // low-rank cotangent, rank x n_dof each
+  int rank;
+  const double* G;          // scaled G, nnz_s x 9
+  const float2* Gdf;        // its float pairs
+  double* partial;          // n_plies x nchunks x 81
+  int* flag;                // set by the double-float pass on a non-finite partial
+  int* emax;                // largest biased exponent of the cotangent seen by that pass
+  int conditional;          // run only if the double-float result is not kept
+};
+
+template <bool LOWRANK, bool DF>
+__global__ void __launch_bounds__(1024) adj_ply(AdjArgs a) {
+  if (a.conditional && *a.flag == 0 && *a.emax >= kAdjMinExp && *a.emax <= kAdjMaxExp) return;
+  extern __shared__ double sm[];
+  const int l = blockIdx.y, chunk = blockIdx.x;
+  const int t0 = a.term_begin[l], nterm = a.term_begin[l + 1] - t0;
+  const int nthr = blockDim.x, tid = threadIdx.x;
+  int64_t* sA = reinterpret_cast<int64_t*>(sm);           // CSR slab start of the pair's thickness row
+  double* sQ = sm + a.mt;                                  // Q (4 doubles, or 8 floats: hi[4] lo[4])
+  int* sI = reinterpret_cast<int*>(sQ + 4 * (size_t)a.mt);  // len_t, k_t, i_t, j_t
+  double* red = reinterpret_cast<double*>(sI + 4 * (size_t)a.mt);  // 9 x nthr
+  for (int k = tid; k < nterm; k += nthr) {
+    const int pr = a.term_pair[t0 + k];
+    sA[k] = a.tp_A[pr];
+    sI[4 * k + 0] = a.tp_lt[pr];
+    sI[4 * k + 1] = a.tp_k[pr];
+    sI[4 * k + 2] = a.tp_row[pr];
+    sI[4 * k + 3] = a.tp_col[pr];
+    if (DF) {
+      float* q = reinterpret_cast<float*>(sQ + 4 * (size_t)k);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) q[j] = a.term_qdf[(size_t)(t0 + k) * 8 + j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) sQ[4 * (size_t)k + j] = a.term_q[(size_t)(t0 + k) * 4 + j];
+    }
+  }
+  __syncthreads();
+  const int lsp3 = 3 * a.lsp;
+  const bool valid = tid < 9 * a.lsp;
+  const int c = valid ? tid / lsp3 : 0, rem = valid ? tid % lsp3 : 0;
+  const int ks = rem / 3, d = rem % 3;
+  float Sh[9], Sl[9];
+  double S[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    Sh[k] = Sl[k] = 0.0f;
+    S[k] = 0.0;
+  }
+  int emax = 0;
+  const int64_t r0 = (int64_t)chunk * kAdjRows;
+  for (int r = 0; r < kAdjRows; ++r) {
+    const int64_t is = r0 + r;
+    if (is >= a.ns) break;
+    const int ix = (int)(is % a.nx), iy = (int)(is / a.nx);
+    const int lx = a.lenX[ix], ls = lx * a.lenY[iy];
+    if (!valid || ks >= ls) continue;
+    const int64_t ls0 = a.LSb[is];
+    const int64_t rowbase = 9 * ls0 + 3 * (int64_t)c * ls;
+    const int off = 3 * ks + d, seg = 3 * ls;
+    int64_t jbase = 0;
+    if (LOWRANK) {
+      const int jx = a.loX[ix] + ks % lx, jy = a.loY[iy] + ks / lx;
+      jbase = (int64_t)jy * a.nx + jx;
+    }
+    float zh[4] = {0.0f, 0.0f, 0.0f, 0.0f}, zl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    double z[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int tb = 0; tb < nterm; tb += kAdjBatch) {
+      double gv[kAdjBatch];
+      if (!LOWRANK) {
+#pragma unroll
+        for (int j = 0; j < kAdjBatch; ++j) {
+          const int t = tb + j;
+          gv[j] = (t < nterm) ? a.gbar[sA[t] + sI[4 * t] * rowbase + (int64_t)sI[4 * t + 1] * seg + off] : 0.0;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kAdjBatch; ++j) {
+        const int t = tb + j;
+        if (t >= nterm) break;
+        if (DF) {
+          float gh = 0.0f, gl = 0.0f;
+          if (LOWRANK) {
+            const int64_t iu = 3 * ((int64_t)sI[4 * t + 2] * a.ns + is) + c;
+            const int64_t iv = 3 * ((int64_t)sI[4 * t + 3] * a.ns + jbase) + d;
+            for (int q = 0; q < a.rank; ++q) {
+              float uh, ul, vh, vl, p, e;
+              const int eu = split_df(a.u[(size_t)q * a.n_dof + iu], uh, ul);
+              const int ev = split_df(a.v[(size_t)q * a.n_dof + iv], vh, vl);
+              if (eu > 0 && ev > 0) emax = max(emax, eu + ev - 1023);
+              df_mul(uh, ul, vh, vl, p, e);
+              df_add(p, e, gh, gl);
+            }
+          } else {
+            emax = max(emax, split_df(gv[j], gh, gl));
+          }
+          const float* q = reinterpret_cast<const float*>(sQ + 4 * (size_t)t);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            float p, e;
+            df_mul(gh, gl, q[k], q[4 + k], p, e);
+            df_add(p, e, zh[k], zl[k]);
+          }
+        } else {
+          double g = LOWRANK ? 0.0 : gv[j];
+          if (LOWRANK) {
+            const int64_t iu = 3 * ((int64_t)sI[4 * t + 2] * a.ns + is) + c;
+            const int64_t iv = 3 * ((int64_t)sI[4 * t + 3] * a.ns + jbase) + d;
+            g = 0.0;
+            for (int q = 0; q < a.rank; ++q) g += a.u[(size_t)q * a.n_dof + iu] * a.v[(size_t)q * a.n_dof + iv];
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k) z[k] += g * sQ[4 * (size_t)t + k];
+        }
+      }
+    }
+    // S[ab] += z_type(ab) * G_ab, type(ab) = 2 [a is z] + [b is z]
+    const int64_t gi = (ls0 + ks) * 9;
+    if (DF) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {  // renormalise the pairs
+        const float hsum = __fadd_rn(zh[k], zl[k]);
+        zl[k] = __fsub_rn(zl[k], __fsub_rn(hsum, zh[k]));
+        zh[k] = hsum;
+      }
+#pragma unroll
+      for (int ab = 0; ab < 9; ++ab) {
+        const int ty = 2 * (ab / 3 == 2) + (ab % 3 == 2);
+        const float2 gq = a.Gdf[gi + ab];
+        float p, e;
+        df_mul(zh[ty], zl[ty], gq.x, gq.y, p, e);
+        df_add(p, e, Sh[ab], Sl[ab]);
+      }
+    } else {
+#pragma unroll
+      for (int ab = 0; ab < 9; ++ab) {
+        const int ty = 2 * (ab / 3 == 2) + (ab % 3 == 2);
+        S[ab] += z[ty] * a.G[gi + ab];
+      }
+    }
+  }
+  if (DF) {
+    emax = __reduce_max_sync(0xffffffffu, emax);
+    if ((tid & 31) == 0) atomicMax(a.emax, emax);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int ab = 0; ab < 9; ++ab)
+    red[(size_t)ab * nthr + tid] = valid ? (DF ? (double)Sh[ab] + (double)Sl[ab] : S[ab]) : 0.0;
+  __syncthreads();
+  if (tid < 81) {
+    const int cd = tid / 9, ab = tid % 9, cc = cd / 3, dd = cd % 3;
+    double acc = 0.0;
+    for (int k = 0; k < a.lsp; ++k) acc += red[(size_t)ab * nthr + cc * lsp3 + 3 * k + dd];
+    a.partial[((size_t)l * a.nchunks + chunk) * 81 + tid] = acc;
+    if (DF && !isfinite(acc)) atomicOr(a.flag, 1);
+  }
+}
+
+// Double-float pass for a CSR cotangent (the common case), leaner than the
+// generic kernel: the CTA first tabulates, in shared memory, the CSR offset of
+// every (row of its chunk, c, thickness pair of its ply) -- 32-bit when
+// nnz < 2^31 -- so a thread's load is one shared read and one add; all of a
+// row's cotangent loads of one batch are issued before any arithmetic; the four
+// Q types of a term come from shared memory as two float4. Used when a ply
+// meets at most kAdjFastTerms thickness pairs.
+constexpr int kAdjRowTerms = 9;
+constexpr int kAdjFastTerms = 32;
+
+template <typename Idx>
+__global__ void __launch_bounds__(1024) adj_ply_df(AdjArgs a) {
+  extern __shared__ double sm[];
+  const int l = blockIdx.y, chunk = blockIdx.x;
+  const int t0 = a.term_begin[l], nterm = a.term_begin[l + 1] - t0;
+  const int nthr = blockDim.x, tid = threadIdx.x;
+  float4* sQh = reinterpret_cast<float4*>(sm);                  // kAdjFastTerms
+  float4* sQl = sQh + kAdjFastTerms;                             // kAdjFastTerms
+  double* red = reinterpret_cast<double*>(sQl + kAdjFastTerms);  // 9 x nthr
+  Idx* sBase = reinterpret_cast<Idx*>(red + (size_t)9 * nthr);   // kAdjRows x 3 x kAdjFastTerms
+  int* sLs = reinterpret_cast<int*>(sBase + kAdjRows * 3 * kAdjFastTerms);  // kAdjRows
+  int* sLs0 = sLs + kAdjRows;                                    // kAdjRows (in-plane pair offset of the row)
+  const int64_t r0 = (int64_t)chunk * kAdjRows;
+  const int nrows = (int)min((int64_t)kAdjRows, a.ns - r0);
+  for (int k = tid; k < nterm; k += nthr) {
+    const float* q = a.term_qdf + (size_t)(t0 + k) * 8;
+    sQh[k] = make_float4(q[0], q[1], q[2], q[3]);
+    sQl[k] = make_float4(q[4], q[5], q[6], q[7]);
+  }
+  if (tid < nrows) {
+    const int is = (int)(r0 + tid);
+    sLs[tid] = a.lenX[is % a.nx] * a.lenY[is / a.nx];
+    sLs0[tid] = (int)a.LSb[is];
+  }
+  __syncthreads();
+  for (int k = tid; k < nrows * 3 * nterm; k += nthr) {
+    const int r = k / (3 * nterm), c3 = (k / nterm) % 3, t = k % nterm;
+    const int pr = a.term_pair[t0 + t];
+    const int64_t ls = sLs[r];
+    sBase[(r * 3 + c3) * kAdjFastTerms + t] =
+        (Idx)(a.tp_A[pr] + (int64_t)a.tp_lt[pr] * (9 * (int64_t)sLs0[r] + 3 * c3 * ls) + (int64_t)a.tp_k[pr] * 3 * ls);
+  }
+  __syncthreads();
+  const int lsp3 = 3 * a.lsp;
+  const bool valid = tid < 9 * a.lsp;
+  const int c = valid ? tid / lsp3 : 0, rem = valid ? tid % lsp3 : 0;
+  const int ks = rem / 3, d = rem % 3;
+  float Sh[9], Sl[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Sh[k] = Sl[k] = 0.0f;
+  int emax = 0;
+  for (int r = 0; r < nrows; ++r) {
+    const int ls = sLs[r];
+    if (!valid || ks >= ls) continue;
+    const Idx* bp = sBase + (r * 3 + c) * kAdjFastTerms;
+    const Idx off = (Idx)(3 * ks + d);
+    float zh[4] = {0.0f, 0.0f, 0.0f, 0.0f}, zl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int tb = 0; tb < nterm; tb += kAdjRowTerms) {
+      double v[kAdjRowTerms];
+#pragma unroll
+      for (int j = 0; j < kAdjRowTerms; ++j) v[j] = (tb + j < nterm) ? a.gbar[bp[tb + j] + off] : 0.0;
+#pragma unroll
+      for (int j = 0; j < kAdjRowTerms; ++j) {
+        const int t = tb + j;
+        if (t < nterm) {
+          float gh, gl;
+          emax = max(emax, split_df_fast(v[j], gh, gl));
+          const float4 qh = sQh[t], ql = sQl[t];
+          float p, e;
+          df_mul(gh, gl, qh.x, ql.x, p, e);
+          df_add(p, e, zh[0], zl[0]);
+          df_mul(gh, gl, qh.y, ql.y, p, e);
+          df_add(p, e, zh[1], zl[1]);
+          df_mul(gh, gl, qh.z, ql.z, p, e);
+          df_add(p, e, zh[2], zl[2]);
+          df_mul(gh, gl, qh.w, ql.w, p, e);
+          df_add(p, e, zh[3], zl[3]);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {  // renormalise the pairs
+      const float hsum = __fadd_rn(zh[k], zl[k]);
+      zl[k] = __fsub_rn(zl[k], __fsub_rn(hsum, zh[k]));
+      zh[k] = hsum;
+    }
+    const float2* gp = a.Gdf + ((int64_t)sLs0[r] + ks) * 9;
+#pragma unroll
+    for (int ab = 0; ab < 9; ++ab) {
+      const int ty = 2 * (ab / 3 == 2) + (ab % 3 == 2);
+      const float2 gq = gp[ab];
+      float p, e;
+      df_mul(zh[ty], zl[ty], gq.x, gq.y, p, e);
+      df_add(p, e, Sh[ab], Sl[ab]);
+    }
+  }
+  emax = __reduce_max_sync(0xffffffffu, emax);
+  if ((tid & 31) == 0) atomicMax(a.emax, emax);
+  __syncthreads();
+#pragma unroll
+  for (int ab = 0; ab < 9; ++ab) red[(size_t)ab * nthr + tid] = valid ? (double)Sh[ab] + (double)Sl[ab] : 0.0;
+  __syncthreads();
+  if (tid < 81) {
+    const int cd = tid / 9, ab = tid % 9, cc = cd / 3, dd = cd % 3;
+    double acc = 0.0;
+    for (int k = 0; k < a.lsp; ++k) acc += red[(size_t)ab * nthr + cc * lsp3 + 3 * k + dd];
+    a.partial[((size_t)l * a.nchunks + chunk) * 81 + tid] = acc;
+    if (!isfinite(acc)) atomicOr(a.flag, 1);
+  }
+}
+
+static size_t adj_df_smem(int nthr, size_t idx_bytes) {
+  return (size_t)kAdjFastTerms * 32 + (size_t)9 * nthr * sizeof(double) + (size_t)kAdjRows * 3 * kAdjFastTerms * idx_bytes +
+         2 * kAdjRows * sizeof(int);
+}
+
+struct AdjReduceArgs {
+  int nchunks;
+  double qscale[4];
+  const double* gscale;
+  const double* partial;
+  const double *ply_M, *ply_dM, *mat_C;
+  const int* ply_mat;
+  double *dD, *dtheta, *plyC;
+};
+
+// One CTA per ply: the 81 sums (scales restored), dL/dD_l, dL/dtheta_l and
+// the ply's share of dL/dC (21 constants).
+__global__ void __launch_bounds__(128) adj_reduce(AdjReduceArgs a) {
+  __shared__ double S[81], dD[36], pr[36], T[36];
+  const int l = blockIdx.x, t = threadIdx.x;
+  if (t < 81) {
+    const int ab = t % 9;
+    const int ty = 2 * (ab / 3 == 2) + (ab % 3 == 2);
+    double acc = 0.0;
+    for (int ch = 0; ch < a.nchunks; ++ch) acc += a.partial[((size_t)l * a.nchunks + ch) * 81 + t];
+    S[t] = acc * a.qscale[ty] * a.gscale[ab];
+  }
+  __syncthreads();
+  // Voigt index of the symmetric pair (i, j): 11, 22, 33, 12, 13, 23
+  const int V[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+  if (t < 36) {
+    const int I = t / 6, J = t % 6;
+    double acc = 0.0;
+    for (int c = 0; c < 3; ++c)
+      for (int x = 0; x < 3; ++x) {
+        if (V[c][x] != I) continue;
+        for (int d = 0; d < 3; ++d)
+          for (int y = 0; y < 3; ++y)
+            if (V[d][y] == J) acc += S[(c * 3 + d) * 9 + x * 3 + y];
+      }
+    dD[t] = acc;
+    if (a.dD) a.dD[(size_t)l * 36 + t] = acc;
+  }
+  __syncthreads();
+  const double* M = a.ply_M + (size_t)l * 36;
+  const double* dM = a.ply_dM + (size_t)l * 36;
+  const double* C = a.mat_C + (size_t)a.ply_mat[l] * 36;
+  if (t < 36) {
+    const int I = t / 6, J = t % 6;
+    double x = 0.0, y = 0.0;
+    for (int K = 0; K < 6; ++K)
+      for (int L = 0; L < 6; ++L) {
+        x += (dM[I * 6 + K] * M[J * 6 + L] + M[I * 6 + K] * dM[J * 6 + L]) * C[K * 6 + L];
+        y += M[K * 6 + I] * dD[K * 6 + L] * M[L * 6 + J];
+      }
+    pr[t] = dD[t] * x;
+    T[t] = y;
+  }
+  __syncthreads();
+  if (t == 0 && a.dtheta) {
+    double acc = 0.0;
+    for (int k = 0; k < 36; ++k) acc += pr[k];
+    a.dtheta[l] = acc;
+  }
+  if (t < 21) {
+    int p = 0, r = t;
+    while (r >= 6 - p) {
+      r -= 6 - p;
+      ++p;
+    }
+    const int q = p + r;
+    a.plyC[(size_t)l * 21 + t] = (p == q) ? T[p * 6 + q] : T[p * 6 + q] + T[q * 6 + p];
+  }
+}
+
+// dL/dC_m = sum over the plies of material m, in ply order.
+__global__ void adj_material(int nply, int nmat, const int* __restrict__ ply_mat, const double* __restrict__ plyC,
+                             double* __restrict__ dC) {
+  for (int k = threadIdx.x; k < nmat * 21; k += blockDim.x) {
+    const int m = k / 21, j = k % 21;
+    double acc = 0.0;
+    for (int l = 0; l < nply; ++l)
+      if (ply_mat[l] == m) acc += plyC[(size_t)l * 21 + j];
+    dC[k] = acc;
+  }
+}
+
+static int adj_nchunks(const Plan& P) { return (int)((P.ns + kAdjRows - 1) / kAdjRows); }
+static int adj_block(const Plan& P) { return std::max(96, ((9 * max_len_s(P) + 31) / 32) * 32); }
+static size_t adj_smem(const Plan& P) {
+  // generic kernel: per term 8 (offset) + 32 (Q) + 16 (indices); fast kernel: 32 + 8 + 8 and 16 bytes of
+  // alignment slack. The larger of the two, then the reduction buffer.
+  return (size_t)P.adj_max_terms * (8 + 32 + 16) + 16 + (size_t)9 * adj_block(P) * sizeof(double);
+}
+
+static lam_status ensure_adjoint(Plan& P) {
+  Device& D = *P.dev;
+  if (D.adj_ready) return LAM_OK;
+  lam_status st;
+  auto& L = D.allocs;
+  if ((st = upload(P, L, &D.adj_begin, P.adj_begin)) != LAM_OK) return st;
+  if ((st = upload(P, L, &D.adj_pair, P.adj_pair)) != LAM_OK) return st;
+  if ((st = upload(P, L, &D.adj_q, P.adj_q)) != LAM_OK) return st;
+  if ((st = upload(P, L, &D.adj_qdf, P.adj_qdf)) != LAM_OK) return st;
+  double* p = nullptr;
+  if ((st = alloc_dev(L, &D.adj_G, (size_t)9 * P.nnz_s)) != LAM_OK) return st;
+  if ((st = alloc_dev(L, &p, (size_t)9 * P.nnz_s)) != LAM_OK) return st;
+  D.adj_Gdf = reinterpret_cast<float2*>(p);
+  if ((st = alloc_dev(L, &p, 18)) != LAM_OK) return st;
+  D.adj_gmax = reinterpret_cast<unsigned long long*>(p);
+  if ((st = alloc_dev(L, &D.adj_partial, (size_t)P.plies.size() * adj_nchunks(P) * 81)) != LAM_OK) return st;
+  if ((st = alloc_dev(L, &D.adj_plyC, (size_t)P.plies.size() * 21)) != LAM_OK) return st;
+  if ((st = alloc_dev(L, &p, 1)) != LAM_OK) return st;
+  D.adj_flag = reinterpret_cast<int*>(p);  // flag, then emax
+  D.adj_ready = true;
+  return LAM_OK;
+}
+
+template <bool LOWRANK, bool DF>
+static lam_status launch_adj_ply(const Plan& P, const AdjArgs& a, cudaStream_t s) {
+  const size_t smem = adj_smem(P);
+  LAM_CUDA(cudaFuncSetAttribute(adj_ply<LOWRANK, DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((unsigned)adj_nchunks(P), (unsigned)P.plies.size());
+  adj_ply<LOWRANK, DF><<<grid, adj_block(P), smem, s>>>(a);
   LAM_CUDA(cudaGetLastError());
-  const int launched = 1;
-  prof_end(P, LAM_KERNEL_INPLANE, launched, s, ev);
+  return LAM_OK;
+}
+
+template <typename Idx>
+static lam_status launch_adj_df(const Plan& P, const AdjArgs& a, cudaStream_t s) {
+  const size_t smem = adj_df_smem(adj_block(P), sizeof(Idx));
+  LAM_CUDA(cudaFuncSetAttribute(adj_ply_df<Idx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((unsigned)adj_nchunks(P), (unsigned)P.plies.size());
+  adj_ply_df<Idx><<<grid, adj_block(P), smem, s>>>(a);
+  LAM_CUDA(cudaGetLastError());
+  return LAM_OK;
+}
+
+static lam_status adjoint(Plan& P, const lam_cotangent& cot, double* dC, double* dtheta, double* dDout,
+                          cudaStream_t s) {
+  Device& D = *P.dev;
+  lam_status st;
+  if ((st = inplane_gram(P, s)) != LAM_OK) return st;
+  cudaEvent_t ev = prof_begin(P, s);
+  LAM_CUDA(cudaMemsetAsync(D.adj_gmax, 0, 9 * sizeof(unsigned long long), s));
+  LAM_CUDA(cudaMemsetAsync(D.adj_flag, 0, 2 * sizeof(int), s));
+  AdjGatherArgs g{};
+  g.nx = P.u.n;
+  g.nel_u = P.u.nel;
+  g.nlx = P.u.p + 1;
+  g.nls = ka_nls(P);
+  g.npl = ka_npl(P);
+  g.LSb = D.LSb;
+  g.lenX = D.lenX;
+  g.lenY = D.lenY;
+  g.loX = D.loX;
+  g.loY = D.loY;
+  g.eloX = D.eloX;
+  g.ehiX = D.ehiX;
+  g.eloY = D.eloY;
+  g.ehiY = D.ehiY;
+  g.firstU = D.firstU;
+  g.firstV = D.firstV;
+  g.EG = D.EG;
+  g.G = D.adj_G;
+  g.gmax = D.adj_gmax;
+  adj_gather<<<(unsigned)P.ns, adj_block(P), 0, s>>>(g);
+  LAM_CUDA(cudaGetLastError());
+  double* gscale = reinterpret_cast<double*>(D.adj_gmax + 9);
+  const int64_t n9 = 9 * P.nnz_s;
+  adj_split<<<(unsigned)std::min<int64_t>((n9 + 255) / 256, 152 * 8), 256, 0, s>>>(n9, D.adj_G, D.adj_Gdf, D.adj_gmax,
+                                                                                    gscale);
+  LAM_CUDA(cudaGetLastError());
+  AdjArgs a{};
+  a.ns = P.ns;
+  a.n_dof = P.n_dof;
+  a.nx = P.u.n;
+  a.lsp = max_len_s(P);
+  a.nchunks = adj_nchunks(P);
+  a.mt = P.adj_max_terms;
+  a.LSb = D.LSb;
+  a.lenX = D.lenX;
+  a.lenY = D.lenY;
+  a.loX = D.loX;
+  a.loY = D.loY;
+  a.term_begin = D.adj_begin;
+  a.term_pair = D.adj_pair;
+  a.term_q = D.adj_q;
+  a.term_qdf = D.adj_qdf;
+  a.tp_A = D.tp_A;
+  a.tp_lt = D.tp_lt;
+  a.tp_k = D.tp_k;
+  a.tp_row = D.tp_row;
+  a.tp_col = D.tp_col;
+  a.gbar = cot.values;
+  a.u = cot.u;
+  a.v = cot.v;
+  a.rank = cot.rank;
+  a.G = D.adj_G;
+  a.Gdf = D.adj_Gdf;
+  a.partial = D.adj_partial;
+  a.flag = D.adj_flag;
+  a.emax = D.adj_flag + 1;
+  const bool lowrank = cot.kind == LAM_COTANGENT_LOWRANK;
+  const bool force64 = (cot.flags & LAM_ADJOINT_FP64) != 0;
+  int launched = 4;  // memsets excluded: gather, split, FP64 pass, reduce
+  if (!force64) {
+    a.conditional = 0;
+    if (lowrank)
+      st = launch_adj_ply<true, true>(P, a, s);
+    else if (P.adj_max_terms > kAdjFastTerms)
+      st = launch_adj_ply<false, true>(P, a, s);
+    else if (P.nnz < ((int64_t)1 << 31))
+      st = launch_adj_df<int32_t>(P, a, s);
+    else
+      st = launch_adj_df<int64_t>(P, a, s);
+    if (st != LAM_OK) return st;
+    ++launched;
+  }
+  a.conditional = force64 ? 0 : 1;
+  st = lowrank ? launch_adj_ply<true, false>(P, a, s) : launch_adj_ply<false, false>(P, a, s);
+  if (st != LAM_OK) return st;
+  AdjReduceArgs r{};
+  r.nchunks = a.nchunks;
+  for (int k = 0; k < 4; ++k) r.qscale[k] = P.adj_qscale[k];
+  r.gscale = gscale;
+  r.partial = D.adj_partial;
+  r.ply_M = D.ply_M;
+  r.ply_dM = D.ply_dM;
+  r.mat_C = D.mat_C;
+  r.ply_mat = D.ply_mat;
+  r.dD = dDout;
+  r.dtheta = dtheta;
+  r.plyC = D.adj_plyC;
+  adj_reduce<<<(unsigned)P.plies.size(), 128, 0, s>>>(r);
+  LAM_CUDA(cudaGetLastError());
+  if (dC) {
+    adj_material<<<1, 256, 0, s>>>((int)P.plies.size(), (int)P.mats.size(), D.ply_mat, D.adj_plyC, dC);
+    LAM_CUDA(cudaGetLastError());
+    ++launched;
+  }
+  prof_end(P, LAM_KERNEL_ADJOINT, launched, s, ev);
   return LAM_OK;
 }
 
@@ -1372,6 +2072,43 @@ lam_status lam_assemble_standard(lam_plan* plan, double* d_values, void* stream)
   }
   lam::prof_end(P, LAM_KERNEL_STANDARD, launched, s, ev);
   return LAM_OK;
+}
+
+lam_status lam_adjoint(lam_plan* plan, const lam_cotangent* cot, double* d_dC, double* d_dtheta, double* d_dD,
+                       void* stream) {
+  if (!plan || !cot) {
+    lam::set_error("lam_adjoint: NULL argument");
+    return LAM_ERR_INVALID_ARG;
+  }
+  if (cot->kind == LAM_COTANGENT_CSR) {
+    if (!cot->values) {
+      lam::set_error("lam_adjoint: CSR cotangent without values");
+      return LAM_ERR_INVALID_ARG;
+    }
+  } else if (cot->kind == LAM_COTANGENT_LOWRANK) {
+    if (cot->rank < 1 || !cot->u || !cot->v) {
+      lam::set_error("lam_adjoint: low-rank cotangent needs rank >= 1 and both u and v");
+      return LAM_ERR_INVALID_ARG;
+    }
+  } else {
+    lam::set_error("lam_adjoint: unknown cotangent kind %d", (int)cot->kind);
+    return LAM_ERR_INVALID_ARG;
+  }
+  if ((cot->flags & ~LAM_ADJOINT_FP64) != 0) {
+    lam::set_error("lam_adjoint: unknown flags 0x%x", (unsigned)cot->flags);
+    return LAM_ERR_INVALID_ARG;
+  }
+  lam::Plan& P = plan->p;
+  if (P.adj_max_terms > lam::kAdjMaxTerms) {
+    lam::set_error("lam_adjoint: a ply meets %d thickness pairs (at most %d)", P.adj_max_terms, lam::kAdjMaxTerms);
+    return LAM_ERR_UNSUPPORTED;
+  }
+  if (!d_dC && !d_dtheta && !d_dD) return LAM_OK;
+  lam_status st;
+  if ((st = lam::check_limits(P)) != LAM_OK) return st;
+  if ((st = lam::ensure_device(P)) != LAM_OK) return st;
+  if ((st = lam::ensure_adjoint(P)) != LAM_OK) return st;
+  return lam::adjoint(P, *cot, d_dC, d_dtheta, d_dD, static_cast<cudaStream_t>(stream));
 }
 
 lam_status lam_profile_enable(lam_plan* plan, int32_t enable) {

@@ -2,6 +2,7 @@
 // structure, (material, angle) configurations, thickness pieces and pair
 // classes, and the analytic sizes of the sparsity pattern. No CUDA here.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -271,36 +272,48 @@ static void build_inplane_table(const Basis& B, const std::vector<double>& gx, c
 // Configurations: Eq. D for a ply rotated about z, by the Bond stress
 // transformation M (sigma_global = M sigma_material): D_global = M D M^T.
 // ---------------------------------------------------------------------------
-static void bond_rotate(const double* C21, double theta, double* D) {
-  double Dm[6][6];
-  int k = 0;
-  for (int I = 0; I < 6; ++I)
-    for (int J = I; J < 6; ++J) {
-      Dm[I][J] = Dm[J][I] = C21[k];
-      ++k;
-    }
+// Bond matrix M(theta) for the Voigt order 11, 22, 33, 12, 13, 23 and its
+// derivative in theta (dM may be NULL).
+static void bond_matrix(double theta, double* M, double* dM) {
   const double c = std::cos(theta), s = std::sin(theta);
   const double R[3][3] = {{c, -s, 0.0}, {s, c, 0.0}, {0.0, 0.0, 1.0}};
+  const double dR[3][3] = {{-s, -c, 0.0}, {c, -s, 0.0}, {0.0, 0.0, 0.0}};
   static const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
-  double M[6][6];
   for (int I = 0; I < 6; ++I) {
     const int a = ii[I], b = jj[I];
     for (int J = 0; J < 6; ++J) {
       const int p = ii[J], q = jj[J];
-      M[I][J] = (J < 3) ? R[a][p] * R[b][q] : R[a][p] * R[b][q] + R[a][q] * R[b][p];
+      M[I * 6 + J] = (J < 3) ? R[a][p] * R[b][q] : R[a][p] * R[b][q] + R[a][q] * R[b][p];
+      if (dM)
+        dM[I * 6 + J] = (J < 3) ? dR[a][p] * R[b][q] + R[a][p] * dR[b][q]
+                                : dR[a][p] * R[b][q] + R[a][p] * dR[b][q] + dR[a][q] * R[b][p] + R[a][q] * dR[b][p];
     }
   }
-  double T[6][6];
+}
+
+static void material_matrix(const double* C21, double* Dm) {
+  int k = 0;
+  for (int I = 0; I < 6; ++I)
+    for (int J = I; J < 6; ++J) {
+      Dm[I * 6 + J] = Dm[J * 6 + I] = C21[k];
+      ++k;
+    }
+}
+
+static void bond_rotate(const double* C21, double theta, double* D) {
+  double Dm[36], M[36], T[36];
+  material_matrix(C21, Dm);
+  bond_matrix(theta, M, nullptr);
   for (int I = 0; I < 6; ++I)
     for (int J = 0; J < 6; ++J) {
       double acc = 0.0;
-      for (int K = 0; K < 6; ++K) acc += M[I][K] * Dm[K][J];
-      T[I][J] = acc;
+      for (int K = 0; K < 6; ++K) acc += M[I * 6 + K] * Dm[K * 6 + J];
+      T[I * 6 + J] = acc;
     }
   for (int I = 0; I < 6; ++I)
     for (int J = 0; J < 6; ++J) {
       double acc = 0.0;
-      for (int K = 0; K < 6; ++K) acc += T[I][K] * M[J][K];
+      for (int K = 0; K < 6; ++K) acc += T[I * 6 + K] * M[J * 6 + K];
       D[I * 6 + J] = acc;
     }
 }
@@ -342,7 +355,81 @@ lam_status rebuild_configs(Plan& P) {
             P.cfgE[(size_t)m * 81 + (c * 3 + d) * 9 + a * 3 + b] = D[voigt_index(c, a) * 6 + voigt_index(d, b)];
   }
   for (auto& pc : P.pieces) pc.cfg = P.ply_cfg[pc.ply];
+  const size_t npl = P.plies.size();
+  P.ply_M.assign(npl * 36, 0.0);
+  P.ply_dM.assign(npl * 36, 0.0);
+  P.ply_mat.assign(npl, 0);
+  for (size_t l = 0; l < npl; ++l) {
+    bond_matrix(P.plies[l].angle_rad, &P.ply_M[l * 36], &P.ply_dM[l * 36]);
+    P.ply_mat[l] = P.plies[l].material;
+  }
+  P.mat_C.assign(P.mats.size() * 36, 0.0);
+  for (size_t m = 0; m < P.mats.size(); ++m) material_matrix(P.mats[m].C, &P.mat_C[m * 36]);
   return LAM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint terms: Eq. Q restricted to each ply, for every thickness pair whose
+// common support meets the ply, grouped by ply. Geometry only (the plies'
+// positions do not change after plan creation).
+// ---------------------------------------------------------------------------
+static void build_adjoint_terms(Plan& P) {
+  const Basis& T = P.t;
+  const int nq = P.nqt, q1 = T.p + 1, npl = (int)P.plies.size();
+  std::vector<std::vector<std::pair<int, std::array<double, 4>>>> per_ply(npl);
+  for (int64_t pr = 0; pr < P.nnz_t; ++pr) {
+    const int i = P.tp_row[pr], j = P.tp_col[pr];
+    std::vector<std::array<double, 4>> acc(npl, std::array<double, 4>{0.0, 0.0, 0.0, 0.0});
+    std::vector<char> hit(npl, 0);
+    for (int e = P.tp_e0[pr]; e <= P.tp_e1[pr]; ++e) {
+      const int a = i - T.first[e], b = j - T.first[e];
+      for (int pc = P.piece_begin[e]; pc < P.piece_begin[e + 1]; ++pc) {
+        const int l = P.pieces[pc].ply;
+        hit[l] = 1;
+        for (int g = 0; g < nq; ++g) {
+          const double* tb = &P.tabT[((size_t)pc * nq + g) * q1 * 2];
+          const double w = P.wT[(size_t)pc * nq + g];
+          acc[l][0] += w * tb[a * 2] * tb[b * 2];
+          acc[l][1] += w * tb[a * 2] * tb[b * 2 + 1];
+          acc[l][2] += w * tb[a * 2 + 1] * tb[b * 2];
+          acc[l][3] += w * tb[a * 2 + 1] * tb[b * 2 + 1];
+        }
+      }
+    }
+    for (int l = 0; l < npl; ++l)
+      if (hit[l]) per_ply[l].push_back({(int)pr, acc[l]});
+  }
+  double mx[4] = {0.0, 0.0, 0.0, 0.0};
+  for (auto& v : per_ply)
+    for (auto& t : v)
+      for (int k = 0; k < 4; ++k) mx[k] = std::max(mx[k], std::fabs(t.second[k]));
+  for (int k = 0; k < 4; ++k) {
+    int e = 0;
+    std::frexp(mx[k], &e);  // mx < 2^e
+    P.adj_qscale[k] = mx[k] > 0.0 ? std::ldexp(1.0, e) : 1.0;
+  }
+  P.adj_begin.assign(npl + 1, 0);
+  P.adj_pair.clear();
+  P.adj_q.clear();
+  P.adj_qdf.clear();
+  P.adj_max_terms = 0;
+  for (int l = 0; l < npl; ++l) {
+    P.adj_begin[l] = (int)P.adj_pair.size();
+    P.adj_max_terms = std::max(P.adj_max_terms, (int)per_ply[l].size());
+    for (auto& t : per_ply[l]) {
+      P.adj_pair.push_back(t.first);
+      float hi[4], lo[4];
+      for (int k = 0; k < 4; ++k) {
+        const double q = t.second[k] / P.adj_qscale[k];
+        P.adj_q.push_back(q);
+        hi[k] = (float)q;
+        lo[k] = (float)(q - (double)hi[k]);
+      }
+      for (int k = 0; k < 4; ++k) P.adj_qdf.push_back(hi[k]);
+      for (int k = 0; k < 4; ++k) P.adj_qdf.push_back(lo[k]);
+    }
+  }
+  P.adj_begin[npl] = (int)P.adj_pair.size();
 }
 
 // ---------------------------------------------------------------------------
@@ -658,6 +745,7 @@ lam_status build_plan(Plan& P, const lam_inplane* inplane, const lam_basis1d* th
     P.tp_k[pr] = P.tp_col[pr] - P.t.lo[it];
   }
   if ((st = build_classes(P)) != LAM_OK) return st;
+  build_adjoint_terms(P);
   build_colourings(P);
   return LAM_OK;
 }

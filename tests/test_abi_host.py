@@ -178,3 +178,21 @@ def test_plan_gauss_and_rotation_via_sizes(lam):
     with pytest.raises(lam.LamError) as e:
         lam.Plan.from_laminate(L)
     assert e.value.status == 2
+
+
+def test_adjoint_rejects_invalid_cotangents(lam):
+    """Argument checks of lam_adjoint run before any device work."""
+    p = lam.Plan.from_laminate(W.cross_ply_plate())
+    L = lam.load()
+    for kind, rank, values, u, v, flags in ((7, 1, 0x1000, None, None, 0),     # unknown kind
+                                            (0, 1, None, None, None, 0),       # CSR without values
+                                            (1, 0, None, 0x1000, 0x1000, 0),   # rank 0
+                                            (1, 1, None, 0x1000, None, 0),     # v missing
+                                            (0, 1, 0x1000, None, None, 4)):    # unknown flag
+        c = lam._Cotangent()
+        c.kind, c.rank, c.values, c.u, c.v, c.flags = kind, rank, values, u, v, flags
+        st = L.lam_adjoint(p.handle, ctypes.byref(c), 0x2000, None, None, None)
+        assert st == 1, (kind, rank, flags)
+        assert "lam_adjoint" in lam.last_error()
+    assert L.lam_adjoint(p.handle, None, 0x2000, None, None, None) == 1
+

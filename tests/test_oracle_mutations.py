@@ -31,8 +31,8 @@ MUTATIONS = {
     "coxdeboor_dropped_term": ("  if (d2 > 0.0) v += (t[i + p + 1] - x) / d2 * bs_value(t, i + 1, p - 1, span, x);\n",
                                "\n"),
     # rotation by -theta
-    "rotation_sign": ("double R[3][3] = {{c, -s, 0.0}, {s, c, 0.0}, {0.0, 0.0, 1.0}};",
-                      "double R[3][3] = {{c, s, 0.0}, {-s, c, 0.0}, {0.0, 0.0, 1.0}};"),
+    "rotation_sign": ("double R[3][3] = {{c, -s, 0.0}, {s, c, 0.0}, {0.0, 0.0, 1.0}};\n  static const int pairs",
+                      "double R[3][3] = {{c, s, 0.0}, {-s, c, 0.0}, {0.0, 0.0, 1.0}};\n  static const int pairs"),
     # tensor (1/2) instead of engineering shear in gamma_12
     "half_shear": ("B[3][0] = g[1]; B[3][1] = g[0];", "B[3][0] = 0.5 * g[1]; B[3][1] = 0.5 * g[0];"),
     # Jacobian determinant dropped from the weight

@@ -102,16 +102,18 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_sha() -> str:
-    h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1905_05417_gb300", "csrc", "lam_kernels.cu"), "rb") as f:
-        h.update(f.read())
-    return h.hexdigest()
+def kernel_source_sha(kernel: str) -> str:
+    """sha256 of one kernel's definition in lam_kernels.cu (from its
+    __global__ line to the closing brace at column 0)."""
+    text = open(os.path.join(ROOT, "paper_1905_05417_gb300", "csrc", "lam_kernels.cu")).read().splitlines()
+    start = next(i for i, ln in enumerate(text) if "__global__" in ln and f" {kernel}(" in ln)
+    end = next(i for i in range(start, len(text)) if text[i] == "}")
+    return hashlib.sha256("\n".join(text[start:end + 1]).encode()).hexdigest()
 
 
-def recorded_traffic(summary: str):
-    """DRAM bytes per launch recorded by an ncu capture, if the kernel source
-    has not changed since; else None."""
+def recorded_traffic(summary: str, kernel: str):
+    """DRAM bytes per launch recorded by an ncu capture of `kernel`, if that
+    kernel's source has not changed since; else None."""
     path = os.path.join(ROOT, "profiles", summary)
     try:
         text = open(path).read()
@@ -119,7 +121,7 @@ def recorded_traffic(summary: str):
         return None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
     s = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
-    if not m or not s or s.group(1) != kernel_source_sha():
+    if not m or not s or s.group(1) != kernel_source_sha(kernel):
         return None
     return float(m.group(1))
 
@@ -271,6 +273,64 @@ def make_workload(args):
     return W.curved_plate(n_el=args.n_el, degree=3, repeats=args.repeats)
 
 
+def run_adjoint(args, L, dev, flush, peak, peak_kind, world):
+    """Gradient of L = sum(gbar * K) in the 21 constants and 24 ply angles of
+    the 32 x 32 cubic [0/90]_12 plate (94.3 M stored entries), gbar ~ N(0, 1)
+    on K's pattern from a seeded generator. Times lam_adjoint (Gram blocks,
+    contraction, chain rule) and, beside it, the split assembly of the same plate."""
+    import torch
+    import workloads as W
+    lam = W.adjoint_plate()
+    plan = L.Plan.from_laminate(lam)
+    nnz, nnz_s = plan.nnz, plan.info["nnz_inplane"]
+    gen = torch.Generator(device=dev).manual_seed(1905)
+    g = torch.randn(nnz, dtype=torch.float64, device=dev, generator=gen)
+    vals = torch.empty(nnz, dtype=torch.float64, device=dev)
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        barrier()
+        plan.profile_enable(True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            evs[k][0].record()
+            fn()
+            evs[k][1].record()
+        torch.cuda.synchronize()
+        barrier()
+        pr = plan.profile()
+        plan.profile_enable(False)
+        return max_over_ranks(sum(a.elapsed_time(b) for a, b in evs) / steps, dev), pr
+
+    steps = args.adjoint_steps
+    ms, pr = timed(lambda: plan.adjoint(values=g, want_dD=False), steps)
+    ms_fwd, _ = timed(lambda: plan.assemble_split(vals), steps)
+    ms64, _ = timed(lambda: plan.adjoint(values=g, want_dD=False, fp64=True), max(2, steps // 4))
+    k = pr["adjoint"]
+    k_ms = k["ms"] / max(1, k["launches"])
+    k_bytes = 8 * nnz + 8 * 9 * nnz_s
+    achieved = k_bytes / (k_ms / 1e3) / 1e9
+    out = {"workload": "adjoint plate: cubic B-spline 32x32 unit square, [0/90]_12 (24 plies x 0.0025), "
+                       "CSR cotangent N(0,1) (torch seed 1905), outputs dL/dC (21) and dL/dtheta (24)",
+           "metric": "cotangent entries contracted per second", "value": aggregate_throughput(nnz, world, ms / 1e3),
+           "unit": UNIT, "ms_per_step": ms, "steps": steps, "nnz": nnz,
+           "split_assembly_ms_same_plate": ms_fwd, "adjoint_over_assembly": ms / ms_fwd,
+           "fp64_pass_ms": ms64,
+           "kernels_ms_per_step": {kk: pr[kk]["ms"] / steps for kk in L.KERNEL_KINDS if pr[kk]["launches"]},
+           "gpu_launches": sum(pr[kk]["launches"] for kk in L.KERNEL_KINDS) // steps,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "traffic": recorded_traffic("adj_ply_df_adjoint_plate_p3_32x32_24plies.md", "adj_ply_df"),
+                        "kernel": "adj_ply_df", "bytes_per_launch": k_bytes, "ms_per_launch": k_ms,
+                        "peak_kind": f"{peak_kind} copy bandwidth"}}
+    plan.close()
+    del g, vals
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_lam(args):
     import torch
     rank, local, world = dist_init("nccl")
@@ -346,6 +406,9 @@ def run_lam(args):
                                 "peak_kind": "nominal FP64 rate (1.20 TFLOP/s measured by a DFMA probe)"},
                    "gpu_launches": sum(sprof[k]["launches"] for k in L.KERNEL_KINDS)}
 
+    # ---- adjoint (lam_adjoint) on the 32 x 32 cubic 24-ply plate, CSR cotangent
+    adj = run_adjoint(args, L, dev, flush, peak, peak_kind, world) if args.adjoint_steps > 0 else None
+
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if args.e2e_steps > 0:
@@ -377,8 +440,8 @@ def run_lam(args):
     kc_ms = kc["ms"] / max(1, kc["launches"])
     kc_bytes = 8 * nnz + 72 * nnz_s
     achieved = kc_bytes / (kc_ms / 1e3) / 1e9
-    summary = "kc_combine_curved_p3_64x64_48plies.md"
-    traffic = recorded_traffic(summary) if (args.n_el, args.repeats) == (64, 6) else None
+    traffic = (recorded_traffic("kc_stream_curved_p3_64x64_48plies.md", "kc_stream")
+               if (args.n_el, args.repeats) == (64, 6) else None)
     clk = clocks.summary()
     line = {
         "metric": METRIC,
@@ -390,7 +453,7 @@ def run_lam(args):
                    "l2": "256 MiB device write before every timed step (L2 is 129 MB); outputs 5.8 GB per step"},
         "step_hbm_frac": 8 * nnz / (ms / 1e3) / 1e9 / peak,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": "kc_combine", "bytes_per_launch": kc_bytes,
+                     "traffic": traffic, "kernel": "kc_stream", "bytes_per_launch": kc_bytes,
                      "ms_per_launch": kc_ms, "peak_kind": f"{peak_kind} copy bandwidth"},
         "kernels_ms_per_step": {k: prof[k]["ms"] / args.steps for k in L.KERNEL_KINDS if prof[k]["launches"]},
         "gpu_launches": launches,
@@ -402,6 +465,8 @@ def run_lam(args):
         line["speedup_split_vs_standard"] = std["ms_per_step"] / ms
     if e2e is not None:
         line["e2e"] = e2e
+    if adj is not None:
+        line["adjoint"] = adj
     if cpu is not None:
         line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
     print(json.dumps(line), flush=True)
@@ -418,6 +483,7 @@ def main(argv=None):
     ap.add_argument("--standard-steps", type=int, default=2)
     ap.add_argument("--standard-warmup", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--adjoint-steps", type=int, default=20, help="timed lam_adjoint calls (0 = skip)")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--n-el", type=int, default=64, help="in-plane elements per direction (64 = the benchmark)")

@@ -265,8 +265,9 @@ typedef enum {
   LAM_KERNEL_INPLANE = 2,   /* K-a: in-plane Gram blocks (Eq. P without D) */
   LAM_KERNEL_COMBINE = 3,   /* K-c: Eq. Km_2 into the CSR values */
   LAM_KERNEL_STANDARD = 4,  /* K-d: Section 2.4 element quadrature */
-  LAM_KERNEL_ADJOINT = 5,   /* lam_adjoint: Gram gather, ply contraction, chain rule */
-  LAM_KERNEL_KINDS = 6
+  LAM_KERNEL_ADJOINT = 5,   /* lam_adjoint: the cotangent contraction per (rows, ply) */
+  LAM_KERNEL_ADJOINT_AUX = 6, /* lam_adjoint: Gram gather and scaling, FP64 re-pass check, chain rule */
+  LAM_KERNEL_KINDS = 7
 } lam_kernel_kind;
 
 /* Per-plan profile: device time of every kernel launch, measured with CUDA

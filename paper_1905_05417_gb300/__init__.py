@@ -39,7 +39,7 @@ SYMBOLS = ("lam_plan_create", "lam_plan_destroy", "lam_plan_get_info", "lam_patt
            "lam_assemble_standard", "lam_assemble_split_host", "lam_assemble_split_noalloc", "lam_plan_update",
            "lam_adjoint", "lam_profile_enable",
            "lam_profile_get", "lam_last_error", "lam_version")
-KERNEL_KINDS = ("pattern", "thickness", "inplane", "combine", "standard", "adjoint")
+KERNEL_KINDS = ("pattern", "thickness", "inplane", "combine", "standard", "adjoint", "adjoint_aux")
 COTANGENT_CSR = 0
 COTANGENT_LOWRANK = 1
 ADJOINT_FP64 = 1
@@ -78,7 +78,7 @@ class _Options(ctypes.Structure):
 
 
 class _Profile(ctypes.Structure):
-    _fields_ = [("enabled", ctypes.c_int32), ("launches", ctypes.c_int64 * 6), ("ms", ctypes.c_double * 6),
+    _fields_ = [("enabled", ctypes.c_int32), ("launches", ctypes.c_int64 * 7), ("ms", ctypes.c_double * 7),
                 ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64)]
 
 

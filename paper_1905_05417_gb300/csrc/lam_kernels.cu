@@ -1810,6 +1810,7 @@ static lam_status adjoint(Plan& P, const lam_cotangent& cot, double* dC, double*
   adj_split<<<(unsigned)std::min<int64_t>((n9 + 255) / 256, 152 * 8), 256, 0, s>>>(n9, D.adj_G, D.adj_Gdf, D.adj_gmax,
                                                                                     gscale);
   LAM_CUDA(cudaGetLastError());
+  prof_end(P, LAM_KERNEL_ADJOINT_AUX, 2, s, ev);
   AdjArgs a{};
   a.ns = P.ns;
   a.n_dof = P.n_dof;
@@ -1842,7 +1843,7 @@ static lam_status adjoint(Plan& P, const lam_cotangent& cot, double* dC, double*
   a.emax = D.adj_flag + 1;
   const bool lowrank = cot.kind == LAM_COTANGENT_LOWRANK;
   const bool force64 = (cot.flags & LAM_ADJOINT_FP64) != 0;
-  int launched = 4;  // memsets excluded: gather, split, FP64 pass, reduce
+  ev = prof_begin(P, s);
   if (!force64) {
     a.conditional = 0;
     if (lowrank)
@@ -1854,11 +1855,17 @@ static lam_status adjoint(Plan& P, const lam_cotangent& cot, double* dC, double*
     else
       st = launch_adj_df<int64_t>(P, a, s);
     if (st != LAM_OK) return st;
-    ++launched;
+    prof_end(P, LAM_KERNEL_ADJOINT, 1, s, ev);
+    ev = prof_begin(P, s);
   }
-  a.conditional = force64 ? 0 : 1;
+  a.conditional = force64 ? 0 : 1;  // otherwise it runs only when the double-float result is rejected
   st = lowrank ? launch_adj_ply<true, false>(P, a, s) : launch_adj_ply<false, false>(P, a, s);
   if (st != LAM_OK) return st;
+  if (force64) {
+    prof_end(P, LAM_KERNEL_ADJOINT, 1, s, ev);
+    ev = prof_begin(P, s);
+  }
+  int aux = force64 ? 1 : 2;  // the reduce, and the conditional FP64 pass
   AdjReduceArgs r{};
   r.nchunks = a.nchunks;
   for (int k = 0; k < 4; ++k) r.qscale[k] = P.adj_qscale[k];
@@ -1876,9 +1883,9 @@ static lam_status adjoint(Plan& P, const lam_cotangent& cot, double* dC, double*
   if (dC) {
     adj_material<<<1, 256, 0, s>>>((int)P.plies.size(), (int)P.mats.size(), D.ply_mat, D.adj_plyC, dC);
     LAM_CUDA(cudaGetLastError());
-    ++launched;
+    ++aux;
   }
-  prof_end(P, LAM_KERNEL_ADJOINT, launched, s, ev);
+  prof_end(P, LAM_KERNEL_ADJOINT_AUX, aux, s, ev);
   return LAM_OK;
 }
 

@@ -60,6 +60,9 @@ struct Device {
   int *pair_cls = nullptr, *st_begin = nullptr, *st_cls = nullptr, *st_rep = nullptr, *st_first = nullptr;
 
   double* EG = nullptr;  // element Gram blocks: n_el x 9 x pairs
+  int* kc_flag = nullptr;      // streaming combine: FP64 re-pass flag, then the largest exponent
+  float2* cfgEdf = nullptr;    // float pairs of cfgE
+  int n_sm = 0;
   double* q = nullptr;   // nnz_t x n_cfg x 4
   // adjoint: geometry tables and workspace (allocated by the first lam_adjoint)
   bool adj_ready = false;
@@ -485,6 +488,83 @@ __device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, f
   sh = t;
 }
 
+// g = hi + lo with |g - hi - lo| <= 2^-46 |g| for 2^-80 <= |g| < 2^128: hi is
+// g truncated to 24 significant bits, lo the top 23 of the remaining 29 bits,
+// both formed from the bits of g with integer and exact float operations (no
+// FP64 arithmetic). Smaller magnitudes keep hi only (|g| >= 2^-126) or vanish;
+// larger ones, infinities and NaNs give a non-finite hi, which the caller's
+// finiteness check turns into the FP64 evaluation. Returns the biased FP64
+// exponent of g (0 for zero).
+__device__ __forceinline__ int split_df(double g, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(g);
+  const unsigned int H = (unsigned int)(b >> 32), Lw = (unsigned int)b;
+  const unsigned int sign = H & 0x80000000u;
+  const int E = (int)((H >> 20) & 0x7FFu);
+  const unsigned int nb = sign | ((unsigned int)(E - 896) << 23) | ((H & 0xFFFFFu) << 3) | (Lw >> 29);
+  hi = __int_as_float((int)((E < 897) ? sign : ((E > 1150) ? (sign | 0x7F800000u) : nb)));
+  const float r = __fsub_rn(__int_as_float((int)(0x4B000000u | ((Lw & 0x1FFFFFFFu) >> 6))), 8388608.0f);
+  const int se = (E >= 943 && E <= 1150) ? (E - 942) : 0;  // exponent field of 2^(E - 1069); 0 gives 0.0f
+  lo = __int_as_float(__float_as_int(__fmul_rn(r, __int_as_float(se << 23))) | (int)sign);
+  return E;
+}
+
+// The split of split_df for the hot loop, in fewer integer operations: valid
+// for 2^-80 <= |g| < 2^128 (biased exponent 943 ... 1150); below, hi = lo = 0.
+// Above, the result is meaningless: the caller tracks the largest exponent and
+// the FP64 pass recomputes everything when it exceeds 1150.
+__device__ __forceinline__ int split_df_fast(double g, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(g);
+  const unsigned int H = (unsigned int)(b >> 32), Lw = (unsigned int)b;
+  const int E = (int)((H >> 20) & 0x7FFu);
+  // (H << 3 | Lw >> 29) holds E mod 512 and the top 23 mantissa bits; rebias E by -896
+  const unsigned int hb = ((__funnelshift_l(Lw, H, 3) - (384u << 23)) & 0x7FFFFFFFu) | (H & 0x80000000u);
+  const unsigned int sb = (hb & 0xFF800000u) - (46u << 23);  // sign * 2^(E - 1069)
+  const float r = __fsub_rn(__int_as_float((int)(0x4B000000u | ((Lw >> 6) & 0x7FFFFFu))), 8388608.0f);
+  const bool keep = E >= 943;
+  hi = keep ? __int_as_float((int)hb) : 0.0f;
+  lo = keep ? __fmul_rn(r, __int_as_float((int)sb)) : 0.0f;
+  return E;
+}
+
+// (p, e) with p + e = a * b to about 2^-47 relative, a and b given as float pairs
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float& p, float& e) {
+  p = __fmul_rn(ah, bh);
+  e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+}
+
+// (sh, sl) += (ph, pl) by Knuth's two-sum on the high parts
+__device__ __forceinline__ void df_add(float ph, float pl, float& sh, float& sl) {
+  const float t = __fadd_rn(sh, ph);
+  const float z = __fsub_rn(t, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(ph, z));
+  sl = __fadd_rn(sl, __fadd_rn(err, pl));
+  sh = t;
+}
+
+// The double nearest (to about 2^-47 relative) to the float pair h + l,
+// |l| <= ulp(h) / 2, formed from the bits with integer operations and one FMA
+// (GB300 converts between float and double at the FP64 rate). |h| is widened
+// exactly; l, measured in units of 2^-46 of |h|'s binade, is added to the bit
+// pattern (l taken twice as large when h is a power of two and l lowers it into
+// the binade below). l is dropped for |h| < 2^-81; h = 0 gives 0.
+__device__ __forceinline__ double df_to_double(float h, float l) {
+  const unsigned int hb = __float_as_uint(h);
+  const unsigned int mag = hb & 0x7FFFFFFFu, sign = hb & 0x80000000u;
+  const int eh = (int)(mag >> 23);
+  const unsigned long long dh =
+      ((unsigned long long)((mag >> 3) + (896u << 20)) << 32) | (unsigned long long)(mag << 29);
+  const float lr = __uint_as_float(__float_as_uint(l) ^ sign);  // l relative to the sign of h
+  const int se = 300 - eh;                                      // exponent field of 2^(173 - eh)
+  const bool use_l = eh >= 46 && se <= 254;
+  const float t = __fmaf_rn(lr, __uint_as_float((unsigned int)(use_l ? se : 0) << 23), 12582912.0f);
+  long long L = (long long)(int)(__float_as_uint(t) - 0x4B400000u);
+  if ((mag & 0x7FFFFFu) == 0u && L < 0) L *= 2;
+  const unsigned long long dm = (mag == 0u) ? 0ull : dh + (unsigned long long)(L * 64);
+  return __longlong_as_double((long long)(dm | ((unsigned long long)sign << 32)));
+}
+
 __global__ void __launch_bounds__(256) ka_local(KaLocalArgs a) {
   extern __shared__ double sm[];
   const InplaneArgs& ip = a.ip;
@@ -583,6 +663,11 @@ struct KcArgs {
   int nst, slice_stride, nt;
   const int64_t* tp_A;
   const int *tp_lt, *tp_k;
+  // double-float streaming combine
+  const float2* cfgEdf;  // float pairs of cfgE
+  int* flag;             // set when the FP64 pass must recompute
+  int* emax;             // largest float exponent field of an entry
+  int conditional;       // FP64 pass: run only if *flag != 0
 };
 
 __device__ __forceinline__ int upper_pair(int a, int b, int n) { return a * n - a * (a - 1) / 2 + (b - a); }
@@ -712,46 +797,48 @@ __global__ void __launch_bounds__(1024, 2) kc_combine(KcArgs a) {
 // warp copies the three segments of one thickness pair, issuing all of a
 // segment's shared loads before its global stores. The other CTA on the SM
 // computes while this one stores.
+//
+// DF = true: phase 1 in double-float arithmetic on the FP32 pipes (G, D and Q
+// split into float pairs; products to about 2^-47, two-sums), slices turned
+// into doubles by df_to_double. A slice that is not finite, or a matrix whose
+// largest entry is below 2^-60, sets the flag; the FP64 form (DF = false,
+// conditional) then recomputes every row on the same stream.
 // ---------------------------------------------------------------------------
 constexpr int kStreamThreads = 512;
 constexpr int kSegUnroll = 6;  // 32 * 6 >= 3 * len_s for rows of at most 512 / 9 neighbours
+constexpr int kKcMinExp = 127 - 60;  // float exponent field of 2^-60
 
-template <bool MONO, bool CHUNKED>
+// P_{m,ab}[c][d] for one configuration as float pairs: MONO gives (pa, pb)
+// (the two products a monoclinic block needs), otherwise p11, p12, p21, p22.
+__device__ __forceinline__ void df_dot(const float2* __restrict__ E, const float* gh, const float* gl, int k0, int k1,
+                                       int k2, int k3, int n, float& h, float& l) {
+  const int ks[4] = {k0, k1, k2, k3};
+  h = 0.0f;
+  l = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (j < n) {
+      const float2 e = E[ks[j]];
+      float p, q;
+      df_mul(e.x, e.y, gh[ks[j]], gl[ks[j]], p, q);
+      df_add(p, q, h, l);
+    }
+  }
+  const float hs = __fadd_rn(h, l);
+  l = __fsub_rn(l, __fsub_rn(hs, h));
+  h = hs;
+}
+
+template <bool MONO, bool CHUNKED, bool DF>
 __global__ void __launch_bounds__(kStreamThreads, 2) kc_stream(KcArgs a) {
+  if (!DF && a.conditional && *a.flag == 0) return;
   extern __shared__ double sm[];
-  const int64_t is = blockIdx.x;
-  const int ix = (int)(is % a.nx), iy = (int)(is / a.nx);
-  const int lx = a.lenX[ix];
-  const int ls = lx * a.lenY[iy];
-  const int n9 = 9 * ls;
-  const int64_t ls0 = a.LSb[is];
   const int nthr = blockDim.x, tid = threadIdx.x;
   double* slices = sm;                                  // ncls x stride (the G row first)
-  double* Qs = sm + (size_t)a.ncls * a.slice_stride;    // nst x 4, terms sorted by configuration
+  double* Qs = sm + (size_t)a.ncls * a.slice_stride;    // nst x 4, terms sorted by configuration (float pairs if DF)
   int* tcls = reinterpret_cast<int*>(Qs + (size_t)a.nst * 4);
   int* tfirst = tcls + a.nst;
-  // phase 0: the row's G blocks into slices[0 .. 9 ls); Q, class and first-term flag of every term
-  for (int item = tid; item < n9; item += nthr) {
-    const int ks = item / 9, ab = item % 9;
-    const int jx = a.loX[ix] + ks % lx, jy = a.loY[iy] + ks / lx;
-    const int ex0 = max(a.eloX[ix], a.eloX[jx]), ex1 = min(a.ehiX[ix], a.ehiX[jx]);
-    const int ey0 = max(a.eloY[iy], a.eloY[jy]), ey1 = min(a.ehiY[iy], a.ehiY[jy]);
-    const int ba = (ab % 3) * 3 + ab / 3;
-    double acc = 0.0;
-    for (int ey = ey0; ey <= ey1; ++ey) {
-      const int fy = a.firstV[ey];
-      for (int ex = ex0; ex <= ex1; ++ex) {
-        const int fx = a.firstU[ex];
-        const int li = (iy - fy) * a.nlx + (ix - fx), lj = (jy - fy) * a.nlx + (jx - fx);
-        const size_t e9 = ((size_t)ey * a.nel_u + ex) * 9;
-        if (li <= lj)
-          acc += a.EG[(e9 + ab) * a.npl + upper_pair(li, lj, a.nls)];
-        else
-          acc += a.EG[(e9 + ba) * a.npl + upper_pair(lj, li, a.nls)];
-      }
-    }
-    slices[item] = acc;
-  }
+  // Q, class and first-term flag of every sorted term (the same for every row)
   for (int k = tid; k < a.nst; k += nthr) {
     tcls[k] = a.st_cls[k];
     tfirst[k] = a.st_first[k];
@@ -759,81 +846,193 @@ __global__ void __launch_bounds__(kStreamThreads, 2) kc_stream(KcArgs a) {
   for (int m = 0; m < a.ncfg; ++m)
     for (int k = a.st_begin[m] + tid; k < a.st_begin[m + 1]; k += nthr) {
       const double* src = a.q + ((size_t)a.st_rep[k] * a.ncfg + m) * 4;
-      Qs[4 * k + 0] = src[0];
-      Qs[4 * k + 1] = src[1];
-      Qs[4 * k + 2] = src[2];
-      Qs[4 * k + 3] = src[3];
-    }
-  __syncthreads();
-  const int item = tid;
-  const bool active = item < n9;
-  int c = 0, ks = 0, d = 0;
-  double g[9];
-  if (active) {
-    c = item / (3 * ls);
-    const int rem = item % (3 * ls);
-    ks = rem / 3;
-    d = rem % 3;
+      if (DF) {
+        float2* q2 = reinterpret_cast<float2*>(Qs + 4 * (size_t)k);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) g[k] = slices[ks * 9 + k];
-  }
-  __syncthreads();  // the G row is in registers; its space is reused by the slices
-  if (active) {
-    const int cd = c * 3 + d;
-    const bool block_type = ((c == 2) == (d == 2));
-    const int offa = block_type ? 0 : 1, offb = block_type ? 3 : 2;
-    for (int m = 0; m < a.ncfg; ++m) {
-      const double* E = a.cfgE + (size_t)m * 81 + cd * 9;
-      double pa, pb, p11 = 0.0, p12 = 0.0, p21 = 0.0, p22 = 0.0;
-      if (MONO) {
-        if (block_type) {
-          pa = E[0] * g[0] + E[1] * g[1] + E[3] * g[3] + E[4] * g[4];
-          pb = E[8] * g[8];
-        } else {
-          pa = E[2] * g[2] + E[5] * g[5];
-          pb = E[6] * g[6] + E[7] * g[7];
+        for (int j = 0; j < 4; ++j) {
+          float h, l;
+          split_df(src[j], h, l);
+          q2[j] = make_float2(h, l);
         }
       } else {
-        p11 = E[0] * g[0] + E[1] * g[1] + E[3] * g[3] + E[4] * g[4];
-        p12 = E[2] * g[2] + E[5] * g[5];
-        p21 = E[6] * g[6] + E[7] * g[7];
-        p22 = E[8] * g[8];
-        pa = pb = 0.0;
-      }
-      const int k1 = a.st_begin[m + 1];
-      for (int t = a.st_begin[m]; t < k1; ++t) {
-        const double v = MONO ? Qs[4 * t + offa] * pa + Qs[4 * t + offb] * pb
-                              : Qs[4 * t] * p11 + Qs[4 * t + 1] * p12 + Qs[4 * t + 2] * p21 + Qs[4 * t + 3] * p22;
-        double* dst = slices + (size_t)tcls[t] * a.slice_stride + item;
-        *dst = tfirst[t] ? v : *dst + v;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) Qs[4 * k + j] = src[j];
       }
     }
+  int emax = 0;
+  bool bad = false;
+  for (int64_t is = blockIdx.x; is < a.ns; is += gridDim.x) {
+    const int ix = (int)(is % a.nx), iy = (int)(is / a.nx);
+    const int lx = a.lenX[ix];
+    const int ls = lx * a.lenY[iy];
+    const int n9 = 9 * ls;
+    const int64_t ls0 = a.LSb[is];
+    // phase 0: the row's G blocks into slices[0 .. 9 ls)
+    for (int item = tid; item < n9; item += nthr) {
+      const int ks = item / 9, ab = item % 9;
+      const int jx = a.loX[ix] + ks % lx, jy = a.loY[iy] + ks / lx;
+      const int ex0 = max(a.eloX[ix], a.eloX[jx]), ex1 = min(a.ehiX[ix], a.ehiX[jx]);
+      const int ey0 = max(a.eloY[iy], a.eloY[jy]), ey1 = min(a.ehiY[iy], a.ehiY[jy]);
+      const int ba = (ab % 3) * 3 + ab / 3;
+      double acc = 0.0;
+      for (int ey = ey0; ey <= ey1; ++ey) {
+        const int fy = a.firstV[ey];
+        for (int ex = ex0; ex <= ex1; ++ex) {
+          const int fx = a.firstU[ex];
+          const int li = (iy - fy) * a.nlx + (ix - fx), lj = (jy - fy) * a.nlx + (jx - fx);
+          const size_t e9 = ((size_t)ey * a.nel_u + ex) * 9;
+          if (li <= lj)
+            acc += a.EG[(e9 + ab) * a.npl + upper_pair(li, lj, a.nls)];
+          else
+            acc += a.EG[(e9 + ba) * a.npl + upper_pair(lj, li, a.nls)];
+        }
+      }
+      slices[item] = acc;
+    }
+    __syncthreads();
+    const int item = tid;
+    const bool active = item < n9;
+    int c = 0, ks = 0, d = 0;
+    double g[9];
+    float gh[9], gl[9];
+    if (active) {
+      c = item / (3 * ls);
+      const int rem = item % (3 * ls);
+      ks = rem / 3;
+      d = rem % 3;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        g[k] = slices[ks * 9 + k];
+        if (DF) split_df(g[k], gh[k], gl[k]);
+      }
+    }
+    __syncthreads();  // the G row is in registers; its space is reused by the slices
+    if (active) {
+      const int cd = c * 3 + d;
+      const bool block_type = ((c == 2) == (d == 2));
+      const int offa = block_type ? 0 : 1, offb = block_type ? 3 : 2;
+      for (int m = 0; m < a.ncfg; ++m) {
+        const int k1 = a.st_begin[m + 1];
+        if (DF) {
+          const float2* E = a.cfgEdf + (size_t)m * 81 + cd * 9;
+          float ah, al, bh, bl, ch = 0.0f, cl = 0.0f, dh = 0.0f, dl = 0.0f;
+          if (MONO) {
+            if (block_type) {
+              df_dot(E, gh, gl, 0, 1, 3, 4, 4, ah, al);
+              df_dot(E, gh, gl, 8, 8, 8, 8, 1, bh, bl);
+            } else {
+              df_dot(E, gh, gl, 2, 5, 0, 0, 2, ah, al);
+              df_dot(E, gh, gl, 6, 7, 0, 0, 2, bh, bl);
+            }
+          } else {
+            df_dot(E, gh, gl, 0, 1, 3, 4, 4, ah, al);
+            df_dot(E, gh, gl, 2, 5, 0, 0, 2, bh, bl);
+            df_dot(E, gh, gl, 6, 7, 0, 0, 2, ch, cl);
+            df_dot(E, gh, gl, 8, 8, 8, 8, 1, dh, dl);
+          }
+          for (int t = a.st_begin[m]; t < k1; ++t) {
+            const float2* q2 = reinterpret_cast<const float2*>(Qs + 4 * (size_t)t);
+            float vh, vl, p, e;
+            if (MONO) {
+              const float2 qa = q2[offa], qb = q2[offb];
+              df_mul(qa.x, qa.y, ah, al, vh, vl);
+              df_mul(qb.x, qb.y, bh, bl, p, e);
+              df_add(p, e, vh, vl);
+            } else {
+              df_mul(q2[0].x, q2[0].y, ah, al, vh, vl);
+              df_mul(q2[1].x, q2[1].y, bh, bl, p, e);
+              df_add(p, e, vh, vl);
+              df_mul(q2[2].x, q2[2].y, ch, cl, p, e);
+              df_add(p, e, vh, vl);
+              df_mul(q2[3].x, q2[3].y, dh, dl, p, e);
+              df_add(p, e, vh, vl);
+            }
+            float2* dst = reinterpret_cast<float2*>(slices + (size_t)tcls[t] * a.slice_stride + item);
+            if (!tfirst[t]) {
+              const float2 o = *dst;
+              df_add(o.x, o.y, vh, vl);
+            }
+            *dst = make_float2(vh, vl);
+          }
+        } else {
+          const double* E = a.cfgE + (size_t)m * 81 + cd * 9;
+          double pa, pb, p11 = 0.0, p12 = 0.0, p21 = 0.0, p22 = 0.0;
+          if (MONO) {
+            if (block_type) {
+              pa = E[0] * g[0] + E[1] * g[1] + E[3] * g[3] + E[4] * g[4];
+              pb = E[8] * g[8];
+            } else {
+              pa = E[2] * g[2] + E[5] * g[5];
+              pb = E[6] * g[6] + E[7] * g[7];
+            }
+          } else {
+            p11 = E[0] * g[0] + E[1] * g[1] + E[3] * g[3] + E[4] * g[4];
+            p12 = E[2] * g[2] + E[5] * g[5];
+            p21 = E[6] * g[6] + E[7] * g[7];
+            p22 = E[8] * g[8];
+            pa = pb = 0.0;
+          }
+          for (int t = a.st_begin[m]; t < k1; ++t) {
+            const double v = MONO ? Qs[4 * t + offa] * pa + Qs[4 * t + offb] * pb
+                                  : Qs[4 * t] * p11 + Qs[4 * t + 1] * p12 + Qs[4 * t + 2] * p21 + Qs[4 * t + 3] * p22;
+            double* dst = slices + (size_t)tcls[t] * a.slice_stride + item;
+            *dst = tfirst[t] ? v : *dst + v;
+          }
+        }
+      }
+      if (DF) {  // float pairs -> doubles, in place (each thread its own column)
+        for (int u = 0; u < a.ncls; ++u) {
+          double* dst = slices + (size_t)u * a.slice_stride + item;
+          const float2 v = *reinterpret_cast<const float2*>(dst);
+          const float hs = __fadd_rn(v.x, v.y);
+          const float ls_ = __fsub_rn(v.y, __fsub_rn(hs, v.x));
+          const int ef = (int)((__float_as_uint(hs) >> 23) & 0xFFu);
+          bad |= (ef == 255);
+          emax = max(emax, ef);
+          *dst = df_to_double(hs, ls_);
+        }
+      }
+    }
+    __syncthreads();
+    // phase 2: thickness pairs (i_t, k_t) in address order, one warp per pair.
+    // Row (i_t, i_s, c) holds len_t segments of 3 len_s values; the pair's three
+    // segments (c = 0, 1, 2) sit one row apart. Each copy issues all of its
+    // shared loads before its global stores.
+    const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
+    const int seg_len = 3 * ls;
+    const int64_t p_begin = CHUNKED ? a.LTb[a.it_lo] : 0;
+    const int64_t p_end = CHUNKED ? a.LTb[a.it_hi] : a.LTb[a.nt];
+    for (int64_t pr = p_begin + warp; pr < p_end; pr += nwarps) {
+      const int64_t A = a.tp_A[pr];
+      const int lt = a.tp_lt[pr], kt = a.tp_k[pr], u = a.pair_cls[pr];
+      const double* src = slices + (size_t)u * a.slice_stride;
+      double* dst = a.values + (A + (int64_t)lt * 9 * ls0 + (int64_t)kt * seg_len - a.out_offset);
+      const int64_t row_step = (int64_t)lt * seg_len;
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) {
+        double v[kSegUnroll];
+#pragma unroll
+        for (int j = 0; j < kSegUnroll; ++j) v[j] = (lane + 32 * j < seg_len) ? src[cc * seg_len + lane + 32 * j] : 0.0;
+#pragma unroll
+        for (int j = 0; j < kSegUnroll; ++j)
+          if (lane + 32 * j < seg_len) dst[cc * row_step + lane + 32 * j] = v[j];
+      }
+    }
+    __syncthreads();  // the slices are rewritten by the next row
   }
-  __syncthreads();
-  // phase 2: thickness pairs (i_t, k_t) in address order, one warp per pair.
-  // Row (i_t, i_s, c) holds len_t segments of 3 len_s values; the pair's three
-  // segments (c = 0, 1, 2) sit one row apart. Each copy issues all of its
-  // shared loads before its global stores.
-  const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
-  const int seg_len = 3 * ls;
-  const int64_t p_begin = CHUNKED ? a.LTb[a.it_lo] : 0;
-  const int64_t p_end = CHUNKED ? a.LTb[a.it_hi] : a.LTb[a.nt];
-  for (int64_t pr = p_begin + warp; pr < p_end; pr += nwarps) {
-    const int64_t A = a.tp_A[pr];
-    const int lt = a.tp_lt[pr], kt = a.tp_k[pr], u = a.pair_cls[pr];
-    const double* src = slices + (size_t)u * a.slice_stride;
-    double* dst = a.values + (A + (int64_t)lt * 9 * ls0 + (int64_t)kt * seg_len - a.out_offset);
-    const int64_t row_step = (int64_t)lt * seg_len;
-#pragma unroll
-    for (int cc = 0; cc < 3; ++cc) {
-      double v[kSegUnroll];
-#pragma unroll
-      for (int j = 0; j < kSegUnroll; ++j) v[j] = (lane + 32 * j < seg_len) ? src[cc * seg_len + lane + 32 * j] : 0.0;
-#pragma unroll
-      for (int j = 0; j < kSegUnroll; ++j)
-        if (lane + 32 * j < seg_len) dst[cc * row_step + lane + 32 * j] = v[j];
+  if (DF) {
+    emax = __reduce_max_sync(0xffffffffu, emax);
+    const bool any_bad = __any_sync(0xffffffffu, bad);
+    if ((tid & 31) == 0) {
+      atomicMax(a.emax, emax);
+      if (any_bad) atomicOr(a.flag, 1);
     }
   }
+}
+
+// After the double-float pass: flag the FP64 pass when no entry reached 2^-60.
+__global__ void kc_check(int* flag, const int* emax) {
+  if (*emax < kKcMinExp) *flag = 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -1000,6 +1199,13 @@ static lam_status ensure_device(Plan& P) {
       free_device(P);
       return st;
     }
+    double* fl = nullptr;
+    if ((st = alloc_dev(L, &fl, 1)) != LAM_OK) {
+      free_device(P);
+      return st;
+    }
+    D->kc_flag = reinterpret_cast<int*>(fl);
+    LAM_CUDA(cudaDeviceGetAttribute(&D->n_sm, cudaDevAttrMultiProcessorCount, cur));
   }
   if (P.cfg_dirty) {
     Device* D = P.dev;
@@ -1021,6 +1227,15 @@ static lam_status ensure_device(Plan& P) {
     UP(L, D->occ_k, P.occ_k);
     UP(L, D->occ_it, P.occ_it);
     UP(L, D->cfgE, P.cfgE);
+    std::vector<float> edf(P.cfgE.size() * 2);
+    for (size_t k = 0; k < P.cfgE.size(); ++k) {
+      const float h = (float)P.cfgE[k];
+      edf[2 * k] = h;
+      edf[2 * k + 1] = (float)(P.cfgE[k] - (double)h);
+    }
+    float* edf_dev = nullptr;
+    UP(L, edf_dev, edf);
+    D->cfgEdf = reinterpret_cast<float2*>(edf_dev);
     UP(L, D->pair_cls, P.pair_cls);
     UP(L, D->st_begin, P.st_begin);
     UP(L, D->st_cls, P.st_cls);
@@ -1130,17 +1345,32 @@ static KcArgs kc_args(const Plan& P, double* values) {
   k.tp_A = D.tp_A;
   k.tp_lt = D.tp_lt;
   k.tp_k = D.tp_k;
+  k.cfgEdf = D.cfgEdf;
+  k.flag = D.kc_flag;
+  k.emax = D.kc_flag + 1;
+  k.conditional = 0;
   return k;
 }
 
+// Double-float pass, the exponent check, then the FP64 pass that runs only if
+// the flag is set (2 CTAs per SM, each looping over rows).
 template <bool MONO, bool CHUNKED>
 static lam_status launch_kcs(const Plan& P, const KcArgs& k, cudaStream_t s) {
   const size_t smem = kcs_smem(P);
-  LAM_CUDA(cudaFuncSetAttribute(kc_stream<MONO, CHUNKED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LAM_CUDA(cudaFuncSetAttribute(kc_stream<MONO, CHUNKED, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LAM_CUDA(cudaFuncSetAttribute(kc_stream<MONO, CHUNKED, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LAM_CUDA(cudaMemsetAsync(k.flag, 0, 2 * sizeof(int), s));
   cudaEvent_t ev = prof_begin(const_cast<Plan&>(P), s);
-  kc_stream<MONO, CHUNKED><<<(unsigned)P.ns, kStreamThreads, smem, s>>>(k);
+  kc_stream<MONO, CHUNKED, true><<<(unsigned)P.ns, kStreamThreads, smem, s>>>(k);
   LAM_CUDA(cudaGetLastError());
-  prof_end(const_cast<Plan&>(P), LAM_KERNEL_COMBINE, 1, s, ev);
+  kc_check<<<1, 1, 0, s>>>(k.flag, k.emax);
+  LAM_CUDA(cudaGetLastError());
+  KcArgs k64 = k;
+  k64.conditional = 1;
+  const int64_t grid64 = std::min<int64_t>(P.ns, 2 * (int64_t)std::max(1, P.dev->n_sm));
+  kc_stream<MONO, CHUNKED, false><<<(unsigned)grid64, kStreamThreads, smem, s>>>(k64);
+  LAM_CUDA(cudaGetLastError());
+  prof_end(const_cast<Plan&>(P), LAM_KERNEL_COMBINE, 3, s, ev);
   return LAM_OK;
 }
 
@@ -1229,61 +1459,6 @@ constexpr int kAdjBatch = 8;        // cotangent loads issued together
 constexpr int kAdjMinExp = 1023 - 60;
 // ... and likewise when an entry (low-rank: a product of entries) reaches 2^128.
 constexpr int kAdjMaxExp = 1150;
-
-// g = hi + lo with |g - hi - lo| <= 2^-46 |g| for 2^-80 <= |g| < 2^128: hi is
-// g truncated to 24 significant bits, lo the top 23 of the remaining 29 bits,
-// both formed from the bits of g with integer and exact float operations (no
-// FP64 arithmetic). Smaller magnitudes keep hi only (|g| >= 2^-126) or vanish;
-// larger ones, infinities and NaNs give a non-finite hi, which the caller's
-// finiteness check turns into the FP64 evaluation. Returns the biased FP64
-// exponent of g (0 for zero).
-__device__ __forceinline__ int split_df(double g, float& hi, float& lo) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(g);
-  const unsigned int H = (unsigned int)(b >> 32), Lw = (unsigned int)b;
-  const unsigned int sign = H & 0x80000000u;
-  const int E = (int)((H >> 20) & 0x7FFu);
-  const unsigned int nb = sign | ((unsigned int)(E - 896) << 23) | ((H & 0xFFFFFu) << 3) | (Lw >> 29);
-  hi = __int_as_float((int)((E < 897) ? sign : ((E > 1150) ? (sign | 0x7F800000u) : nb)));
-  const float r = __fsub_rn(__int_as_float((int)(0x4B000000u | ((Lw & 0x1FFFFFFFu) >> 6))), 8388608.0f);
-  const int se = (E >= 943 && E <= 1150) ? (E - 942) : 0;  // exponent field of 2^(E - 1069); 0 gives 0.0f
-  lo = __int_as_float(__float_as_int(__fmul_rn(r, __int_as_float(se << 23))) | (int)sign);
-  return E;
-}
-
-// The split of split_df for the hot loop, in fewer integer operations: valid
-// for 2^-80 <= |g| < 2^128 (biased exponent 943 ... 1150); below, hi = lo = 0.
-// Above, the result is meaningless: the caller tracks the largest exponent and
-// the FP64 pass recomputes everything when it exceeds 1150.
-__device__ __forceinline__ int split_df_fast(double g, float& hi, float& lo) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(g);
-  const unsigned int H = (unsigned int)(b >> 32), Lw = (unsigned int)b;
-  const int E = (int)((H >> 20) & 0x7FFu);
-  // (H << 3 | Lw >> 29) holds E mod 512 and the top 23 mantissa bits; rebias E by -896
-  const unsigned int hb = ((__funnelshift_l(Lw, H, 3) - (384u << 23)) & 0x7FFFFFFFu) | (H & 0x80000000u);
-  const unsigned int sb = (hb & 0xFF800000u) - (46u << 23);  // sign * 2^(E - 1069)
-  const float r = __fsub_rn(__int_as_float((int)(0x4B000000u | ((Lw >> 6) & 0x7FFFFFu))), 8388608.0f);
-  const bool keep = E >= 943;
-  hi = keep ? __int_as_float((int)hb) : 0.0f;
-  lo = keep ? __fmul_rn(r, __int_as_float((int)sb)) : 0.0f;
-  return E;
-}
-
-// (p, e) with p + e = a * b to about 2^-47 relative, a and b given as float pairs
-__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float& p, float& e) {
-  p = __fmul_rn(ah, bh);
-  e = __fmaf_rn(ah, bh, -p);
-  e = __fmaf_rn(ah, bl, e);
-  e = __fmaf_rn(al, bh, e);
-}
-
-// (sh, sl) += (ph, pl) by Knuth's two-sum on the high parts
-__device__ __forceinline__ void df_add(float ph, float pl, float& sh, float& sl) {
-  const float t = __fadd_rn(sh, ph);
-  const float z = __fsub_rn(t, sh);
-  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(ph, z));
-  sl = __fadd_rn(sl, __fadd_rn(err, pl));
-  sh = t;
-}
 
 struct AdjGatherArgs {
   int nx, nel_u, nlx, nls, npl;

@@ -526,6 +526,20 @@ __device__ __forceinline__ int split_df_fast(double g, float& hi, float& lo) {
   return E;
 }
 
+// split_df_fast of g * 2^-k (exact scaling folded into the exponent rebias):
+// valid when g * 2^-k lies in [2^-80, 2^128); smaller scaled values give 0.
+__device__ __forceinline__ void split_df_off(double g, int k, float& hi, float& lo) {
+  const unsigned int H = (unsigned int)__double2hiint(g), Lw = (unsigned int)__double2loint(g);
+  const int E = (int)((H >> 20) & 0x7FFu);
+  const unsigned int hb =
+      ((__funnelshift_l(Lw, H, 3) - (((unsigned int)(384 + k) & 511u) << 23)) & 0x7FFFFFFFu) | (H & 0x80000000u);
+  const unsigned int sb = (hb & 0xFF800000u) - (46u << 23);
+  const float r = __fsub_rn(__int_as_float((int)(0x4B000000u | ((Lw >> 6) & 0x7FFFFFu))), 8388608.0f);
+  const bool keep = E - k >= 943 && E - k <= 1150;
+  hi = keep ? __int_as_float((int)hb) : 0.0f;
+  lo = keep ? __fmul_rn(r, __int_as_float((int)sb)) : 0.0f;
+}
+
 // (p, e) with p + e = a * b to about 2^-47 relative, a and b given as float pairs
 __device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float& p, float& e) {
   p = __fmul_rn(ah, bh);
@@ -574,7 +588,23 @@ __global__ void __launch_bounds__(256) ka_local(KaLocalArgs a) {
   double* qd = phiw + (size_t)nqs * nls * 3;
   const int e = blockIdx.x;
   const int ex = e % ip.nel_u, ey = e / ip.nel_u;
+  __shared__ int s_emax[2];
+  if (threadIdx.x < 2) s_emax[threadIdx.x] = 0;
   inplane_points(ip, ex, ey, phi, phiw, qd);
+  // Per element, the point values are scaled by powers of two so that the
+  // largest lies in [1, 2) (exact), which keeps the float pairs far from float
+  // overflow and underflow whatever the geometry's scale; EG is scaled back.
+  {
+    int ep = 0, ew = 0;
+    for (int t = threadIdx.x; t < nqs * nls * 3; t += blockDim.x) {
+      ep = max(ep, (__double2hiint(phi[t]) >> 20) & 0x7FF);
+      ew = max(ew, (__double2hiint(phiw[t]) >> 20) & 0x7FF);
+    }
+    atomicMax(&s_emax[0], ep);
+    atomicMax(&s_emax[1], ew);
+  }
+  __syncthreads();
+  const int kp = s_emax[0] > 0 ? s_emax[0] - 1023 : 0, kw = s_emax[1] > 0 ? s_emax[1] - 1023 : 0;
   // FP64 point values -> float pairs (hi0 hi1 hi2 lo0 lo1 lo2), in place
   float* phf = reinterpret_cast<float*>(phi);
   float* pwf = reinterpret_cast<float*>(phiw);
@@ -588,11 +618,13 @@ __global__ void __launch_bounds__(256) ka_local(KaLocalArgs a) {
     // each item's 6 floats overwrite exactly its own 3 doubles (no other item's)
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const float vh = __double2float_rn(v[k]), wh = __double2float_rn(w[k]);
-      phf[(size_t)t * 6 + k] = vh;
-      phf[(size_t)t * 6 + 3 + k] = __double2float_rn(v[k] - (double)vh);
-      pwf[(size_t)t * 6 + k] = wh;
-      pwf[(size_t)t * 6 + 3 + k] = __double2float_rn(w[k] - (double)wh);
+      float h, l;
+      split_df_off(v[k], kp, h, l);
+      phf[(size_t)t * 6 + k] = h;
+      phf[(size_t)t * 6 + 3 + k] = l;
+      split_df_off(w[k], kw, h, l);
+      pwf[(size_t)t * 6 + k] = h;
+      pwf[(size_t)t * 6 + 3 + k] = l;
     }
   }
   __syncthreads();
@@ -625,7 +657,13 @@ __global__ void __launch_bounds__(256) ka_local(KaLocalArgs a) {
         for (int y = 0; y < 3; ++y) df_mac(ah[x], al[x], bh[y], bl[y], sh[x * 3 + y], sl[x * 3 + y]);
     }
 #pragma unroll
-    for (int k = 0; k < 9; ++k) out[(size_t)k * npl + t] = (double)sh[k] + (double)sl[k];
+    for (int k = 0; k < 9; ++k) {
+      const float hs = __fadd_rn(sh[k], sl[k]);
+      const float ls = __fsub_rn(sl[k], __fsub_rn(hs, sh[k]));
+      long long b = __double_as_longlong(df_to_double(hs, ls));
+      if (b & 0x7FFFFFFFFFFFFFFFll) b += (long long)(kp + kw) * (1ll << 52);  // times 2^(kp + kw), exact
+      out[(size_t)k * npl + t] = __longlong_as_double(b);
+    }
   }
 }
 

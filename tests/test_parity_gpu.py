@@ -217,3 +217,26 @@ def test_curved_plate_full_size_sampled_split(L):
 
 def test_adjoint_plate_full_size_sampled_standard(L):
     _sampled_parity(L, W.adjoint_plate(), "standard", n_rows=60, seed=1)
+
+
+# ---------------------------------------------------------------- scale robustness of the double-float steps
+@pytest.mark.parametrize("scale", [2.0 ** -90, 2.0 ** 90])
+def test_extreme_geometry_scale(L, scale):
+    """In-plane coordinates scaled by 2^+-90: K-a's per-element power-of-two
+    scaling keeps its float pairs in range; entries of K then span ~2^360, the
+    largest ones overflow float in the combine's double-float pass (2^90) and
+    the FP64 pass recomputes."""
+    curved = W.curved_map(0.04)
+    lam = W.laminate("geom", W.BSPLINE, 2, 3, [0, 45, 90], 0.01,
+                     mapping=lambda xi, eta: tuple(scale * c for c in curved(xi, eta)))
+    assert_parity(gpu_matrix(L, lam, "split"), O.assemble(lam))
+
+
+@pytest.mark.parametrize("scale", [2.0 ** -200, 2.0 ** 200])
+def test_extreme_material_scale(L, scale):
+    """Constants scaled by 2^+-200: every entry of K is beyond float range, the
+    combine's double-float pass flags it and the FP64 pass recomputes."""
+    lam = W.curved_plate(n_el=3, degree=3, repeats=1)
+    lam.C21 = lam.C21 * scale
+    got = gpu_matrix(L, lam, "split")
+    assert_parity(got, O.assemble(lam))

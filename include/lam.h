@@ -124,9 +124,10 @@ typedef struct {
   int32_t n_classes;      /* distinct thickness slices used by the combine */
   int32_t monoclinic;     /* 1 if every configuration has D[I][J] == 0 for I < 4 <= J */
   int32_t n_pieces;       /* (thickness element, ply) pieces */
-  int32_t combine_streaming; /* form of the combine: 1 streaming (a row's class slices in shared memory,
-                                CSR written in address order), 0 class-major (rows too large or too many
-                                classes for shared memory) */
+  int32_t combine_streaming; /* form of the combine: 1 streaming (one CTA per in-plane row, class slices in
+                                shared memory, CSR written in address order), 0 class-major (rows of more
+                                than 56 in-plane neighbours) */
+  int32_t combine_chunks;    /* streaming: chunks of thickness rows whose classes fit in shared memory */
 } lam_plan_info;
 
 typedef struct lam_plan lam_plan;

@@ -92,7 +92,7 @@ class _Info(ctypes.Structure):
     _fields_ = [("n_dof", ctypes.c_int64), ("nnz", ctypes.c_int64), ("n_s", ctypes.c_int64), ("n_t", ctypes.c_int64),
                 ("nnz_inplane", ctypes.c_int64), ("nnz_thickness", ctypes.c_int64), ("n_configs", ctypes.c_int32),
                 ("n_classes", ctypes.c_int32), ("monoclinic", ctypes.c_int32), ("n_pieces", ctypes.c_int32),
-                ("combine_streaming", ctypes.c_int32)]
+                ("combine_streaming", ctypes.c_int32), ("combine_chunks", ctypes.c_int32)]
 
 
 _lib = None

@@ -80,9 +80,16 @@ struct Plan {
   int ncls = 0;
   std::vector<int> cls_rep;              // representative pair of each class
   std::vector<int> pair_cls;             // class of every thickness pair
-  std::vector<int> st_begin;             // class terms sorted by configuration: [m] range, size n_cfg + 1
-  std::vector<int> st_cls, st_rep, st_cfg;  // class, representative pair and configuration of each sorted term
-  std::vector<int> st_first;                // 1 if the sorted term is the first one of its class
+  std::vector<std::vector<int>> cls_cfgs;  // configurations with nonzero Q of every class
+  // streaming combine, in thickness chunks: chunk ch covers thickness rows
+  // [ck_it[ch], ck_it[ch + 1]); the classes of its pairs take slots
+  // 0 .. ck_nslot[ch] - 1 of the row's shared-memory slices; its terms
+  // (slot, configuration, representative pair), sorted by configuration, are
+  // ck_term[ch] .. ck_term[ch + 1] - 1; ckt_first marks the first term of a slot.
+  int kc_slots = 0;                      // slots that fit in shared memory
+  std::vector<int> ck_it, ck_term, ck_nslot;
+  std::vector<int> ckt_slot, ckt_cfg, ckt_rep, ckt_first;
+  std::vector<int> pair_slot;            // slot of every thickness pair within its chunk
   std::vector<int> cls_term_begin;       // size ncls + 1
   std::vector<int> cls_terms;            // configuration ids with nonzero Q
   std::vector<int> cls_occ_begin;        // size ncls + 1
@@ -131,7 +138,9 @@ struct Plan {
 
 // Launch geometry of the combine shared by host and device code: the
 // streaming form keeps a row's class slices in shared memory (one 512-thread
-// CTA per row, two per SM); otherwise the class-major form runs.
+// CTA per row, two per SM), a chunk of thickness rows at a time; rows of more
+// than 512 / 9 in-plane neighbours take the class-major form.
+constexpr size_t kSliceBudget = 110 * 1024;  // shared memory for the slices of one CTA
 inline int max_len_s(const Plan& P) {
   int mx = 0, my = 0;
   for (int v : P.u.len) mx = mx > v ? mx : v;
@@ -139,17 +148,24 @@ inline int max_len_s(const Plan& P) {
   return mx * my;
 }
 inline int kcs_stride(const Plan& P) { return 9 * max_len_s(P); }
-inline size_t kcs_smem(const Plan& P) {
-  size_t b = (size_t)P.ncls * kcs_stride(P) * sizeof(double) +      // class slices (the G row first)
-             P.st_cls.size() * (4 * sizeof(double) + 2 * sizeof(int));  // sorted terms: Q, class, flag
-  return (b + 15) & ~(size_t)15;
+inline int kcs_max_terms(const Plan& P) {
+  int mt = 1;
+  for (size_t ch = 0; ch + 1 < P.ck_term.size(); ++ch) mt = mt > P.ck_term[ch + 1] - P.ck_term[ch] ? mt : P.ck_term[ch + 1] - P.ck_term[ch];
+  return mt;
 }
-inline bool use_stream(const Plan& P) { return 9 * max_len_s(P) <= 512 && kcs_smem(P) <= 110 * 1024; }
+inline size_t kcs_smem(const Plan& P) {
+  int slots = 1;
+  for (int v : P.ck_nslot) slots = slots > v ? slots : v;
+  // slices, then per term of a chunk: Q (4 float pairs or 4 doubles), slot, first flag, configuration
+  return (size_t)slots * kcs_stride(P) * sizeof(double) + (size_t)kcs_max_terms(P) * (32 + 12) + 16;
+}
+inline bool use_stream(const Plan& P) { return 9 * max_len_s(P) <= 512 && !P.ck_nslot.empty(); }
 
 // lam_plan.cpp
 lam_status build_plan(Plan& P, const lam_inplane* inplane, const lam_basis1d* thickness, const lam_ply* plies,
                       int32_t n_plies, const lam_material* materials, int32_t n_materials, const lam_options* opt);
 lam_status rebuild_configs(Plan& P);
+void build_chunks(Plan& P);
 void set_error(const char* fmt, ...);
 void free_device(Plan& P);  // lam_kernels.cu
 

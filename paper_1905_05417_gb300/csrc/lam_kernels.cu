@@ -57,7 +57,10 @@ struct Device {
   int* col3_elem = nullptr;
   // workspace
   int *eloX = nullptr, *ehiX = nullptr, *eloY = nullptr, *ehiY = nullptr;
-  int *pair_cls = nullptr, *st_begin = nullptr, *st_cls = nullptr, *st_rep = nullptr, *st_first = nullptr;
+  int* pair_cls = nullptr;
+  int *ck_it = nullptr, *ck_term = nullptr, *ck_nslot = nullptr, *pair_slot = nullptr;
+  int *ckt_slot = nullptr, *ckt_cfg = nullptr, *ckt_rep = nullptr, *ckt_first = nullptr;
+  float2* qdf = nullptr;  // float pairs of q
 
   double* EG = nullptr;  // element Gram blocks: n_el x 9 x pairs
   int* kc_flag = nullptr;      // streaming combine: FP64 re-pass flag, then the largest exponent
@@ -269,12 +272,124 @@ __global__ void kp_col_ind(PatArgs a, int32_t* __restrict__ col) {
 // ---------------------------------------------------------------------------
 // K-b: thickness pair integrals (Eq. Q), summed per configuration.
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Double-float arithmetic (pairs of floats on the FP32 pipes)
+// ---------------------------------------------------------------------------
+// a * b added to the double-float accumulator (sh, sl), with a = ah + al and
+// b = bh + bl split into float pairs. The product is taken to about 2^-48
+// relative (the rounding error of ah * bh by FMA, plus the two cross terms;
+// al * bl is below that), the sum by Knuth's two-sum. Intrinsics keep the
+// compiler from contracting the error-free transformations.
+__device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, float& sh, float& sl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+  const float t = __fadd_rn(sh, p);
+  const float z = __fsub_rn(t, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(p, z));
+  sl = __fadd_rn(sl, __fadd_rn(err, e));
+  sh = t;
+}
+
+// g = hi + lo with |g - hi - lo| <= 2^-46 |g| for 2^-80 <= |g| < 2^128: hi is
+// g truncated to 24 significant bits, lo the top 23 of the remaining 29 bits,
+// both formed from the bits of g with integer and exact float operations (no
+// FP64 arithmetic). Smaller magnitudes keep hi only (|g| >= 2^-126) or vanish;
+// larger ones, infinities and NaNs give a non-finite hi, which the caller's
+// finiteness check turns into the FP64 evaluation. Returns the biased FP64
+// exponent of g (0 for zero).
+__device__ __forceinline__ int split_df(double g, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(g);
+  const unsigned int H = (unsigned int)(b >> 32), Lw = (unsigned int)b;
+  const unsigned int sign = H & 0x80000000u;
+  const int E = (int)((H >> 20) & 0x7FFu);
+  const unsigned int nb = sign | ((unsigned int)(E - 896) << 23) | ((H & 0xFFFFFu) << 3) | (Lw >> 29);
+  hi = __int_as_float((int)((E < 897) ? sign : ((E > 1150) ? (sign | 0x7F800000u) : nb)));
+  const float r = __fsub_rn(__int_as_float((int)(0x4B000000u | ((Lw & 0x1FFFFFFFu) >> 6))), 8388608.0f);
+  const int se = (E >= 943 && E <= 1150) ? (E - 942) : 0;  // exponent field of 2^(E - 1069); 0 gives 0.0f
+  lo = __int_as_float(__float_as_int(__fmul_rn(r, __int_as_float(se << 23))) | (int)sign);
+  return E;
+}
+
+// The split of split_df for the hot loop, in fewer integer operations: valid
+// for 2^-80 <= |g| < 2^128 (biased exponent 943 ... 1150); below, hi = lo = 0.
+// Above, the result is meaningless: the caller tracks the largest exponent and
+// the FP64 pass recomputes everything when it exceeds 1150.
+__device__ __forceinline__ int split_df_fast(double g, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(g);
+  const unsigned int H = (unsigned int)(b >> 32), Lw = (unsigned int)b;
+  const int E = (int)((H >> 20) & 0x7FFu);
+  // (H << 3 | Lw >> 29) holds E mod 512 and the top 23 mantissa bits; rebias E by -896
+  const unsigned int hb = ((__funnelshift_l(Lw, H, 3) - (384u << 23)) & 0x7FFFFFFFu) | (H & 0x80000000u);
+  const unsigned int sb = (hb & 0xFF800000u) - (46u << 23);  // sign * 2^(E - 1069)
+  const float r = __fsub_rn(__int_as_float((int)(0x4B000000u | ((Lw >> 6) & 0x7FFFFFu))), 8388608.0f);
+  const bool keep = E >= 943;
+  hi = keep ? __int_as_float((int)hb) : 0.0f;
+  lo = keep ? __fmul_rn(r, __int_as_float((int)sb)) : 0.0f;
+  return E;
+}
+
+// split_df_fast of g * 2^-k (exact scaling folded into the exponent rebias):
+// valid when g * 2^-k lies in [2^-80, 2^128); smaller scaled values give 0.
+__device__ __forceinline__ void split_df_off(double g, int k, float& hi, float& lo) {
+  const unsigned int H = (unsigned int)__double2hiint(g), Lw = (unsigned int)__double2loint(g);
+  const int E = (int)((H >> 20) & 0x7FFu);
+  const unsigned int hb =
+      ((__funnelshift_l(Lw, H, 3) - (((unsigned int)(384 + k) & 511u) << 23)) & 0x7FFFFFFFu) | (H & 0x80000000u);
+  const unsigned int sb = (hb & 0xFF800000u) - (46u << 23);
+  const float r = __fsub_rn(__int_as_float((int)(0x4B000000u | ((Lw >> 6) & 0x7FFFFFu))), 8388608.0f);
+  const bool keep = E - k >= 943 && E - k <= 1150;
+  hi = keep ? __int_as_float((int)hb) : 0.0f;
+  lo = keep ? __fmul_rn(r, __int_as_float((int)sb)) : 0.0f;
+}
+
+// (p, e) with p + e = a * b to about 2^-47 relative, a and b given as float pairs
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float& p, float& e) {
+  p = __fmul_rn(ah, bh);
+  e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+}
+
+// (sh, sl) += (ph, pl) by Knuth's two-sum on the high parts
+__device__ __forceinline__ void df_add(float ph, float pl, float& sh, float& sl) {
+  const float t = __fadd_rn(sh, ph);
+  const float z = __fsub_rn(t, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(ph, z));
+  sl = __fadd_rn(sl, __fadd_rn(err, pl));
+  sh = t;
+}
+
+// The double nearest (to about 2^-47 relative) to the float pair h + l,
+// |l| <= ulp(h) / 2, formed from the bits with integer operations and one FMA
+// (GB300 converts between float and double at the FP64 rate). |h| is widened
+// exactly; l, measured in units of 2^-46 of |h|'s binade, is added to the bit
+// pattern (l taken twice as large when h is a power of two and l lowers it into
+// the binade below). l is dropped for |h| < 2^-81; h = 0 gives 0.
+__device__ __forceinline__ double df_to_double(float h, float l) {
+  const unsigned int hb = __float_as_uint(h);
+  const unsigned int mag = hb & 0x7FFFFFFFu, sign = hb & 0x80000000u;
+  const int eh = (int)(mag >> 23);
+  const unsigned long long dh =
+      ((unsigned long long)((mag >> 3) + (896u << 20)) << 32) | (unsigned long long)(mag << 29);
+  const float lr = __uint_as_float(__float_as_uint(l) ^ sign);  // l relative to the sign of h
+  const int se = 300 - eh;                                      // exponent field of 2^(173 - eh)
+  const bool use_l = eh >= 46 && se <= 254;
+  const float t = __fmaf_rn(lr, __uint_as_float((unsigned int)(use_l ? se : 0) << 23), 12582912.0f);
+  long long L = (long long)(int)(__float_as_uint(t) - 0x4B400000u);
+  if ((mag & 0x7FFFFFu) == 0u && L < 0) L *= 2;
+  const unsigned long long dm = (mag == 0u) ? 0ull : dh + (unsigned long long)(L * 64);
+  return __longlong_as_double((long long)(dm | ((unsigned long long)sign << 32)));
+}
+
 struct KbArgs {
   int64_t npairs;
   int ncfg, nqt, q1;
   const int *tp_row, *tp_col, *tp_e0, *tp_e1, *firstT, *piece_begin, *piece_cfg;
   const double *tabT, *wT;
   double* q;
+  float2* qdf;  // float pairs of q (may be NULL)
 };
 
 __global__ void kb_thickness(KbArgs a) {
@@ -303,6 +418,12 @@ __global__ void kb_thickness(KbArgs a) {
       o[3] += q22;
     }
   }
+  if (a.qdf)
+    for (int k = 0; k < a.ncfg * 4; ++k) {
+      float h, l;
+      split_df(out[k], h, l);
+      a.qdf[pr * a.ncfg * 4 + k] = make_float2(h, l);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -471,114 +592,6 @@ struct KaLocalArgs {
   double* EG;
 };
 
-// a * b added to the double-float accumulator (sh, sl), with a = ah + al and
-// b = bh + bl split into float pairs. The product is taken to about 2^-48
-// relative (the rounding error of ah * bh by FMA, plus the two cross terms;
-// al * bl is below that), the sum by Knuth's two-sum. Intrinsics keep the
-// compiler from contracting the error-free transformations.
-__device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, float& sh, float& sl) {
-  const float p = __fmul_rn(ah, bh);
-  float e = __fmaf_rn(ah, bh, -p);
-  e = __fmaf_rn(ah, bl, e);
-  e = __fmaf_rn(al, bh, e);
-  const float t = __fadd_rn(sh, p);
-  const float z = __fsub_rn(t, sh);
-  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(p, z));
-  sl = __fadd_rn(sl, __fadd_rn(err, e));
-  sh = t;
-}
-
-// g = hi + lo with |g - hi - lo| <= 2^-46 |g| for 2^-80 <= |g| < 2^128: hi is
-// g truncated to 24 significant bits, lo the top 23 of the remaining 29 bits,
-// both formed from the bits of g with integer and exact float operations (no
-// FP64 arithmetic). Smaller magnitudes keep hi only (|g| >= 2^-126) or vanish;
-// larger ones, infinities and NaNs give a non-finite hi, which the caller's
-// finiteness check turns into the FP64 evaluation. Returns the biased FP64
-// exponent of g (0 for zero).
-__device__ __forceinline__ int split_df(double g, float& hi, float& lo) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(g);
-  const unsigned int H = (unsigned int)(b >> 32), Lw = (unsigned int)b;
-  const unsigned int sign = H & 0x80000000u;
-  const int E = (int)((H >> 20) & 0x7FFu);
-  const unsigned int nb = sign | ((unsigned int)(E - 896) << 23) | ((H & 0xFFFFFu) << 3) | (Lw >> 29);
-  hi = __int_as_float((int)((E < 897) ? sign : ((E > 1150) ? (sign | 0x7F800000u) : nb)));
-  const float r = __fsub_rn(__int_as_float((int)(0x4B000000u | ((Lw & 0x1FFFFFFFu) >> 6))), 8388608.0f);
-  const int se = (E >= 943 && E <= 1150) ? (E - 942) : 0;  // exponent field of 2^(E - 1069); 0 gives 0.0f
-  lo = __int_as_float(__float_as_int(__fmul_rn(r, __int_as_float(se << 23))) | (int)sign);
-  return E;
-}
-
-// The split of split_df for the hot loop, in fewer integer operations: valid
-// for 2^-80 <= |g| < 2^128 (biased exponent 943 ... 1150); below, hi = lo = 0.
-// Above, the result is meaningless: the caller tracks the largest exponent and
-// the FP64 pass recomputes everything when it exceeds 1150.
-__device__ __forceinline__ int split_df_fast(double g, float& hi, float& lo) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(g);
-  const unsigned int H = (unsigned int)(b >> 32), Lw = (unsigned int)b;
-  const int E = (int)((H >> 20) & 0x7FFu);
-  // (H << 3 | Lw >> 29) holds E mod 512 and the top 23 mantissa bits; rebias E by -896
-  const unsigned int hb = ((__funnelshift_l(Lw, H, 3) - (384u << 23)) & 0x7FFFFFFFu) | (H & 0x80000000u);
-  const unsigned int sb = (hb & 0xFF800000u) - (46u << 23);  // sign * 2^(E - 1069)
-  const float r = __fsub_rn(__int_as_float((int)(0x4B000000u | ((Lw >> 6) & 0x7FFFFFu))), 8388608.0f);
-  const bool keep = E >= 943;
-  hi = keep ? __int_as_float((int)hb) : 0.0f;
-  lo = keep ? __fmul_rn(r, __int_as_float((int)sb)) : 0.0f;
-  return E;
-}
-
-// split_df_fast of g * 2^-k (exact scaling folded into the exponent rebias):
-// valid when g * 2^-k lies in [2^-80, 2^128); smaller scaled values give 0.
-__device__ __forceinline__ void split_df_off(double g, int k, float& hi, float& lo) {
-  const unsigned int H = (unsigned int)__double2hiint(g), Lw = (unsigned int)__double2loint(g);
-  const int E = (int)((H >> 20) & 0x7FFu);
-  const unsigned int hb =
-      ((__funnelshift_l(Lw, H, 3) - (((unsigned int)(384 + k) & 511u) << 23)) & 0x7FFFFFFFu) | (H & 0x80000000u);
-  const unsigned int sb = (hb & 0xFF800000u) - (46u << 23);
-  const float r = __fsub_rn(__int_as_float((int)(0x4B000000u | ((Lw >> 6) & 0x7FFFFFu))), 8388608.0f);
-  const bool keep = E - k >= 943 && E - k <= 1150;
-  hi = keep ? __int_as_float((int)hb) : 0.0f;
-  lo = keep ? __fmul_rn(r, __int_as_float((int)sb)) : 0.0f;
-}
-
-// (p, e) with p + e = a * b to about 2^-47 relative, a and b given as float pairs
-__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float& p, float& e) {
-  p = __fmul_rn(ah, bh);
-  e = __fmaf_rn(ah, bh, -p);
-  e = __fmaf_rn(ah, bl, e);
-  e = __fmaf_rn(al, bh, e);
-}
-
-// (sh, sl) += (ph, pl) by Knuth's two-sum on the high parts
-__device__ __forceinline__ void df_add(float ph, float pl, float& sh, float& sl) {
-  const float t = __fadd_rn(sh, ph);
-  const float z = __fsub_rn(t, sh);
-  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(ph, z));
-  sl = __fadd_rn(sl, __fadd_rn(err, pl));
-  sh = t;
-}
-
-// The double nearest (to about 2^-47 relative) to the float pair h + l,
-// |l| <= ulp(h) / 2, formed from the bits with integer operations and one FMA
-// (GB300 converts between float and double at the FP64 rate). |h| is widened
-// exactly; l, measured in units of 2^-46 of |h|'s binade, is added to the bit
-// pattern (l taken twice as large when h is a power of two and l lowers it into
-// the binade below). l is dropped for |h| < 2^-81; h = 0 gives 0.
-__device__ __forceinline__ double df_to_double(float h, float l) {
-  const unsigned int hb = __float_as_uint(h);
-  const unsigned int mag = hb & 0x7FFFFFFFu, sign = hb & 0x80000000u;
-  const int eh = (int)(mag >> 23);
-  const unsigned long long dh =
-      ((unsigned long long)((mag >> 3) + (896u << 20)) << 32) | (unsigned long long)(mag << 29);
-  const float lr = __uint_as_float(__float_as_uint(l) ^ sign);  // l relative to the sign of h
-  const int se = 300 - eh;                                      // exponent field of 2^(173 - eh)
-  const bool use_l = eh >= 46 && se <= 254;
-  const float t = __fmaf_rn(lr, __uint_as_float((unsigned int)(use_l ? se : 0) << 23), 12582912.0f);
-  long long L = (long long)(int)(__float_as_uint(t) - 0x4B400000u);
-  if ((mag & 0x7FFFFFu) == 0u && L < 0) L *= 2;
-  const unsigned long long dm = (mag == 0u) ? 0ull : dh + (unsigned long long)(L * 64);
-  return __longlong_as_double((long long)(dm | ((unsigned long long)sign << 32)));
-}
-
 __global__ void __launch_bounds__(256) ka_local(KaLocalArgs a) {
   extern __shared__ double sm[];
   const InplaneArgs& ip = a.ip;
@@ -697,8 +710,10 @@ struct KcArgs {
   // streaming combine
   const int64_t* LTb;
   const int* pair_cls;
-  const int *st_begin, *st_cls, *st_rep, *st_first;
-  int nst, slice_stride, nt;
+  int nchunk, slice_stride, nt, nslot_max, max_terms;
+  const int *ck_it, *ck_term, *ck_nslot, *pair_slot;
+  const int *ckt_slot, *ckt_cfg, *ckt_rep, *ckt_first;
+  const float2* qdf;
   const int64_t* tp_A;
   const int *tp_lt, *tp_k;
   // double-float streaming combine
@@ -872,31 +887,11 @@ __global__ void __launch_bounds__(kStreamThreads, 2) kc_stream(KcArgs a) {
   if (!DF && a.conditional && *a.flag == 0) return;
   extern __shared__ double sm[];
   const int nthr = blockDim.x, tid = threadIdx.x;
-  double* slices = sm;                                  // ncls x stride (the G row first)
-  double* Qs = sm + (size_t)a.ncls * a.slice_stride;    // nst x 4, terms sorted by configuration (float pairs if DF)
-  int* tcls = reinterpret_cast<int*>(Qs + (size_t)a.nst * 4);
-  int* tfirst = tcls + a.nst;
-  // Q, class and first-term flag of every sorted term (the same for every row)
-  for (int k = tid; k < a.nst; k += nthr) {
-    tcls[k] = a.st_cls[k];
-    tfirst[k] = a.st_first[k];
-  }
-  for (int m = 0; m < a.ncfg; ++m)
-    for (int k = a.st_begin[m] + tid; k < a.st_begin[m + 1]; k += nthr) {
-      const double* src = a.q + ((size_t)a.st_rep[k] * a.ncfg + m) * 4;
-      if (DF) {
-        float2* q2 = reinterpret_cast<float2*>(Qs + 4 * (size_t)k);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          float h, l;
-          split_df(src[j], h, l);
-          q2[j] = make_float2(h, l);
-        }
-      } else {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) Qs[4 * k + j] = src[j];
-      }
-    }
+  double* slices = sm;  // slots x stride (the G row first)
+  double* sQ = sm + (size_t)a.nslot_max * a.slice_stride;                  // chunk terms: Q
+  int* sSlot = reinterpret_cast<int*>(sQ + 4 * (size_t)a.max_terms);       // slot
+  int* sFirst = sSlot + a.max_terms;                                       // first term of its slot
+  int* sCfg = sFirst + a.max_terms;                                        // configuration
   int emax = 0;
   bool bad = false;
   for (int64_t is = blockIdx.x; is < a.ns; is += gridDim.x) {
@@ -945,31 +940,63 @@ __global__ void __launch_bounds__(kStreamThreads, 2) kc_stream(KcArgs a) {
       }
     }
     __syncthreads();  // the G row is in registers; its space is reused by the slices
-    if (active) {
-      const int cd = c * 3 + d;
-      const bool block_type = ((c == 2) == (d == 2));
-      const int offa = block_type ? 0 : 1, offb = block_type ? 3 : 2;
-      for (int m = 0; m < a.ncfg; ++m) {
-        const int k1 = a.st_begin[m + 1];
+    const int cd = c * 3 + d;
+    const bool block_type = ((c == 2) == (d == 2));
+    const int offa = block_type ? 0 : 1, offb = block_type ? 3 : 2;
+    const int seg_len = 3 * ls;
+    const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
+    for (int ch = 0; ch < a.nchunk; ++ch) {
+      int it0 = a.ck_it[ch], it1 = a.ck_it[ch + 1];
+      if (CHUNKED) {
+        it0 = max(it0, a.it_lo);
+        it1 = min(it1, a.it_hi);
+        if (it0 >= it1) continue;  // the same for every thread
+      }
+      // the chunk's terms into shared memory
+      const int tb = a.ck_term[ch], nterm = a.ck_term[ch + 1] - tb;
+      for (int k = tid; k < nterm; k += nthr) {
+        const int t = tb + k, m = a.ckt_cfg[t];
+        const size_t qi = ((size_t)a.ckt_rep[t] * a.ncfg + m) * 4;
         if (DF) {
-          const float2* E = a.cfgEdf + (size_t)m * 81 + cd * 9;
-          float ah, al, bh, bl, ch = 0.0f, cl = 0.0f, dh = 0.0f, dl = 0.0f;
-          if (MONO) {
-            if (block_type) {
-              df_dot(E, gh, gl, 0, 1, 3, 4, 4, ah, al);
-              df_dot(E, gh, gl, 8, 8, 8, 8, 1, bh, bl);
-            } else {
-              df_dot(E, gh, gl, 2, 5, 0, 0, 2, ah, al);
-              df_dot(E, gh, gl, 6, 7, 0, 0, 2, bh, bl);
+          float2* q2 = reinterpret_cast<float2*>(sQ + 4 * (size_t)k);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) q2[j] = a.qdf[qi + j];
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) sQ[4 * (size_t)k + j] = a.q[qi + j];
+        }
+        sSlot[k] = a.ckt_slot[t];
+        sFirst[k] = a.ckt_first[t];
+        sCfg[k] = m;
+      }
+      __syncthreads();
+      // phase 1: slice of every class of the chunk (terms sorted by configuration)
+      if (active) {
+        const int t1 = nterm;
+        int cur = -1;
+        if (DF) {
+          float ah = 0.0f, al = 0.0f, bh = 0.0f, bl = 0.0f, ch_ = 0.0f, cl = 0.0f, dh = 0.0f, dl = 0.0f;
+          for (int t = 0; t < t1; ++t) {
+            const int m = sCfg[t];
+            if (m != cur) {
+              cur = m;
+              const float2* E = a.cfgEdf + (size_t)m * 81 + cd * 9;
+              if (MONO) {
+                if (block_type) {
+                  df_dot(E, gh, gl, 0, 1, 3, 4, 4, ah, al);
+                  df_dot(E, gh, gl, 8, 8, 8, 8, 1, bh, bl);
+                } else {
+                  df_dot(E, gh, gl, 2, 5, 0, 0, 2, ah, al);
+                  df_dot(E, gh, gl, 6, 7, 0, 0, 2, bh, bl);
+                }
+              } else {
+                df_dot(E, gh, gl, 0, 1, 3, 4, 4, ah, al);
+                df_dot(E, gh, gl, 2, 5, 0, 0, 2, bh, bl);
+                df_dot(E, gh, gl, 6, 7, 0, 0, 2, ch_, cl);
+                df_dot(E, gh, gl, 8, 8, 8, 8, 1, dh, dl);
+              }
             }
-          } else {
-            df_dot(E, gh, gl, 0, 1, 3, 4, 4, ah, al);
-            df_dot(E, gh, gl, 2, 5, 0, 0, 2, bh, bl);
-            df_dot(E, gh, gl, 6, 7, 0, 0, 2, ch, cl);
-            df_dot(E, gh, gl, 8, 8, 8, 8, 1, dh, dl);
-          }
-          for (int t = a.st_begin[m]; t < k1; ++t) {
-            const float2* q2 = reinterpret_cast<const float2*>(Qs + 4 * (size_t)t);
+            const float2* q2 = reinterpret_cast<const float2*>(sQ + 4 * (size_t)t);
             float vh, vl, p, e;
             if (MONO) {
               const float2 qa = q2[offa], qb = q2[offb];
@@ -980,83 +1007,83 @@ __global__ void __launch_bounds__(kStreamThreads, 2) kc_stream(KcArgs a) {
               df_mul(q2[0].x, q2[0].y, ah, al, vh, vl);
               df_mul(q2[1].x, q2[1].y, bh, bl, p, e);
               df_add(p, e, vh, vl);
-              df_mul(q2[2].x, q2[2].y, ch, cl, p, e);
+              df_mul(q2[2].x, q2[2].y, ch_, cl, p, e);
               df_add(p, e, vh, vl);
               df_mul(q2[3].x, q2[3].y, dh, dl, p, e);
               df_add(p, e, vh, vl);
             }
-            float2* dst = reinterpret_cast<float2*>(slices + (size_t)tcls[t] * a.slice_stride + item);
-            if (!tfirst[t]) {
+            float2* dst = reinterpret_cast<float2*>(slices + (size_t)sSlot[t] * a.slice_stride + item);
+            if (!sFirst[t]) {
               const float2 o = *dst;
               df_add(o.x, o.y, vh, vl);
             }
             *dst = make_float2(vh, vl);
           }
+          // float pairs -> doubles, in place (each thread its own column)
+          const int ns_ = a.ck_nslot[ch];
+          for (int u = 0; u < ns_; ++u) {
+            double* dst = slices + (size_t)u * a.slice_stride + item;
+            const float2 v = *reinterpret_cast<const float2*>(dst);
+            const float hs = __fadd_rn(v.x, v.y);
+            const float lsum = __fsub_rn(v.y, __fsub_rn(hs, v.x));
+            const int ef = (int)((__float_as_uint(hs) >> 23) & 0xFFu);
+            bad |= (ef == 255);
+            emax = max(emax, ef);
+            *dst = df_to_double(hs, lsum);
+          }
         } else {
-          const double* E = a.cfgE + (size_t)m * 81 + cd * 9;
-          double pa, pb, p11 = 0.0, p12 = 0.0, p21 = 0.0, p22 = 0.0;
-          if (MONO) {
-            if (block_type) {
-              pa = E[0] * g[0] + E[1] * g[1] + E[3] * g[3] + E[4] * g[4];
-              pb = E[8] * g[8];
-            } else {
-              pa = E[2] * g[2] + E[5] * g[5];
-              pb = E[6] * g[6] + E[7] * g[7];
+          double pa = 0.0, pb = 0.0, p11 = 0.0, p12 = 0.0, p21 = 0.0, p22 = 0.0;
+          for (int t = 0; t < t1; ++t) {
+            const int m = sCfg[t];
+            if (m != cur) {
+              cur = m;
+              const double* E = a.cfgE + (size_t)m * 81 + cd * 9;
+              if (MONO) {
+                if (block_type) {
+                  pa = E[0] * g[0] + E[1] * g[1] + E[3] * g[3] + E[4] * g[4];
+                  pb = E[8] * g[8];
+                } else {
+                  pa = E[2] * g[2] + E[5] * g[5];
+                  pb = E[6] * g[6] + E[7] * g[7];
+                }
+              } else {
+                p11 = E[0] * g[0] + E[1] * g[1] + E[3] * g[3] + E[4] * g[4];
+                p12 = E[2] * g[2] + E[5] * g[5];
+                p21 = E[6] * g[6] + E[7] * g[7];
+                p22 = E[8] * g[8];
+              }
             }
-          } else {
-            p11 = E[0] * g[0] + E[1] * g[1] + E[3] * g[3] + E[4] * g[4];
-            p12 = E[2] * g[2] + E[5] * g[5];
-            p21 = E[6] * g[6] + E[7] * g[7];
-            p22 = E[8] * g[8];
-            pa = pb = 0.0;
-          }
-          for (int t = a.st_begin[m]; t < k1; ++t) {
-            const double v = MONO ? Qs[4 * t + offa] * pa + Qs[4 * t + offb] * pb
-                                  : Qs[4 * t] * p11 + Qs[4 * t + 1] * p12 + Qs[4 * t + 2] * p21 + Qs[4 * t + 3] * p22;
-            double* dst = slices + (size_t)tcls[t] * a.slice_stride + item;
-            *dst = tfirst[t] ? v : *dst + v;
+            const double* Q = sQ + 4 * (size_t)t;
+            const double v = MONO ? Q[offa] * pa + Q[offb] * pb : Q[0] * p11 + Q[1] * p12 + Q[2] * p21 + Q[3] * p22;
+            double* dst = slices + (size_t)sSlot[t] * a.slice_stride + item;
+            *dst = sFirst[t] ? v : *dst + v;
           }
         }
       }
-      if (DF) {  // float pairs -> doubles, in place (each thread its own column)
-        for (int u = 0; u < a.ncls; ++u) {
-          double* dst = slices + (size_t)u * a.slice_stride + item;
-          const float2 v = *reinterpret_cast<const float2*>(dst);
-          const float hs = __fadd_rn(v.x, v.y);
-          const float ls_ = __fsub_rn(v.y, __fsub_rn(hs, v.x));
-          const int ef = (int)((__float_as_uint(hs) >> 23) & 0xFFu);
-          bad |= (ef == 255);
-          emax = max(emax, ef);
-          *dst = df_to_double(hs, ls_);
+      __syncthreads();
+      // phase 2: the chunk's thickness pairs (i_t, k_t) in address order, one
+      // warp per pair. Row (i_t, i_s, c) holds len_t segments of 3 len_s
+      // values; the pair's three segments (c = 0, 1, 2) sit one row apart. Each
+      // copy issues all of its shared loads before its global stores.
+      const int64_t p_end = a.LTb[it1];
+      for (int64_t pr = a.LTb[it0] + warp; pr < p_end; pr += nwarps) {
+        const int64_t A = a.tp_A[pr];
+        const int lt = a.tp_lt[pr], kt = a.tp_k[pr], u = a.pair_slot[pr];
+        const double* src = slices + (size_t)u * a.slice_stride;
+        double* dst = a.values + (A + (int64_t)lt * 9 * ls0 + (int64_t)kt * seg_len - a.out_offset);
+        const int64_t row_step = (int64_t)lt * seg_len;
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+          double v[kSegUnroll];
+#pragma unroll
+          for (int j = 0; j < kSegUnroll; ++j) v[j] = (lane + 32 * j < seg_len) ? src[cc * seg_len + lane + 32 * j] : 0.0;
+#pragma unroll
+          for (int j = 0; j < kSegUnroll; ++j)
+            if (lane + 32 * j < seg_len) dst[cc * row_step + lane + 32 * j] = v[j];
         }
       }
+      __syncthreads();  // the slices are rewritten by the next chunk or row
     }
-    __syncthreads();
-    // phase 2: thickness pairs (i_t, k_t) in address order, one warp per pair.
-    // Row (i_t, i_s, c) holds len_t segments of 3 len_s values; the pair's three
-    // segments (c = 0, 1, 2) sit one row apart. Each copy issues all of its
-    // shared loads before its global stores.
-    const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
-    const int seg_len = 3 * ls;
-    const int64_t p_begin = CHUNKED ? a.LTb[a.it_lo] : 0;
-    const int64_t p_end = CHUNKED ? a.LTb[a.it_hi] : a.LTb[a.nt];
-    for (int64_t pr = p_begin + warp; pr < p_end; pr += nwarps) {
-      const int64_t A = a.tp_A[pr];
-      const int lt = a.tp_lt[pr], kt = a.tp_k[pr], u = a.pair_cls[pr];
-      const double* src = slices + (size_t)u * a.slice_stride;
-      double* dst = a.values + (A + (int64_t)lt * 9 * ls0 + (int64_t)kt * seg_len - a.out_offset);
-      const int64_t row_step = (int64_t)lt * seg_len;
-#pragma unroll
-      for (int cc = 0; cc < 3; ++cc) {
-        double v[kSegUnroll];
-#pragma unroll
-        for (int j = 0; j < kSegUnroll; ++j) v[j] = (lane + 32 * j < seg_len) ? src[cc * seg_len + lane + 32 * j] : 0.0;
-#pragma unroll
-        for (int j = 0; j < kSegUnroll; ++j)
-          if (lane + 32 * j < seg_len) dst[cc * row_step + lane + 32 * j] = v[j];
-      }
-    }
-    __syncthreads();  // the slices are rewritten by the next row
   }
   if (DF) {
     emax = __reduce_max_sync(0xffffffffu, emax);
@@ -1275,10 +1302,14 @@ static lam_status ensure_device(Plan& P) {
     UP(L, edf_dev, edf);
     D->cfgEdf = reinterpret_cast<float2*>(edf_dev);
     UP(L, D->pair_cls, P.pair_cls);
-    UP(L, D->st_begin, P.st_begin);
-    UP(L, D->st_cls, P.st_cls);
-    UP(L, D->st_rep, P.st_rep);
-    UP(L, D->st_first, P.st_first);
+    UP(L, D->ck_it, P.ck_it);
+    UP(L, D->ck_term, P.ck_term);
+    UP(L, D->ck_nslot, P.ck_nslot);
+    UP(L, D->pair_slot, P.pair_slot);
+    UP(L, D->ckt_slot, P.ckt_slot);
+    UP(L, D->ckt_cfg, P.ckt_cfg);
+    UP(L, D->ckt_rep, P.ckt_rep);
+    UP(L, D->ckt_first, P.ckt_first);
     UP(L, D->ply_M, P.ply_M);
     UP(L, D->ply_dM, P.ply_dM);
     UP(L, D->mat_C, P.mat_C);
@@ -1287,6 +1318,12 @@ static lam_status ensure_device(Plan& P) {
       free_device(P);
       return st;
     }
+    double* qdf = nullptr;
+    if ((st = alloc_dev(L, &qdf, (size_t)P.nnz_t * P.cfg_mat.size() * 4)) != LAM_OK) {
+      free_device(P);
+      return st;
+    }
+    D->qdf = reinterpret_cast<float2*>(qdf);
     P.cfg_dirty = false;
   }
 #undef UP
@@ -1373,13 +1410,21 @@ static KcArgs kc_args(const Plan& P, double* values) {
   k.values = values;
   k.LTb = D.LTb;
   k.pair_cls = D.pair_cls;
-  k.st_begin = D.st_begin;
-  k.st_cls = D.st_cls;
-  k.st_rep = D.st_rep;
-  k.nst = (int)P.st_cls.size();
+  k.nchunk = (int)P.ck_nslot.size();
+  k.nslot_max = 1;
+  for (int v : P.ck_nslot) k.nslot_max = std::max(k.nslot_max, v);
+  k.max_terms = kcs_max_terms(P);
+  k.ck_it = D.ck_it;
+  k.ck_term = D.ck_term;
+  k.ck_nslot = D.ck_nslot;
+  k.pair_slot = D.pair_slot;
+  k.ckt_slot = D.ckt_slot;
+  k.ckt_cfg = D.ckt_cfg;
+  k.ckt_rep = D.ckt_rep;
+  k.ckt_first = D.ckt_first;
+  k.qdf = D.qdf;
   k.slice_stride = kcs_stride(P);
   k.nt = (int)P.nt;
-  k.st_first = D.st_first;
   k.tp_A = D.tp_A;
   k.tp_lt = D.tp_lt;
   k.tp_k = D.tp_k;
@@ -1466,6 +1511,7 @@ static lam_status split_integrals(Plan& P, cudaStream_t s) {
   kb.tabT = D.tabT;
   kb.wT = D.wT;
   kb.q = D.q;
+  kb.qdf = D.qdf;
   cudaEvent_t ev = prof_begin(P, s);
   kb_thickness<<<(unsigned)((P.nnz_t + 127) / 128), 128, 0, s>>>(kb);
   LAM_CUDA(cudaGetLastError());

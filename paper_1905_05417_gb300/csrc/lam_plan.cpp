@@ -545,29 +545,8 @@ static lam_status build_classes(Plan& P) {
   P.ncls = (int)reps.size();
   P.cls_rep = reps;
   P.pair_cls = cls_of;
-  // the same terms, grouped by configuration
-  P.st_begin.assign(nc + 1, 0);
-  P.st_cls.clear();
-  P.st_rep.clear();
-  P.st_cfg.clear();
-  for (int m = 0; m < nc; ++m) {
-    P.st_begin[m] = (int)P.st_cls.size();
-    for (int u = 0; u < (int)reps.size(); ++u)
-      for (int m2 : terms[reps[u]])
-        if (m2 == m) {
-          P.st_cls.push_back(u);
-          P.st_rep.push_back(reps[u]);
-          P.st_cfg.push_back(m);
-        }
-  }
-  P.st_begin[nc] = (int)P.st_cls.size();
-  P.st_first.assign(P.st_cls.size(), 0);
-  std::vector<char> seen(P.ncls, 0);
-  for (size_t k = 0; k < P.st_cls.size(); ++k)
-    if (!seen[P.st_cls[k]]) {
-      seen[P.st_cls[k]] = 1;
-      P.st_first[k] = 1;
-    }
+  P.cls_cfgs.assign(P.ncls, {});
+  for (int u = 0; u < P.ncls; ++u) P.cls_cfgs[u] = terms[reps[u]];
   P.cls_term_begin.assign(P.ncls + 1, 0);
   P.cls_terms.clear();
   for (int u = 0; u < P.ncls; ++u) {
@@ -593,6 +572,101 @@ static lam_status build_classes(Plan& P) {
     P.occ_it[o] = i;
   }
   return LAM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Thickness chunks of the streaming combine: consecutive thickness rows whose
+// pairs use at most kc_slots distinct classes (the slices of one in-plane row
+// that fit in shared memory). A uniform stack is one chunk; uneven plies, where
+// almost every pair is its own class, give chunks of a few plies.
+// ---------------------------------------------------------------------------
+static void build_chunks_with(Plan& P, int slots) {
+  P.ck_it.clear();
+  P.ck_term.clear();
+  P.ck_nslot.clear();
+  P.ckt_slot.clear();
+  P.ckt_cfg.clear();
+  P.ckt_rep.clear();
+  P.ckt_first.clear();
+  P.pair_slot.assign(P.nnz_t, 0);
+  P.kc_slots = slots;
+  std::vector<int> slot_of(P.ncls, -1), members;
+  auto close = [&](int it1) {
+    // terms of the chunk's classes, sorted by configuration
+    const int t0 = (int)P.ckt_slot.size();
+    std::vector<std::array<int, 3>> tm;  // (cfg, slot, class)
+    for (int u : members)
+      for (int m : P.cls_cfgs[u]) tm.push_back({m, slot_of[u], u});
+    std::stable_sort(tm.begin(), tm.end(), [](const std::array<int, 3>& x, const std::array<int, 3>& y) {
+      return x[0] < y[0];
+    });
+    std::vector<char> seen(members.size(), 0);
+    for (auto& t : tm) {
+      P.ckt_cfg.push_back(t[0]);
+      P.ckt_slot.push_back(t[1]);
+      P.ckt_rep.push_back(P.cls_rep[t[2]]);
+      P.ckt_first.push_back(seen[t[1]] ? 0 : 1);
+      seen[t[1]] = 1;
+    }
+    P.ck_term.push_back(t0);
+    P.ck_nslot.push_back((int)members.size());
+    (void)it1;
+    for (int u : members) slot_of[u] = -1;
+    members.clear();
+  };
+  P.ck_it.push_back(0);
+  for (int it = 0; it < (int)P.nt; ++it) {
+    int fresh = 0;
+    std::vector<int> row;
+    for (int64_t pr = P.LTb[it]; pr < P.LTb[it + 1]; ++pr) {
+      const int u = P.pair_cls[pr];
+      if (slot_of[u] < 0 && std::find(row.begin(), row.end(), u) == row.end()) {
+        row.push_back(u);
+        ++fresh;
+      }
+    }
+    if ((int)members.size() + fresh > P.kc_slots) {
+      close(it);
+      P.ck_it.push_back(it);
+    }
+    for (int64_t pr = P.LTb[it]; pr < P.LTb[it + 1]; ++pr) {
+      const int u = P.pair_cls[pr];
+      if (slot_of[u] < 0) {
+        slot_of[u] = (int)members.size();
+        members.push_back(u);
+      }
+      P.pair_slot[pr] = slot_of[u];
+    }
+  }
+  close((int)P.nt);
+  P.ck_it.push_back((int)P.nt);
+  P.ck_term.push_back((int)P.ckt_slot.size());
+}
+
+void build_chunks(Plan& P) {
+  int max_lt = 1;
+  for (int v : P.t.len) max_lt = std::max(max_lt, v);
+  const size_t stride_bytes = (size_t)kcs_stride(P) * sizeof(double);
+  int slots = (int)(kSliceBudget / stride_bytes);
+  if (9 * max_len_s(P) <= 512) {
+    // fewer slots (more chunks) until two CTAs fit on an SM; at least one thickness row per chunk
+    for (; slots >= max_lt; --slots) {
+      build_chunks_with(P, slots);
+      if (kcs_smem(P) <= kSliceBudget + 3 * 1024) return;
+    }
+    build_chunks_with(P, max_lt);
+    if (kcs_smem(P) <= 200 * 1024) return;
+  }
+  // class-major combine
+  P.kc_slots = 0;
+  P.ck_it.clear();
+  P.ck_term.clear();
+  P.ck_nslot.clear();
+  P.ckt_slot.clear();
+  P.ckt_cfg.clear();
+  P.ckt_rep.clear();
+  P.ckt_first.clear();
+  P.pair_slot.assign(P.nnz_t, 0);
 }
 
 static void build_colourings(Plan& P) {
@@ -745,6 +819,7 @@ lam_status build_plan(Plan& P, const lam_inplane* inplane, const lam_basis1d* th
     P.tp_k[pr] = P.tp_col[pr] - P.t.lo[it];
   }
   if ((st = build_classes(P)) != LAM_OK) return st;
+  build_chunks(P);
   build_adjoint_terms(P);
   build_colourings(P);
   return LAM_OK;
@@ -807,6 +882,7 @@ lam_status lam_plan_get_info(const lam_plan* plan, lam_plan_info* info) {
   info->monoclinic = P.monoclinic ? 1 : 0;
   info->n_pieces = (int32_t)P.pieces.size();
   info->combine_streaming = lam::use_stream(P) ? 1 : 0;
+  info->combine_chunks = (int32_t)P.ck_nslot.size();
   return LAM_OK;
 }
 
@@ -837,6 +913,7 @@ lam_status lam_plan_update(lam_plan* plan, const double* ply_angle_rad, int32_t 
   if (materials) P.mats.assign(materials, materials + n_materials);
   lam::rebuild_configs(P);
   lam::build_classes(P);
+  lam::build_chunks(P);
   P.cfg_dirty = true;  // configuration tables are re-uploaded by the next device call
   return LAM_OK;
 }

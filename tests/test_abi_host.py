@@ -104,14 +104,16 @@ def test_configurations_and_classes(lam):
 
 
 def test_combine_variant_selection(lam):
-    assert lam.Plan.from_laminate(W.curved_plate()).info["combine_streaming"] == 1
+    info = lam.Plan.from_laminate(W.curved_plate()).info
+    assert info["combine_streaming"] == 1 and info["combine_chunks"] == 1  # 31 classes fit at once
     assert lam.Plan.from_laminate(W.cross_ply_plate()).info["combine_streaming"] == 1
     quartic = W.laminate("p4", W.BSPLINE, 4, 8, [0, 45], 0.02, n_el_y=8, thickness_degree=1)
-    assert lam.Plan.from_laminate(quartic).info["combine_streaming"] == 0
+    assert lam.Plan.from_laminate(quartic).info["combine_streaming"] == 0  # 81 neighbours: 729 threads
     rng = np.random.default_rng(5)
     uneven = W.laminate("u", W.BSPLINE, 1, 3, [0.0] * 70, rng.uniform(0.0005, 0.002, 70), thickness_degree=1)
     p = lam.Plan.from_laminate(uneven)
-    assert p.info["n_classes"] > 150 and p.info["combine_streaming"] == 0  # slices beyond shared memory
+    # hundreds of classes: streamed in chunks of thickness rows
+    assert p.info["n_classes"] > 150 and p.info["combine_streaming"] == 1 and p.info["combine_chunks"] >= 2
 
 
 def test_update_rebuilds_configurations(lam):

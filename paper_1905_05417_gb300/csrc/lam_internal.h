@@ -140,13 +140,25 @@ struct Plan {
 // streaming form keeps a row's class slices in shared memory (one 512-thread
 // CTA per row, two per SM), a chunk of thickness rows at a time; rows of more
 // than 512 / 9 in-plane neighbours take the class-major form.
-constexpr size_t kSliceBudget = 110 * 1024;  // shared memory for the slices of one CTA
 inline int max_len_s(const Plan& P) {
   int mx = 0, my = 0;
   for (int v : P.u.len) mx = mx > v ? mx : v;
   for (int v : P.v.len) my = my > v ? my : v;
   return mx * my;
 }
+// threads of a streaming-combine CTA (one per (c, k_s, d) of the largest row)
+inline int kcs_block(const Plan& P) {
+  const int t = ((9 * max_len_s(P) + 31) / 32) * 32;
+  return t < 128 ? 128 : t;
+}
+// CTAs of that size an SM holds at 64 registers per thread, and the shared
+// memory each of them may use (228 KB per SM, 1 KB reserved per CTA)
+inline int kcs_ctas_per_sm(const Plan& P) {
+  int n = 65536 / (64 * kcs_block(P));
+  if (n > 2048 / kcs_block(P)) n = 2048 / kcs_block(P);
+  return n < 1 ? 1 : (n > 8 ? 8 : n);
+}
+inline size_t kcs_budget(const Plan& P) { return (size_t)(233472 / kcs_ctas_per_sm(P)) - 1024; }
 inline int kcs_stride(const Plan& P) { return 9 * max_len_s(P); }
 inline int kcs_max_terms(const Plan& P) {
   int mt = 1;

@@ -857,7 +857,6 @@ __global__ void __launch_bounds__(1024, 2) kc_combine(KcArgs a) {
 // largest entry is below 2^-60, sets the flag; the FP64 form (DF = false,
 // conditional) then recomputes every row on the same stream.
 // ---------------------------------------------------------------------------
-constexpr int kStreamThreads = 512;
 constexpr int kSegUnroll = 6;  // 32 * 6 >= 3 * len_s for rows of at most 512 / 9 neighbours
 constexpr int kKcMinExp = 127 - 60;  // float exponent field of 2^-60
 
@@ -883,7 +882,7 @@ __device__ __forceinline__ void df_dot(const float2* __restrict__ E, const float
 }
 
 template <bool MONO, bool CHUNKED, bool DF>
-__global__ void __launch_bounds__(kStreamThreads, 2) kc_stream(KcArgs a) {
+__global__ void __maxnreg__(64) kc_stream(KcArgs a) {
   if (!DF && a.conditional && *a.flag == 0) return;
   extern __shared__ double sm[];
   const int nthr = blockDim.x, tid = threadIdx.x;
@@ -1444,14 +1443,14 @@ static lam_status launch_kcs(const Plan& P, const KcArgs& k, cudaStream_t s) {
   LAM_CUDA(cudaFuncSetAttribute(kc_stream<MONO, CHUNKED, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   LAM_CUDA(cudaMemsetAsync(k.flag, 0, 2 * sizeof(int), s));
   cudaEvent_t ev = prof_begin(const_cast<Plan&>(P), s);
-  kc_stream<MONO, CHUNKED, true><<<(unsigned)P.ns, kStreamThreads, smem, s>>>(k);
+  kc_stream<MONO, CHUNKED, true><<<(unsigned)P.ns, kcs_block(P), smem, s>>>(k);
   LAM_CUDA(cudaGetLastError());
   kc_check<<<1, 1, 0, s>>>(k.flag, k.emax);
   LAM_CUDA(cudaGetLastError());
   KcArgs k64 = k;
   k64.conditional = 1;
-  const int64_t grid64 = std::min<int64_t>(P.ns, 2 * (int64_t)std::max(1, P.dev->n_sm));
-  kc_stream<MONO, CHUNKED, false><<<(unsigned)grid64, kStreamThreads, smem, s>>>(k64);
+  const int64_t grid64 = std::min<int64_t>(P.ns, (int64_t)kcs_ctas_per_sm(P) * std::max(1, P.dev->n_sm));
+  kc_stream<MONO, CHUNKED, false><<<(unsigned)grid64, kcs_block(P), smem, s>>>(k64);
   LAM_CUDA(cudaGetLastError());
   prof_end(const_cast<Plan&>(P), LAM_KERNEL_COMBINE, 3, s, ev);
   return LAM_OK;

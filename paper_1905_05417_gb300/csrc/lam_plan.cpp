@@ -647,12 +647,14 @@ void build_chunks(Plan& P) {
   int max_lt = 1;
   for (int v : P.t.len) max_lt = std::max(max_lt, v);
   const size_t stride_bytes = (size_t)kcs_stride(P) * sizeof(double);
-  int slots = (int)(kSliceBudget / stride_bytes);
+  const size_t budget = kcs_budget(P);
+  int slots = (int)(budget / stride_bytes);
   if (9 * max_len_s(P) <= 512) {
-    // fewer slots (more chunks) until two CTAs fit on an SM; at least one thickness row per chunk
+    // fewer slots (more chunks) until the CTAs an SM can hold by registers fit
+    // by shared memory too; at least one thickness row per chunk
     for (; slots >= max_lt; --slots) {
       build_chunks_with(P, slots);
-      if (kcs_smem(P) <= kSliceBudget + 3 * 1024) return;
+      if (kcs_smem(P) <= budget) return;
     }
     build_chunks_with(P, max_lt);
     if (kcs_smem(P) <= 200 * 1024) return;

@@ -73,7 +73,7 @@ SMALL = {
     # rows of 81 in-plane neighbours (729 values > 512 threads): the class-major combine
     "quartic_inplane": lambda: W.laminate("p4", W.BSPLINE, 4, 8, [0, 45], 0.02, mapping=W.curved_map(),
                                           n_el_y=8, thickness_degree=1),
-    # uneven plies: hundreds of distinct Q vectors, the class-major combine
+    # uneven plies: hundreds of distinct Q vectors, the streaming combine in chunks
     "uneven_plies_many_classes": lambda: W.laminate(
         "uneven", W.BSPLINE, 1, 3, list(np.random.default_rng(4).choice([0.0, 45.0, -45.0, 90.0], 70)),
         np.random.default_rng(5).uniform(0.0005, 0.002, 70), mapping=W.curved_map(), thickness_degree=1),
@@ -217,6 +217,43 @@ def test_curved_plate_full_size_sampled_split(L):
 
 def test_adjoint_plate_full_size_sampled_standard(L):
     _sampled_parity(L, W.adjoint_plate(), "standard", n_rows=60, seed=1)
+
+
+def _uneven(materials, seed):
+    rng = np.random.default_rng(seed)
+    n = 9
+    return W.laminate("uneven_q", W.BSPLINE, 2, 5, list(rng.choice([0.0, 45.0, -45.0, 90.0], n)),
+                      rng.uniform(0.0005, 0.002, n), mapping=W.curved_map(0.03), materials=materials,
+                      ply_material=list(rng.integers(0, len(materials), n)))
+
+
+def test_uneven_plies_four_materials(L):
+    """A batch-like stack (quadratic in-plane, uneven plies, four materials)."""
+    mats = np.array([W.ply_C21() * (1 + 0.25 * k) for k in range(4)])
+    lam = _uneven(mats, 21)
+    p = L.Plan.from_laminate(lam)
+    assert p.info["combine_streaming"] == 1 and p.info["monoclinic"] == 1
+    assert_parity(gpu_matrix(L, lam, "split"), O.assemble(lam))
+
+
+def test_uneven_plies_triclinic(L):
+    rng = np.random.default_rng(3)
+    lam = _uneven(np.array([W.random_C21(rng), W.random_C21(rng)]), 22)
+    p = L.Plan.from_laminate(lam)
+    assert p.info["combine_streaming"] == 1 and p.info["monoclinic"] == 0
+    assert_parity(gpu_matrix(L, lam, "split"), O.assemble(lam))
+
+
+def test_chunked_host_output_uneven_plies(L):
+    lam = _uneven(np.array([W.ply_C21()]), 23)
+    p = L.Plan.from_laminate(lam)
+    import torch
+    d = p.assemble_split()
+    torch.cuda.synchronize()
+    h = np.empty(p.nnz)
+    p.assemble_split_host(h)
+    assert np.array_equal(d.cpu().numpy(), h)
+    p.close()
 
 
 # ---------------------------------------------------------------- scale robustness of the double-float steps

@@ -259,6 +259,50 @@ typedef struct {
 lam_status lam_adjoint(lam_plan* plan, const lam_cotangent* cotangent, double* d_dC, double* d_dtheta,
                        double* d_dD, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many laminates assembled together (the paper assembles one
+ * laminate; this is the batched form of lam_assemble_split for design loops
+ * over stack-ups). Instances whose in-plane discretisation is identical (basis
+ * kinds, degrees, knots, control points, weights, Gauss orders) share one set
+ * of in-plane Gram blocks, so K-a runs once per distinct mesh whatever the
+ * materials, angles or ply counts. One launch computes Eq. Q for every
+ * instance, one launch the Gram blocks of every mesh, and one persistent
+ * launch combines every in-plane row of every instance from an atomic work
+ * queue (largest instances first). The first lam_batch_assemble times the
+ * persistent launch at 1..4 CTAs per SM, keeps the fastest, and captures the
+ * whole sequence in a CUDA graph that later calls replay.
+ * ------------------------------------------------------------------------- */
+typedef struct lam_batch lam_batch;
+
+typedef struct {
+  int32_t n_plans;
+  int32_t n_meshes;        /* distinct in-plane discretisations (K-a runs once for each) */
+  int64_t nnz_total;       /* stored entries over all instances */
+  int32_t n_persistent;    /* instances combined by the persistent launch (the others: lam_assemble_split) */
+  int32_t ctas_per_sm;     /* chosen by the autotuner, 0 before the first lam_batch_assemble */
+  int32_t graph;           /* 1 once the launches are replayed from a CUDA graph */
+  int32_t reserved;
+  double tuned_ms[4];      /* autotuner: one assembly with 1..4 CTAs per SM (0 = not tried) */
+} lam_batch_info;
+
+/* Batch of n_plans plans (borrowed: they must outlive the batch, all on the
+ * current device). The batch holds their configuration as of this call: after
+ * lam_plan_update on one of them, lam_batch_assemble returns
+ * LAM_ERR_INVALID_ARG (recreate the batch). Allocates the shared Gram blocks
+ * and the launch tables on the device. */
+lam_status lam_batch_create(lam_batch** out, lam_plan* const* plans, int32_t n_plans);
+
+/* Assembles every instance: d_values is a HOST array of n_plans device
+ * pointers, entry k receiving plan k's nnz values (the order of lam_pattern).
+ * Asynchronous on `stream`, except the first call, which tunes and captures
+ * the graph and returns after the device has finished. */
+lam_status lam_batch_assemble(lam_batch* batch, double* const* d_values, void* stream);
+
+lam_status lam_batch_get_info(const lam_batch* batch, lam_batch_info* info);
+
+/* Releases the batch (not its plans). Synchronises the device. */
+lam_status lam_batch_destroy(lam_batch* batch);
+
 /* Kernel kinds counted by the profiler. */
 typedef enum {
   LAM_KERNEL_PATTERN = 0,   /* kp_row_ptr, kp_col_ind */

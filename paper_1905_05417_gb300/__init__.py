@@ -26,7 +26,8 @@ import numpy as np
 __all__ = [
     "LamError", "Plan", "load", "plan_create", "plan_destroy", "plan_get_info", "pattern", "assemble_split",
     "assemble_standard", "assemble_split_host", "assemble_split_noalloc", "plan_update", "profile_enable", "profile_get", "last_error",
-    "version", "adjoint", "StiffnessFunction", "SYMBOLS", "KERNEL_KINDS", "BSPLINE", "LAGRANGE",
+    "version", "adjoint", "StiffnessFunction", "Batch", "batch_create", "batch_assemble", "batch_get_info",
+    "batch_destroy", "SYMBOLS", "KERNEL_KINDS", "BSPLINE", "LAGRANGE",
 ]
 
 BSPLINE = 0
@@ -37,7 +38,8 @@ LIB_PATH = os.path.join(_HERE, "liblam.so")
 # every symbol include/lam.h declares
 SYMBOLS = ("lam_plan_create", "lam_plan_destroy", "lam_plan_get_info", "lam_pattern", "lam_assemble_split",
            "lam_assemble_standard", "lam_assemble_split_host", "lam_assemble_split_noalloc", "lam_plan_update",
-           "lam_adjoint", "lam_profile_enable",
+           "lam_adjoint", "lam_batch_create", "lam_batch_assemble", "lam_batch_get_info", "lam_batch_destroy",
+           "lam_profile_enable",
            "lam_profile_get", "lam_last_error", "lam_version")
 KERNEL_KINDS = ("pattern", "thickness", "inplane", "combine", "standard", "adjoint", "adjoint_aux")
 COTANGENT_CSR = 0
@@ -88,6 +90,12 @@ class _Cotangent(ctypes.Structure):
                 ("v", ctypes.c_void_p)]
 
 
+class _BatchInfo(ctypes.Structure):
+    _fields_ = [("n_plans", ctypes.c_int32), ("n_meshes", ctypes.c_int32), ("nnz_total", ctypes.c_int64),
+                ("n_persistent", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("graph", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("tuned_ms", ctypes.c_double * 4)]
+
+
 class _Info(ctypes.Structure):
     _fields_ = [("n_dof", ctypes.c_int64), ("nnz", ctypes.c_int64), ("n_s", ctypes.c_int64), ("n_t", ctypes.c_int64),
                 ("nnz_inplane", ctypes.c_int64), ("nnz_thickness", ctypes.c_int64), ("n_configs", ctypes.c_int32),
@@ -121,6 +129,10 @@ def load() -> ctypes.CDLL:
     L.lam_assemble_split_noalloc.argtypes = [vp, vp, vp]
     L.lam_plan_update.argtypes = [vp, _D, ctypes.c_int32, ctypes.POINTER(_Material), ctypes.c_int32]
     L.lam_adjoint.argtypes = [vp, ctypes.POINTER(_Cotangent), vp, vp, vp, vp]
+    L.lam_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int32]
+    L.lam_batch_assemble.argtypes = [vp, ctypes.POINTER(vp), vp]
+    L.lam_batch_get_info.argtypes = [vp, ctypes.POINTER(_BatchInfo)]
+    L.lam_batch_destroy.argtypes = [vp]
     L.lam_profile_enable.argtypes = [vp, ctypes.c_int32]
     L.lam_profile_get.argtypes = [vp, ctypes.POINTER(_Profile)]
     L.lam_last_error.restype = ctypes.c_char_p
@@ -281,6 +293,33 @@ def adjoint(handle, d_dC=None, d_dtheta=None, d_dD=None, values=None, u=None, v=
            "lam_adjoint")
 
 
+def batch_create(plan_handles) -> ctypes.c_void_p:
+    """lam_batch_create over plan handles (the plans must outlive the batch)."""
+    arr = (ctypes.c_void_p * len(plan_handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h
+                                                    for h in plan_handles])
+    out = ctypes.c_void_p()
+    _check(load().lam_batch_create(ctypes.byref(out), arr, len(plan_handles)), "lam_batch_create")
+    return out
+
+
+def batch_assemble(handle, d_values, stream=None) -> None:
+    """d_values: one device tensor (or address) per plan, in the plans' order."""
+    arr = (ctypes.c_void_p * len(d_values))(*[_ptr(v) for v in d_values])
+    _check(load().lam_batch_assemble(handle, arr, _stream_handle(stream)), "lam_batch_assemble")
+
+
+def batch_get_info(handle) -> dict:
+    info = _BatchInfo()
+    _check(load().lam_batch_get_info(handle, ctypes.byref(info)), "lam_batch_get_info")
+    out = {name: getattr(info, name) for name, _ in _BatchInfo._fields_ if name not in ("reserved", "tuned_ms")}
+    out["tuned_ms"] = list(info.tuned_ms)
+    return out
+
+
+def batch_destroy(handle) -> None:
+    _check(load().lam_batch_destroy(handle), "lam_batch_destroy")
+
+
 def profile_enable(handle, enable: bool = True) -> None:
     """lam_profile_enable: start (or stop) timing every launch; counters restart."""
     _check(load().lam_profile_enable(handle, 1 if enable else 0), "lam_profile_enable")
@@ -379,6 +418,36 @@ class Plan:
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
             plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many plans assembled together (lam_batch_*); keeps the plans alive."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        self.handle = batch_create([p.handle for p in self.plans])
+
+    @property
+    def info(self) -> dict:
+        return batch_get_info(self.handle)
+
+    def assemble(self, values=None, stream=None):
+        import torch
+        if values is None:
+            values = [torch.empty(p.nnz, dtype=torch.float64, device="cuda") for p in self.plans]
+        batch_assemble(self.handle, values, stream)
+        return values
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

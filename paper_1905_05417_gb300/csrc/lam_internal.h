@@ -120,6 +120,7 @@ struct Plan {
   Device* dev = nullptr;
   int device_id = -1;
   bool cfg_dirty = true;         // configuration tables must be (re)uploaded
+  int cfg_version = 0;           // incremented by lam_plan_update (batches check it)
 
   // profiler (lam_profile_*): events are cudaEvent_t, kept opaque here
   struct Pending {

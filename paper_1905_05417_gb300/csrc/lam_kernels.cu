@@ -392,9 +392,7 @@ struct KbArgs {
   float2* qdf;  // float pairs of q (may be NULL)
 };
 
-__global__ void kb_thickness(KbArgs a) {
-  const int64_t pr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (pr >= a.npairs) return;
+__device__ __forceinline__ void kb_pair(const KbArgs& a, int64_t pr) {
   double* out = a.q + pr * a.ncfg * 4;
   for (int k = 0; k < a.ncfg * 4; ++k) out[k] = 0.0;
   const int i = a.tp_row[pr], j = a.tp_col[pr];
@@ -424,6 +422,11 @@ __global__ void kb_thickness(KbArgs a) {
       split_df(out[k], h, l);
       a.qdf[pr * a.ncfg * 4 + k] = make_float2(h, l);
     }
+}
+
+__global__ void kb_thickness(KbArgs a) {
+  const int64_t pr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pr < a.npairs) kb_pair(a, pr);
 }
 
 // ---------------------------------------------------------------------------
@@ -592,14 +595,12 @@ struct KaLocalArgs {
   double* EG;
 };
 
-__global__ void __launch_bounds__(256) ka_local(KaLocalArgs a) {
-  extern __shared__ double sm[];
+__device__ __forceinline__ void ka_elem(const KaLocalArgs& a, int e, double* sm) {
   const InplaneArgs& ip = a.ip;
   const int nlx = ip.pu + 1, nly = ip.pv + 1, nls = nlx * nly, nqs = ip.nqu * ip.nqv;
   double* phi = sm;
   double* phiw = phi + (size_t)nqs * nls * 3;
   double* qd = phiw + (size_t)nqs * nls * 3;
-  const int e = blockIdx.x;
   const int ex = e % ip.nel_u, ey = e / ip.nel_u;
   __shared__ int s_emax[2];
   if (threadIdx.x < 2) s_emax[threadIdx.x] = 0;
@@ -678,6 +679,11 @@ __global__ void __launch_bounds__(256) ka_local(KaLocalArgs a) {
       out[(size_t)k * npl + t] = __longlong_as_double(b);
     }
   }
+}
+
+__global__ void __launch_bounds__(256) ka_local(KaLocalArgs a) {
+  extern __shared__ double sm[];
+  ka_elem(a, blockIdx.x, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -881,213 +887,219 @@ __device__ __forceinline__ void df_dot(const float2* __restrict__ E, const float
   h = hs;
 }
 
+// One in-plane row i_s of the streaming combine (phases 0 to 2 for every
+// chunk of thickness rows). `sm` is the CTA's dynamic shared memory; emax and
+// bad accumulate the double-float pass's range checks.
 template <bool MONO, bool CHUNKED, bool DF>
-__global__ void __maxnreg__(64) kc_stream(KcArgs a) {
-  if (!DF && a.conditional && *a.flag == 0) return;
-  extern __shared__ double sm[];
+__device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm, int& emax, bool& bad) {
   const int nthr = blockDim.x, tid = threadIdx.x;
   double* slices = sm;  // slots x stride (the G row first)
   double* sQ = sm + (size_t)a.nslot_max * a.slice_stride;                  // chunk terms: Q
   int* sSlot = reinterpret_cast<int*>(sQ + 4 * (size_t)a.max_terms);       // slot
   int* sFirst = sSlot + a.max_terms;                                       // first term of its slot
   int* sCfg = sFirst + a.max_terms;                                        // configuration
-  int emax = 0;
-  bool bad = false;
-  for (int64_t is = blockIdx.x; is < a.ns; is += gridDim.x) {
-    const int ix = (int)(is % a.nx), iy = (int)(is / a.nx);
-    const int lx = a.lenX[ix];
-    const int ls = lx * a.lenY[iy];
-    const int n9 = 9 * ls;
-    const int64_t ls0 = a.LSb[is];
-    // phase 0: the row's G blocks into slices[0 .. 9 ls)
-    for (int item = tid; item < n9; item += nthr) {
-      const int ks = item / 9, ab = item % 9;
-      const int jx = a.loX[ix] + ks % lx, jy = a.loY[iy] + ks / lx;
-      const int ex0 = max(a.eloX[ix], a.eloX[jx]), ex1 = min(a.ehiX[ix], a.ehiX[jx]);
-      const int ey0 = max(a.eloY[iy], a.eloY[jy]), ey1 = min(a.ehiY[iy], a.ehiY[jy]);
-      const int ba = (ab % 3) * 3 + ab / 3;
-      double acc = 0.0;
-      for (int ey = ey0; ey <= ey1; ++ey) {
-        const int fy = a.firstV[ey];
-        for (int ex = ex0; ex <= ex1; ++ex) {
-          const int fx = a.firstU[ex];
-          const int li = (iy - fy) * a.nlx + (ix - fx), lj = (jy - fy) * a.nlx + (jx - fx);
-          const size_t e9 = ((size_t)ey * a.nel_u + ex) * 9;
-          if (li <= lj)
-            acc += a.EG[(e9 + ab) * a.npl + upper_pair(li, lj, a.nls)];
-          else
-            acc += a.EG[(e9 + ba) * a.npl + upper_pair(lj, li, a.nls)];
-        }
-      }
-      slices[item] = acc;
-    }
-    __syncthreads();
-    const int item = tid;
-    const bool active = item < n9;
-    int c = 0, ks = 0, d = 0;
-    double g[9];
-    float gh[9], gl[9];
-    if (active) {
-      c = item / (3 * ls);
-      const int rem = item % (3 * ls);
-      ks = rem / 3;
-      d = rem % 3;
-#pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        g[k] = slices[ks * 9 + k];
-        if (DF) split_df(g[k], gh[k], gl[k]);
+  const int ix = (int)(is % a.nx), iy = (int)(is / a.nx);
+  const int lx = a.lenX[ix];
+  const int ls = lx * a.lenY[iy];
+  const int n9 = 9 * ls;
+  const int64_t ls0 = a.LSb[is];
+  // phase 0: the row's G blocks into slices[0 .. 9 ls)
+  for (int item = tid; item < n9; item += nthr) {
+    const int ks = item / 9, ab = item % 9;
+    const int jx = a.loX[ix] + ks % lx, jy = a.loY[iy] + ks / lx;
+    const int ex0 = max(a.eloX[ix], a.eloX[jx]), ex1 = min(a.ehiX[ix], a.ehiX[jx]);
+    const int ey0 = max(a.eloY[iy], a.eloY[jy]), ey1 = min(a.ehiY[iy], a.ehiY[jy]);
+    const int ba = (ab % 3) * 3 + ab / 3;
+    double acc = 0.0;
+    for (int ey = ey0; ey <= ey1; ++ey) {
+      const int fy = a.firstV[ey];
+      for (int ex = ex0; ex <= ex1; ++ex) {
+        const int fx = a.firstU[ex];
+        const int li = (iy - fy) * a.nlx + (ix - fx), lj = (jy - fy) * a.nlx + (jx - fx);
+        const size_t e9 = ((size_t)ey * a.nel_u + ex) * 9;
+        if (li <= lj)
+          acc += a.EG[(e9 + ab) * a.npl + upper_pair(li, lj, a.nls)];
+        else
+          acc += a.EG[(e9 + ba) * a.npl + upper_pair(lj, li, a.nls)];
       }
     }
-    __syncthreads();  // the G row is in registers; its space is reused by the slices
-    const int cd = c * 3 + d;
-    const bool block_type = ((c == 2) == (d == 2));
-    const int offa = block_type ? 0 : 1, offb = block_type ? 3 : 2;
-    const int seg_len = 3 * ls;
-    const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
-    for (int ch = 0; ch < a.nchunk; ++ch) {
-      int it0 = a.ck_it[ch], it1 = a.ck_it[ch + 1];
-      if (CHUNKED) {
-        it0 = max(it0, a.it_lo);
-        it1 = min(it1, a.it_hi);
-        if (it0 >= it1) continue;  // the same for every thread
-      }
-      // the chunk's terms into shared memory
-      const int tb = a.ck_term[ch], nterm = a.ck_term[ch + 1] - tb;
-      for (int k = tid; k < nterm; k += nthr) {
-        const int t = tb + k, m = a.ckt_cfg[t];
-        const size_t qi = ((size_t)a.ckt_rep[t] * a.ncfg + m) * 4;
-        if (DF) {
-          float2* q2 = reinterpret_cast<float2*>(sQ + 4 * (size_t)k);
+    slices[item] = acc;
+  }
+  __syncthreads();
+  const int item = tid;
+  const bool active = item < n9;
+  int c = 0, ks = 0, d = 0;
+  double g[9];
+  float gh[9], gl[9];
+  if (active) {
+    c = item / (3 * ls);
+    const int rem = item % (3 * ls);
+    ks = rem / 3;
+    d = rem % 3;
 #pragma unroll
-          for (int j = 0; j < 4; ++j) q2[j] = a.qdf[qi + j];
-        } else {
-#pragma unroll
-          for (int j = 0; j < 4; ++j) sQ[4 * (size_t)k + j] = a.q[qi + j];
-        }
-        sSlot[k] = a.ckt_slot[t];
-        sFirst[k] = a.ckt_first[t];
-        sCfg[k] = m;
-      }
-      __syncthreads();
-      // phase 1: slice of every class of the chunk (terms sorted by configuration)
-      if (active) {
-        const int t1 = nterm;
-        int cur = -1;
-        if (DF) {
-          float ah = 0.0f, al = 0.0f, bh = 0.0f, bl = 0.0f, ch_ = 0.0f, cl = 0.0f, dh = 0.0f, dl = 0.0f;
-          for (int t = 0; t < t1; ++t) {
-            const int m = sCfg[t];
-            if (m != cur) {
-              cur = m;
-              const float2* E = a.cfgEdf + (size_t)m * 81 + cd * 9;
-              if (MONO) {
-                if (block_type) {
-                  df_dot(E, gh, gl, 0, 1, 3, 4, 4, ah, al);
-                  df_dot(E, gh, gl, 8, 8, 8, 8, 1, bh, bl);
-                } else {
-                  df_dot(E, gh, gl, 2, 5, 0, 0, 2, ah, al);
-                  df_dot(E, gh, gl, 6, 7, 0, 0, 2, bh, bl);
-                }
-              } else {
-                df_dot(E, gh, gl, 0, 1, 3, 4, 4, ah, al);
-                df_dot(E, gh, gl, 2, 5, 0, 0, 2, bh, bl);
-                df_dot(E, gh, gl, 6, 7, 0, 0, 2, ch_, cl);
-                df_dot(E, gh, gl, 8, 8, 8, 8, 1, dh, dl);
-              }
-            }
-            const float2* q2 = reinterpret_cast<const float2*>(sQ + 4 * (size_t)t);
-            float vh, vl, p, e;
-            if (MONO) {
-              const float2 qa = q2[offa], qb = q2[offb];
-              df_mul(qa.x, qa.y, ah, al, vh, vl);
-              df_mul(qb.x, qb.y, bh, bl, p, e);
-              df_add(p, e, vh, vl);
-            } else {
-              df_mul(q2[0].x, q2[0].y, ah, al, vh, vl);
-              df_mul(q2[1].x, q2[1].y, bh, bl, p, e);
-              df_add(p, e, vh, vl);
-              df_mul(q2[2].x, q2[2].y, ch_, cl, p, e);
-              df_add(p, e, vh, vl);
-              df_mul(q2[3].x, q2[3].y, dh, dl, p, e);
-              df_add(p, e, vh, vl);
-            }
-            float2* dst = reinterpret_cast<float2*>(slices + (size_t)sSlot[t] * a.slice_stride + item);
-            if (!sFirst[t]) {
-              const float2 o = *dst;
-              df_add(o.x, o.y, vh, vl);
-            }
-            *dst = make_float2(vh, vl);
-          }
-          // float pairs -> doubles, in place (each thread its own column)
-          const int ns_ = a.ck_nslot[ch];
-          for (int u = 0; u < ns_; ++u) {
-            double* dst = slices + (size_t)u * a.slice_stride + item;
-            const float2 v = *reinterpret_cast<const float2*>(dst);
-            const float hs = __fadd_rn(v.x, v.y);
-            const float lsum = __fsub_rn(v.y, __fsub_rn(hs, v.x));
-            const int ef = (int)((__float_as_uint(hs) >> 23) & 0xFFu);
-            bad |= (ef == 255);
-            emax = max(emax, ef);
-            *dst = df_to_double(hs, lsum);
-          }
-        } else {
-          double pa = 0.0, pb = 0.0, p11 = 0.0, p12 = 0.0, p21 = 0.0, p22 = 0.0;
-          for (int t = 0; t < t1; ++t) {
-            const int m = sCfg[t];
-            if (m != cur) {
-              cur = m;
-              const double* E = a.cfgE + (size_t)m * 81 + cd * 9;
-              if (MONO) {
-                if (block_type) {
-                  pa = E[0] * g[0] + E[1] * g[1] + E[3] * g[3] + E[4] * g[4];
-                  pb = E[8] * g[8];
-                } else {
-                  pa = E[2] * g[2] + E[5] * g[5];
-                  pb = E[6] * g[6] + E[7] * g[7];
-                }
-              } else {
-                p11 = E[0] * g[0] + E[1] * g[1] + E[3] * g[3] + E[4] * g[4];
-                p12 = E[2] * g[2] + E[5] * g[5];
-                p21 = E[6] * g[6] + E[7] * g[7];
-                p22 = E[8] * g[8];
-              }
-            }
-            const double* Q = sQ + 4 * (size_t)t;
-            const double v = MONO ? Q[offa] * pa + Q[offb] * pb : Q[0] * p11 + Q[1] * p12 + Q[2] * p21 + Q[3] * p22;
-            double* dst = slices + (size_t)sSlot[t] * a.slice_stride + item;
-            *dst = sFirst[t] ? v : *dst + v;
-          }
-        }
-      }
-      __syncthreads();
-      // phase 2: the chunk's thickness pairs (i_t, k_t) in address order, one
-      // warp per pair. Row (i_t, i_s, c) holds len_t segments of 3 len_s
-      // values; the pair's three segments (c = 0, 1, 2) sit one row apart. Each
-      // copy issues all of its shared loads before its global stores.
-      const int64_t p_end = a.LTb[it1];
-      for (int64_t pr = a.LTb[it0] + warp; pr < p_end; pr += nwarps) {
-        const int64_t A = a.tp_A[pr];
-        const int lt = a.tp_lt[pr], kt = a.tp_k[pr], u = a.pair_slot[pr];
-        const double* src = slices + (size_t)u * a.slice_stride;
-        double* dst = a.values + (A + (int64_t)lt * 9 * ls0 + (int64_t)kt * seg_len - a.out_offset);
-        const int64_t row_step = (int64_t)lt * seg_len;
-#pragma unroll
-        for (int cc = 0; cc < 3; ++cc) {
-          double v[kSegUnroll];
-#pragma unroll
-          for (int j = 0; j < kSegUnroll; ++j) v[j] = (lane + 32 * j < seg_len) ? src[cc * seg_len + lane + 32 * j] : 0.0;
-#pragma unroll
-          for (int j = 0; j < kSegUnroll; ++j)
-            if (lane + 32 * j < seg_len) dst[cc * row_step + lane + 32 * j] = v[j];
-        }
-      }
-      __syncthreads();  // the slices are rewritten by the next chunk or row
+    for (int k = 0; k < 9; ++k) {
+      g[k] = slices[ks * 9 + k];
+      if (DF) split_df(g[k], gh[k], gl[k]);
     }
   }
+  __syncthreads();  // the G row is in registers; its space is reused by the slices
+  const int cd = c * 3 + d;
+  const bool block_type = ((c == 2) == (d == 2));
+  const int offa = block_type ? 0 : 1, offb = block_type ? 3 : 2;
+  const int seg_len = 3 * ls;
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
+  for (int ch = 0; ch < a.nchunk; ++ch) {
+    int it0 = a.ck_it[ch], it1 = a.ck_it[ch + 1];
+    if (CHUNKED) {
+      it0 = max(it0, a.it_lo);
+      it1 = min(it1, a.it_hi);
+      if (it0 >= it1) continue;  // the same for every thread
+    }
+    // the chunk's terms into shared memory
+    const int tb = a.ck_term[ch], nterm = a.ck_term[ch + 1] - tb;
+    for (int k = tid; k < nterm; k += nthr) {
+      const int t = tb + k, m = a.ckt_cfg[t];
+      const size_t qi = ((size_t)a.ckt_rep[t] * a.ncfg + m) * 4;
+      if (DF) {
+        float2* q2 = reinterpret_cast<float2*>(sQ + 4 * (size_t)k);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) q2[j] = a.qdf[qi + j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) sQ[4 * (size_t)k + j] = a.q[qi + j];
+      }
+      sSlot[k] = a.ckt_slot[t];
+      sFirst[k] = a.ckt_first[t];
+      sCfg[k] = m;
+    }
+    __syncthreads();
+    // phase 1: slice of every class of the chunk (terms sorted by configuration)
+    if (active) {
+      const int t1 = nterm;
+      int cur = -1;
+      if (DF) {
+        float ah = 0.0f, al = 0.0f, bh = 0.0f, bl = 0.0f, ch_ = 0.0f, cl = 0.0f, dh = 0.0f, dl = 0.0f;
+        for (int t = 0; t < t1; ++t) {
+          const int m = sCfg[t];
+          if (m != cur) {
+            cur = m;
+            const float2* E = a.cfgEdf + (size_t)m * 81 + cd * 9;
+            if (MONO) {
+              if (block_type) {
+                df_dot(E, gh, gl, 0, 1, 3, 4, 4, ah, al);
+                df_dot(E, gh, gl, 8, 8, 8, 8, 1, bh, bl);
+              } else {
+                df_dot(E, gh, gl, 2, 5, 0, 0, 2, ah, al);
+                df_dot(E, gh, gl, 6, 7, 0, 0, 2, bh, bl);
+              }
+            } else {
+              df_dot(E, gh, gl, 0, 1, 3, 4, 4, ah, al);
+              df_dot(E, gh, gl, 2, 5, 0, 0, 2, bh, bl);
+              df_dot(E, gh, gl, 6, 7, 0, 0, 2, ch_, cl);
+              df_dot(E, gh, gl, 8, 8, 8, 8, 1, dh, dl);
+            }
+          }
+          const float2* q2 = reinterpret_cast<const float2*>(sQ + 4 * (size_t)t);
+          float vh, vl, p, e;
+          if (MONO) {
+            const float2 qa = q2[offa], qb = q2[offb];
+            df_mul(qa.x, qa.y, ah, al, vh, vl);
+            df_mul(qb.x, qb.y, bh, bl, p, e);
+            df_add(p, e, vh, vl);
+          } else {
+            df_mul(q2[0].x, q2[0].y, ah, al, vh, vl);
+            df_mul(q2[1].x, q2[1].y, bh, bl, p, e);
+            df_add(p, e, vh, vl);
+            df_mul(q2[2].x, q2[2].y, ch_, cl, p, e);
+            df_add(p, e, vh, vl);
+            df_mul(q2[3].x, q2[3].y, dh, dl, p, e);
+            df_add(p, e, vh, vl);
+          }
+          float2* dst = reinterpret_cast<float2*>(slices + (size_t)sSlot[t] * a.slice_stride + item);
+          if (!sFirst[t]) {
+            const float2 o = *dst;
+            df_add(o.x, o.y, vh, vl);
+          }
+          *dst = make_float2(vh, vl);
+        }
+        // float pairs -> doubles, in place (each thread its own column)
+        const int ns_ = a.ck_nslot[ch];
+        for (int u = 0; u < ns_; ++u) {
+          double* dst = slices + (size_t)u * a.slice_stride + item;
+          const float2 v = *reinterpret_cast<const float2*>(dst);
+          const float hs = __fadd_rn(v.x, v.y);
+          const float lsum = __fsub_rn(v.y, __fsub_rn(hs, v.x));
+          const int ef = (int)((__float_as_uint(hs) >> 23) & 0xFFu);
+          bad |= (ef == 255);
+          emax = max(emax, ef);
+          *dst = df_to_double(hs, lsum);
+        }
+      } else {
+        double pa = 0.0, pb = 0.0, p11 = 0.0, p12 = 0.0, p21 = 0.0, p22 = 0.0;
+        for (int t = 0; t < t1; ++t) {
+          const int m = sCfg[t];
+          if (m != cur) {
+            cur = m;
+            const double* E = a.cfgE + (size_t)m * 81 + cd * 9;
+            if (MONO) {
+              if (block_type) {
+                pa = E[0] * g[0] + E[1] * g[1] + E[3] * g[3] + E[4] * g[4];
+                pb = E[8] * g[8];
+              } else {
+                pa = E[2] * g[2] + E[5] * g[5];
+                pb = E[6] * g[6] + E[7] * g[7];
+              }
+            } else {
+              p11 = E[0] * g[0] + E[1] * g[1] + E[3] * g[3] + E[4] * g[4];
+              p12 = E[2] * g[2] + E[5] * g[5];
+              p21 = E[6] * g[6] + E[7] * g[7];
+              p22 = E[8] * g[8];
+            }
+          }
+          const double* Q = sQ + 4 * (size_t)t;
+          const double v = MONO ? Q[offa] * pa + Q[offb] * pb : Q[0] * p11 + Q[1] * p12 + Q[2] * p21 + Q[3] * p22;
+          double* dst = slices + (size_t)sSlot[t] * a.slice_stride + item;
+          *dst = sFirst[t] ? v : *dst + v;
+        }
+      }
+    }
+    __syncthreads();
+    // phase 2: the chunk's thickness pairs (i_t, k_t) in address order, one
+    // warp per pair. Row (i_t, i_s, c) holds len_t segments of 3 len_s
+    // values; the pair's three segments (c = 0, 1, 2) sit one row apart. Each
+    // copy issues all of its shared loads before its global stores.
+    const int64_t p_end = a.LTb[it1];
+    for (int64_t pr = a.LTb[it0] + warp; pr < p_end; pr += nwarps) {
+      const int64_t A = a.tp_A[pr];
+      const int lt = a.tp_lt[pr], kt = a.tp_k[pr], u = a.pair_slot[pr];
+      const double* src = slices + (size_t)u * a.slice_stride;
+      double* dst = a.values + (A + (int64_t)lt * 9 * ls0 + (int64_t)kt * seg_len - a.out_offset);
+      const int64_t row_step = (int64_t)lt * seg_len;
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) {
+        double v[kSegUnroll];
+#pragma unroll
+        for (int j = 0; j < kSegUnroll; ++j) v[j] = (lane + 32 * j < seg_len) ? src[cc * seg_len + lane + 32 * j] : 0.0;
+#pragma unroll
+        for (int j = 0; j < kSegUnroll; ++j)
+          if (lane + 32 * j < seg_len) dst[cc * row_step + lane + 32 * j] = v[j];
+      }
+    }
+    __syncthreads();  // the slices are rewritten by the next chunk or row
+  }
+}
+
+template <bool MONO, bool CHUNKED, bool DF>
+__global__ void __maxnreg__(64) kc_stream(KcArgs a) {
+  if (!DF && a.conditional && *a.flag == 0) return;
+  extern __shared__ double sm[];
+  int emax = 0;
+  bool bad = false;
+  for (int64_t is = blockIdx.x; is < a.ns; is += gridDim.x) kcs_row<MONO, CHUNKED, DF>(a, is, sm, emax, bad);
   if (DF) {
     emax = __reduce_max_sync(0xffffffffu, emax);
     const bool any_bad = __any_sync(0xffffffffu, bad);
-    if ((tid & 31) == 0) {
+    if ((threadIdx.x & 31) == 0) {
       atomicMax(a.emax, emax);
       if (any_bad) atomicOr(a.flag, 1);
     }
@@ -2666,3 +2678,468 @@ extern "C" lam_status lam_assemble_split_noalloc(const lam_plan* plan, double* d
   LAM_CUDA(cudaGetLastError());
   return LAM_OK;
 }
+
+// ===========================================================================
+// Batches (lam_batch_*): one launch per stage for many laminates.
+// ===========================================================================
+namespace lam {
+
+__device__ __forceinline__ int find_slot(const int64_t* prefix, int n, int64_t g) {
+  int lo = 0, hi = n;  // prefix[lo] <= g < prefix[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= g)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// Eq. Q for every thickness pair of every instance.
+__global__ void kb_batch(const KbArgs* __restrict__ args, const int64_t* __restrict__ prefix, int n) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= prefix[n]) return;
+  const int i = find_slot(prefix, n, g);
+  kb_pair(args[i], g - prefix[i]);
+}
+
+// In-plane Gram blocks of every element of every distinct mesh.
+__global__ void __launch_bounds__(256) ka_batch(const KaLocalArgs* __restrict__ args, const int64_t* __restrict__ prefix,
+                                                int n) {
+  extern __shared__ double sm[];
+  const int i = find_slot(prefix, n, blockIdx.x);
+  ka_elem(args[i], (int)(blockIdx.x - prefix[i]), sm);
+}
+
+struct BatchKcArgs {
+  const KcArgs* kc;           // per instance
+  const int64_t* row_prefix;  // rows of the instances in work order, n + 1
+  const int* order;           // work order -> instance
+  const int* mono;            // per instance: monoclinic
+  int n;
+  unsigned long long* counter;
+  int* flags;                 // per instance: FP64 re-pass flag, largest exponent
+};
+
+// Persistent combine: CTAs take (instance, in-plane row) items from an atomic
+// counter until none are left. DF = false re-runs only the flagged instances.
+// MONO = true when every instance is monoclinic (the general form is exact for
+// the others too).
+template <bool MONO, bool DF>
+__global__ void __maxnreg__(64) kc_batch(BatchKcArgs b) {
+  extern __shared__ double sm[];
+  __shared__ unsigned long long s_item;
+  const int64_t total = b.row_prefix[b.n];
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(b.counter, 1ull);
+    __syncthreads();
+    const int64_t g = (int64_t)s_item;
+    __syncthreads();
+    if (g >= total) break;
+    const int k = find_slot(b.row_prefix, b.n, g);
+    const int inst = b.order[k];
+    if (!DF && b.flags[2 * inst] == 0) continue;
+    int emax = 0;
+    bool bad = false;
+    kcs_row<MONO, false, DF>(b.kc[inst], g - b.row_prefix[k], sm, emax, bad);
+    if (DF) {
+      emax = __reduce_max_sync(0xffffffffu, emax);
+      const bool any_bad = __any_sync(0xffffffffu, bad);
+      if ((threadIdx.x & 31) == 0) {
+        atomicMax(&b.flags[2 * inst + 1], emax);
+        if (any_bad) atomicOr(&b.flags[2 * inst], 1);
+      }
+    }
+  }
+}
+
+__global__ void kc_batch_check(int* flags, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && flags[2 * i + 1] < kKcMinExp) flags[2 * i] = 1;
+}
+
+}  // namespace lam
+
+struct lam_batch {
+  std::vector<lam_plan*> plans;
+  std::vector<int> versions;
+  int device = -1;
+  int n_meshes = 0;
+  int64_t nnz_total = 0;
+  std::vector<int> persistent;    // instances of the persistent combine (index into plans)
+  std::vector<int> fallback;      // instances assembled by lam_assemble_split
+  std::vector<int> inst_slot;     // plan -> index in persistent, or -1
+  std::vector<void*> allocs;
+  // launch tables
+  lam::KbArgs* d_kb = nullptr;
+  int64_t* d_pair_prefix = nullptr;
+  int64_t total_pairs = 0;
+  lam::KaLocalArgs* d_ka = nullptr;
+  int64_t* d_elem_prefix = nullptr;
+  int64_t total_elems = 0;
+  lam::KcArgs* d_kc = nullptr;
+  lam::KcArgs* h_kc = nullptr;    // pinned host copy (value pointers change per call)
+  int64_t* d_row_prefix = nullptr;
+  int* d_order = nullptr;
+  int* d_mono = nullptr;
+  int* d_flags = nullptr;
+  unsigned long long* d_counter = nullptr;
+  int ka_block = 32, kc_block = 128;
+  bool all_mono = true;
+  size_t ka_smem = 0, kc_smem = 0;
+  int n_sm = 1, max_ctas = 1;
+  // tuning and graph
+  int ctas_per_sm = 0;
+  double tuned_ms[4] = {0, 0, 0, 0};
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<double*> last_values;
+};
+
+namespace lam {
+
+template <typename T>
+static lam_status batch_upload(lam_batch& B, T** dst, const T* src, size_t n) {
+  void* p = nullptr;
+  LAM_CUDA(cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)));
+  B.allocs.push_back(p);
+  if (n) LAM_CUDA(cudaMemcpy(p, src, n * sizeof(T), cudaMemcpyHostToDevice));
+  *dst = static_cast<T*>(p);
+  return LAM_OK;
+}
+
+static bool same_mesh(const Plan& a, const Plan& b) {
+  auto same_basis = [](const Basis& x, const Basis& y) { return x.kind == y.kind && x.p == y.p && x.knots == y.knots; };
+  return same_basis(a.u, b.u) && same_basis(a.v, b.v) && a.ctrl == b.ctrl && a.weights == b.weights &&
+         a.nqu == b.nqu && a.nqv == b.nqv;
+}
+
+// The persistent sequence: memsets, Eq. Q, Gram blocks, double-float combine,
+// exponent check, conditional FP64 combine.
+static lam_status batch_launch(lam_batch& B, int ctas_per_sm, cudaStream_t s) {
+  const int n = (int)B.persistent.size();
+  if (n == 0) return LAM_OK;
+  LAM_CUDA(cudaMemsetAsync(B.d_flags, 0, 2 * n * sizeof(int), s));
+  LAM_CUDA(cudaMemsetAsync(B.d_counter, 0, 2 * sizeof(unsigned long long), s));
+  kb_batch<<<(unsigned)((B.total_pairs + 127) / 128), 128, 0, s>>>(B.d_kb, B.d_pair_prefix, n);
+  LAM_CUDA(cudaGetLastError());
+  ka_batch<<<(unsigned)B.total_elems, B.ka_block, B.ka_smem, s>>>(B.d_ka, B.d_elem_prefix, B.n_meshes);
+  LAM_CUDA(cudaGetLastError());
+  BatchKcArgs b{};
+  b.kc = B.d_kc;
+  b.row_prefix = B.d_row_prefix;
+  b.order = B.d_order;
+  b.mono = B.d_mono;
+  b.n = n;
+  b.counter = B.d_counter;
+  b.flags = B.d_flags;
+  const unsigned grid = (unsigned)(ctas_per_sm * B.n_sm);
+  if (B.all_mono)
+    kc_batch<true, true><<<grid, B.kc_block, B.kc_smem, s>>>(b);
+  else
+    kc_batch<false, true><<<grid, B.kc_block, B.kc_smem, s>>>(b);
+  LAM_CUDA(cudaGetLastError());
+  kc_batch_check<<<(n + 127) / 128, 128, 0, s>>>(B.d_flags, n);
+  LAM_CUDA(cudaGetLastError());
+  b.counter = B.d_counter + 1;
+  if (B.all_mono)
+    kc_batch<true, false><<<grid, B.kc_block, B.kc_smem, s>>>(b);
+  else
+    kc_batch<false, false><<<grid, B.kc_block, B.kc_smem, s>>>(b);
+  LAM_CUDA(cudaGetLastError());
+  return LAM_OK;
+}
+
+static void batch_free(lam_batch* B) {
+  if (!B) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (B->device >= 0) cudaSetDevice(B->device);
+  cudaDeviceSynchronize();
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->capture_stream) cudaStreamDestroy(B->capture_stream);
+  for (void* p : B->allocs) cudaFree(p);
+  if (B->h_kc) cudaFreeHost(B->h_kc);
+  if (cur >= 0) cudaSetDevice(cur);
+  delete B;
+}
+
+}  // namespace lam
+
+extern "C" {
+
+lam_status lam_batch_create(lam_batch** out, lam_plan* const* plans, int32_t n_plans) {
+  if (!out || !plans || n_plans < 1) {
+    lam::set_error("lam_batch_create: NULL argument or no plans");
+    return LAM_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  for (int i = 0; i < n_plans; ++i) {
+    if (!plans[i]) {
+      lam::set_error("lam_batch_create: plan %d is NULL", i);
+      return LAM_ERR_INVALID_ARG;
+    }
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i]) {
+        lam::set_error("lam_batch_create: plan %d appears twice", i);
+        return LAM_ERR_INVALID_ARG;
+      }
+  }
+  lam_batch* B = new (std::nothrow) lam_batch();
+  if (!B) {
+    lam::set_error("lam_batch_create: out of host memory");
+    return LAM_ERR_OOM;
+  }
+  lam_status st = LAM_OK;
+#define BCHECK(x)           \
+  do {                      \
+    if ((st = (x)) != LAM_OK) { \
+      lam::batch_free(B);   \
+      return st;            \
+    }                       \
+  } while (0)
+  int cur = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    lam::set_error("lam_batch_create: no CUDA device");
+    delete B;
+    return LAM_ERR_CUDA;
+  }
+  B->device = cur;
+  B->plans.assign(plans, plans + n_plans);
+  for (int i = 0; i < n_plans; ++i) {
+    lam::Plan& P = plans[i]->p;
+    BCHECK(lam::check_limits(P));
+    BCHECK(lam::ensure_device(P));
+    B->versions.push_back(P.cfg_version);
+    B->nnz_total += P.nnz;
+  }
+  cudaDeviceGetAttribute(&B->n_sm, cudaDevAttrMultiProcessorCount, cur);
+  // distinct meshes and their shared Gram-block buffers
+  std::vector<int> mesh_of(n_plans, -1), mesh_rep;
+  for (int i = 0; i < n_plans; ++i) {
+    for (size_t g = 0; g < mesh_rep.size() && mesh_of[i] < 0; ++g)
+      if (lam::same_mesh(plans[mesh_rep[g]]->p, plans[i]->p)) mesh_of[i] = (int)g;
+    if (mesh_of[i] < 0) {
+      mesh_of[i] = (int)mesh_rep.size();
+      mesh_rep.push_back(i);
+    }
+  }
+  B->n_meshes = (int)mesh_rep.size();
+  std::vector<double*> mesh_EG(B->n_meshes);
+  std::vector<lam::KaLocalArgs> ka(B->n_meshes);
+  std::vector<int64_t> elem_prefix(B->n_meshes + 1, 0);
+  for (int g = 0; g < B->n_meshes; ++g) {
+    const lam::Plan& P = plans[mesh_rep[g]]->p;
+    BCHECK(lam::alloc_dev(B->allocs, &mesh_EG[g], (size_t)P.u.nel * P.v.nel * 9 * lam::ka_npl(P)));
+    ka[g] = lam::KaLocalArgs{};
+    ka[g].ip = lam::inplane_args(P);
+    ka[g].nel = P.u.nel * P.v.nel;
+    ka[g].EG = mesh_EG[g];
+    elem_prefix[g + 1] = elem_prefix[g] + ka[g].nel;
+    B->ka_block = std::max(B->ka_block, lam::ka_block(P));
+    B->ka_smem = std::max(B->ka_smem, lam::ka_smem(P));
+  }
+  B->total_elems = elem_prefix[B->n_meshes];
+  // instances of the persistent combine, largest first
+  B->inst_slot.assign(n_plans, -1);
+  for (int i = 0; i < n_plans; ++i) {
+    if (lam::use_stream(plans[i]->p))
+      B->persistent.push_back(i);
+    else
+      B->fallback.push_back(i);
+  }
+  std::stable_sort(B->persistent.begin(), B->persistent.end(),
+                   [&](int x, int y) { return plans[x]->p.nnz > plans[y]->p.nnz; });
+  const int n = (int)B->persistent.size();
+  std::vector<lam::KbArgs> kb(n);
+  std::vector<lam::KcArgs> kc(n);
+  std::vector<int64_t> pair_prefix(n + 1, 0), row_prefix(n + 1, 0);
+  std::vector<int> order(n), mono(n);
+  for (int k = 0; k < n; ++k) {
+    const int i = B->persistent[k];
+    B->inst_slot[i] = k;
+    lam::Plan& P = plans[i]->p;
+    const lam::Device& D = *P.dev;
+    lam::KbArgs& a = kb[k];
+    a = lam::KbArgs{};
+    a.npairs = P.nnz_t;
+    a.ncfg = (int)P.cfg_mat.size();
+    a.nqt = P.nqt;
+    a.q1 = P.t.p + 1;
+    a.tp_row = D.tp_row;
+    a.tp_col = D.tp_col;
+    a.tp_e0 = D.tp_e0;
+    a.tp_e1 = D.tp_e1;
+    a.firstT = D.firstT;
+    a.piece_begin = D.piece_begin;
+    a.piece_cfg = D.piece_cfg;
+    a.tabT = D.tabT;
+    a.wT = D.wT;
+    a.q = D.q;
+    a.qdf = D.qdf;
+    pair_prefix[k + 1] = pair_prefix[k] + P.nnz_t;
+    kc[k] = lam::kc_args(P, nullptr);
+    kc[k].EG = mesh_EG[mesh_of[i]];
+    order[k] = k;
+    mono[k] = P.monoclinic ? 1 : 0;
+    B->all_mono = B->all_mono && P.monoclinic;
+    row_prefix[k + 1] = row_prefix[k] + P.ns;
+    B->kc_block = std::max(B->kc_block, lam::kcs_block(P));
+    B->kc_smem = std::max(B->kc_smem, lam::kcs_smem(P));
+  }
+  B->total_pairs = pair_prefix[n];
+  BCHECK(lam::batch_upload(*B, &B->d_kb, kb.data(), kb.size()));
+  BCHECK(lam::batch_upload(*B, &B->d_pair_prefix, pair_prefix.data(), pair_prefix.size()));
+  BCHECK(lam::batch_upload(*B, &B->d_ka, ka.data(), ka.size()));
+  BCHECK(lam::batch_upload(*B, &B->d_elem_prefix, elem_prefix.data(), elem_prefix.size()));
+  BCHECK(lam::batch_upload(*B, &B->d_kc, kc.data(), kc.size()));
+  BCHECK(lam::batch_upload(*B, &B->d_row_prefix, row_prefix.data(), row_prefix.size()));
+  BCHECK(lam::batch_upload(*B, &B->d_order, order.data(), order.size()));
+  BCHECK(lam::batch_upload(*B, &B->d_mono, mono.data(), mono.size()));
+  std::vector<int> zeros(2 * std::max(n, 1), 0);
+  BCHECK(lam::batch_upload(*B, &B->d_flags, zeros.data(), zeros.size()));
+  std::vector<unsigned long long> cz(2, 0ull);
+  BCHECK(lam::batch_upload(*B, &B->d_counter, cz.data(), cz.size()));
+  if (cudaMallocHost(reinterpret_cast<void**>(&B->h_kc), std::max(n, 1) * sizeof(lam::KcArgs)) != cudaSuccess) {
+    lam::set_error("lam_batch_create: cudaMallocHost failed");
+    lam::batch_free(B);
+    return LAM_ERR_OOM;
+  }
+  std::copy(kc.begin(), kc.end(), B->h_kc);
+  B->last_values.assign(n_plans, nullptr);
+  // resident CTAs per SM by registers (64 per thread) and by shared memory
+  int by_regs = std::max(1, 65536 / (64 * B->kc_block));
+  int by_smem = (int)(233472 / (B->kc_smem + 1024 + 16));
+  B->max_ctas = std::max(1, std::min(4, std::min(by_regs, by_smem)));
+  if (B->ka_smem > 48 * 1024) {
+    if (cudaFuncSetAttribute(lam::ka_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->ka_smem) != cudaSuccess) {
+      lam::set_error("lam_batch_create: K-a shared memory");
+      lam::batch_free(B);
+      return LAM_ERR_UNSUPPORTED;
+    }
+  }
+  const int ks = (int)B->kc_smem;
+  if (cudaFuncSetAttribute(lam::kc_batch<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ks) != cudaSuccess ||
+      cudaFuncSetAttribute(lam::kc_batch<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ks) != cudaSuccess ||
+      cudaFuncSetAttribute(lam::kc_batch<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ks) != cudaSuccess ||
+      cudaFuncSetAttribute(lam::kc_batch<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ks) != cudaSuccess) {
+    lam::set_error("lam_batch_create: combine shared memory (%zu bytes)", B->kc_smem);
+    lam::batch_free(B);
+    return LAM_ERR_UNSUPPORTED;
+  }
+#undef BCHECK
+  lam::set_error("");
+  *out = B;
+  return LAM_OK;
+}
+
+lam_status lam_batch_assemble(lam_batch* B, double* const* d_values, void* stream) {
+  if (!B || !d_values) {
+    lam::set_error("lam_batch_assemble: NULL argument");
+    return LAM_ERR_INVALID_ARG;
+  }
+  const int np = (int)B->plans.size();
+  for (int i = 0; i < np; ++i) {
+    if (!d_values[i]) {
+      lam::set_error("lam_batch_assemble: values of plan %d are NULL", i);
+      return LAM_ERR_INVALID_ARG;
+    }
+    if (B->plans[i]->p.cfg_version != B->versions[i]) {
+      lam::set_error("lam_batch_assemble: plan %d was updated after the batch was created; recreate the batch", i);
+      return LAM_ERR_INVALID_ARG;
+    }
+  }
+  int cur = -1;
+  LAM_CUDA(cudaGetDevice(&cur));
+  if (cur != B->device) {
+    lam::set_error("lam_batch_assemble: batch lives on device %d, current device is %d", B->device, cur);
+    return LAM_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  lam_status st;
+  // value pointers of the persistent instances
+  bool changed = false;
+  for (int i = 0; i < np; ++i)
+    if (B->inst_slot[i] >= 0 && B->last_values[i] != d_values[i]) changed = true;
+  const int n = (int)B->persistent.size();
+  if (changed && n > 0) {
+    // the pinned staging copy must not be rewritten while an earlier upload from it may be pending
+    LAM_CUDA(cudaDeviceSynchronize());
+    for (int i = 0; i < np; ++i)
+      if (B->inst_slot[i] >= 0) {
+        B->h_kc[B->inst_slot[i]].values = d_values[i];
+        B->last_values[i] = d_values[i];
+      }
+    LAM_CUDA(cudaMemcpyAsync(B->d_kc, B->h_kc, n * sizeof(lam::KcArgs), cudaMemcpyHostToDevice, s));
+  }
+  if (n > 0 && B->ctas_per_sm == 0) {
+    // autotune: one full sequence per candidate, after a warm-up
+    if ((st = lam::batch_launch(*B, 1, s)) != LAM_OK) return st;
+    cudaEvent_t e0, e1;
+    LAM_CUDA(cudaEventCreate(&e0));
+    LAM_CUDA(cudaEventCreate(&e1));
+    double best = 1e300;
+    for (int c = 1; c <= B->max_ctas; ++c) {
+      LAM_CUDA(cudaEventRecord(e0, s));
+      if ((st = lam::batch_launch(*B, c, s)) != LAM_OK) return st;
+      LAM_CUDA(cudaEventRecord(e1, s));
+      LAM_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      LAM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      B->tuned_ms[c - 1] = ms;
+      if (ms < best) {
+        best = ms;
+        B->ctas_per_sm = c;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // capture the tuned sequence on a stream of the batch's own
+    LAM_CUDA(cudaStreamCreateWithFlags(&B->capture_stream, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    LAM_CUDA(cudaStreamBeginCapture(B->capture_stream, cudaStreamCaptureModeThreadLocal));
+    st = lam::batch_launch(*B, B->ctas_per_sm, B->capture_stream);
+    cudaError_t ce = cudaStreamEndCapture(B->capture_stream, &graph);
+    if (st != LAM_OK) return st;
+    if (ce != cudaSuccess) {
+      lam::set_error("lam_batch_assemble: graph capture failed: %s", cudaGetErrorString(ce));
+      return LAM_ERR_CUDA;
+    }
+    ce = cudaGraphInstantiate(&B->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+      B->exec = nullptr;
+      lam::set_error("lam_batch_assemble: graph instantiation failed: %s", cudaGetErrorString(ce));
+      return LAM_ERR_CUDA;
+    }
+  } else if (n > 0) {
+    LAM_CUDA(cudaGraphLaunch(B->exec, s));
+  }
+  for (int i : B->fallback)
+    if ((st = lam_assemble_split(B->plans[i], d_values[i], stream)) != LAM_OK) return st;
+  return LAM_OK;
+}
+
+lam_status lam_batch_get_info(const lam_batch* B, lam_batch_info* info) {
+  if (!B || !info) {
+    lam::set_error("lam_batch_get_info: NULL argument");
+    return LAM_ERR_INVALID_ARG;
+  }
+  *info = lam_batch_info{};
+  info->n_plans = (int32_t)B->plans.size();
+  info->n_meshes = B->n_meshes;
+  info->nnz_total = B->nnz_total;
+  info->n_persistent = (int32_t)B->persistent.size();
+  info->ctas_per_sm = B->ctas_per_sm;
+  info->graph = B->exec ? 1 : 0;
+  for (int k = 0; k < 4; ++k) info->tuned_ms[k] = B->tuned_ms[k];
+  return LAM_OK;
+}
+
+lam_status lam_batch_destroy(lam_batch* B) {
+  lam::batch_free(B);
+  return LAM_OK;
+}
+
+}  // extern "C"

@@ -916,7 +916,8 @@ lam_status lam_plan_update(lam_plan* plan, const double* ply_angle_rad, int32_t 
   lam::rebuild_configs(P);
   lam::build_classes(P);
   lam::build_chunks(P);
-  P.cfg_dirty = true;  // configuration tables are re-uploaded by the next device call
+  P.cfg_dirty = true;
+  ++P.cfg_version;  // configuration tables are re-uploaded by the next device call
   return LAM_OK;
 }
 

@@ -198,3 +198,16 @@ def test_adjoint_rejects_invalid_cotangents(lam):
         assert "lam_adjoint" in lam.last_error()
     assert L.lam_adjoint(p.handle, None, 0x2000, None, None, None) == 1
 
+
+
+def test_batch_rejects_invalid_arguments(lam):
+    """Argument checks of lam_batch_create run before any device work."""
+    L = lam.load()
+    p = lam.Plan.from_laminate(W.cross_ply_plate())
+    out = ctypes.c_void_p()
+    arr = (ctypes.c_void_p * 2)(p.handle.value, p.handle.value)
+    assert L.lam_batch_create(ctypes.byref(out), arr, 2) == 1          # the same plan twice
+    assert L.lam_batch_create(ctypes.byref(out), arr, 0) == 1          # no plans
+    assert L.lam_batch_create(None, arr, 1) == 1
+    assert L.lam_batch_assemble(None, None, None) == 1
+    assert L.lam_batch_destroy(None) == 0

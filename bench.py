@@ -331,6 +331,61 @@ def run_adjoint(args, L, dev, flush, peak, peak_kind, world):
     return out
 
 
+def run_batch(args, L, dev, flush, peak, peak_kind, world):
+    """The 256 seeded laminates (quadratic meshes 16..48 squared, 8..64 plies of
+    uneven thickness, 1..4 materials; 1.9e10 stored entries, 155 GB of values)
+    assembled by one lam_batch_assemble per step, and the same plans one by one
+    with lam_assemble_split for comparison."""
+    import torch
+    import workloads as W
+    lams = W.batch_laminates()
+    plans = [L.Plan.from_laminate(l) for l in lams]
+    nnz = sum(p.nnz for p in plans)
+    values = [torch.empty(p.nnz, dtype=torch.float64, device=dev) for p in plans]
+    batch = L.Batch(plans)
+    batch.assemble(values)  # tunes and captures the graph
+    for _ in range(args.warmup):
+        batch.assemble(values)
+    torch.cuda.synchronize()
+    barrier()
+    steps = args.batch_steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        evs[k][0].record()
+        batch.assemble(values)
+        evs[k][1].record()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs) / steps, dev)
+    # the same plans one by one (lam_assemble_split per plan), one timed pass
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.zero_()
+    a.record()
+    for p, v in zip(plans, values):
+        p.assemble_split(v)
+    b.record()
+    torch.cuda.synchronize()
+    seq_ms = a.elapsed_time(b)
+    info = batch.info
+    achieved = 8 * nnz / (ms / 1e3) / 1e9
+    out = {"workload": "256 laminates from default_rng(517): quadratic B-spline meshes {16,24,32,48}^2 on the "
+                       "unit square, 8..64 plies of thickness U[0.0005, 0.002], angles {0, +-45, 90}, 1..4 materials",
+           "metric": "stored entries assembled per second", "value": aggregate_throughput(nnz, world, ms / 1e3),
+           "unit": UNIT, "ms_per_step": ms, "steps": steps, "nnz_total": nnz, "n_plans": len(plans),
+           "n_meshes": info["n_meshes"], "n_persistent": info["n_persistent"], "ctas_per_sm": info["ctas_per_sm"],
+           "autotuner_ms": [round(x, 3) for x in info["tuned_ms"] if x > 0], "cuda_graph": bool(info["graph"]),
+           "one_plan_at_a_time_ms": seq_ms, "speedup_vs_one_at_a_time": seq_ms / ms,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "traffic": None, "kernel": "whole batch (8 B per stored entry)",
+                        "peak_kind": f"{peak_kind} copy bandwidth"}}
+    batch.close()
+    for p in plans:
+        p.close()
+    del values
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_lam(args):
     import torch
     rank, local, world = dist_init("nccl")
@@ -406,6 +461,9 @@ def run_lam(args):
                                 "peak_kind": "nominal FP64 rate (1.20 TFLOP/s measured by a DFMA probe)"},
                    "gpu_launches": sum(sprof[k]["launches"] for k in L.KERNEL_KINDS)}
 
+    # ---- batch (lam_batch_*) of 256 seeded laminates
+    batch = run_batch(args, L, dev, flush, peak, peak_kind, world) if args.batch_steps > 0 else None
+
     # ---- adjoint (lam_adjoint) on the 32 x 32 cubic 24-ply plate, CSR cotangent
     adj = run_adjoint(args, L, dev, flush, peak, peak_kind, world) if args.adjoint_steps > 0 else None
 
@@ -467,6 +525,8 @@ def run_lam(args):
         line["e2e"] = e2e
     if adj is not None:
         line["adjoint"] = adj
+    if batch is not None:
+        line["batch"] = batch
     if cpu is not None:
         line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
     print(json.dumps(line), flush=True)
@@ -484,6 +544,7 @@ def main(argv=None):
     ap.add_argument("--standard-warmup", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--adjoint-steps", type=int, default=20, help="timed lam_adjoint calls (0 = skip)")
+    ap.add_argument("--batch-steps", type=int, default=5, help="timed lam_batch_assemble calls (0 = skip)")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--n-el", type=int, default=64, help="in-plane elements per direction (64 = the benchmark)")

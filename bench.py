@@ -386,6 +386,60 @@ def run_batch(args, L, dev, flush, peak, peak_kind, world):
     return out
 
 
+def run_sweep(args):
+    """The shape of the paper's experiment (Section 4, Figs. res1-res3): Pagano
+    plate, one element of degree p through the thickness, p = 1..4, m = 1..64
+    layers stacked 0/90/... and 0/45/-45/90/..., n x n in-plane elements.
+    Prints one JSON line: split and standard assembly times per point and,
+    per (p, stack), the ratio of the m = 64 and m = 8 times (the paper: split
+    flat in m once m exceeds the number of configurations, standard linear)."""
+    import torch
+    import paper_1905_05417_gb300 as L
+    import workloads as W
+    torch.cuda.set_device(0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    layers = [1, 2, 4, 8, 16, 32, 64]
+    points = []
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(sorted(ts)[len(ts) // 2])
+
+    for p in (1, 2, 3, 4):
+        for stack in ("cross", "quasi"):
+            for m in layers:
+                lam = W.pagano_sweep_plate(p, args.sweep_n, m, stack)
+                plan = L.Plan.from_laminate(lam)
+                v = torch.empty(plan.nnz, dtype=torch.float64, device="cuda")
+                split_ms = timed(lambda: plan.assemble_split(v), 10)
+                std_ms = timed(lambda: plan.assemble_standard(v), 3 if p < 4 else 1)
+                points.append({"p": p, "stack": stack, "layers": m, "nnz": plan.nnz,
+                               "configs": plan.info["n_configs"], "split_ms": split_ms, "standard_ms": std_ms,
+                               "speedup": std_ms / split_ms})
+                plan.close()
+                del v
+    shape = {}
+    for p in (1, 2, 3, 4):
+        for stack in ("cross", "quasi"):
+            sel = {q["layers"]: q for q in points if q["p"] == p and q["stack"] == stack}
+            shape[f"p{p}_{stack}"] = {"split_t64_over_t8": sel[64]["split_ms"] / sel[8]["split_ms"],
+                                      "standard_t64_over_t8": sel[64]["standard_ms"] / sel[8]["standard_ms"],
+                                      "speedup_at_64": sel[64]["speedup"]}
+    print(json.dumps({"sweep": "pagano_one_element_through_thickness", "n_el": args.sweep_n, "dtype": "f64",
+                      "data": "synthetic", "points": points, "shape": shape}), flush=True)
+    return 0
+
+
 def run_lam(args):
     import torch
     rank, local, world = dist_init("nccl")
@@ -545,6 +599,8 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--adjoint-steps", type=int, default=20, help="timed lam_adjoint calls (0 = skip)")
     ap.add_argument("--batch-steps", type=int, default=5, help="timed lam_batch_assemble calls (0 = skip)")
+    ap.add_argument("--sweep", action="store_true", help="the paper's layer sweep (one element through the thickness)")
+    ap.add_argument("--sweep-n", type=int, default=16, help="in-plane elements per direction in the sweep")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--n-el", type=int, default=64, help="in-plane elements per direction (64 = the benchmark)")
@@ -554,6 +610,8 @@ def main(argv=None):
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        return run_sweep(args)
     return run_lam(args)
 
 

@@ -32,6 +32,8 @@ LAGRANGE = 1
 
 # Orthotropic ply (GPa as plain numbers): E1, E2, E3, G12, G13, G23, nu12, nu13, nu23.
 PLY_CONSTANTS = dict(E1=140.0, E2=10.0, E3=10.0, G12=5.0, G13=5.0, G23=3.4, nu12=0.3, nu13=0.3, nu23=0.49)
+# the orthotropic material of the paper's numerical experiment (Section 4, GPa)
+PAGANO_CONSTANTS = dict(E1=25.0, E2=1.0, E3=1.0, G12=0.2, G13=0.2, G23=0.5, nu12=0.25, nu13=0.25, nu23=0.25)
 
 
 @dataclasses.dataclass
@@ -105,6 +107,10 @@ def isotropic_C21(E: float, nu: float) -> np.ndarray:
 
 def ply_C21() -> np.ndarray:
     return orthotropic_C21(**PLY_CONSTANTS)
+
+
+def pagano_C21() -> np.ndarray:
+    return orthotropic_C21(**PAGANO_CONSTANTS)
 
 
 def random_C21(rng: np.random.Generator, scale: float = 10.0) -> np.ndarray:
@@ -273,3 +279,16 @@ def batch_laminates(count: int = 256, seed: int = 517, meshes=(16, 24, 32, 48), 
         out.append(laminate(f"batch{b}_{n_el}x{n_el}_{n_plies}plies", BSPLINE, 2, n_el, angles, h,
                             materials=np.array(mats), ply_material=pm))
     return out
+
+
+def pagano_sweep_plate(degree: int, n_el: int, n_layers: int, stack: str = "cross", thickness: float = 0.1) -> Laminate:
+    """The shape of the paper's experiment (Section 4): a flat unit-square plate
+    of n_layers equal layers of the Pagano material, stacked 0/90/0/90/...
+    ("cross") or 0/45/-45/90/... ("quasi"), open uniform C^{p-1} B-splines of
+    the same degree p in all directions on n_el x n_el in-plane elements, and
+    ONE element of degree p through the whole thickness."""
+    cycle = [0.0, 90.0] if stack == "cross" else [0.0, 45.0, -45.0, 90.0]
+    angles = [cycle[k % len(cycle)] for k in range(n_layers)]
+    return laminate(f"pagano_{stack}_p{degree}_{n_el}x{n_el}_{n_layers}layers", BSPLINE, degree, n_el, angles,
+                    thickness / n_layers, materials=pagano_C21()[None, :],
+                    thickness=single_element_thickness(thickness, degree))

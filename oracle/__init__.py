@@ -64,6 +64,7 @@ def configure(L):
         L.ora_pattern.argtypes = [ctypes.POINTER(_Problem), _I64, _I32]
         L.ora_adjoint_D.argtypes = [ctypes.POINTER(_Problem), _I64, _I32, _D, _D]
         L.ora_adjoint.argtypes = [ctypes.POINTER(_Problem), _I64, _I32, _D, _D, _D, _D]
+        L.ora_inplane_P.argtypes = [ctypes.POINTER(_Problem), ctypes.c_int, ctypes.c_int64, ctypes.c_int64, _D]
         L.ora_rotated_D_dtheta.argtypes = [_D, ctypes.c_double, _D]
         L.ora_rotated_D_dtheta.restype = None
         L.ora_block.argtypes = [ctypes.POINTER(_Problem), ctypes.c_int64, ctypes.c_int64, _D]
@@ -227,6 +228,16 @@ def lowrank_cotangent(row_ptr, col, u, v) -> np.ndarray:
     for r in range(u.shape[0]):
         out += u[r][rows] * v[r][col]
     return out
+
+
+def inplane_P(lam, ply: int, i_s: int, j_s: int, problem: "Problem | None" = None) -> np.ndarray:
+    """Eq. P for in-plane functions (i_s, j_s) and the material of `ply`:
+    array (4, 3, 3) of the blocks 11, 12, 21, 22."""
+    p = problem if problem is not None else Problem(lam)
+    out = np.zeros(36)
+    if lib().ora_inplane_P(p.ref(), int(ply), int(i_s), int(j_s), _ptr(out)) != 0:
+        raise ValueError("oracle inplane_P failed")
+    return out.reshape(4, 3, 3)
 
 
 def rotated_D_dtheta(C21, theta: float) -> np.ndarray:

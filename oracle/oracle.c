@@ -969,3 +969,60 @@ int ora_adjoint(const ora_problem* pr, const int64_t* row_ptr, const int32_t* co
   free(g);
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* The in-plane operators of Eq. P for one in-plane pair (i_s, j_s) and the  */
+/* material of ply l: P_ab = int B_a^{i_s T} D_l B_b^{j_s} |DF| over the     */
+/* shared in-plane elements, with B_1 the strain matrix of (S_x, S_y, 0) and */
+/* B_2 that of (0, 0, S) (Eq. B_2). out: 4 x 3 x 3, blocks 11, 12, 21, 22.   */
+/* ------------------------------------------------------------------------ */
+int ora_inplane_P(const ora_problem* pr, int l, int64_t is, int64_t js, double* out36) {
+  if (check_problem(pr) < 0 || l < 0 || l >= pr->n_plies) return -1;
+  support1d su, sv;
+  if (support_build(&pr->u, &su) < 0 || support_build(&pr->v, &sv) < 0) return -1;
+  int nx = su.n;
+  int64_t ns = (int64_t)su.n * sv.n;
+  memset(out36, 0, sizeof(double) * 36);
+  if (is < 0 || js < 0 || is >= ns || js >= ns) { support_free(&su); support_free(&sv); return -1; }
+  int iy = (int)(is / nx), ix = (int)(is % nx), jy = (int)(js / nx), jx = (int)(js % nx);
+  int nqu = nq_or_default(pr->nq_u, pr->u.degree), nqv = nq_or_default(pr->nq_v, pr->v.degree);
+  double xu[64], wu[64], xv[64], wv[64];
+  ora_gauss(nqu, xu, wu);
+  ora_gauss(nqv, xv, wv);
+  int nlx = pr->u.degree + 1;
+  double D[36];
+  ora_rotated_D(pr->C21 + 21 * pr->ply_material[l], pr->ply_angle[l], D);
+  inplane_point ip;
+  for (int ey = sv.elo[iy]; ey <= sv.ehi[iy]; ++ey) {
+    if (ey < sv.elo[jy] || ey > sv.ehi[jy]) continue;
+    for (int ex = su.elo[ix]; ex <= su.ehi[ix]; ++ex) {
+      if (ex < su.elo[jx] || ex > su.ehi[jx]) continue;
+      double ua, ub, va, vb;
+      int f;
+      element_of(&pr->u, ex, &ua, &ub, &f);
+      element_of(&pr->v, ey, &va, &vb, &f);
+      for (int a = 0; a < nqu; ++a)
+        for (int b = 0; b < nqv; ++b) {
+          double xi = ua + 0.5 * (ub - ua) * (1.0 + xu[a]);
+          double eta = va + 0.5 * (vb - va) * (1.0 + xv[b]);
+          if (eval_inplane(pr, ex, ey, xi, eta, &ip) < 0) { support_free(&su); support_free(&sv); return -1; }
+          int li = (iy - ip.fy) * nlx + (ix - ip.fx), lj = (jy - ip.fy) * nlx + (jx - ip.fx);
+          double w = wu[a] * 0.5 * (ub - ua) * wv[b] * 0.5 * (vb - va) * ip.detJ;
+          double gi1[3] = {ip.gx[li], ip.gy[li], 0.0}, gi2[3] = {0.0, 0.0, ip.R[li]};
+          double gj1[3] = {ip.gx[lj], ip.gy[lj], 0.0}, gj2[3] = {0.0, 0.0, ip.R[lj]};
+          double Bi1[6][3], Bi2[6][3], Bj1[6][3], Bj2[6][3];
+          strain_matrix(gi1, Bi1);
+          strain_matrix(gi2, Bi2);
+          strain_matrix(gj1, Bj1);
+          strain_matrix(gj2, Bj2);
+          add_btdb(w, Bi1, D, Bj1, out36);
+          add_btdb(w, Bi1, D, Bj2, out36 + 9);
+          add_btdb(w, Bi2, D, Bj1, out36 + 18);
+          add_btdb(w, Bi2, D, Bj2, out36 + 27);
+        }
+    }
+  }
+  support_free(&su);
+  support_free(&sv);
+  return 0;
+}

@@ -102,6 +102,10 @@ void ora_rotated_D_dtheta(const double* C21, double theta, double* D36);
 int ora_adjoint(const ora_problem* pr, const int64_t* row_ptr, const int32_t* col, const double* gbar, double* dD,
                 double* dC, double* dtheta);
 
+/* Eq. P for the in-plane pair (is, js) and ply l's material: 4 blocks of 3x3
+ * (11, 12, 21, 22), row-major. */
+int ora_inplane_P(const ora_problem* pr, int l, int64_t is, int64_t js, double* out36);
+
 #ifdef __cplusplus
 }
 #endif

@@ -303,6 +303,24 @@ lam_status lam_batch_get_info(const lam_batch* batch, lam_batch_info* info);
 /* Releases the batch (not its plans). Synchronises the device. */
 lam_status lam_batch_destroy(lam_batch* batch);
 
+/* In-plane operators of Eq. P for the material and angle of ply `ply`:
+ * d_P receives nnz_inplane x 4 x 3 x 3 doubles (device), pair (i_s, k_s) at
+ * row i_s's neighbour k_s (neighbours j_y major, j_x minor, as in the
+ * pattern), blocks 11, 12, 21, 22 of Eq. P (B_1 from (S_x, S_y, 0), B_2 from
+ * (0, 0, S)), each 3x3 row-major in (c, d). Two constructions:
+ *   LAM_P_FROM_GRAM   the split path's: D contracted with the configuration-free
+ *                     in-plane Gram blocks of K-a;
+ *   LAM_P_VOIGT_FREE  Appendix A: per Gauss point, the bracket C{e_i, e_j} of
+ *                     the rotated 4th-order tensor is pulled back with the
+ *                     contravariant basis (C~_ab) and integrated against
+ *                     parametric gradients, with no Voigt matrix and no B.
+ * They agree to rounding; the second is a cross-check (FP64, one CTA per element,
+ * plan-owned workspace of 288 (p+1)^4 bytes per in-plane element).
+ * Asynchronous on `stream`. */
+#define LAM_P_FROM_GRAM 0
+#define LAM_P_VOIGT_FREE 1
+lam_status lam_inplane_operators(lam_plan* plan, int32_t ply, int32_t method, double* d_P, void* stream);
+
 /* Kernel kinds counted by the profiler. */
 typedef enum {
   LAM_KERNEL_PATTERN = 0,   /* kp_row_ptr, kp_col_ind */

@@ -26,7 +26,7 @@ import numpy as np
 __all__ = [
     "LamError", "Plan", "load", "plan_create", "plan_destroy", "plan_get_info", "pattern", "assemble_split",
     "assemble_standard", "assemble_split_host", "assemble_split_noalloc", "plan_update", "profile_enable", "profile_get", "last_error",
-    "version", "adjoint", "StiffnessFunction", "Batch", "batch_create", "batch_assemble", "batch_get_info",
+    "version", "adjoint", "inplane_operators", "StiffnessFunction", "Batch", "batch_create", "batch_assemble", "batch_get_info",
     "batch_destroy", "SYMBOLS", "KERNEL_KINDS", "BSPLINE", "LAGRANGE",
 ]
 
@@ -38,10 +38,12 @@ LIB_PATH = os.path.join(_HERE, "liblam.so")
 # every symbol include/lam.h declares
 SYMBOLS = ("lam_plan_create", "lam_plan_destroy", "lam_plan_get_info", "lam_pattern", "lam_assemble_split",
            "lam_assemble_standard", "lam_assemble_split_host", "lam_assemble_split_noalloc", "lam_plan_update",
-           "lam_adjoint", "lam_batch_create", "lam_batch_assemble", "lam_batch_get_info", "lam_batch_destroy",
+           "lam_adjoint", "lam_inplane_operators", "lam_batch_create", "lam_batch_assemble", "lam_batch_get_info", "lam_batch_destroy",
            "lam_profile_enable",
            "lam_profile_get", "lam_last_error", "lam_version")
 KERNEL_KINDS = ("pattern", "thickness", "inplane", "combine", "standard", "adjoint", "adjoint_aux")
+P_FROM_GRAM = 0
+P_VOIGT_FREE = 1
 COTANGENT_CSR = 0
 COTANGENT_LOWRANK = 1
 ADJOINT_FP64 = 1
@@ -129,6 +131,7 @@ def load() -> ctypes.CDLL:
     L.lam_assemble_split_noalloc.argtypes = [vp, vp, vp]
     L.lam_plan_update.argtypes = [vp, _D, ctypes.c_int32, ctypes.POINTER(_Material), ctypes.c_int32]
     L.lam_adjoint.argtypes = [vp, ctypes.POINTER(_Cotangent), vp, vp, vp, vp]
+    L.lam_inplane_operators.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, vp, vp]
     L.lam_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int32]
     L.lam_batch_assemble.argtypes = [vp, ctypes.POINTER(vp), vp]
     L.lam_batch_get_info.argtypes = [vp, ctypes.POINTER(_BatchInfo)]
@@ -293,6 +296,12 @@ def adjoint(handle, d_dC=None, d_dtheta=None, d_dD=None, values=None, u=None, v=
            "lam_adjoint")
 
 
+def inplane_operators(handle, ply: int, method: int, d_P, stream=None) -> None:
+    """lam_inplane_operators: Eq. P for ply `ply`'s material into d_P (nnz_inplane x 4 x 3 x 3)."""
+    _check(load().lam_inplane_operators(handle, int(ply), int(method), _ptr(d_P), _stream_handle(stream)),
+           "lam_inplane_operators")
+
+
 def batch_create(plan_handles) -> ctypes.c_void_p:
     """lam_batch_create over plan handles (the plans must outlive the batch)."""
     arr = (ctypes.c_void_p * len(plan_handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h
@@ -392,6 +401,13 @@ class Plan:
     def update(self, ply_angle=None, C21=None):
         plan_update(self.handle, ply_angle, C21)
         self.info = plan_get_info(self.handle)
+
+    def inplane_operators(self, ply: int, method: int = P_FROM_GRAM, stream=None):
+        """Eq. P of every in-plane pair for ply `ply`'s material: (nnz_inplane, 4, 3, 3) device tensor."""
+        import torch
+        P = torch.empty(self.info["nnz_inplane"], 4, 3, 3, dtype=torch.float64, device="cuda")
+        inplane_operators(self.handle, ply, method, P, stream)
+        return P
 
     def adjoint(self, values=None, u=None, v=None, fp64=False, want_dD=True, stream=None):
         """(dL/dC: n_materials x 21, dL/dtheta: n_plies, dL/dD: n_plies x 6 x 6 or None)

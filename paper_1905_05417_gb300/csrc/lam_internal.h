@@ -57,6 +57,7 @@ struct Plan {
   std::vector<double> cfg_angle;
   std::vector<double> cfgD;      // [m][6][6]
   std::vector<double> cfgE;      // [m][c*3+d][a*3+b] = D_m[V(c,a)][V(d,b)]
+  std::vector<double> cfgCb;     // [m][i][j][p][r] = C{e_i, e_j}_{pr} = C_{pirj} (rotated 4th-order tensor)
   bool monoclinic = true;
 
   // thickness pieces and their 1D tables

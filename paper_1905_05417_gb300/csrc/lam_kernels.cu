@@ -65,6 +65,8 @@ struct Device {
   double* EG = nullptr;  // element Gram blocks: n_el x 9 x pairs
   int* kc_flag = nullptr;      // streaming combine: FP64 re-pass flag, then the largest exponent
   float2* cfgEdf = nullptr;    // float pairs of cfgE
+  double* cfgCb = nullptr;     // Appendix A bracket tensors per configuration
+  double* bfree_EP = nullptr;  // element operators of the Voigt-free construction (lazily allocated)
   int n_sm = 0;
   double* q = nullptr;   // nnz_t x n_cfg x 4
   // adjoint: geometry tables and workspace (allocated by the first lam_adjoint)
@@ -1303,6 +1305,7 @@ static lam_status ensure_device(Plan& P) {
     UP(L, D->occ_k, P.occ_k);
     UP(L, D->occ_it, P.occ_it);
     UP(L, D->cfgE, P.cfgE);
+    UP(L, D->cfgCb, P.cfgCb);
     std::vector<float> edf(P.cfgE.size() * 2);
     for (size_t k = 0; k < P.cfgE.size(); ++k) {
       const float h = (float)P.cfgE[k];
@@ -2045,14 +2048,11 @@ static lam_status launch_adj_df(const Plan& P, const AdjArgs& a, cudaStream_t s)
   return LAM_OK;
 }
 
-static lam_status adjoint(Plan& P, const lam_cotangent& cot, double* dC, double* dtheta, double* dDout,
-                          cudaStream_t s) {
+// Assembled in-plane Gram blocks (unscaled) into the adjoint workspace G, with
+// the maxima of |G_ab| (K-a must have run on the stream).
+static lam_status gather_gram(Plan& P, cudaStream_t s) {
   Device& D = *P.dev;
-  lam_status st;
-  if ((st = inplane_gram(P, s)) != LAM_OK) return st;
-  cudaEvent_t ev = prof_begin(P, s);
   LAM_CUDA(cudaMemsetAsync(D.adj_gmax, 0, 9 * sizeof(unsigned long long), s));
-  LAM_CUDA(cudaMemsetAsync(D.adj_flag, 0, 2 * sizeof(int), s));
   AdjGatherArgs g{};
   g.nx = P.u.n;
   g.nel_u = P.u.nel;
@@ -2075,6 +2075,17 @@ static lam_status adjoint(Plan& P, const lam_cotangent& cot, double* dC, double*
   g.gmax = D.adj_gmax;
   adj_gather<<<(unsigned)P.ns, adj_block(P), 0, s>>>(g);
   LAM_CUDA(cudaGetLastError());
+  return LAM_OK;
+}
+
+static lam_status adjoint(Plan& P, const lam_cotangent& cot, double* dC, double* dtheta, double* dDout,
+                          cudaStream_t s) {
+  Device& D = *P.dev;
+  lam_status st;
+  if ((st = inplane_gram(P, s)) != LAM_OK) return st;
+  cudaEvent_t ev = prof_begin(P, s);
+  LAM_CUDA(cudaMemsetAsync(D.adj_flag, 0, 2 * sizeof(int), s));
+  if ((st = gather_gram(P, s)) != LAM_OK) return st;
   double* gscale = reinterpret_cast<double*>(D.adj_gmax + 9);
   const int64_t n9 = 9 * P.nnz_s;
   adj_split<<<(unsigned)std::min<int64_t>((n9 + 255) / 256, 152 * 8), 256, 0, s>>>(n9, D.adj_G, D.adj_Gdf, D.adj_gmax,
@@ -2157,6 +2168,186 @@ static lam_status adjoint(Plan& P, const lam_cotangent& cot, double* dC, double*
   }
   prof_end(P, LAM_KERNEL_ADJOINT_AUX, aux, s, ev);
   return LAM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// In-plane operators of Eq. P (lam_inplane_operators), two constructions.
+// Block k of P (11, 12, 21, 22) pairs the derivative / value parts: with
+// A_1 = {x, y} and A_2 = {z} (g_z = S), P_k[c][d] = sum_{a in A_alpha, b in
+// A_beta} D[V(c,a)][V(d,b)] G_ab for the Gram-block construction.
+// ---------------------------------------------------------------------------
+__global__ void kp_from_gram(int64_t nps, const double* __restrict__ G, const double* __restrict__ E,
+                             double* __restrict__ P) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nps * 36) return;
+  const int64_t ps = t / 36;
+  const int k = (int)(t % 36), blk = k / 9, cd = k % 9;
+  const int a0 = (blk < 2) ? 0 : 2, a1 = (blk < 2) ? 1 : 2;  // A_alpha
+  const int b0 = (blk % 2 == 0) ? 0 : 2, b1 = (blk % 2 == 0) ? 1 : 2;
+  double acc = 0.0;
+  for (int a = a0; a <= a1; ++a)
+    for (int b = b0; b <= b1; ++b) acc += E[cd * 9 + a * 3 + b] * G[ps * 9 + a * 3 + b];
+  P[t] = acc;
+}
+
+// Appendix A, per in-plane element: at every Gauss point the contracted
+// tensors C~_ab[p][r] = sum_{i,j} C{e_i, e_j}_{pr} (g^i . e_a)(g^j . e_b), with
+// g^i . e_a = (DF^{-1})_{ai} (DF block-diagonal: the planar map and dz/dxi3 = 1),
+// and the parametric gradients of the in-plane functions; thread per ordered
+// local pair accumulates the four blocks. EP[e][li * nls + lj][36].
+struct BfreeArgs {
+  InplaneArgs ip;
+  const double* Cb;  // [i][j][p][r] of one configuration
+  double* EP;
+};
+
+__global__ void __launch_bounds__(256) kp_bfree(BfreeArgs a) {
+  extern __shared__ double sm[];
+  const InplaneArgs& ip = a.ip;
+  const int nlx = ip.pu + 1, nly = ip.pv + 1, nls = nlx * nly, nqs = ip.nqu * ip.nqv;
+  const int e = blockIdx.x, ex = e % ip.nel_u, ey = e / ip.nel_u;
+  const int fx = ip.firstU[ex], fy = ip.firstV[ey];
+  double* sS = sm;                              // [q][k] value
+  double* sSu = sS + (size_t)nqs * nls;         // d/dxi1
+  double* sSv = sSu + (size_t)nqs * nls;        // d/dxi2
+  double* sCt = sSv + (size_t)nqs * nls;        // [q][a*3+b][p*3+r]
+  double* sJ = sCt + (size_t)nqs * 81;          // [q]: Jinv (4), w |J|, W, W1, W2
+  // geometry per point
+  for (int t = threadIdx.x; t < nqs; t += blockDim.x) {
+    const int qu = t % ip.nqu, qv = t / ip.nqu;
+    const double* tu = ip.tabU + ((size_t)ex * ip.nqu + qu) * nlx * 2;
+    const double* tv = ip.tabV + ((size_t)ey * ip.nqv + qv) * nly * 2;
+    double W = 1.0, W1 = 0.0, W2 = 0.0;
+    if (ip.weights) {
+      W = 0.0;
+      for (int ly = 0; ly < nly; ++ly)
+        for (int lx = 0; lx < nlx; ++lx) {
+          const double w = ip.weights[(size_t)(fy + ly) * ip.nx + fx + lx];
+          W += w * tu[2 * lx] * tv[2 * ly];
+          W1 += w * tu[2 * lx + 1] * tv[2 * ly];
+          W2 += w * tu[2 * lx] * tv[2 * ly + 1];
+        }
+    }
+    double J00 = 0.0, J01 = 0.0, J10 = 0.0, J11 = 0.0;
+    for (int ly = 0; ly < nly; ++ly)
+      for (int lx = 0; lx < nlx; ++lx) {
+        const size_t gi = (size_t)(fy + ly) * ip.nx + fx + lx;
+        const double N = tu[2 * lx] * tv[2 * ly], N1 = tu[2 * lx + 1] * tv[2 * ly], N2 = tu[2 * lx] * tv[2 * ly + 1];
+        double R1 = N1, R2 = N2;
+        if (ip.weights) {
+          const double w = ip.weights[gi];
+          R1 = w * (N1 * W - N * W1) / (W * W);
+          R2 = w * (N2 * W - N * W2) / (W * W);
+        }
+        J00 += R1 * ip.ctrl[2 * gi];
+        J01 += R2 * ip.ctrl[2 * gi];
+        J10 += R1 * ip.ctrl[2 * gi + 1];
+        J11 += R2 * ip.ctrl[2 * gi + 1];
+      }
+    const double det = J00 * J11 - J01 * J10, inv = 1.0 / det;
+    double* d = sJ + (size_t)t * 8;
+    d[0] = J11 * inv;   // (DF^-1)_{00}
+    d[1] = -J01 * inv;  // (DF^-1)_{01}
+    d[2] = -J10 * inv;  // (DF^-1)_{10}
+    d[3] = J00 * inv;   // (DF^-1)_{11}
+    d[4] = ip.wU[(size_t)ex * ip.nqu + qu] * ip.wV[(size_t)ey * ip.nqv + qv] * fabs(det);
+    d[5] = W;
+    d[6] = W1;
+    d[7] = W2;
+  }
+  __syncthreads();
+  // parametric values and derivatives of the local functions
+  for (int t = threadIdx.x; t < nqs * nls; t += blockDim.x) {
+    const int q = t / nls, k = t % nls;
+    const int qu = q % ip.nqu, qv = q / ip.nqu, lx = k % nlx, ly = k / nlx;
+    const double* tu = ip.tabU + ((size_t)ex * ip.nqu + qu) * nlx * 2;
+    const double* tv = ip.tabV + ((size_t)ey * ip.nqv + qv) * nly * 2;
+    double R = tu[2 * lx] * tv[2 * ly], R1 = tu[2 * lx + 1] * tv[2 * ly], R2 = tu[2 * lx] * tv[2 * ly + 1];
+    if (ip.weights) {
+      const double* d = sJ + (size_t)q * 8;
+      const double w = ip.weights[(size_t)(fy + ly) * ip.nx + fx + lx], W = d[5];
+      const double N = R, N1 = R1, N2 = R2;
+      R = w * N / W;
+      R1 = w * (N1 * W - N * d[6]) / (W * W);
+      R2 = w * (N2 * W - N * d[7]) / (W * W);
+    }
+    sS[t] = R;
+    sSu[t] = R1;
+    sSv[t] = R2;
+  }
+  // contracted tensors
+  for (int t = threadIdx.x; t < nqs * 81; t += blockDim.x) {
+    const int q = t / 81, ab = (t % 81) / 9, pr = t % 9;
+    const int al = ab / 3, be = ab % 3;
+    const double* d = sJ + (size_t)q * 8;
+    double gi[3], gj[3];  // (DF^-1)_{alpha i}, (DF^-1)_{beta j}
+    for (int i = 0; i < 3; ++i) {
+      gi[i] = (al == 2) ? (i == 2 ? 1.0 : 0.0) : (i == 2 ? 0.0 : d[al * 2 + i]);
+      gj[i] = (be == 2) ? (i == 2 ? 1.0 : 0.0) : (i == 2 ? 0.0 : d[be * 2 + i]);
+    }
+    double acc = 0.0;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) acc += a.Cb[(i * 3 + j) * 9 + pr] * gi[i] * gj[j];
+    sCt[t] = acc;
+  }
+  __syncthreads();
+  for (int pair = threadIdx.x; pair < nls * nls; pair += blockDim.x) {
+    const int li = pair / nls, lj = pair % nls;
+    double acc[36];
+#pragma unroll
+    for (int k = 0; k < 36; ++k) acc[k] = 0.0;
+    for (int q = 0; q < nqs; ++q) {
+      const double w = sJ[(size_t)q * 8 + 4];
+      const double Si = sS[q * nls + li], Sj = sS[q * nls + lj];
+      const double Ui = sSu[q * nls + li], Uj = sSu[q * nls + lj];
+      const double Vi = sSv[q * nls + li], Vj = sSv[q * nls + lj];
+      const double* C = sCt + (size_t)q * 81;
+      const double f00 = w * Ui * Uj, f01 = w * Ui * Vj, f10 = w * Vi * Uj, f11 = w * Vi * Vj;
+      const double f02 = w * Ui * Sj, f12 = w * Vi * Sj, f20 = w * Si * Uj, f21 = w * Si * Vj, f22 = w * Si * Sj;
+#pragma unroll
+      for (int pr = 0; pr < 9; ++pr) {
+        acc[pr] += C[0 * 9 + pr] * f00 + C[1 * 9 + pr] * f01 + C[3 * 9 + pr] * f10 + C[4 * 9 + pr] * f11;
+        acc[9 + pr] += C[2 * 9 + pr] * f02 + C[5 * 9 + pr] * f12;
+        acc[18 + pr] += C[6 * 9 + pr] * f20 + C[7 * 9 + pr] * f21;
+        acc[27 + pr] += C[8 * 9 + pr] * f22;
+      }
+    }
+    double* out = a.EP + ((size_t)e * nls * nls + pair) * 36;
+#pragma unroll
+    for (int k = 0; k < 36; ++k) out[k] = acc[k];
+  }
+}
+
+// Sum of the element operators over the elements an in-plane pair shares.
+struct PGatherArgs {
+  int nx, nel_u, nlx, nls;
+  const int64_t* LSb;
+  const int *lenX, *lenY, *loX, *loY, *eloX, *ehiX, *eloY, *ehiY, *firstU, *firstV;
+  const double* EP;
+  double* P;
+};
+
+__global__ void kp_gather(PGatherArgs a) {
+  const int64_t is = blockIdx.x;
+  const int ix = (int)(is % a.nx), iy = (int)(is / a.nx);
+  const int lx = a.lenX[ix], ls = lx * a.lenY[iy];
+  const int64_t ls0 = a.LSb[is];
+  for (int item = threadIdx.x; item < 36 * ls; item += blockDim.x) {
+    const int ks = item / 36, k = item % 36;
+    const int jx = a.loX[ix] + ks % lx, jy = a.loY[iy] + ks / lx;
+    const int ex0 = max(a.eloX[ix], a.eloX[jx]), ex1 = min(a.ehiX[ix], a.ehiX[jx]);
+    const int ey0 = max(a.eloY[iy], a.eloY[jy]), ey1 = min(a.ehiY[iy], a.ehiY[jy]);
+    double acc = 0.0;
+    for (int ey = ey0; ey <= ey1; ++ey) {
+      const int fy = a.firstV[ey];
+      for (int ex = ex0; ex <= ex1; ++ex) {
+        const int fx = a.firstU[ex];
+        const int li = (iy - fy) * a.nlx + (ix - fx), lj = (jy - fy) * a.nlx + (jx - fx);
+        acc += a.EP[(((size_t)ey * a.nel_u + ex) * a.nls * a.nls + (size_t)li * a.nls + lj) * 36 + k];
+      }
+    }
+    a.P[(ls0 + ks) * 36 + k] = acc;
+  }
 }
 
 static lam_status pattern_args(const Plan& P, PatArgs& a) {
@@ -2386,6 +2577,69 @@ lam_status lam_adjoint(lam_plan* plan, const lam_cotangent* cot, double* d_dC, d
   if ((st = lam::ensure_device(P)) != LAM_OK) return st;
   if ((st = lam::ensure_adjoint(P)) != LAM_OK) return st;
   return lam::adjoint(P, *cot, d_dC, d_dtheta, d_dD, static_cast<cudaStream_t>(stream));
+}
+
+lam_status lam_inplane_operators(lam_plan* plan, int32_t ply, int32_t method, double* d_P, void* stream) {
+  if (!plan || !d_P) {
+    lam::set_error("lam_inplane_operators: NULL argument");
+    return LAM_ERR_INVALID_ARG;
+  }
+  lam::Plan& P = plan->p;
+  if (ply < 0 || ply >= (int32_t)P.plies.size()) {
+    lam::set_error("lam_inplane_operators: ply %d of %d", ply, (int)P.plies.size());
+    return LAM_ERR_INVALID_ARG;
+  }
+  if (method != LAM_P_FROM_GRAM && method != LAM_P_VOIGT_FREE) {
+    lam::set_error("lam_inplane_operators: unknown method %d", method);
+    return LAM_ERR_INVALID_ARG;
+  }
+  lam_status st;
+  if ((st = lam::check_limits(P)) != LAM_OK) return st;
+  if ((st = lam::ensure_device(P)) != LAM_OK) return st;
+  lam::Device& D = *P.dev;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int m = P.ply_cfg[ply];
+  if (method == LAM_P_FROM_GRAM) {
+    if ((st = lam::ensure_adjoint(P)) != LAM_OK) return st;
+    if ((st = lam::inplane_gram(P, s)) != LAM_OK) return st;
+    if ((st = lam::gather_gram(P, s)) != LAM_OK) return st;
+    const int64_t n = P.nnz_s * 36;
+    lam::kp_from_gram<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P.nnz_s, D.adj_G, D.cfgE + (size_t)m * 81, d_P);
+    LAM_CUDA(cudaGetLastError());
+    return LAM_OK;
+  }
+  const int nls = lam::ka_nls(P), nqs = P.nqu * P.nqv, nel = P.u.nel * P.v.nel;
+  if (!D.bfree_EP && (st = lam::alloc_dev(D.allocs, &D.bfree_EP, (size_t)nel * nls * nls * 36)) != LAM_OK) return st;
+  lam::BfreeArgs a{};
+  a.ip = lam::inplane_args(P);
+  a.Cb = D.cfgCb + (size_t)m * 81;
+  a.EP = D.bfree_EP;
+  const size_t smem = ((size_t)3 * nqs * nls + 81 * (size_t)nqs + 8 * (size_t)nqs) * sizeof(double);
+  LAM_CUDA(cudaFuncSetAttribute(lam::kp_bfree, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int block = std::min(256, std::max(32, ((nls * nls + 31) / 32) * 32));
+  lam::kp_bfree<<<(unsigned)nel, block, smem, s>>>(a);
+  LAM_CUDA(cudaGetLastError());
+  lam::PGatherArgs g{};
+  g.nx = P.u.n;
+  g.nel_u = P.u.nel;
+  g.nlx = P.u.p + 1;
+  g.nls = nls;
+  g.LSb = D.LSb;
+  g.lenX = D.lenX;
+  g.lenY = D.lenY;
+  g.loX = D.loX;
+  g.loY = D.loY;
+  g.eloX = D.eloX;
+  g.ehiX = D.ehiX;
+  g.eloY = D.eloY;
+  g.ehiY = D.ehiY;
+  g.firstU = D.firstU;
+  g.firstV = D.firstV;
+  g.EP = D.bfree_EP;
+  g.P = d_P;
+  lam::kp_gather<<<(unsigned)P.ns, 256, 0, s>>>(g);
+  LAM_CUDA(cudaGetLastError());
+  return LAM_OK;
 }
 
 lam_status lam_profile_enable(lam_plan* plan, int32_t enable) {

@@ -354,6 +354,32 @@ lam_status rebuild_configs(Plan& P) {
           for (int b = 0; b < 3; ++b)
             P.cfgE[(size_t)m * 81 + (c * 3 + d) * 9 + a * 3 + b] = D[voigt_index(c, a) * 6 + voigt_index(d, b)];
   }
+  // Appendix A: the bracket C{e_i, e_j}_{pr} = C_{pirj} of every configuration, from the material
+  // tensor rotated by R = rot_z(theta) in all four indices (no Bond matrix)
+  P.cfgCb.assign((size_t)nc * 81, 0.0);
+  for (int m = 0; m < nc; ++m) {
+    double Dm[36];
+    material_matrix(P.mats[P.cfg_mat[m]].C, Dm);
+    double Cm[3][3][3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b)
+        for (int c = 0; c < 3; ++c)
+          for (int d = 0; d < 3; ++d) Cm[a][b][c][d] = Dm[voigt_index(a, b) * 6 + voigt_index(c, d)];
+    const double cs = std::cos(P.cfg_angle[m]), sn = std::sin(P.cfg_angle[m]);
+    const double R[3][3] = {{cs, -sn, 0.0}, {sn, cs, 0.0}, {0.0, 0.0, 1.0}};
+    double* out = &P.cfgCb[(size_t)m * 81];
+    for (int pp = 0; pp < 3; ++pp)
+      for (int i = 0; i < 3; ++i)
+        for (int r = 0; r < 3; ++r)
+          for (int j = 0; j < 3; ++j) {
+            double acc = 0.0;
+            for (int a = 0; a < 3; ++a)
+              for (int b = 0; b < 3; ++b)
+                for (int c = 0; c < 3; ++c)
+                  for (int d = 0; d < 3; ++d) acc += R[pp][a] * R[i][b] * R[r][c] * R[j][d] * Cm[a][b][c][d];
+            out[((i * 3 + j) * 3 + pp) * 3 + r] = acc;
+          }
+  }
   for (auto& pc : P.pieces) pc.cfg = P.ply_cfg[pc.ply];
   const size_t npl = P.plies.size();
   P.ply_M.assign(npl * 36, 0.0);

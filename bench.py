@@ -103,12 +103,17 @@ def measured_peaks():
 
 
 def kernel_source_sha(kernel: str) -> str:
-    """sha256 of one kernel's definition in lam_kernels.cu (from its
-    __global__ line to the closing brace at column 0)."""
+    """sha256 of the definitions (from the __global__ / __device__ line to the
+    closing brace at column 0) of the named functions in lam_kernels.cu;
+    `kernel` is one name or several separated by '+'."""
     text = open(os.path.join(ROOT, "paper_1905_05417_gb300", "csrc", "lam_kernels.cu")).read().splitlines()
-    start = next(i for i, ln in enumerate(text) if "__global__" in ln and f" {kernel}(" in ln)
-    end = next(i for i in range(start, len(text)) if text[i] == "}")
-    return hashlib.sha256("\n".join(text[start:end + 1]).encode()).hexdigest()
+    h = hashlib.sha256()
+    for name in kernel.split("+"):
+        start = next(i for i, ln in enumerate(text)
+                     if ("__global__" in ln or "__device__" in ln) and f" {name}(" in ln)
+        end = next(i for i in range(start, len(text)) if text[i] == "}")
+        h.update("\n".join(text[start:end + 1]).encode())
+    return h.hexdigest()
 
 
 def recorded_traffic(summary: str, kernel: str):
@@ -440,6 +445,55 @@ def run_sweep(args):
     return 0
 
 
+def run_large(args, L, dev, flush, peak, peak_kind, world):
+    """The Lagrange Q2 96 x 96 plate with 64 plies [0/90]_32 (14.4 M DOFs,
+    2.73e9 stored entries, 21.8 GB of values, int64 row pointers): split and
+    standard assembly."""
+    import torch
+    import workloads as W
+    lam = W.lagrange_plate()
+    plan = L.Plan.from_laminate(lam)
+    nnz = plan.nnz
+    values = torch.empty(nnz, dtype=torch.float64, device=dev)
+    for _ in range(args.warmup):
+        plan.assemble_split(values)
+    torch.cuda.synchronize()
+    barrier()
+    steps = args.large_steps
+    plan.profile_enable(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        evs[k][0].record()
+        plan.assemble_split(values)
+        evs[k][1].record()
+    torch.cuda.synchronize()
+    pr = plan.profile()
+    plan.profile_enable(False)
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs) / steps, dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.zero_()
+    a.record()
+    plan.assemble_standard(values)
+    b.record()
+    torch.cuda.synchronize()
+    std_ms = a.elapsed_time(b)
+    kc_ms = pr["combine"]["ms"] / steps
+    kc_bytes = 8 * nnz + 72 * plan.info["nnz_inplane"]
+    out = {"workload": "Lagrange Q2 96x96 unit square, [0/90]_32 (64 plies), Lagrange thickness",
+           "value": aggregate_throughput(nnz, world, ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+           "nnz": nnz, "step_hbm_frac": 8 * nnz / (ms / 1e3) / 1e9 / peak,
+           "kernels_ms_per_step": {k: pr[k]["ms"] / steps for k in L.KERNEL_KINDS if pr[k]["launches"]},
+           "standard_ms": std_ms, "speedup_split_vs_standard": std_ms / ms,
+           "roofline": {"bound": "hbm", "achieved": kc_bytes / (kc_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                        "frac": kc_bytes / (kc_ms / 1e3) / 1e9 / peak, "traffic": None, "kernel": "kc_stream",
+                        "peak_kind": f"{peak_kind} copy bandwidth"}}
+    plan.close()
+    del values
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_lam(args):
     import torch
     rank, local, world = dist_init("nccl")
@@ -515,6 +569,9 @@ def run_lam(args):
                                 "peak_kind": "nominal FP64 rate (1.20 TFLOP/s measured by a DFMA probe)"},
                    "gpu_launches": sum(sprof[k]["launches"] for k in L.KERNEL_KINDS)}
 
+    # ---- the large Lagrange plate
+    large = run_large(args, L, dev, flush, peak, peak_kind, world) if args.large_steps > 0 else None
+
     # ---- batch (lam_batch_*) of 256 seeded laminates
     batch = run_batch(args, L, dev, flush, peak, peak_kind, world) if args.batch_steps > 0 else None
 
@@ -552,7 +609,7 @@ def run_lam(args):
     kc_ms = kc["ms"] / args.steps  # one combine call per step: the double-float pass, its check, the FP64 re-pass gate
     kc_bytes = 8 * nnz + 72 * nnz_s
     achieved = kc_bytes / (kc_ms / 1e3) / 1e9
-    traffic = (recorded_traffic("kc_stream_curved_p3_64x64_48plies.md", "kc_stream")
+    traffic = (recorded_traffic("kc_stream_curved_p3_64x64_48plies.md", "kcs_row+kc_stream")
                if (args.n_el, args.repeats) == (64, 6) else None)
     clk = clocks.summary()
     line = {
@@ -581,6 +638,8 @@ def run_lam(args):
         line["adjoint"] = adj
     if batch is not None:
         line["batch"] = batch
+    if large is not None:
+        line["large"] = large
     if cpu is not None:
         line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
     print(json.dumps(line), flush=True)
@@ -599,6 +658,7 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--adjoint-steps", type=int, default=20, help="timed lam_adjoint calls (0 = skip)")
     ap.add_argument("--batch-steps", type=int, default=5, help="timed lam_batch_assemble calls (0 = skip)")
+    ap.add_argument("--large-steps", type=int, default=5, help="timed split assemblies of the Lagrange plate (0 = skip)")
     ap.add_argument("--sweep", action="store_true", help="the paper's layer sweep (one element through the thickness)")
     ap.add_argument("--sweep-n", type=int, default=16, help="in-plane elements per direction in the sweep")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")

@@ -168,7 +168,7 @@ def test_update_angles_then_reassemble(L):
 
 
 # ---------------------------------------------------------------- full sizes, sampled
-def _sampled_parity(L, lam, path, n_rows=120, seed=0):
+def _sampled_parity(L, lam, path, n_rows=120, seed=0, whole_pattern=True):
     import torch
     p = L.Plan.from_laminate(lam)
     row_ptr, col = p.pattern()
@@ -177,10 +177,13 @@ def _sampled_parity(L, lam, path, n_rows=120, seed=0):
     rp = row_ptr.cpu().numpy()
     cl = col.cpu().numpy()
     v = vals.cpu().numpy()
-    # the whole pattern, bit for bit, against the oracle's own construction
-    rp_o, cl_o = O.pattern(lam)
-    assert np.array_equal(rp, rp_o) and np.array_equal(cl, cl_o)
-    del rp_o, cl_o
+    if whole_pattern:
+        # the whole pattern, bit for bit, against the oracle's own construction
+        rp_o, cl_o = O.pattern(lam)
+        assert np.array_equal(rp, rp_o) and np.array_equal(cl, cl_o)
+        del rp_o, cl_o
+    else:
+        assert rp[0] == 0 and rp[-1] == p.nnz and np.all(np.diff(rp) > 0)
     assert np.all(np.isfinite(v))
     rng = np.random.default_rng(seed)
     n = p.n_dof
@@ -277,3 +280,10 @@ def test_extreme_material_scale(L, scale):
     lam.C21 = lam.C21 * scale
     got = gpu_matrix(L, lam, "split")
     assert_parity(got, O.assemble(lam))
+
+
+def test_lagrange_plate_full_size_sampled(L):
+    """Lagrange Q2 96x96, 64 plies (2.73e9 stored entries, int64 row pointers):
+    sampled blocks against the oracle's block integrator and symmetry; the
+    pattern's construction is checked whole on the other plates."""
+    _sampled_parity(L, W.lagrange_plate(), "split", n_rows=40, whole_pattern=False)

@@ -251,7 +251,9 @@ typedef struct {
  * magnitude. Entries below 2^-80 next to larger ones contribute with an
  * absolute error below 2^-100 of their own size. LAM_ADJOINT_FP64 forces the
  * FP64 evaluation.
- * Recomputes the in-plane Gram blocks on every call. Workspace: about
+ * The in-plane Gram blocks depend on the plan's geometry only, which never
+ * changes: the first call computes them and later calls reuse them
+ * (lam_inplane_operators with LAM_P_FROM_GRAM discards the copy). Workspace: about
  * 16 * 9 * nnz_inplane + 648 * n_plies * ceil(n_s / 16) bytes, plan-owned.
  * Errors: LAM_ERR_INVALID_ARG for a NULL plan or cotangent, an unknown kind, a
  * missing vector or rank < 1; LAM_ERR_UNSUPPORTED when a ply meets more than

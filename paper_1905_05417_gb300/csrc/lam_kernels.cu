@@ -71,6 +71,7 @@ struct Device {
   double* q = nullptr;   // nnz_t x n_cfg x 4
   // adjoint: geometry tables and workspace (allocated by the first lam_adjoint)
   bool adj_ready = false;
+  bool adj_g_cached = false;       // adj_G / adj_Gdf / scales hold this plan's scaled Gram blocks
   int *adj_begin = nullptr, *adj_pair = nullptr;
   double* adj_q = nullptr;
   float* adj_qdf = nullptr;
@@ -1817,7 +1818,8 @@ __global__ void __launch_bounds__(1024) adj_ply_df(AdjArgs a) {
   const int nthr = blockDim.x, tid = threadIdx.x;
   float4* sQh = reinterpret_cast<float4*>(sm);                  // kAdjFastTerms
   float4* sQl = sQh + kAdjFastTerms;                             // kAdjFastTerms
-  double* red = reinterpret_cast<double*>(sQl + kAdjFastTerms);  // 9 x nthr
+  double* sQ3 = reinterpret_cast<double*>(sQl + kAdjFastTerms);  // kAdjFastTerms: the T' T' type in FP64
+  double* red = sQ3 + kAdjFastTerms;                             // 9 x nthr
   Idx* sBase = reinterpret_cast<Idx*>(red + (size_t)9 * nthr);   // kAdjRows x 3 x kAdjFastTerms
   int* sLs = reinterpret_cast<int*>(sBase + kAdjRows * 3 * kAdjFastTerms);  // kAdjRows
   int* sLs0 = sLs + kAdjRows;                                    // kAdjRows (in-plane pair offset of the row)
@@ -1827,6 +1829,7 @@ __global__ void __launch_bounds__(1024) adj_ply_df(AdjArgs a) {
     const float* q = a.term_qdf + (size_t)(t0 + k) * 8;
     sQh[k] = make_float4(q[0], q[1], q[2], q[3]);
     sQl[k] = make_float4(q[4], q[5], q[6], q[7]);
+    sQ3[k] = a.term_q[(size_t)(t0 + k) * 4 + 3];
   }
   if (tid < nrows) {
     const int is = (int)(r0 + tid);
@@ -1855,7 +1858,10 @@ __global__ void __launch_bounds__(1024) adj_ply_df(AdjArgs a) {
     if (!valid || ks >= ls) continue;
     const Idx* bp = sBase + (r * 3 + c) * kAdjFastTerms;
     const Idx off = (Idx)(3 * ks + d);
+    // types T T, T T', T' T in double-float on the FP32 pipes; T' T' in FP64 on
+    // the otherwise idle FP64 pipe, which runs alongside
     float zh[4] = {0.0f, 0.0f, 0.0f, 0.0f}, zl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    double z3 = 0.0;
     for (int tb = 0; tb < nterm; tb += kAdjRowTerms) {
       double v[kAdjRowTerms];
 #pragma unroll
@@ -1874,13 +1880,13 @@ __global__ void __launch_bounds__(1024) adj_ply_df(AdjArgs a) {
           df_add(p, e, zh[1], zl[1]);
           df_mul(gh, gl, qh.z, ql.z, p, e);
           df_add(p, e, zh[2], zl[2]);
-          df_mul(gh, gl, qh.w, ql.w, p, e);
-          df_add(p, e, zh[3], zl[3]);
+          z3 = __fma_rn(v[j], sQ3[t], z3);
         }
       }
     }
+    split_df(z3, zh[3], zl[3]);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {  // renormalise the pairs
+    for (int k = 0; k < 3; ++k) {  // renormalise the pairs
       const float hsum = __fadd_rn(zh[k], zl[k]);
       zl[k] = __fsub_rn(zl[k], __fsub_rn(hsum, zh[k]));
       zh[k] = hsum;
@@ -1911,7 +1917,7 @@ __global__ void __launch_bounds__(1024) adj_ply_df(AdjArgs a) {
 }
 
 static size_t adj_df_smem(int nthr, size_t idx_bytes) {
-  return (size_t)kAdjFastTerms * 32 + (size_t)9 * nthr * sizeof(double) + (size_t)kAdjRows * 3 * kAdjFastTerms * idx_bytes +
+  return (size_t)kAdjFastTerms * 40 + (size_t)9 * nthr * sizeof(double) + (size_t)kAdjRows * 3 * kAdjFastTerms * idx_bytes +
          2 * kAdjRows * sizeof(int);
 }
 
@@ -1927,15 +1933,20 @@ struct AdjReduceArgs {
 
 // One CTA per ply: the 81 sums (scales restored), dL/dD_l, dL/dtheta_l and
 // the ply's share of dL/dC (21 constants).
-__global__ void __launch_bounds__(128) adj_reduce(AdjReduceArgs a) {
-  __shared__ double S[81], dD[36], pr[36], T[36];
+__global__ void __launch_bounds__(384) adj_reduce(AdjReduceArgs a) {
+  __shared__ double S[81], dD[36], pr[36], T[36], part[4][81];
   const int l = blockIdx.x, t = threadIdx.x;
+  if (t < 4 * 81) {  // four threads per sum, then a fixed-order combination
+    const int k = t % 81, q = t / 81;
+    double acc = 0.0;
+    for (int ch = q; ch < a.nchunks; ch += 4) acc += a.partial[((size_t)l * a.nchunks + ch) * 81 + k];
+    part[q][k] = acc;
+  }
+  __syncthreads();
   if (t < 81) {
     const int ab = t % 9;
     const int ty = 2 * (ab / 3 == 2) + (ab % 3 == 2);
-    double acc = 0.0;
-    for (int ch = 0; ch < a.nchunks; ++ch) acc += a.partial[((size_t)l * a.nchunks + ch) * 81 + t];
-    S[t] = acc * a.qscale[ty] * a.gscale[ab];
+    S[t] = (((part[0][t] + part[1][t]) + part[2][t]) + part[3][t]) * a.qscale[ty] * a.gscale[ab];
   }
   __syncthreads();
   // Voigt index of the symmetric pair (i, j): 11, 22, 33, 12, 13, 23
@@ -2082,16 +2093,22 @@ static lam_status adjoint(Plan& P, const lam_cotangent& cot, double* dC, double*
                           cudaStream_t s) {
   Device& D = *P.dev;
   lam_status st;
-  if ((st = inplane_gram(P, s)) != LAM_OK) return st;
-  cudaEvent_t ev = prof_begin(P, s);
-  LAM_CUDA(cudaMemsetAsync(D.adj_flag, 0, 2 * sizeof(int), s));
-  if ((st = gather_gram(P, s)) != LAM_OK) return st;
   double* gscale = reinterpret_cast<double*>(D.adj_gmax + 9);
-  const int64_t n9 = 9 * P.nnz_s;
-  adj_split<<<(unsigned)std::min<int64_t>((n9 + 255) / 256, 152 * 8), 256, 0, s>>>(n9, D.adj_G, D.adj_Gdf, D.adj_gmax,
-                                                                                    gscale);
-  LAM_CUDA(cudaGetLastError());
-  prof_end(P, LAM_KERNEL_ADJOINT_AUX, 2, s, ev);
+  cudaEvent_t ev;
+  if (!D.adj_g_cached) {
+    // the in-plane Gram blocks depend on the geometry only, which a plan never
+    // changes: computed on the first call and kept
+    if ((st = inplane_gram(P, s)) != LAM_OK) return st;
+    ev = prof_begin(P, s);
+    if ((st = gather_gram(P, s)) != LAM_OK) return st;
+    const int64_t n9 = 9 * P.nnz_s;
+    adj_split<<<(unsigned)std::min<int64_t>((n9 + 255) / 256, 152 * 8), 256, 0, s>>>(n9, D.adj_G, D.adj_Gdf,
+                                                                                      D.adj_gmax, gscale);
+    LAM_CUDA(cudaGetLastError());
+    prof_end(P, LAM_KERNEL_ADJOINT_AUX, 2, s, ev);
+    D.adj_g_cached = true;
+  }
+  LAM_CUDA(cudaMemsetAsync(D.adj_flag, 0, 2 * sizeof(int), s));
   AdjArgs a{};
   a.ns = P.ns;
   a.n_dof = P.n_dof;
@@ -2159,7 +2176,7 @@ static lam_status adjoint(Plan& P, const lam_cotangent& cot, double* dC, double*
   r.dD = dDout;
   r.dtheta = dtheta;
   r.plyC = D.adj_plyC;
-  adj_reduce<<<(unsigned)P.plies.size(), 128, 0, s>>>(r);
+  adj_reduce<<<(unsigned)P.plies.size(), 384, 0, s>>>(r);
   LAM_CUDA(cudaGetLastError());
   if (dC) {
     adj_material<<<1, 256, 0, s>>>((int)P.plies.size(), (int)P.mats.size(), D.ply_mat, D.adj_plyC, dC);
@@ -2602,6 +2619,7 @@ lam_status lam_inplane_operators(lam_plan* plan, int32_t ply, int32_t method, do
   if (method == LAM_P_FROM_GRAM) {
     if ((st = lam::ensure_adjoint(P)) != LAM_OK) return st;
     if ((st = lam::inplane_gram(P, s)) != LAM_OK) return st;
+    D.adj_g_cached = false;  // the adjoint's scaled copy is overwritten here
     if ((st = lam::gather_gram(P, s)) != LAM_OK) return st;
     const int64_t n = P.nnz_s * 36;
     lam::kp_from_gram<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P.nnz_s, D.adj_G, D.cfgE + (size_t)m * 81, d_P);

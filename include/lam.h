@@ -243,6 +243,8 @@ typedef struct {
  *   d_dtheta  n_plies doubles, per radian;
  *   d_dD      n_plies x 36 doubles, dL/dD_l[I][J] row-major, every entry of
  *             D_l taken as independent.
+ * Low-rank cotangents are contracted in factorised form (G v per thickness
+ * function, then u^T (G v) per thickness pair) in FP64. For CSR cotangents:
  * Arithmetic: products and sums run in double-float arithmetic on the FP32
  * pipes (about 2^-44 relative per term) with FP64 partial sums. The whole
  * gradient is recomputed in FP64 on the same stream when a partial result is

@@ -72,6 +72,8 @@ struct Device {
   // adjoint: geometry tables and workspace (allocated by the first lam_adjoint)
   bool adj_ready = false;
   bool adj_g_cached = false;       // adj_G / adj_Gdf / scales hold this plan's scaled Gram blocks
+  double* adj_W = nullptr;         // low rank: n_t x n_s x 27 (G v per thickness function)
+  double* adj_X = nullptr;         // low rank: nnz_t x 81 (u^T G v per thickness pair)
   int *adj_begin = nullptr, *adj_pair = nullptr;
   double* adj_q = nullptr;
   float* adj_qdf = nullptr;
@@ -1921,6 +1923,83 @@ static size_t adj_df_smem(int nthr, size_t idx_bytes) {
          2 * kAdjRows * sizeof(int);
 }
 
+// ---------------------------------------------------------------------------
+// Low-rank cotangent (L = sum_q u_q^T K v_q), factorised: with scaled G,
+//   W_q(j_t, i_s)[ab][d] = sum_{k_s} G_ab(i_s, k_s) v_q(j_t, j_s(k_s), d),
+//   X(i_t, j_t)[c][d][ab] = sum_q sum_{i_s} u_q(i_t, i_s, c) W_q(j_t, i_s)[ab][d],
+//   S_l[cd][ab] = sum over the ply's thickness pairs of Q_{l,type(ab)} X,
+// in FP64 (about 9 FMA per in-plane pair, thickness function and rank, against
+// 9 per stored entry for the general cotangent).
+// ---------------------------------------------------------------------------
+struct AdjLrArgs {
+  int64_t ns, nt, n_dof;
+  int nx;
+  const int64_t* LSb;
+  const int *lenX, *lenY, *loX, *loY;
+  const double* G;
+  const double* u;  // rank q's vectors (offset applied by the host)
+  const double* v;
+  double* W;
+  double* X;
+  int64_t npairs;
+  const int *tp_row, *tp_col;
+  int accumulate;   // add to X (ranks after the first)
+};
+
+__global__ void adj_lr_w(AdjLrArgs a) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= a.nt * a.ns * 27) return;
+  const int k = (int)(t % 27);
+  const int64_t r = t / 27, is = r % a.ns, jt = r / a.ns;
+  const int ab = k / 3, d = k % 3;
+  const int ix = (int)(is % a.nx), iy = (int)(is / a.nx);
+  const int lx = a.lenX[ix], ls = lx * a.lenY[iy];
+  const int64_t ls0 = a.LSb[is];
+  double acc = 0.0;
+  for (int ks = 0; ks < ls; ++ks) {
+    const int64_t js = (int64_t)(a.loY[iy] + ks / lx) * a.nx + a.loX[ix] + ks % lx;
+    acc += a.G[(ls0 + ks) * 9 + ab] * a.v[3 * (jt * a.ns + js) + d];
+  }
+  a.W[t] = acc;
+}
+
+// One CTA per thickness pair, 3 x 81 threads: each sums a third of the
+// in-plane functions, then the thirds are added in a fixed order.
+__global__ void __launch_bounds__(256) adj_lr_x(AdjLrArgs a) {
+  __shared__ double part[3][81];
+  const int64_t pr = blockIdx.x;
+  const int it = a.tp_row[pr], jt = a.tp_col[pr];
+  const int t = threadIdx.x;
+  if (t < 243) {
+    const int o = t % 81, q = t / 81;
+    const int c = o / 27, dab = o % 27;  // o = (c * 3 + d) * 9 + ab
+    const int d = (o / 9) % 3, ab = o % 9;
+    (void)dab;
+    double acc = 0.0;
+    for (int64_t is = q; is < a.ns; is += 3)
+      acc += a.u[3 * ((int64_t)it * a.ns + is) + c] * a.W[((int64_t)jt * a.ns + is) * 27 + ab * 3 + d];
+    part[q][o] = acc;
+  }
+  __syncthreads();
+  if (t < 81) {
+    const double v = (part[0][t] + part[1][t]) + part[2][t];
+    a.X[pr * 81 + t] = a.accumulate ? a.X[pr * 81 + t] + v : v;
+  }
+}
+
+// Per ply: S_l[cd][ab] = sum over its terms of Q_{type(ab)} X(pair), written as
+// the ply's single partial for adj_reduce.
+__global__ void adj_lr_ply(const int* __restrict__ term_begin, const int* __restrict__ term_pair,
+                           const double* __restrict__ term_q, const double* __restrict__ X, double* __restrict__ partial) {
+  const int l = blockIdx.x, t = threadIdx.x;
+  if (t >= 81) return;
+  const int ab = t % 9;
+  const int ty = 2 * (ab / 3 == 2) + (ab % 3 == 2);
+  double acc = 0.0;
+  for (int k = term_begin[l]; k < term_begin[l + 1]; ++k) acc += term_q[(size_t)k * 4 + ty] * X[(size_t)term_pair[k] * 81 + t];
+  partial[(size_t)l * 81 + t] = acc;
+}
+
 struct AdjReduceArgs {
   int nchunks;
   double qscale[4];
@@ -2033,6 +2112,8 @@ static lam_status ensure_adjoint(Plan& P) {
   D.adj_gmax = reinterpret_cast<unsigned long long*>(p);
   if ((st = alloc_dev(L, &D.adj_partial, (size_t)P.plies.size() * adj_nchunks(P) * 81)) != LAM_OK) return st;
   if ((st = alloc_dev(L, &D.adj_plyC, (size_t)P.plies.size() * 21)) != LAM_OK) return st;
+  if ((st = alloc_dev(L, &D.adj_W, (size_t)P.nt * P.ns * 27)) != LAM_OK) return st;
+  if ((st = alloc_dev(L, &D.adj_X, (size_t)P.nnz_t * 81)) != LAM_OK) return st;
   if ((st = alloc_dev(L, &p, 1)) != LAM_OK) return st;
   D.adj_flag = reinterpret_cast<int*>(p);  // flag, then emax
   D.adj_ready = true;
@@ -2141,8 +2222,42 @@ static lam_status adjoint(Plan& P, const lam_cotangent& cot, double* dC, double*
   a.emax = D.adj_flag + 1;
   const bool lowrank = cot.kind == LAM_COTANGENT_LOWRANK;
   const bool force64 = (cot.flags & LAM_ADJOINT_FP64) != 0;
+  int nchunks_out = a.nchunks;
   ev = prof_begin(P, s);
-  if (!force64) {
+  if (lowrank && !force64) {
+    // factorised form, FP64 throughout
+    AdjLrArgs lr{};
+    lr.ns = P.ns;
+    lr.nt = P.nt;
+    lr.n_dof = P.n_dof;
+    lr.nx = P.u.n;
+    lr.LSb = D.LSb;
+    lr.lenX = D.lenX;
+    lr.lenY = D.lenY;
+    lr.loX = D.loX;
+    lr.loY = D.loY;
+    lr.G = D.adj_G;
+    lr.W = D.adj_W;
+    lr.X = D.adj_X;
+    lr.npairs = P.nnz_t;
+    lr.tp_row = D.tp_row;
+    lr.tp_col = D.tp_col;
+    const int64_t nw = P.nt * P.ns * 27;
+    for (int q = 0; q < cot.rank; ++q) {
+      lr.u = cot.u + (size_t)q * P.n_dof;
+      lr.v = cot.v + (size_t)q * P.n_dof;
+      lr.accumulate = q > 0;
+      adj_lr_w<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(lr);
+      LAM_CUDA(cudaGetLastError());
+      adj_lr_x<<<(unsigned)P.nnz_t, 256, 0, s>>>(lr);
+      LAM_CUDA(cudaGetLastError());
+    }
+    adj_lr_ply<<<(unsigned)P.plies.size(), 96, 0, s>>>(D.adj_begin, D.adj_pair, D.adj_q, D.adj_X, D.adj_partial);
+    LAM_CUDA(cudaGetLastError());
+    prof_end(P, LAM_KERNEL_ADJOINT, 2 * cot.rank + 1, s, ev);
+    ev = prof_begin(P, s);
+    nchunks_out = 1;
+  } else if (!force64) {
     a.conditional = 0;
     if (lowrank)
       st = launch_adj_ply<true, true>(P, a, s);
@@ -2156,16 +2271,20 @@ static lam_status adjoint(Plan& P, const lam_cotangent& cot, double* dC, double*
     prof_end(P, LAM_KERNEL_ADJOINT, 1, s, ev);
     ev = prof_begin(P, s);
   }
-  a.conditional = force64 ? 0 : 1;  // otherwise it runs only when the double-float result is rejected
-  st = lowrank ? launch_adj_ply<true, false>(P, a, s) : launch_adj_ply<false, false>(P, a, s);
-  if (st != LAM_OK) return st;
-  if (force64) {
-    prof_end(P, LAM_KERNEL_ADJOINT, 1, s, ev);
-    ev = prof_begin(P, s);
+  int aux = 1;  // the reduce
+  if (!(lowrank && !force64)) {
+    a.conditional = force64 ? 0 : 1;  // otherwise it runs only when the double-float result is rejected
+    st = lowrank ? launch_adj_ply<true, false>(P, a, s) : launch_adj_ply<false, false>(P, a, s);
+    if (st != LAM_OK) return st;
+    if (force64) {
+      prof_end(P, LAM_KERNEL_ADJOINT, 1, s, ev);
+      ev = prof_begin(P, s);
+    } else {
+      ++aux;  // the conditional FP64 pass
+    }
   }
-  int aux = force64 ? 1 : 2;  // the reduce, and the conditional FP64 pass
   AdjReduceArgs r{};
-  r.nchunks = a.nchunks;
+  r.nchunks = nchunks_out;
   for (int k = 0; k < 4; ++k) r.qscale[k] = P.adj_qscale[k];
   r.gscale = gscale;
   r.partial = D.adj_partial;

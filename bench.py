@@ -311,6 +311,8 @@ def run_adjoint(args, L, dev, flush, peak, peak_kind, world):
         return max_over_ranks(sum(a.elapsed_time(b) for a, b in evs) / steps, dev), pr
 
     steps = args.adjoint_steps
+    u = torch.randn(1, plan.n_dof, dtype=torch.float64, device=dev, generator=gen)
+    ms_lr, _ = timed(lambda: plan.adjoint(u=u, v=u, want_dD=False), steps)
     ms, pr = timed(lambda: plan.adjoint(values=g, want_dD=False), steps)
     ms_fwd, _ = timed(lambda: plan.assemble_split(vals), steps)
     ms64, _ = timed(lambda: plan.adjoint(values=g, want_dD=False, fp64=True), max(2, steps // 4))
@@ -323,6 +325,8 @@ def run_adjoint(args, L, dev, flush, peak, peak_kind, world):
            "metric": "cotangent entries contracted per second", "value": aggregate_throughput(nnz, world, ms / 1e3),
            "unit": UNIT, "ms_per_step": ms, "steps": steps, "nnz": nnz,
            "split_assembly_ms_same_plate": ms_fwd, "adjoint_over_assembly": ms / ms_fwd,
+           "compliance_gradient_ms": ms_lr,
+           "compliance_gradient": "L = u^T K u, u ~ N(0,1) per DOF (torch seed 1905): the low-rank cotangent u u^T",
            "fp64_pass_ms": ms64,
            "kernels_ms_per_step": {kk: pr[kk]["ms"] / steps for kk in L.KERNEL_KINDS if pr[kk]["launches"]},
            "gpu_launches": sum(pr[kk]["launches"] for kk in L.KERNEL_KINDS) // steps,

@@ -200,3 +200,37 @@ def test_autograd_function(L):
     ref = O.adjoint(lam, rp, col, g.cpu().numpy())
     assert rel(C.grad.numpy(), ref[0]) <= 1e-10
     assert rel(th.grad.numpy(), ref[1]) <= 1e-9
+
+
+def test_full_size_compliance_gradient_finite_differences(L, full):
+    """The compliance loss L = u^T K u (a rank-one cotangent u u^T) on the full
+    plate: the factorised low-rank adjoint against central differences of
+    u^T K(theta, C) u computed with the split assembly and a CSR product."""
+    import torch
+    lam, p, _ = full
+    u = torch.randn(p.n_dof, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    row_ptr, col = p.pattern()
+    dC, dth, _ = p.adjoint(u=u[None, :], v=u[None, :], want_dD=False)
+    dC, dth = dC.cpu().numpy(), dth.cpu().numpy()
+    ang0, C0 = lam.ply_angle.copy(), lam.C21.copy()
+
+    def Lof(ang, C):
+        p.update(ply_angle=ang, C21=C)
+        K = torch.sparse_csr_tensor(row_ptr, col, p.assemble_split(), size=(p.n_dof, p.n_dof))
+        return float(torch.dot(u, K @ u))
+
+    h = 1e-6
+    for l in (0, 11, 23):
+        a1, a2 = ang0.copy(), ang0.copy()
+        a1[l] += h
+        a2[l] -= h
+        fd = (Lof(a1, C0) - Lof(a2, C0)) / (2 * h)
+        assert abs(fd - dth[l]) <= 1e-6 * np.abs(dth).max(), (l, fd, dth[l])
+    for k in (0, 3, 9, 15, 20):
+        hk = 1e-6 * abs(C0[0, k]) if C0[0, k] != 0 else 1e-6
+        c1, c2 = C0.copy(), C0.copy()
+        c1[0, k] += hk
+        c2[0, k] -= hk
+        fd = (Lof(ang0, c1) - Lof(ang0, c2)) / (2 * hk)
+        assert abs(fd - dC[0, k]) <= 1e-6 * np.abs(dC).max(), (k, fd, dC[0, k])
+    p.update(ply_angle=ang0, C21=C0)

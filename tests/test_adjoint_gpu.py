@@ -210,6 +210,7 @@ def test_full_size_compliance_gradient_finite_differences(L, full):
     lam, p, _ = full
     u = torch.randn(p.n_dof, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
     row_ptr, col = p.pattern()
+    col = col.long()  # torch's CSR wants one index type
     dC, dth, _ = p.adjoint(u=u[None, :], v=u[None, :], want_dD=False)
     dC, dth = dC.cpu().numpy(), dth.cpu().numpy()
     ang0, C0 = lam.ply_angle.copy(), lam.C21.copy()

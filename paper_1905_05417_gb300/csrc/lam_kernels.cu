@@ -600,6 +600,171 @@ struct KaLocalArgs {
   double* EG;
 };
 
+// (h, l) = a * b as a normalised float pair (|l| <= ulp(h) / 2).
+__device__ __forceinline__ void df_prod(float ah, float al, float bh, float bl, float& h, float& l) {
+  float p, e;
+  df_mul(ah, al, bh, bl, p, e);
+  h = __fadd_rn(p, e);
+  l = __fsub_rn(e, __fsub_rn(h, p));
+}
+__device__ __forceinline__ void df_norm(float& h, float& l) {
+  const float s = __fadd_rn(h, l);
+  l = __fsub_rn(l, __fsub_rn(s, h));
+  h = s;
+}
+
+// The element's point values for the Gram products (Eq. of G_ab: g = (dR/dx,
+// dR/dy, R) at every Gauss point), written as float pairs phf / pwf with the
+// layout hi0 hi1 hi2 lo0 lo1 lo2 per (point, local function), pwf = w|DF| phf.
+//   A  (FP64) per (point, sum): the geometry sums over the element's functions,
+//      factorised over the tensor product (sum over x inside, over y outside):
+//      the four entries of DF, or for NURBS the nine sums W, dW/dxi_k and the
+//      same with w X and w Y, from which DF follows by the quotient rule;
+//   P  (FP64) per point: DF^-1 and w|DF| (and 1/W, W_,1/W, W_,2/W);
+//   B  (double-float) per (point, function): R, its parametric derivatives,
+//      the physical gradient and the weighted copy, on the FP32 pipes.
+// DF^-1 is carried as DF^-1 2^-kd and w|DF| as w|DF| 2^-kq (powers of two per
+// element, largest entries in [1, 2)), so float pairs hold any geometry scale;
+// the Gram block (a, b) is scaled back by 2^(kq + kd ([a < 2] + [b < 2])).
+__device__ __forceinline__ void ka_point_values(const InplaneArgs& ip, int ex, int ey, double* phi, double* phiw,
+                                                double* qd, int* s_k) {
+  const int nlx = ip.pu + 1, nly = ip.pv + 1, nls = nlx * nly, nqs = ip.nqu * ip.nqv;
+  const int fx = ip.firstU[ex], fy = ip.firstV[ey];
+  const bool rat = ip.weights != nullptr;
+  const int nsum = rat ? 9 : 4;
+  double* S = phi;   // phase A results, nqs x nsum (consumed before phase B writes phf)
+  double* hc = phiw; // homogeneous control values (w, w X, w Y) of a NURBS element
+  if (rat) {
+    for (int k = threadIdx.x; k < nls; k += blockDim.x) {
+      const size_t gi = (size_t)(fy + k / nlx) * ip.nx + fx + k % nlx;
+      const double w = ip.weights[gi];
+      hc[k] = w;
+      hc[nls + k] = w * ip.ctrl[2 * gi];
+      hc[2 * nls + k] = w * ip.ctrl[2 * gi + 1];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < nqs * nsum; t += blockDim.x) {
+    const int q = t / nsum, sidx = t % nsum;
+    const int qu = q % ip.nqu, qv = q / ip.nqu;
+    // der: 0 value, 1 d/dxi1, 2 d/dxi2; dat: X, Y (B-spline) or w, w X, w Y (NURBS)
+    const int dat = rat ? sidx / 3 : sidx / 2, der = rat ? sidx % 3 : 1 + sidx % 2;
+    const double* tu = ip.tabU + ((size_t)ex * ip.nqu + qu) * nlx * 2 + (der == 1 ? 1 : 0);
+    const double* tv = ip.tabV + ((size_t)ey * ip.nqv + qv) * nly * 2 + (der == 2 ? 1 : 0);
+    double acc = 0.0;
+    for (int ly = 0; ly < nly; ++ly) {
+      double row = 0.0;
+      for (int lx = 0; lx < nlx; ++lx) {
+        const double c = rat ? hc[dat * nls + ly * nlx + lx]
+                             : ip.ctrl[2 * ((size_t)(fy + ly) * ip.nx + fx + lx) + dat];
+        row = fma(tu[2 * lx], c, row);
+      }
+      acc = fma(tv[2 * ly], row, acc);
+    }
+    S[t] = acc;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < nqs; q += blockDim.x) {
+    const double* sq = S + (size_t)q * nsum;
+    double J00, J01, J10, J11, iw = 1.0, r1 = 0.0, r2 = 0.0;
+    if (rat) {  // d(A / W) = (dA - (A / W) dW) / W
+      iw = 1.0 / sq[0];
+      r1 = sq[1] * iw;
+      r2 = sq[2] * iw;
+      J00 = (sq[4] - sq[3] * r1) * iw;
+      J01 = (sq[5] - sq[3] * r2) * iw;
+      J10 = (sq[7] - sq[6] * r1) * iw;
+      J11 = (sq[8] - sq[6] * r2) * iw;
+    } else {
+      J00 = sq[0];
+      J01 = sq[1];
+      J10 = sq[2];
+      J11 = sq[3];
+    }
+    const int qu = q % ip.nqu, qv = q / ip.nqu;
+    const double det = J00 * J11 - J01 * J10, inv = 1.0 / det;
+    double* d = qd + (size_t)q * 8;
+    d[0] = J11 * inv;   // dxi1/dx
+    d[1] = -J01 * inv;  // dxi1/dy
+    d[2] = -J10 * inv;  // dxi2/dx
+    d[3] = J00 * inv;   // dxi2/dy
+    d[4] = ip.wU[(size_t)ex * ip.nqu + qu] * ip.wV[(size_t)ey * ip.nqv + qv] * fabs(det);
+    d[5] = iw;
+    d[6] = r1;
+    d[7] = r2;
+    int ed = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ed = max(ed, (__double2hiint(d[k]) >> 20) & 0x7FF);
+    atomicMax(&s_k[0], ed);
+    atomicMax(&s_k[1], (__double2hiint(d[4]) >> 20) & 0x7FF);
+  }
+  __syncthreads();
+  const int kd = s_k[0] > 0 ? s_k[0] - 1023 : 0, kq = s_k[1] > 0 ? s_k[1] - 1023 : 0;
+  float* phf = reinterpret_cast<float*>(phi);
+  float* pwf = reinterpret_cast<float*>(phiw);
+  for (int t = threadIdx.x; t < nqs * nls; t += blockDim.x) {
+    const int q = t / nls, k = t % nls;
+    const int qu = q % ip.nqu, qv = q / ip.nqu, lx = k % nlx, ly = k / nlx;
+    const double* tu = ip.tabU + ((size_t)ex * ip.nqu + qu) * nlx * 2 + 2 * lx;
+    const double* tv = ip.tabV + ((size_t)ey * ip.nqv + qv) * nly * 2 + 2 * ly;
+    const double* d = qd + (size_t)q * 8;
+    float u0h, u0l, u1h, u1l, v0h, v0l, v1h, v1l;
+    split_df_fast(tu[0], u0h, u0l);
+    split_df_fast(tu[1], u1h, u1l);
+    split_df_fast(tv[0], v0h, v0l);
+    split_df_fast(tv[1], v1h, v1l);
+    float Rh, Rl, R1h, R1l, R2h, R2l;
+    df_prod(u0h, u0l, v0h, v0l, Rh, Rl);
+    df_prod(u1h, u1l, v0h, v0l, R1h, R1l);
+    df_prod(u0h, u0l, v1h, v1l, R2h, R2l);
+    if (rat) {  // R = c N, R_,k = c (N_,k - N W_,k / W), c = w / W
+      float ch, cl, rh, rl, th, tl;
+      split_df_fast(ip.weights[(size_t)(fy + ly) * ip.nx + fx + lx] * d[5], ch, cl);
+      split_df_fast(d[6], rh, rl);
+      df_prod(Rh, Rl, -rh, -rl, th, tl);
+      df_add(th, tl, R1h, R1l);
+      df_norm(R1h, R1l);
+      df_prod(R1h, R1l, ch, cl, R1h, R1l);
+      split_df_fast(d[7], rh, rl);
+      df_prod(Rh, Rl, -rh, -rl, th, tl);
+      df_add(th, tl, R2h, R2l);
+      df_norm(R2h, R2l);
+      df_prod(R2h, R2l, ch, cl, R2h, R2l);
+      df_prod(Rh, Rl, ch, cl, Rh, Rl);
+    }
+    float dh[4], dl[4], wh, wl;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) split_df_off(d[j], kd, dh[j], dl[j]);
+    split_df_off(d[4], kq, wh, wl);
+    float gxh, gxl, gyh, gyl;
+    df_mul(dh[0], dl[0], R1h, R1l, gxh, gxl);
+    df_mac(dh[2], dl[2], R2h, R2l, gxh, gxl);
+    df_norm(gxh, gxl);
+    df_mul(dh[1], dl[1], R1h, R1l, gyh, gyl);
+    df_mac(dh[3], dl[3], R2h, R2l, gyh, gyl);
+    df_norm(gyh, gyl);
+    float* f = phf + (size_t)t * 6;
+    float* fw = pwf + (size_t)t * 6;
+    f[0] = gxh;
+    f[1] = gyh;
+    f[2] = Rh;
+    f[3] = gxl;
+    f[4] = gyl;
+    f[5] = Rl;
+    float h, l;
+    df_prod(wh, wl, gxh, gxl, h, l);
+    fw[0] = h;
+    fw[3] = l;
+    df_prod(wh, wl, gyh, gyl, h, l);
+    fw[1] = h;
+    fw[4] = l;
+    df_prod(wh, wl, Rh, Rl, h, l);
+    fw[2] = h;
+    fw[5] = l;
+  }
+  __syncthreads();
+}
+
 __device__ __forceinline__ void ka_elem(const KaLocalArgs& a, int e, double* sm) {
   const InplaneArgs& ip = a.ip;
   const int nlx = ip.pu + 1, nly = ip.pv + 1, nls = nlx * nly, nqs = ip.nqu * ip.nqv;
@@ -607,46 +772,13 @@ __device__ __forceinline__ void ka_elem(const KaLocalArgs& a, int e, double* sm)
   double* phiw = phi + (size_t)nqs * nls * 3;
   double* qd = phiw + (size_t)nqs * nls * 3;
   const int ex = e % ip.nel_u, ey = e / ip.nel_u;
-  __shared__ int s_emax[2];
-  if (threadIdx.x < 2) s_emax[threadIdx.x] = 0;
-  inplane_points(ip, ex, ey, phi, phiw, qd);
-  // Per element, the point values are scaled by powers of two so that the
-  // largest lies in [1, 2) (exact), which keeps the float pairs far from float
-  // overflow and underflow whatever the geometry's scale; EG is scaled back.
-  {
-    int ep = 0, ew = 0;
-    for (int t = threadIdx.x; t < nqs * nls * 3; t += blockDim.x) {
-      ep = max(ep, (__double2hiint(phi[t]) >> 20) & 0x7FF);
-      ew = max(ew, (__double2hiint(phiw[t]) >> 20) & 0x7FF);
-    }
-    atomicMax(&s_emax[0], ep);
-    atomicMax(&s_emax[1], ew);
-  }
+  __shared__ int s_k[2];
+  if (threadIdx.x < 2) s_k[threadIdx.x] = 0;
   __syncthreads();
-  const int kp = s_emax[0] > 0 ? s_emax[0] - 1023 : 0, kw = s_emax[1] > 0 ? s_emax[1] - 1023 : 0;
-  // FP64 point values -> float pairs (hi0 hi1 hi2 lo0 lo1 lo2), in place
-  float* phf = reinterpret_cast<float*>(phi);
-  float* pwf = reinterpret_cast<float*>(phiw);
-  for (int t = threadIdx.x; t < nqs * nls; t += blockDim.x) {
-    double v[3], w[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      v[k] = phi[(size_t)t * 3 + k];
-      w[k] = phiw[(size_t)t * 3 + k];
-    }
-    // each item's 6 floats overwrite exactly its own 3 doubles (no other item's)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      float h, l;
-      split_df_off(v[k], kp, h, l);
-      phf[(size_t)t * 6 + k] = h;
-      phf[(size_t)t * 6 + 3 + k] = l;
-      split_df_off(w[k], kw, h, l);
-      pwf[(size_t)t * 6 + k] = h;
-      pwf[(size_t)t * 6 + 3 + k] = l;
-    }
-  }
-  __syncthreads();
+  ka_point_values(ip, ex, ey, phi, phiw, qd, s_k);
+  const int kd = s_k[0] > 0 ? s_k[0] - 1023 : 0, kq = s_k[1] > 0 ? s_k[1] - 1023 : 0;
+  const float* phf = reinterpret_cast<const float*>(phi);
+  const float* pwf = reinterpret_cast<const float*>(phiw);
   const int npl = nls * (nls + 1) / 2;
   double* out = a.EG + (size_t)e * 9 * npl;
   for (int t = threadIdx.x; t < npl; t += blockDim.x) {
@@ -680,7 +812,8 @@ __device__ __forceinline__ void ka_elem(const KaLocalArgs& a, int e, double* sm)
       const float hs = __fadd_rn(sh[k], sl[k]);
       const float ls = __fsub_rn(sl[k], __fsub_rn(hs, sh[k]));
       long long b = __double_as_longlong(df_to_double(hs, ls));
-      if (b & 0x7FFFFFFFFFFFFFFFll) b += (long long)(kp + kw) * (1ll << 52);  // times 2^(kp + kw), exact
+      const int sc = kq + kd * ((k / 3 < 2 ? 1 : 0) + (k % 3 < 2 ? 1 : 0));
+      if (b & 0x7FFFFFFFFFFFFFFFll) b += (long long)sc * (1ll << 52);  // times 2^sc, exact
       out[(size_t)k * npl + t] = __longlong_as_double(b);
     }
   }

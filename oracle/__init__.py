@@ -39,7 +39,8 @@ class _Problem(ctypes.Structure):
                 ("ply_material", ctypes.POINTER(ctypes.c_int32)),
                 ("ply_angle", ctypes.POINTER(ctypes.c_double)), ("n_materials", ctypes.c_int32),
                 ("C21", ctypes.POINTER(ctypes.c_double)), ("nq_u", ctypes.c_int32), ("nq_v", ctypes.c_int32),
-                ("nq_t", ctypes.c_int32)]
+                ("nq_t", ctypes.c_int32), ("ctrl_dim", ctypes.c_int32),
+                ("extrusion", ctypes.POINTER(ctypes.c_double))]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -108,9 +109,12 @@ class Problem:
         pa = arr(lam.ply_angle)
         C = arr(lam.C21)
         nq = tuple(lam.nq) + (0,) * (3 - len(lam.nq))
+        ext = getattr(lam, "extrusion", None)
+        ext = arr(ext) if ext is not None else None
         self.s = _Problem(basis(lam.u), basis(lam.v), _ptr(ctrl), _ptr(w) if w is not None else _D(),
                           basis(lam.t), len(h), _ptr(h), _ptr(pm, _I32), _ptr(pa), C.shape[0], _ptr(C),
-                          nq[0], nq[1], nq[2])
+                          nq[0], nq[1], nq[2], int(ctrl.shape[1]) if ctrl.ndim == 2 else 2,
+                          _ptr(ext) if ext is not None else _D())
         self.lam = lam
 
     def ref(self):

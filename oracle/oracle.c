@@ -289,13 +289,37 @@ static int check_problem(const ora_problem* pr) {
 }
 
 /* In-plane quantities at one point of in-plane element (ex, ey): values R,
- * parametric derivatives, the Jacobian determinant and the physical in-plane
- * gradient (gx, gy) = DF^{-T} (dR/dxi1, dR/dxi2) of Eq. gradient. */
+ * the Jacobian determinant |DF| and the pulled-back gradients of Eq. gradient
+ * split as in Eq. B_2: the 3D function S^k T has the physical gradient
+ *   grad(S^k T) = T g1[k] + T' S^k r3,
+ * g1[k] = DF^{-T} (dS^k/dxi1, dS^k/dxi2, 0), r3 = DF^{-T} e_3. For the planar
+ * map (S = (x, y, 0), a = e_z) g1[k] = (dS/dx, dS/dy, 0) and r3 = e_3. */
 typedef struct {
   int nlx, nly, fx, fy;
-  double R[64], gx[64], gy[64];
+  double R[64], g1[64][3];
+  double r3[3];
   double detJ;
 } inplane_point;
+
+/* A general extrusion: a surface in R^3 or a direction other than e_z. */
+static int is_shell(const ora_problem* pr) {
+  if (pr->ctrl_dim == 3) return 1;
+  if (pr->extrusion && (pr->extrusion[0] != 0.0 || pr->extrusion[1] != 0.0 || pr->extrusion[2] != 1.0)) return 1;
+  return 0;
+}
+
+static void cross3(const double a[3], const double b[3], double out[3]) {
+  out[0] = a[1] * b[2] - a[2] * b[1];
+  out[1] = a[2] * b[0] - a[0] * b[2];
+  out[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* Gradient of the 3D function (local in-plane k, thickness value T and
+ * derivative dT) at an in-plane point: T g1[k] + (dT R[k]) r3. */
+static void grad3(const inplane_point* ip, int k, double T, double dT, double out[3]) {
+  const double s = dT * ip->R[k];
+  for (int c = 0; c < 3; ++c) out[c] = T * ip->g1[k][c] + s * ip->r3[c];
+}
 
 static int eval_inplane(const ora_problem* pr, int ex, int ey, double xi, double eta, inplane_point* ip) {
   double Nu[8], dNu[8], Nv[8], dNv[8];
@@ -342,25 +366,66 @@ static int eval_inplane(const ora_problem* pr, int ex, int ey, double xi, double
       R2[k] = N2[k];
     }
   }
-  /* J[a][k] = d x_a / d xi_k = sum_i dR_i/dxi_k X_i[a] */
-  double J[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  if (!is_shell(pr)) {
+    /* J[a][k] = d x_a / d xi_k = sum_i dR_i/dxi_k X_i[a] */
+    double J[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    const int cd = pr->ctrl_dim == 3 ? 3 : 2;
+    for (int ly = 0; ly < nly; ++ly)
+      for (int lx = 0; lx < nlx; ++lx) {
+        int k = ly * nlx + lx;
+        const double* X = pr->ctrl + cd * ((fy + ly) * nx + (fx + lx));
+        J[0][0] += R1[k] * X[0];
+        J[0][1] += R2[k] * X[0];
+        J[1][0] += R1[k] * X[1];
+        J[1][1] += R2[k] * X[1];
+      }
+    double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    if (det == 0.0) return -1;
+    /* Jinv[k][a] = d xi_k / d x_a */
+    double Ji[2][2] = {{J[1][1] / det, -J[0][1] / det}, {-J[1][0] / det, J[0][0] / det}};
+    for (int k = 0; k < nl; ++k) {
+      ip->g1[k][0] = Ji[0][0] * R1[k] + Ji[1][0] * R2[k];
+      ip->g1[k][1] = Ji[0][1] * R1[k] + Ji[1][1] * R2[k];
+      ip->g1[k][2] = 0.0;
+    }
+    ip->r3[0] = 0.0;
+    ip->r3[1] = 0.0;
+    ip->r3[2] = 1.0;
+    ip->detJ = fabs(det);
+    return 0;
+  }
+  /* Eq. extrusion: DF = [dS/dxi1 | dS/dxi2 | a] (columns A[0], A[1], A[2]).
+   * The rows of DF^{-1} are the dual vectors g^k = (A[k+1] x A[k+2]) / det DF,
+   * so grad = DF^{-T} grad_xi = sum_k g^k d/dxi_k. */
+  double A[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+  const int cd = pr->ctrl_dim == 3 ? 3 : 2;
   for (int ly = 0; ly < nly; ++ly)
     for (int lx = 0; lx < nlx; ++lx) {
       int k = ly * nlx + lx;
-      const double* X = pr->ctrl + 2 * ((fy + ly) * nx + (fx + lx));
-      J[0][0] += R1[k] * X[0];
-      J[0][1] += R2[k] * X[0];
-      J[1][0] += R1[k] * X[1];
-      J[1][1] += R2[k] * X[1];
+      const double* X = pr->ctrl + cd * ((fy + ly) * nx + (fx + lx));
+      for (int c = 0; c < cd; ++c) {
+        A[0][c] += R1[k] * X[c];
+        A[1][c] += R2[k] * X[c];
+      }
     }
-  double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-  if (det == 0.0) return -1;
-  /* Jinv[k][a] = d xi_k / d x_a */
-  double Ji[2][2] = {{J[1][1] / det, -J[0][1] / det}, {-J[1][0] / det, J[0][0] / det}};
-  for (int k = 0; k < nl; ++k) {
-    ip->gx[k] = Ji[0][0] * R1[k] + Ji[1][0] * R2[k];
-    ip->gy[k] = Ji[0][1] * R1[k] + Ji[1][1] * R2[k];
+  if (pr->extrusion) {
+    A[2][0] = pr->extrusion[0];
+    A[2][1] = pr->extrusion[1];
+    A[2][2] = pr->extrusion[2];
+  } else {
+    A[2][2] = 1.0;
   }
+  double g[3][3], t[3];
+  cross3(A[1], A[2], t);
+  double det = A[0][0] * t[0] + A[0][1] * t[1] + A[0][2] * t[2];
+  if (det == 0.0) return -1;
+  for (int k = 0; k < 3; ++k) {
+    cross3(A[(k + 1) % 3], A[(k + 2) % 3], t);
+    for (int c = 0; c < 3; ++c) g[k][c] = t[c] / det;
+  }
+  for (int k = 0; k < nl; ++k)
+    for (int c = 0; c < 3; ++c) ip->g1[k][c] = g[0][c] * R1[k] + g[1][c] * R2[k];
+  for (int c = 0; c < 3; ++c) ip->r3[c] = g[2][c];
   ip->detJ = fabs(det);
   return 0;
 }
@@ -408,7 +473,8 @@ int ora_element_stiffness(const ora_problem* pr, int32_t ex, int32_t ey, int32_t
           double w = wu[a] * 0.5 * (ub - ua) * wv[b] * 0.5 * (vb - va) * wt[g] * 0.5 * (z1[pc] - z0[pc]) * ip.detJ;
           for (int lt = 0; lt < nlt; ++lt)
             for (int ls = 0; ls < nls; ++ls) {
-              double grad[3] = {ip.gx[ls] * T[lt], ip.gy[ls] * T[lt], ip.R[ls] * dT[lt]};
+              double grad[3];
+              grad3(&ip, ls, T[lt], dT[lt], grad);
               strain_matrix(grad, B[lt * nls + ls]);
             }
           for (int i = 0; i < nl; ++i)
@@ -671,8 +737,9 @@ int ora_block(const ora_problem* pr, int64_t i, int64_t j, double* out9) {
                 int ft;
                 ora_basis1d_eval(&pr->t, et, z, T, dT, &ft);
                 double w = wu[a] * 0.5 * (ub - ua) * wv[b] * 0.5 * (vb - va) * wt[g] * 0.5 * (z1[pc] - z0[pc]) * ip.detJ;
-                double gi[3] = {ip.gx[li] * T[it - ft], ip.gy[li] * T[it - ft], ip.R[li] * dT[it - ft]};
-                double gj[3] = {ip.gx[lj] * T[jt - ft], ip.gy[lj] * T[jt - ft], ip.R[lj] * dT[jt - ft]};
+                double gi[3], gj[3];
+                grad3(&ip, li, T[it - ft], dT[it - ft], gi);
+                grad3(&ip, lj, T[jt - ft], dT[jt - ft], gj);
                 double Bi[6][3], Bj[6][3];
                 strain_matrix(gi, Bi);
                 strain_matrix(gj, Bj);
@@ -738,8 +805,11 @@ int ora_assemble_split(const ora_problem* pr, int64_t* row_ptr, int32_t* col, do
                 int64_t is = (int64_t)(ip.fy + li / nlx) * nx + ip.fx + li % nlx;
                 int64_t js = (int64_t)(ip.fy + lj / nlx) * nx + ip.fx + lj % nlx;
                 double B1i[6][3], B2i[6][3], B1j[6][3], B2j[6][3];
-                double v1i[3] = {ip.gx[li], ip.gy[li], 0.0}, v2i[3] = {0.0, 0.0, ip.R[li]};
-                double v1j[3] = {ip.gx[lj], ip.gy[lj], 0.0}, v2j[3] = {0.0, 0.0, ip.R[lj]};
+                double v1i[3], v2i[3], v1j[3], v2j[3];
+                grad3(&ip, li, 1.0, 0.0, v1i);
+                grad3(&ip, li, 0.0, 1.0, v2i);
+                grad3(&ip, lj, 1.0, 0.0, v1j);
+                grad3(&ip, lj, 0.0, 1.0, v2j);
                 strain_matrix(v1i, B1i);
                 strain_matrix(v2i, B2i);
                 strain_matrix(v1j, B1j);
@@ -872,7 +942,8 @@ int ora_adjoint_D(const ora_problem* pr, const int64_t* row_ptr, const int32_t* 
                 double w = wu[qa] * 0.5 * (ub - ua) * wv[qb] * 0.5 * (vb - va) * wt[g] * 0.5 * (z1[pc] - z0[pc]) * ip.detJ;
                 for (int lt = 0; lt < nlt; ++lt)
                   for (int ls = 0; ls < nls; ++ls) {
-                    double grad[3] = {ip.gx[ls] * T[lt], ip.gy[ls] * T[lt], ip.R[ls] * dT[lt]};
+                    double grad[3];
+                    grad3(&ip, ls, T[lt], dT[lt], grad);
                     strain_matrix(grad, B[lt * nls + ls]);
                   }
                 for (int a = 0; a < nl; ++a)
@@ -1008,8 +1079,11 @@ int ora_inplane_P(const ora_problem* pr, int l, int64_t is, int64_t js, double* 
           if (eval_inplane(pr, ex, ey, xi, eta, &ip) < 0) { support_free(&su); support_free(&sv); return -1; }
           int li = (iy - ip.fy) * nlx + (ix - ip.fx), lj = (jy - ip.fy) * nlx + (jx - ip.fx);
           double w = wu[a] * 0.5 * (ub - ua) * wv[b] * 0.5 * (vb - va) * ip.detJ;
-          double gi1[3] = {ip.gx[li], ip.gy[li], 0.0}, gi2[3] = {0.0, 0.0, ip.R[li]};
-          double gj1[3] = {ip.gx[lj], ip.gy[lj], 0.0}, gj2[3] = {0.0, 0.0, ip.R[lj]};
+          double gi1[3], gi2[3], gj1[3], gj2[3];
+          grad3(&ip, li, 1.0, 0.0, gi1);
+          grad3(&ip, li, 0.0, 1.0, gi2);
+          grad3(&ip, lj, 1.0, 0.0, gj1);
+          grad3(&ip, lj, 0.0, 1.0, gj2);
           double Bi1[6][3], Bi2[6][3], Bj1[6][3], Bj2[6][3];
           strain_matrix(gi1, Bi1);
           strain_matrix(gi2, Bi2);

@@ -17,7 +17,10 @@
  * Conventions (the same ones the library documents, restated here):
  *   - in-plane basis S^{i_s}, i_s = iy*nx + ix; thickness basis T^{i_t};
  *     3D basis index i = i_t*n_s + i_s (Assumption 1); DOF = 3*i + c.
- *   - the thickness coordinate is physical z (extrusion direction a = e_z).
+ *   - the map is the extrusion F(xi) = S(xi^1, xi^2) + xi^3 a (Eq. extrusion):
+ *     S planar (x, y, 0) or a surface in R^3, a = e_z unless given; the
+ *     thickness coordinate xi^3 runs over the thickness knots (physical z
+ *     when a = e_z).
  *   - ply 0 starts at the first thickness knot; plies are stacked upwards.
  *   - materials: 21 Voigt constants (upper triangle, row-major, order
  *     11,22,33,12,13,23, engineering shear) in the material frame; a ply with
@@ -42,7 +45,7 @@ typedef struct {
 
 typedef struct {
   ora_basis1d u, v;        /* in-plane directions xi^1 (x-index) and xi^2 (y-index) */
-  const double* ctrl;      /* n_s x 2 control points (x, y), i_s = iy*nx + ix */
+  const double* ctrl;      /* n_s x ctrl_dim control points, i_s = iy*nx + ix */
   const double* weights;   /* n_s NURBS weights or NULL */
   ora_basis1d t;           /* thickness basis in physical z */
   int32_t n_plies;
@@ -52,6 +55,9 @@ typedef struct {
   int32_t n_materials;
   const double* C21;        /* n_materials x 21 */
   int32_t nq_u, nq_v, nq_t; /* Gauss points per element direction (<= 0: degree + 1) */
+  int32_t ctrl_dim;         /* 2: planar mid-surface, ctrl n_s x 2; 3: surface S in R^3, ctrl n_s x 3
+                               (Eq. extrusion); 0 reads as 2 */
+  const double* extrusion;  /* the constant extrusion direction a of Eq. extrusion (3 values), NULL = e_z */
 } ora_problem;
 
 /* Gauss-Legendre rule with n points on [-1, 1], ascending abscissae. */

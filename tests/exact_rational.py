@@ -211,6 +211,61 @@ def exact_box_blocks(lam, Lx, Ly, C21_exact_per_material, angles_deg, blocks):
     return out
 
 
+def exact_affine_blocks(lam, A, C21_exact_per_material, angles_deg, blocks):
+    """K^{ij} (3x3 float arrays) for the requested (i, j) basis pairs of a
+    laminate under the affine extrusion F(xi) = A (xi1, xi2, xi3) with a
+    constant rational 3x3 matrix A (columns dS/dxi1, dS/dxi2 and the
+    extrusion direction a). With the chain rule d/dx_a = sum_k (A^-1)[k][a]
+    d/dxi_k and the constant Jacobian |det A|,
+
+      K^{ij}_{cd} = |det A| sum_l sum_{a,b} C_l[V(c,a), V(d,b)]
+                    sum_{k,m} (A^-1)[k][a] (A^-1)[m][b] Ix Iy Iz_l,
+
+    Ix = int d^[k=0] N_ix d^[m=0] N_jx dxi1 and likewise in xi2 and (over
+    layer l) xi3: exact 1D integrals in Fractions, as in exact_box_blocks."""
+    import sympy as sp
+    M = sp.Matrix(3, 3, lambda r, c: sp.Rational(A[r][c]))
+    Mi = M.inv()
+    det = abs(M.det())
+    Ai = [[Fraction(int(sp.fraction(Mi[k, a])[0]), int(sp.fraction(Mi[k, a])[1])) for a in range(3)] for k in range(3)]
+    detF = Fraction(int(sp.fraction(det)[0]), int(sp.fraction(det)[1]))
+    Ix = gram_1d(lam.u)
+    Iy = gram_1d(lam.v)
+    z = [Fraction(float(lam.t.knots[0]))]
+    for h in lam.ply_thickness:
+        z.append(z[-1] + Fraction(float(h)))
+    Iz = [gram_1d(lam.t, z[l], z[l + 1]) for l in range(len(lam.ply_thickness))]
+    Ds = {}
+    nx = lam.u.n_functions
+    ns = lam.n_s
+    out = {}
+    for (i, j) in blocks:
+        it, is_ = divmod(i, ns)
+        iy, ix = divmod(is_, nx)
+        jt, js = divmod(j, ns)
+        jy, jx = divmod(js, nx)
+        # parametric products: F[k][m] = int d_k N_i d_m N_j per layer
+        K = np.zeros((3, 3))
+        for l in range(len(lam.ply_thickness)):
+            key = (int(lam.ply_material[l]), angles_deg[l])
+            if key not in Ds:
+                Ds[key] = exact_rotated_D(C21_exact_per_material[key[0]], key[1])
+            D = Ds[key]
+            Fp = [[Ix[(int(k == 0), int(m == 0))].get((ix, jx), 0) * Iy[(int(k == 1), int(m == 1))].get((iy, jy), 0)
+                   * Iz[l][(int(k == 2), int(m == 2))].get((it, jt), 0) for m in range(3)] for k in range(3)]
+            for a in range(3):
+                for b in range(3):
+                    f = sum(Ai[k][a] * Ai[m][b] * Fp[k][m] for k in range(3) for m in range(3)) * detF
+                    f = float(f)
+                    if f == 0.0:
+                        continue
+                    for c in range(3):
+                        for d in range(3):
+                            K[c, d] += D[voigt(c, a), voigt(d, b)] * f
+        out[(i, j)] = K
+    return out
+
+
 def _dense_1d(basis, lo=None, hi=None):
     """The four Gram matrices of gram_1d as dense float arrays."""
     I = gram_1d(basis, lo, hi)

@@ -100,7 +100,7 @@ MUTATIONS = {
     "P12_operands_swapped": ("add_btdb(w, Bi1, D, Bj2, out36 + 9);", "add_btdb(w, Bi2, D, Bj1, out36 + 9);"),
     "P_without_jacobian": ("double w = wu[a] * 0.5 * (ub - ua) * wv[b] * 0.5 * (vb - va) * ip.detJ;\n          double gi1",
                            "double w = wu[a] * 0.5 * (ub - ua) * wv[b] * 0.5 * (vb - va);\n          double gi1"),
-    "P_value_part_uses_derivative": ("gi2[3] = {0.0, 0.0, ip.R[li]}", "gi2[3] = {0.0, 0.0, ip.gx[li]}"),
+    "P_value_part_uses_derivative": ("grad3(&ip, li, 0.0, 1.0, gi2);", "grad3(&ip, li, 1.0, 0.0, gi2);"),
 }
 
 

@@ -25,8 +25,8 @@ MUTATIONS = {
     # the misprint of the third row of B^T (gamma_23 from the third gradient component twice)
     "gamma23_misprint": ("B[5][1] = g[2]; B[5][2] = g[1];", "B[5][1] = g[2]; B[5][2] = g[2];"),
     # pull-back with DF^{-1} instead of DF^{-T}
-    "jacobian_transposed": ("ip->gx[k] = Ji[0][0] * R1[k] + Ji[1][0] * R2[k];",
-                            "ip->gx[k] = Ji[0][0] * R1[k] + Ji[0][1] * R2[k];"),
+    "jacobian_transposed": ("ip->g1[k][0] = Ji[0][0] * R1[k] + Ji[1][0] * R2[k];",
+                            "ip->g1[k][0] = Ji[0][0] * R1[k] + Ji[0][1] * R2[k];"),
     # Cox-de Boor with its second term dropped
     "coxdeboor_dropped_term": ("  if (d2 > 0.0) v += (t[i + p + 1] - x) / d2 * bs_value(t, i + 1, p - 1, span, x);\n",
                                "\n"),
@@ -36,7 +36,22 @@ MUTATIONS = {
     # tensor (1/2) instead of engineering shear in gamma_12
     "half_shear": ("B[3][0] = g[1]; B[3][1] = g[0];", "B[3][0] = 0.5 * g[1]; B[3][1] = 0.5 * g[0];"),
     # Jacobian determinant dropped from the weight
-    "no_jacobian": ("ip->detJ = fabs(det);", "ip->detJ = 1.0;"),
+    "no_jacobian": ("    ip->detJ = fabs(det);\n    return 0;", "    ip->detJ = 1.0;\n    return 0;"),
+    # general extrusion: pull-back with DF^{-1} instead of DF^{-T} (columns of the inverse)
+    "shell_dual_transposed": ("ip->g1[k][c] = g[0][c] * R1[k] + g[1][c] * R2[k];",
+                              "ip->g1[k][c] = g[c][0] * R1[k] + g[c][1] * R2[k];"),
+    # general extrusion: the thickness gradient along a itself instead of its dual vector
+    "shell_r3_is_a": ("for (int c = 0; c < 3; ++c) ip->r3[c] = g[2][c];",
+                      "for (int c = 0; c < 3; ++c) ip->r3[c] = A[2][c];"),
+    # general extrusion: the cofactors not divided by det DF
+    "shell_no_det_division": ("for (int c = 0; c < 3; ++c) g[k][c] = t[c] / det;",
+                              "for (int c = 0; c < 3; ++c) g[k][c] = t[c];"),
+    # general extrusion: only the z component of a taken
+    "shell_extrusion_dropped": ("A[2][0] = pr->extrusion[0];\n    A[2][1] = pr->extrusion[1];",
+                                "A[2][0] = 0.0;\n    A[2][1] = 0.0;"),
+    # general extrusion: the third coordinate of the surface ignored
+    "shell_surface_flattened": ("      for (int c = 0; c < cd; ++c) {\n        A[0][c] += R1[k] * X[c];",
+                                "      for (int c = 0; c < 2; ++c) {\n        A[0][c] += R1[k] * X[c];"),
     # Gauss weights off by a factor
     "gauss_weight": ("w[n - 1 - k] = 2.0 / ((1.0 - z * z) * dpn * dpn);",
                      "w[n - 1 - k] = 1.0 / ((1.0 - z * z) * dpn * dpn);"),
@@ -141,6 +156,23 @@ def battery():
                      for ix in range(1, nx - 1)]
             if np.abs(res[inner]).max() > 1e-10 * np.abs(Kh).max() * np.abs(u).max():
                 failed.append("patch")
+    # general extrusion: exact rational rotated and sheared slab, rigid modes of a curved shell
+    from tests import test_oracle_shell as S
+    A = S.AFFINE_CASES["rotated_general"]
+    lam = S.affine_laminate(A, n_el=1)
+    rp, col, val = O.assemble(lam)
+    blocks = sorted({(r // 3, col[kk] // 3) for r in range(0, lam.n_dof, 7) for kk in range(rp[r], rp[r + 1], 5)})
+    ex = X.exact_affine_blocks(lam, A, [EXACT_C], [45, 0, 90], blocks)
+    err = 0.0
+    for r in range(0, lam.n_dof, 7):
+        for kk in range(rp[r], rp[r + 1], 5):
+            err = max(err, abs(val[kk] - ex[(r // 3, col[kk] // 3)][r % 3, col[kk] % 3]))
+    if not err <= 1e-12 * np.abs(val).max():
+        failed.append("exact_affine_extrusion")
+    lam = W.shell_plate(n_el=2, degree=2, repeats=1, extrusion=(0.3, 0.2, 0.9))
+    K = O.to_dense(*O.assemble(lam), lam.n_dof)
+    if S.rigid_mode_residual(K, S.shell_coords(lam)) > 1e-12:
+        failed.append("shell_rigid_modes")
     # split formula equals the standard one
     lam = W.curved_plate(n_el=2, degree=2, repeats=1)
     a = O.assemble(lam)[2]

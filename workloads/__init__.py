@@ -15,6 +15,9 @@ Workloads (all FP64, physical z through the thickness, ply 0 at z = 0):
   * ``adjoint_plate``    -- cubic, 32x32, 24 plies [0/90]_12 of 0.0025.
   * ``lagrange_plate``   -- Lagrange Q2 on 96x96 elements of the unit square,
     64 plies [0/90]_32 (129 thickness nodes).
+  * ``shell_plate``      -- the curved plate's map lifted onto the surface
+    z = 0.05 sin(pi xi) sin(pi eta) in R^3 and extruded along the tilted
+    direction a = (0.05, -0.03, 1) (Eq. extrusion), 48 plies as curved_plate.
   * ``batch``            -- a seeded list of uneven laminates.
 Every generator takes size parameters so that tests can run the same recipe at
 sizes a plain CPU code finishes in seconds.
@@ -55,7 +58,7 @@ class Laminate:
     name: str
     u: Basis1D
     v: Basis1D
-    ctrl: np.ndarray                 # (n_s, 2) control points, i_s = iy*nx + ix
+    ctrl: np.ndarray                 # (n_s, 2) planar or (n_s, 3) surface control points, i_s = iy*nx + ix
     weights: Optional[np.ndarray]    # (n_s,) NURBS weights or None
     t: Basis1D                       # thickness basis, physical z
     ply_thickness: np.ndarray        # (n_plies,)
@@ -63,6 +66,7 @@ class Laminate:
     ply_angle: np.ndarray            # (n_plies,) radians
     C21: np.ndarray                  # (n_materials, 21) upper-triangle Voigt constants
     nq: Sequence[int] = (0, 0, 0)    # Gauss points per element direction (0 = degree + 1)
+    extrusion: Optional[np.ndarray] = None  # direction a of F = S + xi^3 a (None = e_z)
 
     @property
     def n_s(self) -> int:
@@ -151,8 +155,11 @@ def anchors(b: Basis1D) -> np.ndarray:
 
 
 def control_points(u: Basis1D, v: Basis1D, mapping) -> np.ndarray:
+    """Control points X_i = F(anchor_i): (n_s, 2) for a planar map, (n_s, 3)
+    when `mapping` returns three coordinates (a surface in R^3)."""
     au, av = anchors(u), anchors(v)
-    X = np.zeros((len(av) * len(au), 2))
+    dim = len(mapping(au[0], av[0]))
+    X = np.zeros((len(av) * len(au), dim))
     for iy, eta in enumerate(av):
         for ix, xi in enumerate(au):
             X[iy * len(au) + ix] = mapping(xi, eta)
@@ -173,6 +180,24 @@ def curved_map(amp: float = 0.05):
         y = eta + amp * math.sin(2 * math.pi * eta) * math.cos(2 * math.pi * xi)
         return (x, y)
     return F
+
+
+def bump_map(amp: float = 0.05, inner=None):
+    """A surface in R^3: the planar map `inner` (the curved map by default)
+    lifted onto z = amp sin(pi xi) sin(pi eta)."""
+    inner = curved_map() if inner is None else inner
+
+    def F(xi, eta):
+        x, y = inner(xi, eta)
+        return (x, y, amp * math.sin(math.pi * xi) * math.sin(math.pi * eta))
+    return F
+
+
+def affine_surface_map(A):
+    """S(xi, eta) = A[:, 0] xi + A[:, 1] eta for a 3x3 matrix A (columns
+    dS/dxi1, dS/dxi2 and, used as the extrusion direction, a)."""
+    A = np.asarray(A, np.float64)
+    return lambda xi, eta: tuple(A[:, 0] * xi + A[:, 1] * eta)
 
 
 def thickness_basis(ply_thickness: Sequence[float], degree: int = 2, kind: int = BSPLINE,
@@ -210,7 +235,7 @@ def laminate(name: str, inplane_kind: int, degree: int, n_el: int, angles_deg: S
              ply_h, mapping=identity_map, thickness_degree: int = 2, thickness_kind: int = BSPLINE,
              materials: Optional[np.ndarray] = None, ply_material: Optional[Sequence[int]] = None,
              n_el_y: Optional[int] = None, degree_y: Optional[int] = None, weights=None,
-             thickness: Optional[Basis1D] = None, nq=(0, 0, 0)) -> Laminate:
+             thickness: Optional[Basis1D] = None, nq=(0, 0, 0), extrusion=None) -> Laminate:
     n_el_y = n_el if n_el_y is None else n_el_y
     degree_y = degree if degree_y is None else degree_y
     if inplane_kind == BSPLINE:
@@ -227,7 +252,8 @@ def laminate(name: str, inplane_kind: int, degree: int, n_el: int, angles_deg: S
     return Laminate(name=name, u=u, v=v, ctrl=control_points(u, v, mapping),
                     weights=None if weights is None else np.asarray(weights, np.float64),
                     t=t, ply_thickness=h, ply_material=pm,
-                    ply_angle=np.deg2rad(np.asarray(angles_deg, np.float64)), C21=mats, nq=tuple(nq))
+                    ply_angle=np.deg2rad(np.asarray(angles_deg, np.float64)), C21=mats, nq=tuple(nq),
+                    extrusion=None if extrusion is None else np.asarray(extrusion, np.float64))
 
 
 # --------------------------------------------------------------------------
@@ -244,6 +270,16 @@ def curved_plate(n_el: int = 64, degree: int = 3, repeats: int = 6) -> Laminate:
     angles = stack([0.0, 45.0, -45.0, 90.0], repeats, True)
     return laminate(f"curved_p{degree}_{n_el}x{n_el}_{len(angles)}plies", BSPLINE, degree, n_el, angles, 0.001,
                     mapping=curved_map())
+
+
+def shell_plate(n_el: int = 64, degree: int = 3, repeats: int = 6,
+                extrusion=(0.05, -0.03, 1.0)) -> Laminate:
+    """Curved shell: the curved plate's map lifted onto the bump
+    z = 0.05 sin(pi xi) sin(pi eta) and extruded along a tilted direction a
+    (Eq. extrusion), [0/45/-45/90]_{repeats}s, plies of 0.001 in xi^3."""
+    angles = stack([0.0, 45.0, -45.0, 90.0], repeats, True)
+    return laminate(f"shell_p{degree}_{n_el}x{n_el}_{len(angles)}plies", BSPLINE, degree, n_el, angles, 0.001,
+                    mapping=bump_map(), extrusion=extrusion)
 
 
 def adjoint_plate(n_el: int = 32, degree: int = 3, n_plies: int = 24) -> Laminate:

@@ -498,6 +498,60 @@ def run_large(args, L, dev, flush, peak, peak_kind, world):
     return out
 
 
+def run_shell(args, L, dev, flush, peak, peak_kind, world):
+    """A general extrusion (Eq. extrusion) of the benchmark's size: the curved
+    plate's map lifted onto z = 0.05 sin(pi xi) sin(pi eta), extruded along
+    a = (0.05, -0.03, 1), cubic 64 x 64, 48 plies. Split (6 x 6 Gram blocks, P
+    per configuration, the combine) and one standard assembly."""
+    import torch
+    import workloads as W
+    lam = W.shell_plate()
+    plan = L.Plan.from_laminate(lam)
+    nnz = plan.nnz
+    values = torch.empty(nnz, dtype=torch.float64, device=dev)
+    for _ in range(args.warmup):
+        plan.assemble_split(values)
+    torch.cuda.synchronize()
+    barrier()
+    steps = args.shell_steps
+    plan.profile_enable(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        evs[k][0].record()
+        plan.assemble_split(values)
+        evs[k][1].record()
+    torch.cuda.synchronize()
+    pr = plan.profile()
+    plan.profile_enable(False)
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs) / steps, dev)
+    std_ms = None
+    if args.standard_steps > 0:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        a.record()
+        plan.assemble_standard(values)
+        b.record()
+        torch.cuda.synchronize()
+        std_ms = a.elapsed_time(b)
+    kc_ms = pr["combine"]["ms"] / steps
+    # the combine writes K and reads P of every configuration (36 doubles per pair and configuration)
+    kc_bytes = 8 * nnz + 8 * 36 * plan.info["nnz_inplane"] * plan.info["n_configs"]
+    out = {"workload": "curved shell: the curved plate's map on the surface z = 0.05 sin(pi xi) sin(pi eta), "
+                       "extruded along a = (0.05, -0.03, 1), cubic B-spline 64x64, 48 plies [0/45/-45/90]_6s",
+           "value": aggregate_throughput(nnz, world, ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+           "nnz": nnz, "step_hbm_frac": 8 * nnz / (ms / 1e3) / 1e9 / peak,
+           "kernels_ms_per_step": {k: pr[k]["ms"] / steps for k in L.KERNEL_KINDS if pr[k]["launches"]},
+           "standard_ms": std_ms, "speedup_split_vs_standard": None if std_ms is None else std_ms / ms,
+           "roofline": {"bound": "hbm", "achieved": kc_bytes / (kc_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                        "frac": kc_bytes / (kc_ms / 1e3) / 1e9 / peak, "traffic": None, "kernel": "kc_stream",
+                        "peak_kind": f"{peak_kind} copy bandwidth"}}
+    plan.close()
+    del values
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_lam(args):
     import torch
     rank, local, world = dist_init("nccl")
@@ -575,6 +629,7 @@ def run_lam(args):
 
     # ---- the large Lagrange plate
     large = run_large(args, L, dev, flush, peak, peak_kind, world) if args.large_steps > 0 else None
+    shell = run_shell(args, L, dev, flush, peak, peak_kind, world) if args.shell_steps > 0 else None
 
     # ---- batch (lam_batch_*) of 256 seeded laminates
     batch = run_batch(args, L, dev, flush, peak, peak_kind, world) if args.batch_steps > 0 else None
@@ -644,6 +699,8 @@ def run_lam(args):
         line["batch"] = batch
     if large is not None:
         line["large"] = large
+    if shell is not None:
+        line["shell"] = shell
     if cpu is not None:
         line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
     print(json.dumps(line), flush=True)
@@ -663,6 +720,7 @@ def main(argv=None):
     ap.add_argument("--adjoint-steps", type=int, default=20, help="timed lam_adjoint calls (0 = skip)")
     ap.add_argument("--batch-steps", type=int, default=5, help="timed lam_batch_assemble calls (0 = skip)")
     ap.add_argument("--large-steps", type=int, default=5, help="timed split assemblies of the Lagrange plate (0 = skip)")
+    ap.add_argument("--shell-steps", type=int, default=5, help="timed split assemblies of the curved shell (0 = skip)")
     ap.add_argument("--sweep", action="store_true", help="the paper's layer sweep (one element through the thickness)")
     ap.add_argument("--sweep-n", type=int, default=16, help="in-plane elements per direction in the sweep")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")

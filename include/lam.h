@@ -85,12 +85,23 @@ typedef struct {
   const double* knots;   /* host */
 } lam_basis1d;
 
-/* In-plane discretisation and map (Section 2.2, Eq. gradient). */
+/* In-plane discretisation and map (Section 2.2, Eq. gradient, Eq. extrusion).
+ * The solid is the extrusion F(xi) = S(xi^1, xi^2) + xi^3 a of a surface S,
+ * given by its control points, along a constant direction a (Assumption 1:
+ * DF does not depend on xi^3); xi^3 runs over the thickness knots. A planar
+ * S = (x, y, 0) with a = e_z (ctrl_dim 2, extrusion zero) is the plate case
+ * of the split kernels; any other S or a (a "shell") is a general extrusion,
+ * assembled by the split and standard paths (lam_assemble_split,
+ * lam_assemble_split_host, lam_assemble_standard, lam_inplane_operators) and
+ * refused with LAM_ERR_UNSUPPORTED by lam_adjoint, lam_batch_create and
+ * lam_assemble_split_noalloc. DF = [dS/dxi1 | dS/dxi2 | a] must be regular. */
 typedef struct {
   lam_basis1d u;          /* xi^1 direction, index ix */
   lam_basis1d v;          /* xi^2 direction, index iy */
-  const double* ctrl;     /* host, n_s x 2 (x, y), row i_s = iy * n_x + ix */
+  const double* ctrl;     /* host, n_s x ctrl_dim ((x, y) or (x, y, z)), row i_s = iy * n_x + ix */
   const double* weights;  /* host, n_s NURBS weights (> 0), or NULL (polynomial) */
+  int32_t ctrl_dim;       /* 2 (0 reads as 2): planar S; 3: S is a surface in R^3 */
+  double extrusion[3];    /* the extrusion direction a; (0, 0, 0) reads as e_z */
 } lam_inplane;
 
 /* One ply (Eq. C_layers): thickness > 0, material index, angle in radians. */
@@ -128,6 +139,7 @@ typedef struct {
                                 shared memory, CSR written in address order), 0 class-major (rows of more
                                 than 56 in-plane neighbours) */
   int32_t combine_chunks;    /* streaming: chunks of thickness rows whose classes fit in shared memory */
+  int32_t shell;             /* 1: a general extrusion (surface in R^3 or a != e_z), see lam_inplane */
 } lam_plan_info;
 
 typedef struct lam_plan lam_plan;

@@ -65,7 +65,8 @@ class _Basis1d(ctypes.Structure):
 
 class _Inplane(ctypes.Structure):
     _fields_ = [("u", _Basis1d), ("v", _Basis1d), ("ctrl", ctypes.POINTER(ctypes.c_double)),
-                ("weights", ctypes.POINTER(ctypes.c_double))]
+                ("weights", ctypes.POINTER(ctypes.c_double)), ("ctrl_dim", ctypes.c_int32),
+                ("extrusion", ctypes.c_double * 3)]
 
 
 class _Ply(ctypes.Structure):
@@ -102,7 +103,7 @@ class _Info(ctypes.Structure):
     _fields_ = [("n_dof", ctypes.c_int64), ("nnz", ctypes.c_int64), ("n_s", ctypes.c_int64), ("n_t", ctypes.c_int64),
                 ("nnz_inplane", ctypes.c_int64), ("nnz_thickness", ctypes.c_int64), ("n_configs", ctypes.c_int32),
                 ("n_classes", ctypes.c_int32), ("monoclinic", ctypes.c_int32), ("n_pieces", ctypes.c_int32),
-                ("combine_streaming", ctypes.c_int32), ("combine_chunks", ctypes.c_int32)]
+                ("combine_streaming", ctypes.c_int32), ("combine_chunks", ctypes.c_int32), ("shell", ctypes.c_int32)]
 
 
 _lib = None
@@ -185,8 +186,10 @@ def _ptr(t) -> int:
 
 
 def plan_create(u, v, ctrl, t, ply_thickness, ply_material, ply_angle, C21, weights=None,
-                nq: Sequence[int] = (0, 0, 0), class_tol: float = -1.0) -> ctypes.c_void_p:
-    """lam_plan_create. u, v, t are (kind, degree, knots); C21 is (n_materials, 21)."""
+                nq: Sequence[int] = (0, 0, 0), class_tol: float = -1.0, extrusion=None) -> ctypes.c_void_p:
+    """lam_plan_create. u, v, t are (kind, degree, knots); C21 is (n_materials, 21);
+    ctrl is (n_s, 2) for a planar map or (n_s, 3) for a surface in R^3;
+    extrusion is the direction a of F = S + xi^3 a (None: e_z)."""
     L = load()
     keep = []
 
@@ -198,9 +201,16 @@ def plan_create(u, v, ctrl, t, ply_thickness, ply_material, ply_angle, C21, weig
 
     ctrl = _as_f64(ctrl)
     keep.append(ctrl)
+    cdim = ctrl.shape[1] if ctrl.ndim == 2 else 2
+    if cdim not in (2, 3):
+        raise ValueError("ctrl must have 2 or 3 columns")
     w = None if weights is None else _as_f64(weights)
     keep.append(w)
-    ip = _Inplane(basis(u), basis(v), ctrl.ctypes.data_as(_D), w.ctypes.data_as(_D) if w is not None else _D())
+    a = (0.0, 0.0, 0.0) if extrusion is None else tuple(float(x) for x in extrusion)
+    if len(a) != 3:
+        raise ValueError("extrusion must have 3 components")
+    ip = _Inplane(basis(u), basis(v), ctrl.ctypes.data_as(_D), w.ctypes.data_as(_D) if w is not None else _D(),
+                  cdim, (ctypes.c_double * 3)(*a))
     tb = basis(t)
     h = _as_f64(ply_thickness)
     pm = np.ascontiguousarray(ply_material, dtype=np.int32)
@@ -348,9 +358,9 @@ class Plan:
     """Convenience owner of a lam_plan handle; outputs are torch tensors."""
 
     def __init__(self, u, v, ctrl, t, ply_thickness, ply_material, ply_angle, C21, weights=None,
-                 nq=(0, 0, 0), class_tol=-1.0):
+                 nq=(0, 0, 0), class_tol=-1.0, extrusion=None):
         self.handle = plan_create(u, v, ctrl, t, ply_thickness, ply_material, ply_angle, C21, weights=weights,
-                                  nq=nq, class_tol=class_tol)
+                                  nq=nq, class_tol=class_tol, extrusion=extrusion)
         self.info = plan_get_info(self.handle)
         self.n_plies = len(ply_thickness)
         self.n_materials = int(np.atleast_2d(np.asarray(C21)).shape[0])
@@ -361,7 +371,8 @@ class Plan:
         ctrl, weights, ply_thickness, ply_material, ply_angle, C21, nq."""
         b = lambda x: (x.kind, x.degree, x.knots)
         return cls(b(lam.u), b(lam.v), lam.ctrl, b(lam.t), lam.ply_thickness, lam.ply_material, lam.ply_angle,
-                   lam.C21, weights=lam.weights, nq=tuple(lam.nq), class_tol=class_tol)
+                   lam.C21, weights=lam.weights, nq=tuple(lam.nq), class_tol=class_tol,
+                   extrusion=getattr(lam, "extrusion", None))
 
     @property
     def nnz(self) -> int:

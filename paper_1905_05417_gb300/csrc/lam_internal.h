@@ -39,8 +39,12 @@ struct Device;  // device mirror, defined in lam_kernels.cu
 
 struct Plan {
   Basis u, v, t;
-  std::vector<double> ctrl;      // n_s x 2
+  std::vector<double> ctrl;      // n_s x 2 (x, y)
   std::vector<double> weights;   // n_s, empty when polynomial
+  // general extrusion F = S + xi^3 a (Eq. extrusion): S in R^3 and/or a != e_z
+  bool shell = false;
+  std::vector<double> ctrl3;     // n_s x 3 (x, y, z), shells only
+  double extrusion[3] = {0.0, 0.0, 1.0};
   std::vector<lam_ply> plies;
   std::vector<lam_material> mats;
   int nqu = 0, nqv = 0, nqt = 0;

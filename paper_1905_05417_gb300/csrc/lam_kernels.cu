@@ -67,6 +67,13 @@ struct Device {
   float2* cfgEdf = nullptr;    // float pairs of cfgE
   double* cfgCb = nullptr;     // Appendix A bracket tensors per configuration
   double* bfree_EP = nullptr;  // element operators of the Voigt-free construction (lazily allocated)
+  // general extrusion (Eq. extrusion): surface control points, element Gram
+  // blocks of the six gradient parts, P of every configuration (lazily allocated)
+  double* ctrl3 = nullptr;
+  double* shellEG = nullptr;   // n_el x 36 x pairs
+  double* shellP = nullptr;    // n_cfg x nnz_s x 36
+  size_t shellP_elems = 0;
+  unsigned long long* shell_pmax = nullptr;  // 4 block maxima of |P|
   int n_sm = 0;
   double* q = nullptr;   // nnz_t x n_cfg x 4
   // adjoint: geometry tables and workspace (allocated by the first lam_adjoint)
@@ -190,6 +197,7 @@ void free_device(Plan& P) {
     if (P.dev->ev_copied[k]) cudaEventDestroy(P.dev->ev_copied[k]);
   }
   if (P.dev->copy_stream) cudaStreamDestroy(P.dev->copy_stream);
+  if (P.dev->shellP) cudaFree(P.dev->shellP);
   delete P.dev;
   P.dev = nullptr;
   if (cur >= 0) cudaSetDevice(cur);
@@ -201,7 +209,7 @@ void free_device(Plan& P) {
 
 static int kc_block(const Plan& P) { return ((9 * max_len_s(P) + 31) / 32) * 32; }
 
-static int kc_np(const Plan& P) { return P.monoclinic ? 2 : 4; }
+static int kc_np(const Plan& P) { return (P.monoclinic && !P.shell) ? 2 : 4; }
 
 static int kc_gs_cap(const Plan& P) { return (9 * max_len_s(P) + 1) & ~1; }
 
@@ -230,7 +238,13 @@ static size_t ka_smem(const Plan& P) {
 }
 static size_t kd_smem(const Plan& P) {
   const int nqs = P.nqu * P.nqv, nls = ka_nls(P);
+  if (P.shell) return (size_t)nqs * nls * 4 * sizeof(double) + (size_t)nqs * 16 * sizeof(double);
   return (size_t)nqs * nls * 3 * sizeof(double) + (size_t)nqs * 8 * sizeof(double);
+}
+// K-a of a general extrusion: FP64 point values, float pairs of u and w u, per point 16 doubles
+static size_t ka_shell_smem(const Plan& P) {
+  const int nqs = P.nqu * P.nqv, nls = ka_nls(P);
+  return (size_t)nqs * nls * (4 * sizeof(double) + 24 * sizeof(float)) + (size_t)nqs * 16 * sizeof(double);
 }
 
 // ---------------------------------------------------------------------------
@@ -443,7 +457,103 @@ struct InplaneArgs {
   int nx, nel_u, pu, pv, nqu, nqv;
   const double *tabU, *tabV, *wU, *wV, *ctrl, *weights;
   const int *firstU, *firstV;
+  const double* ctrl3;  // general extrusion: n_s x 3 surface control points (else NULL)
+  double ax, ay, az;    // the extrusion direction a
 };
+
+// pair number of li <= lj, row-major over the upper triangle of n local functions
+__device__ __forceinline__ int upper_pair(int a, int b, int n) { return a * n - a * (a - 1) / 2 + (b - a); }
+
+__device__ __forceinline__ void cross3(const double* u, const double* v, double* w) {
+  w[0] = u[1] * v[2] - u[2] * v[1];
+  w[1] = u[2] * v[0] - u[0] * v[2];
+  w[2] = u[0] * v[1] - u[1] * v[0];
+}
+
+// General extrusion F = S(xi1, xi2) + xi3 a (Eq. extrusion; DF independent of
+// xi3, Assumption 1): DF = [dS/dxi1 | dS/dxi2 | a]. The rows of DF^-1 are the
+// dual vectors g^0 = (A1 x a) / det, g^1 = (a x A0) / det, g^2 = (A0 x A1) / det
+// of the columns A0, A1, a, and the gradient of S^k T is T (R_,1 g^0 + R_,2 g^1)
+// + T' R g^2 (Eq. gradient pulled back through DF^-T).
+//   qs[q * 16 + 0..8]  = g^0, g^1, g^2; [9] = w |DF|; [10..12] = W, W_,1, W_,2
+//   ph[(q * nls + k) * 4 + 0..2] = g1 = R_,1 g^0 + R_,2 g^1; [3] = R
+constexpr int kShellQ = 16;
+__device__ void shell_points(const InplaneArgs& a, int ex, int ey, double* ph, double* qs) {
+  const int nlx = a.pu + 1, nly = a.pv + 1, nls = nlx * nly, nqs = a.nqu * a.nqv;
+  const int fx = a.firstU[ex], fy = a.firstV[ey];
+  for (int t = threadIdx.x; t < nqs; t += blockDim.x) {
+    const int qu = t % a.nqu, qv = t / a.nqu;
+    const double* tu = a.tabU + ((size_t)ex * a.nqu + qu) * nlx * 2;
+    const double* tv = a.tabV + ((size_t)ey * a.nqv + qv) * nly * 2;
+    double W = 1.0, W1 = 0.0, W2 = 0.0;
+    if (a.weights) {
+      W = 0.0;
+      for (int ly = 0; ly < nly; ++ly)
+        for (int lx = 0; lx < nlx; ++lx) {
+          const double w = a.weights[(size_t)(fy + ly) * a.nx + fx + lx];
+          W += w * tu[2 * lx] * tv[2 * ly];
+          W1 += w * tu[2 * lx + 1] * tv[2 * ly];
+          W2 += w * tu[2 * lx] * tv[2 * ly + 1];
+        }
+    }
+    double A0[3] = {0.0, 0.0, 0.0}, A1[3] = {0.0, 0.0, 0.0};
+    for (int ly = 0; ly < nly; ++ly)
+      for (int lx = 0; lx < nlx; ++lx) {
+        const size_t gi = (size_t)(fy + ly) * a.nx + fx + lx;
+        const double N = tu[2 * lx] * tv[2 * ly], N1 = tu[2 * lx + 1] * tv[2 * ly], N2 = tu[2 * lx] * tv[2 * ly + 1];
+        double R1 = N1, R2 = N2;
+        if (a.weights) {
+          const double w = a.weights[gi];
+          R1 = w * (N1 * W - N * W1) / (W * W);
+          R2 = w * (N2 * W - N * W2) / (W * W);
+        }
+        const double* X = a.ctrl3 + 3 * gi;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          A0[c] += R1 * X[c];
+          A1[c] += R2 * X[c];
+        }
+      }
+    const double A2[3] = {a.ax, a.ay, a.az};
+    double g0[3], g1[3], g2[3];
+    cross3(A1, A2, g0);
+    cross3(A2, A0, g1);
+    cross3(A0, A1, g2);
+    const double det = A0[0] * g0[0] + A0[1] * g0[1] + A0[2] * g0[2], inv = 1.0 / det;
+    double* d = qs + (size_t)t * kShellQ;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      d[c] = g0[c] * inv;
+      d[3 + c] = g1[c] * inv;
+      d[6 + c] = g2[c] * inv;
+    }
+    d[9] = a.wU[(size_t)ex * a.nqu + qu] * a.wV[(size_t)ey * a.nqv + qv] * fabs(det);
+    d[10] = W;
+    d[11] = W1;
+    d[12] = W2;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nqs * nls; t += blockDim.x) {
+    const int q = t / nls, k = t % nls;
+    const int qu = q % a.nqu, qv = q / a.nqu, lx = k % nlx, ly = k / nlx;
+    const double* tu = a.tabU + ((size_t)ex * a.nqu + qu) * nlx * 2;
+    const double* tv = a.tabV + ((size_t)ey * a.nqv + qv) * nly * 2;
+    const double* d = qs + (size_t)q * kShellQ;
+    double R = tu[2 * lx] * tv[2 * ly], R1 = tu[2 * lx + 1] * tv[2 * ly], R2 = tu[2 * lx] * tv[2 * ly + 1];
+    if (a.weights) {
+      const double w = a.weights[(size_t)(fy + ly) * a.nx + fx + lx], W = d[10];
+      const double N = R, N1 = R1, N2 = R2;
+      R = w * N / W;
+      R1 = w * (N1 * W - N * d[11]) / (W * W);
+      R2 = w * (N2 * W - N * d[12]) / (W * W);
+    }
+    double* f = ph + (size_t)t * 4;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) f[c] = d[c] * R1 + d[3 + c] * R2;
+    f[3] = R;
+  }
+  __syncthreads();
+}
 
 // qd[q*8 + 0..3] = DF^{-1} (row-major, [k][a]), [4] = w|DF|, [5..7] = W, dW/dxi1, dW/dxi2
 __device__ void inplane_points(const InplaneArgs& a, int ex, int ey, double* phi, double* phiw, double* qd) {
@@ -825,6 +935,180 @@ __global__ void __launch_bounds__(256) ka_local(KaLocalArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// K-a for a general extrusion (Eq. extrusion). B_1 = B(g1) and B_2 = B(R g^2)
+// now have three gradient components each (the planar map has (g_x, g_y, 0)
+// and (0, 0, R)), so the configuration-free Gram of a local pair has 6 x 6
+// entries: G_(alpha a)(beta b) = sum_q w|DF| u^li_(alpha a) u^lj_(beta b),
+// u_1 = g1, u_2 = R g^2. EG[(e * 36 + blk * 9 + a * 3 + b) * npl + pair],
+// blk = 2 alpha + beta, pair li <= lj (the other order is the transposed
+// block: G^ji_(alpha a)(beta b) = G^ij_(beta b)(alpha a)). Point values in
+// FP64 (shell_points); the products in double-float, with u_1, u_2 and w|DF|
+// divided by per-element powers of two (k1, k2, kq) so that the float pairs
+// keep any geometry scale; block (alpha, beta) is scaled back by
+// 2^(kq + k_alpha + k_beta).
+// ---------------------------------------------------------------------------
+struct KaShellArgs {
+  InplaneArgs ip;
+  double* EG;
+};
+
+__device__ __forceinline__ int exp_field(double v) { return (__double2hiint(v) >> 20) & 0x7FF; }
+
+__global__ void __launch_bounds__(256) ka_shell(KaShellArgs a) {
+  extern __shared__ double sm[];
+  const InplaneArgs& ip = a.ip;
+  const int nlx = ip.pu + 1, nly = ip.pv + 1, nls = nlx * nly, nqs = ip.nqu * ip.nqv;
+  const int e = blockIdx.x, ex = e % ip.nel_u, ey = e / ip.nel_u;
+  const int nit = nqs * nls;
+  double* ph = sm;
+  double* qs = ph + (size_t)nit * 4;
+  float* phf = reinterpret_cast<float*>(qs + (size_t)nqs * kShellQ);  // [item][12]: hi 6, lo 6
+  float* pwf = phf + (size_t)nit * 12;
+  __shared__ int s_k[3];
+  if (threadIdx.x < 3) s_k[threadIdx.x] = 0;
+  shell_points(ip, ex, ey, ph, qs);  // begins and ends with a barrier-separated phase
+  {
+    int e1 = 0, e2 = 0, eq = 0;
+    for (int t = threadIdx.x; t < nit; t += blockDim.x) {
+      const double* f = ph + (size_t)t * 4;
+      const double* d = qs + (size_t)(t / nls) * kShellQ;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        e1 = max(e1, exp_field(f[c]));
+        e2 = max(e2, exp_field(f[3] * d[6 + c]));
+      }
+    }
+    for (int q = threadIdx.x; q < nqs; q += blockDim.x) eq = max(eq, exp_field(qs[(size_t)q * kShellQ + 9]));
+    atomicMax(&s_k[0], e1);
+    atomicMax(&s_k[1], e2);
+    atomicMax(&s_k[2], eq);
+  }
+  __syncthreads();
+  const int k1 = s_k[0] > 0 ? s_k[0] - 1023 : 0, k2 = s_k[1] > 0 ? s_k[1] - 1023 : 0;
+  const int kq = s_k[2] > 0 ? s_k[2] - 1023 : 0;
+  for (int t = threadIdx.x; t < nit; t += blockDim.x) {
+    const double* f = ph + (size_t)t * 4;
+    const double* d = qs + (size_t)(t / nls) * kShellQ;
+    const double w = d[9];
+    float* o = phf + (size_t)t * 12;
+    float* ow = pwf + (size_t)t * 12;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const double v = j < 3 ? f[j] : f[3] * d[3 + j];
+      const int kj = j < 3 ? k1 : k2;
+      float h, l;
+      split_df_off(v, kj, h, l);
+      o[j] = h;
+      o[6 + j] = l;
+      split_df_off(w * v, kj + kq, h, l);
+      ow[j] = h;
+      ow[6 + j] = l;
+    }
+  }
+  __syncthreads();
+  const int npl = nls * (nls + 1) / 2;
+  double* out = a.EG + (size_t)e * 36 * npl;
+  for (int t = threadIdx.x; t < 4 * npl; t += blockDim.x) {
+    const int blk = t / npl, pr = t % npl, al = blk >> 1, be = blk & 1;
+    int li = 0, rem = pr;
+    while (rem >= nls - li) {
+      rem -= nls - li;
+      ++li;
+    }
+    const int lj = li + rem;
+    float sh[9], sl[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) sh[k] = sl[k] = 0.0f;
+    for (int q = 0; q < nqs; ++q) {
+      const float* A = pwf + ((size_t)q * nls + li) * 12;
+      const float* B = phf + ((size_t)q * nls + lj) * 12;
+      float ah[3], alo[3], bh[3], blo[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        ah[k] = A[3 * al + k];
+        alo[k] = A[6 + 3 * al + k];
+        bh[k] = B[3 * be + k];
+        blo[k] = B[6 + 3 * be + k];
+      }
+#pragma unroll
+      for (int x = 0; x < 3; ++x)
+#pragma unroll
+        for (int y = 0; y < 3; ++y) df_mac(ah[x], alo[x], bh[y], blo[y], sh[x * 3 + y], sl[x * 3 + y]);
+    }
+    const int sc = kq + (al ? k2 : k1) + (be ? k2 : k1);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float hs = __fadd_rn(sh[k], sl[k]);
+      const float ls = __fsub_rn(sl[k], __fsub_rn(hs, sh[k]));
+      long long b = __double_as_longlong(df_to_double(hs, ls));
+      if (b & 0x7FFFFFFFFFFFFFFFll) b += (long long)sc * (1ll << 52);  // times 2^sc, exact
+      out[(size_t)(blk * 9 + k) * npl + pr] = __longlong_as_double(b);
+    }
+  }
+}
+
+// P of every configuration for a general extrusion: CTA per in-plane row i_s.
+// The row's 6 x 6 Gram blocks are summed over the shared elements (fixed
+// order) into shared memory, then P_(alpha beta)[c][d] = sum_(a,b)
+// D_m[V(c,a)][V(d,b)] G_(alpha a)(beta b) (Eq. P) for every configuration m,
+// into P[(m * nnz_s + pair) * 36 + blk * 9 + c * 3 + d].
+struct KpShellArgs {
+  int nx, nel_u, nlx, nls, npl, ncfg;
+  int64_t nnz_s;
+  const int64_t* LSb;
+  const int *lenX, *lenY, *loX, *loY, *eloX, *ehiX, *eloY, *ehiY, *firstU, *firstV;
+  const double* EG;
+  const double* cfgE;
+  double* P;
+  unsigned long long* pmax;  // largest |P| per block (bit patterns; positive doubles order as integers)
+};
+
+__global__ void __launch_bounds__(256) kp_shell(KpShellArgs a) {
+  extern __shared__ double sG[];
+  __shared__ unsigned long long smax[4];
+  if (threadIdx.x < 4) smax[threadIdx.x] = 0ull;
+  const int64_t is = blockIdx.x;
+  const int ix = (int)(is % a.nx), iy = (int)(is / a.nx);
+  const int lx = a.lenX[ix], ls = lx * a.lenY[iy];
+  const int64_t ls0 = a.LSb[is];
+  for (int item = threadIdx.x; item < 36 * ls; item += blockDim.x) {
+    const int ks = item / 36, k = item % 36, blk = k / 9, ab = k % 9;
+    const int jx = a.loX[ix] + ks % lx, jy = a.loY[iy] + ks / lx;
+    const int ex0 = max(a.eloX[ix], a.eloX[jx]), ex1 = min(a.ehiX[ix], a.ehiX[jx]);
+    const int ey0 = max(a.eloY[iy], a.eloY[jy]), ey1 = min(a.ehiY[iy], a.ehiY[jy]);
+    const int kt = ((blk & 1) * 2 + (blk >> 1)) * 9 + (ab % 3) * 3 + ab / 3;  // the transposed entry
+    double acc = 0.0;
+    for (int ey = ey0; ey <= ey1; ++ey) {
+      const int fy = a.firstV[ey];
+      for (int ex = ex0; ex <= ex1; ++ex) {
+        const int fx = a.firstU[ex];
+        const int li = (iy - fy) * a.nlx + (ix - fx), lj = (jy - fy) * a.nlx + (jx - fx);
+        const size_t e36 = ((size_t)ey * a.nel_u + ex) * 36;
+        if (li <= lj)
+          acc += a.EG[(e36 + k) * a.npl + upper_pair(li, lj, a.nls)];
+        else
+          acc += a.EG[(e36 + kt) * a.npl + upper_pair(lj, li, a.nls)];
+      }
+    }
+    sG[item] = acc;
+  }
+  __syncthreads();
+  const int per_cfg = 36 * ls;
+  for (int item = threadIdx.x; item < a.ncfg * per_cfg; item += blockDim.x) {
+    const int m = item / per_cfg, r = item % per_cfg, ks = r / 36, k = r % 36, blk = k / 9, cd = k % 9;
+    const double* E = a.cfgE + (size_t)m * 81 + cd * 9;
+    const double* g = sG + (size_t)ks * 36 + blk * 9;
+    double p = 0.0;
+#pragma unroll
+    for (int ab = 0; ab < 9; ++ab) p = fma(E[ab], g[ab], p);
+    a.P[((size_t)m * a.nnz_s + ls0 + ks) * 36 + k] = p;
+    atomicMax(&smax[blk], (unsigned long long)__double_as_longlong(fabs(p)));
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) atomicMax(&a.pmax[threadIdx.x], smax[threadIdx.x]);
+}
+
+// ---------------------------------------------------------------------------
 // K-c: fused combine. One CTA per in-plane row i_s; thread <-> (c, k_s, d) of
 // that row. The CTA first forms the row's G blocks (gathered from the element
 // blocks, or loaded from an assembled G), the class Q vectors, and the CSR base
@@ -865,12 +1149,16 @@ struct KcArgs {
   int* flag;             // set when the FP64 pass must recompute
   int* emax;             // largest float exponent field of an entry
   int conditional;       // FP64 pass: run only if *flag != 0
+  // general extrusion: P of every configuration, n_cfg x nnz_s x 36, and the
+  // largest |P| of each block (11, 12, 21, 22) as bit patterns
+  const double* shellP;
+  const unsigned long long* shell_pmax;
 };
 
-__device__ __forceinline__ int upper_pair(int a, int b, int n) { return a * n - a * (a - 1) / 2 + (b - a); }
 
-template <bool MONO, bool CHUNKED, bool GATHER>
+template <bool MONO, bool CHUNKED, bool GATHER, bool SHELL = false>
 __global__ void __launch_bounds__(1024, 2) kc_combine(KcArgs a) {
+  static_assert(!(SHELL && MONO), "a general extrusion couples every block");
   extern __shared__ double sm[];
   constexpr int NP = MONO ? 2 : 4;
   const int64_t is = blockIdx.x;
@@ -887,7 +1175,8 @@ __global__ void __launch_bounds__(1024, 2) kc_combine(KcArgs a) {
   int* tb = reinterpret_cast<int*>(base3 + 3 * (size_t)a.nocc);            // ncls + 1
   int* ob = tb + (a.ncls + 1);                             // ncls + 1
   int* tm = ob + (a.ncls + 1);                             // nterms
-  if (GATHER) {
+  if (SHELL) {
+  } else if (GATHER) {
     for (int item = tid; item < 9 * ls; item += nthr) {
       const int ks = item / 9, ab = item % 9;
       const int jx = a.loX[ix] + ks % lx, jy = a.loY[iy] + ks / lx;
@@ -945,10 +1234,11 @@ __global__ void __launch_bounds__(1024, 2) kc_combine(KcArgs a) {
   const bool block_type = ((c == 2) == (d == 2));
   for (int m = 0; m < a.ncfg; ++m) {
     const double* E = a.cfgE + (size_t)m * 81 + cd * 9;
-    const double p11 = E[0] * g[0] + E[1] * g[1] + E[3] * g[3] + E[4] * g[4];
-    const double p12 = E[2] * g[2] + E[5] * g[5];
-    const double p21 = E[6] * g[6] + E[7] * g[7];
-    const double p22 = E[8] * g[8];
+    const double* Pp = SHELL ? a.shellP + ((size_t)m * a.nnz_s + ls0 + ks) * 36 + cd : nullptr;
+    const double p11 = SHELL ? Pp[0] : E[0] * g[0] + E[1] * g[1] + E[3] * g[3] + E[4] * g[4];
+    const double p12 = SHELL ? Pp[9] : E[2] * g[2] + E[5] * g[5];
+    const double p21 = SHELL ? Pp[18] : E[6] * g[6] + E[7] * g[7];
+    const double p22 = SHELL ? Pp[27] : E[8] * g[8];
     if (MONO) {
       Ps[(m * 2 + 0) * nthr + tid] = block_type ? p11 : p12;
       Ps[(m * 2 + 1) * nthr + tid] = block_type ? p22 : p21;
@@ -1028,8 +1318,9 @@ __device__ __forceinline__ void df_dot(const float2* __restrict__ E, const float
 // One in-plane row i_s of the streaming combine (phases 0 to 2 for every
 // chunk of thickness rows). `sm` is the CTA's dynamic shared memory; emax and
 // bad accumulate the double-float pass's range checks.
-template <bool MONO, bool CHUNKED, bool DF>
+template <bool MONO, bool CHUNKED, bool DF, bool SHELL = false>
 __device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm, int& emax, bool& bad) {
+  static_assert(!(SHELL && MONO), "a general extrusion couples every block");
   const int nthr = blockDim.x, tid = threadIdx.x;
   double* slices = sm;  // slots x stride (the G row first)
   double* sQ = sm + (size_t)a.nslot_max * a.slice_stride;                  // chunk terms: Q
@@ -1041,8 +1332,8 @@ __device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm,
   const int ls = lx * a.lenY[iy];
   const int n9 = 9 * ls;
   const int64_t ls0 = a.LSb[is];
-  // phase 0: the row's G blocks into slices[0 .. 9 ls)
-  for (int item = tid; item < n9; item += nthr) {
+  // phase 0: the row's G blocks into slices[0 .. 9 ls) (a general extrusion reads P instead)
+  for (int item = tid; item < (SHELL ? 0 : n9); item += nthr) {
     const int ks = item / 9, ab = item % 9;
     const int jx = a.loX[ix] + ks % lx, jy = a.loY[iy] + ks / lx;
     const int ex0 = max(a.eloX[ix], a.eloX[jx]), ex1 = min(a.ehiX[ix], a.ehiX[jx]);
@@ -1076,8 +1367,8 @@ __device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm,
     d = rem % 3;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-      g[k] = slices[ks * 9 + k];
-      if (DF) split_df(g[k], gh[k], gl[k]);
+      g[k] = SHELL ? 0.0 : slices[ks * 9 + k];
+      if (DF && !SHELL) split_df(g[k], gh[k], gl[k]);
     }
   }
   __syncthreads();  // the G row is in registers; its space is reused by the slices
@@ -1085,6 +1376,17 @@ __device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm,
   const bool block_type = ((c == 2) == (d == 2));
   const int offa = block_type ? 0 : 1, offb = block_type ? 3 : 2;
   const int seg_len = 3 * ls;
+  // general extrusion, double-float pass: block j of P enters divided by 2^ps[j]
+  // (its largest entry in [1, 2)) and Q_j multiplied by it (exact), so that the
+  // float pairs hold blocks of very different magnitude (P_22 / P_11 ~ L^2).
+  int ps[4] = {0, 0, 0, 0};
+  if (SHELL && DF) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const double mx = __longlong_as_double((long long)a.shell_pmax[j]);
+      ps[j] = mx > 0.0 ? exp_field(mx) - 1023 : 0;
+    }
+  }
   const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
   for (int ch = 0; ch < a.nchunk; ++ch) {
     int it0 = a.ck_it[ch], it1 = a.ck_it[ch + 1];
@@ -1101,7 +1403,10 @@ __device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm,
       if (DF) {
         float2* q2 = reinterpret_cast<float2*>(sQ + 4 * (size_t)k);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) q2[j] = a.qdf[qi + j];
+        for (int j = 0; j < 4; ++j) {
+          const float2 v = a.qdf[qi + j];
+          q2[j] = SHELL ? make_float2(ldexpf(v.x, ps[j]), ldexpf(v.y, ps[j])) : v;
+        }
       } else {
 #pragma unroll
         for (int j = 0; j < 4; ++j) sQ[4 * (size_t)k + j] = a.q[qi + j];
@@ -1122,7 +1427,13 @@ __device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm,
           if (m != cur) {
             cur = m;
             const float2* E = a.cfgEdf + (size_t)m * 81 + cd * 9;
-            if (MONO) {
+            if (SHELL) {
+              const double* Pp = a.shellP + ((size_t)m * a.nnz_s + ls0 + ks) * 36 + cd;
+              split_df_off(Pp[0], ps[0], ah, al);
+              split_df_off(Pp[9], ps[1], bh, bl);
+              split_df_off(Pp[18], ps[2], ch_, cl);
+              split_df_off(Pp[27], ps[3], dh, dl);
+            } else if (MONO) {
               if (block_type) {
                 df_dot(E, gh, gl, 0, 1, 3, 4, 4, ah, al);
                 df_dot(E, gh, gl, 8, 8, 8, 8, 1, bh, bl);
@@ -1179,7 +1490,13 @@ __device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm,
           if (m != cur) {
             cur = m;
             const double* E = a.cfgE + (size_t)m * 81 + cd * 9;
-            if (MONO) {
+            if (SHELL) {
+              const double* Pp = a.shellP + ((size_t)m * a.nnz_s + ls0 + ks) * 36 + cd;
+              p11 = Pp[0];
+              p12 = Pp[9];
+              p21 = Pp[18];
+              p22 = Pp[27];
+            } else if (MONO) {
               if (block_type) {
                 pa = E[0] * g[0] + E[1] * g[1] + E[3] * g[3] + E[4] * g[4];
                 pb = E[8] * g[8];
@@ -1227,13 +1544,13 @@ __device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm,
   }
 }
 
-template <bool MONO, bool CHUNKED, bool DF>
+template <bool MONO, bool CHUNKED, bool DF, bool SHELL = false>
 __global__ void __maxnreg__(64) kc_stream(KcArgs a) {
   if (!DF && a.conditional && *a.flag == 0) return;
   extern __shared__ double sm[];
   int emax = 0;
   bool bad = false;
-  for (int64_t is = blockIdx.x; is < a.ns; is += gridDim.x) kcs_row<MONO, CHUNKED, DF>(a, is, sm, emax, bad);
+  for (int64_t is = blockIdx.x; is < a.ns; is += gridDim.x) kcs_row<MONO, CHUNKED, DF, SHELL>(a, is, sm, emax, bad);
   if (DF) {
     emax = __reduce_max_sync(0xffffffffu, emax);
     const bool any_bad = __any_sync(0xffffffffu, bad);
@@ -1278,15 +1595,22 @@ __device__ __forceinline__ int64_t csr_pos(const KdArgs& a, int it, int64_t is, 
   return 9 * a.LTb[it] * a.nnz_s + 9 * lt * a.LSb[is] + 3 * c * lt * ls + (kt * ls + ks) * 3;
 }
 
+// SHELL: a general extrusion, whose 3D gradients T g1 + T' R g^2 come from
+// shell_points (planar: (g_x T, g_y T, R T')).
+template <bool SHELL>
 __global__ void __launch_bounds__(256) kd_standard(KdArgs a) {
   extern __shared__ double sm[];
   const InplaneArgs& ip = a.ip;
   const int nlx = ip.pu + 1, nly = ip.pv + 1, nls = nlx * nly, nqs = ip.nqu * ip.nqv;
+  constexpr int NV = SHELL ? 4 : 3, NQ = SHELL ? kShellQ : 8, WQ = SHELL ? 9 : 4;
   double* phi = sm;
-  double* qd = phi + (size_t)nqs * nls * 3;
+  double* qd = phi + (size_t)nqs * nls * NV;
   const int e3 = a.elems[blockIdx.x];
   const int ex = e3 % ip.nel_u, ey = (e3 / ip.nel_u) % a.nel_v, et = e3 / (ip.nel_u * a.nel_v);
-  inplane_points(ip, ex, ey, phi, nullptr, qd);
+  if (SHELL)
+    shell_points(ip, ex, ey, phi, qd);
+  else
+    inplane_points(ip, ex, ey, phi, nullptr, qd);
   const int nl = nls * a.q1;
   const int npairs = nl * (nl + 1) / 2;
   const int fx = ip.firstU[ex], fy = ip.firstV[ey], ft = a.firstT[et];
@@ -1307,15 +1631,31 @@ __global__ void __launch_bounds__(256) kd_standard(KdArgs a) {
 #pragma unroll
       for (int k = 0; k < 9; ++k) acc[k] = 0.0;
       for (int qs = 0; qs < nqs; ++qs) {
-        const double* A = phi + ((size_t)qs * nls + lsi) * 3;
-        const double* B = phi + ((size_t)qs * nls + lsj) * 3;
-        const double ws = qd[qs * 8 + 4];
+        const double* A = phi + ((size_t)qs * nls + lsi) * NV;
+        const double* B = phi + ((size_t)qs * nls + lsj) * NV;
+        const double* dq = qd + (size_t)qs * NQ;
+        const double ws = dq[WQ];
         for (int g = 0; g < a.nqt; ++g) {
           const double* tb = a.tabT + ((size_t)pc * a.nqt + g) * a.q1 * 2;
           const double w = ws * a.wT[(size_t)pc * a.nqt + g];
           const double Ti = tb[2 * lti], dTi = tb[2 * lti + 1], Tj = tb[2 * ltj], dTj = tb[2 * ltj + 1];
-          const double a0 = w * A[0] * Ti, a1 = w * A[1] * Ti, a2 = w * A[2] * dTi;
-          const double b0 = B[0] * Tj, b1 = B[1] * Tj, b2 = B[2] * dTj;
+          double a0, a1, a2, b0, b1, b2;
+          if (SHELL) {
+            const double si = dTi * A[3], sj = dTj * B[3];
+            a0 = w * (Ti * A[0] + si * dq[6]);
+            a1 = w * (Ti * A[1] + si * dq[7]);
+            a2 = w * (Ti * A[2] + si * dq[8]);
+            b0 = Tj * B[0] + sj * dq[6];
+            b1 = Tj * B[1] + sj * dq[7];
+            b2 = Tj * B[2] + sj * dq[8];
+          } else {
+            a0 = w * A[0] * Ti;
+            a1 = w * A[1] * Ti;
+            a2 = w * A[2] * dTi;
+            b0 = B[0] * Tj;
+            b1 = B[1] * Tj;
+            b2 = B[2] * dTj;
+          }
           acc[0] += a0 * b0;
           acc[1] += a0 * b1;
           acc[2] += a0 * b2;
@@ -1387,6 +1727,7 @@ static lam_status ensure_device(Plan& P) {
     UP(L, D->loY, P.v.lo);
     UP(L, D->lenY, P.v.len);
     UP(L, D->ctrl, P.ctrl);
+    if (P.shell) UP(L, D->ctrl3, P.ctrl3);
     if (!P.weights.empty()) UP(L, D->weights, P.weights);
     UP(L, D->LSb, P.LSb);
     UP(L, D->col2_elem, P.col2_elem);
@@ -1513,6 +1854,10 @@ static InplaneArgs inplane_args(const Plan& P) {
   ip.weights = D.weights;
   ip.firstU = D.firstU;
   ip.firstV = D.firstV;
+  ip.ctrl3 = D.ctrl3;
+  ip.ax = P.extrusion[0];
+  ip.ay = P.extrusion[1];
+  ip.az = P.extrusion[2];
   return ip;
 }
 
@@ -1582,38 +1927,42 @@ static KcArgs kc_args(const Plan& P, double* values) {
   k.flag = D.kc_flag;
   k.emax = D.kc_flag + 1;
   k.conditional = 0;
+  k.shellP = D.shellP;
+  k.shell_pmax = D.shell_pmax;
   return k;
 }
 
 // Double-float pass, the exponent check, then the FP64 pass that runs only if
 // the flag is set (2 CTAs per SM, each looping over rows).
-template <bool MONO, bool CHUNKED>
+template <bool MONO, bool CHUNKED, bool SHELL = false>
 static lam_status launch_kcs(const Plan& P, const KcArgs& k, cudaStream_t s) {
   const size_t smem = kcs_smem(P);
-  LAM_CUDA(cudaFuncSetAttribute(kc_stream<MONO, CHUNKED, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  LAM_CUDA(cudaFuncSetAttribute(kc_stream<MONO, CHUNKED, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LAM_CUDA(cudaFuncSetAttribute(kc_stream<MONO, CHUNKED, true, SHELL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  LAM_CUDA(cudaFuncSetAttribute(kc_stream<MONO, CHUNKED, false, SHELL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
   LAM_CUDA(cudaMemsetAsync(k.flag, 0, 2 * sizeof(int), s));
   cudaEvent_t ev = prof_begin(const_cast<Plan&>(P), s);
-  kc_stream<MONO, CHUNKED, true><<<(unsigned)P.ns, kcs_block(P), smem, s>>>(k);
+  kc_stream<MONO, CHUNKED, true, SHELL><<<(unsigned)P.ns, kcs_block(P), smem, s>>>(k);
   LAM_CUDA(cudaGetLastError());
   kc_check<<<1, 1, 0, s>>>(k.flag, k.emax);
   LAM_CUDA(cudaGetLastError());
   KcArgs k64 = k;
   k64.conditional = 1;
   const int64_t grid64 = std::min<int64_t>(P.ns, (int64_t)kcs_ctas_per_sm(P) * std::max(1, P.dev->n_sm));
-  kc_stream<MONO, CHUNKED, false><<<(unsigned)grid64, kcs_block(P), smem, s>>>(k64);
+  kc_stream<MONO, CHUNKED, false, SHELL><<<(unsigned)grid64, kcs_block(P), smem, s>>>(k64);
   LAM_CUDA(cudaGetLastError());
   prof_end(const_cast<Plan&>(P), LAM_KERNEL_COMBINE, 3, s, ev);
   return LAM_OK;
 }
 
-template <bool MONO, bool CHUNKED>
+template <bool MONO, bool CHUNKED, bool SHELL = false>
 static lam_status launch_kc(const Plan& P, const KcArgs& k, cudaStream_t s) {
   const size_t smem = kc_smem(P);
-  LAM_CUDA(cudaFuncSetAttribute(kc_combine<MONO, CHUNKED, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  LAM_CUDA(cudaFuncSetAttribute(kc_combine<MONO, CHUNKED, true, SHELL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
   cudaEvent_t ev = prof_begin(const_cast<Plan&>(P), s);
-  kc_combine<MONO, CHUNKED, true><<<(unsigned)P.ns, kc_block(P), smem, s>>>(k);
+  kc_combine<MONO, CHUNKED, true, SHELL><<<(unsigned)P.ns, kc_block(P), smem, s>>>(k);
   LAM_CUDA(cudaGetLastError());
   prof_end(const_cast<Plan&>(P), LAM_KERNEL_COMBINE, 1, s, ev);
   return LAM_OK;
@@ -1622,6 +1971,7 @@ static lam_status launch_kc(const Plan& P, const KcArgs& k, cudaStream_t s) {
 // Combine into `values`: streaming form when a row's slices fit, class-major form otherwise.
 template <bool CHUNKED>
 static lam_status launch_combine(const Plan& P, const KcArgs& k, cudaStream_t s) {
+  if (P.shell) return use_stream(P) ? launch_kcs<false, CHUNKED, true>(P, k, s) : launch_kc<false, CHUNKED, true>(P, k, s);
   if (use_stream(P))
     return P.monoclinic ? launch_kcs<true, CHUNKED>(P, k, s) : launch_kcs<false, CHUNKED>(P, k, s);
   return P.monoclinic ? launch_kc<true, CHUNKED>(P, k, s) : launch_kc<false, CHUNKED>(P, k, s);
@@ -1640,6 +1990,69 @@ static lam_status inplane_gram(Plan& P, cudaStream_t s) {
   ka_local<<<ka.nel, ka_block(P), smem, s>>>(ka);
   LAM_CUDA(cudaGetLastError());
   prof_end(P, LAM_KERNEL_INPLANE, 1, s, ev);
+  return LAM_OK;
+}
+
+// General extrusion: the 6 x 6 element Gram blocks (ka_shell), then P of
+// every configuration per in-plane pair (kp_shell), into D.shellP.
+static lam_status shell_operators(Plan& P, cudaStream_t s) {
+  Device& D = *P.dev;
+  const int nel = P.u.nel * P.v.nel, npl = ka_npl(P), ncfg = (int)P.cfg_mat.size();
+  if (!D.shellEG && alloc_dev(D.allocs, &D.shellEG, (size_t)nel * 36 * npl) != LAM_OK) return LAM_ERR_OOM;
+  if (!D.shell_pmax) {
+    double* pm = nullptr;
+    if (alloc_dev(D.allocs, &pm, 4) != LAM_OK) return LAM_ERR_OOM;
+    D.shell_pmax = reinterpret_cast<unsigned long long*>(pm);
+  }
+  const size_t need = (size_t)ncfg * P.nnz_s * 36;
+  if (D.shellP_elems < need) {
+    if (D.shellP) cudaFree(D.shellP);
+    D.shellP = nullptr;
+    D.shellP_elems = 0;
+    cudaError_t e = cudaMalloc(&D.shellP, need * sizeof(double));
+    if (e != cudaSuccess) {
+      set_error("cudaMalloc(P of the general extrusion, %zu doubles) failed: %s", need, cudaGetErrorString(e));
+      return LAM_ERR_OOM;
+    }
+    D.shellP_elems = need;
+  }
+  KaShellArgs ka{};
+  ka.ip = inplane_args(P);
+  ka.EG = D.shellEG;
+  const size_t smem = ka_shell_smem(P);
+  LAM_CUDA(cudaFuncSetAttribute(ka_shell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaEvent_t ev = prof_begin(P, s);
+  ka_shell<<<(unsigned)nel, 256, smem, s>>>(ka);
+  LAM_CUDA(cudaGetLastError());
+  KpShellArgs kp{};
+  kp.nx = P.u.n;
+  kp.nel_u = P.u.nel;
+  kp.nlx = P.u.p + 1;
+  kp.nls = ka_nls(P);
+  kp.npl = npl;
+  kp.ncfg = ncfg;
+  kp.nnz_s = P.nnz_s;
+  kp.LSb = D.LSb;
+  kp.lenX = D.lenX;
+  kp.lenY = D.lenY;
+  kp.loX = D.loX;
+  kp.loY = D.loY;
+  kp.eloX = D.eloX;
+  kp.ehiX = D.ehiX;
+  kp.eloY = D.eloY;
+  kp.ehiY = D.ehiY;
+  kp.firstU = D.firstU;
+  kp.firstV = D.firstV;
+  kp.EG = D.shellEG;
+  kp.cfgE = D.cfgE;
+  kp.P = D.shellP;
+  kp.pmax = D.shell_pmax;
+  LAM_CUDA(cudaMemsetAsync(D.shell_pmax, 0, 4 * sizeof(unsigned long long), s));
+  const size_t smem_p = (size_t)36 * max_len_s(P) * sizeof(double);
+  LAM_CUDA(cudaFuncSetAttribute(kp_shell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p));
+  kp_shell<<<(unsigned)P.ns, 256, smem_p, s>>>(kp);
+  LAM_CUDA(cudaGetLastError());
+  prof_end(P, LAM_KERNEL_INPLANE, 2, s, ev);
   return LAM_OK;
 }
 
@@ -1666,7 +2079,7 @@ static lam_status split_integrals(Plan& P, cudaStream_t s) {
   kb_thickness<<<(unsigned)((P.nnz_t + 127) / 128), 128, 0, s>>>(kb);
   LAM_CUDA(cudaGetLastError());
   prof_end(P, LAM_KERNEL_THICKNESS, 1, s, ev);
-  return inplane_gram(P, s);
+  return P.shell ? shell_operators(P, s) : inplane_gram(P, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -2461,7 +2874,8 @@ __global__ void kp_from_gram(int64_t nps, const double* __restrict__ G, const do
 
 // Appendix A, per in-plane element: at every Gauss point the contracted
 // tensors C~_ab[p][r] = sum_{i,j} C{e_i, e_j}_{pr} (g^i . e_a)(g^j . e_b), with
-// g^i . e_a = (DF^{-1})_{ai} (DF block-diagonal: the planar map and dz/dxi3 = 1),
+// g^i . e_a = (DF^{-1})_{ai} (block-diagonal for the planar map with dz/dxi3 = 1,
+// full for a general extrusion, Eq. extrusion),
 // and the parametric gradients of the in-plane functions; thread per ordered
 // local pair accumulates the four blocks. EP[e][li * nls + lj][36].
 struct BfreeArgs {
@@ -2480,7 +2894,7 @@ __global__ void __launch_bounds__(256) kp_bfree(BfreeArgs a) {
   double* sSu = sS + (size_t)nqs * nls;         // d/dxi1
   double* sSv = sSu + (size_t)nqs * nls;        // d/dxi2
   double* sCt = sSv + (size_t)nqs * nls;        // [q][a*3+b][p*3+r]
-  double* sJ = sCt + (size_t)nqs * 81;          // [q]: Jinv (4), w |J|, W, W1, W2
+  double* sJ = sCt + (size_t)nqs * 81;          // [q][16]: rows of DF^-1 (9), w |DF|, W, W1, W2
   // geometry per point
   for (int t = threadIdx.x; t < nqs; t += blockDim.x) {
     const int qu = t % ip.nqu, qv = t / ip.nqu;
@@ -2497,7 +2911,8 @@ __global__ void __launch_bounds__(256) kp_bfree(BfreeArgs a) {
           W2 += w * tu[2 * lx] * tv[2 * ly + 1];
         }
     }
-    double J00 = 0.0, J01 = 0.0, J10 = 0.0, J11 = 0.0;
+    // DF = [dS/dxi1 | dS/dxi2 | a] (columns A0, A1, a); planar: S = (x, y, 0), a = e_z
+    double A0[3] = {0.0, 0.0, 0.0}, A1[3] = {0.0, 0.0, 0.0};
     for (int ly = 0; ly < nly; ++ly)
       for (int lx = 0; lx < nlx; ++lx) {
         const size_t gi = (size_t)(fy + ly) * ip.nx + fx + lx;
@@ -2508,21 +2923,53 @@ __global__ void __launch_bounds__(256) kp_bfree(BfreeArgs a) {
           R1 = w * (N1 * W - N * W1) / (W * W);
           R2 = w * (N2 * W - N * W2) / (W * W);
         }
-        J00 += R1 * ip.ctrl[2 * gi];
-        J01 += R2 * ip.ctrl[2 * gi];
-        J10 += R1 * ip.ctrl[2 * gi + 1];
-        J11 += R2 * ip.ctrl[2 * gi + 1];
+        if (ip.ctrl3) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            A0[c] += R1 * ip.ctrl3[3 * gi + c];
+            A1[c] += R2 * ip.ctrl3[3 * gi + c];
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            A0[c] += R1 * ip.ctrl[2 * gi + c];
+            A1[c] += R2 * ip.ctrl[2 * gi + c];
+          }
+        }
       }
-    const double det = J00 * J11 - J01 * J10, inv = 1.0 / det;
-    double* d = sJ + (size_t)t * 8;
-    d[0] = J11 * inv;   // (DF^-1)_{00}
-    d[1] = -J01 * inv;  // (DF^-1)_{01}
-    d[2] = -J10 * inv;  // (DF^-1)_{10}
-    d[3] = J00 * inv;   // (DF^-1)_{11}
-    d[4] = ip.wU[(size_t)ex * ip.nqu + qu] * ip.wV[(size_t)ey * ip.nqv + qv] * fabs(det);
-    d[5] = W;
-    d[6] = W1;
-    d[7] = W2;
+    double* d = sJ + (size_t)t * 16;
+    double det;
+    if (ip.ctrl3) {  // the dual vectors g^k (rows of DF^-1), as in shell_points
+      const double A2[3] = {ip.ax, ip.ay, ip.az};
+      double g0[3], g1[3], g2[3];
+      cross3(A1, A2, g0);
+      cross3(A2, A0, g1);
+      cross3(A0, A1, g2);
+      det = A0[0] * g0[0] + A0[1] * g0[1] + A0[2] * g0[2];
+      const double inv = 1.0 / det;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        d[c] = g0[c] * inv;
+        d[3 + c] = g1[c] * inv;
+        d[6 + c] = g2[c] * inv;
+      }
+    } else {
+      det = A0[0] * A1[1] - A1[0] * A0[1];
+      const double inv = 1.0 / det;
+      d[0] = A1[1] * inv;   // (DF^-1)_{00}
+      d[1] = -A1[0] * inv;  // (DF^-1)_{01}
+      d[2] = 0.0;
+      d[3] = -A0[1] * inv;  // (DF^-1)_{10}
+      d[4] = A0[0] * inv;   // (DF^-1)_{11}
+      d[5] = 0.0;
+      d[6] = 0.0;
+      d[7] = 0.0;
+      d[8] = 1.0;
+    }
+    d[9] = ip.wU[(size_t)ex * ip.nqu + qu] * ip.wV[(size_t)ey * ip.nqv + qv] * fabs(det);
+    d[10] = W;
+    d[11] = W1;
+    d[12] = W2;
   }
   __syncthreads();
   // parametric values and derivatives of the local functions
@@ -2533,12 +2980,12 @@ __global__ void __launch_bounds__(256) kp_bfree(BfreeArgs a) {
     const double* tv = ip.tabV + ((size_t)ey * ip.nqv + qv) * nly * 2;
     double R = tu[2 * lx] * tv[2 * ly], R1 = tu[2 * lx + 1] * tv[2 * ly], R2 = tu[2 * lx] * tv[2 * ly + 1];
     if (ip.weights) {
-      const double* d = sJ + (size_t)q * 8;
-      const double w = ip.weights[(size_t)(fy + ly) * ip.nx + fx + lx], W = d[5];
+      const double* d = sJ + (size_t)q * 16;
+      const double w = ip.weights[(size_t)(fy + ly) * ip.nx + fx + lx], W = d[10];
       const double N = R, N1 = R1, N2 = R2;
       R = w * N / W;
-      R1 = w * (N1 * W - N * d[6]) / (W * W);
-      R2 = w * (N2 * W - N * d[7]) / (W * W);
+      R1 = w * (N1 * W - N * d[11]) / (W * W);
+      R2 = w * (N2 * W - N * d[12]) / (W * W);
     }
     sS[t] = R;
     sSu[t] = R1;
@@ -2548,11 +2995,11 @@ __global__ void __launch_bounds__(256) kp_bfree(BfreeArgs a) {
   for (int t = threadIdx.x; t < nqs * 81; t += blockDim.x) {
     const int q = t / 81, ab = (t % 81) / 9, pr = t % 9;
     const int al = ab / 3, be = ab % 3;
-    const double* d = sJ + (size_t)q * 8;
+    const double* d = sJ + (size_t)q * 16;
     double gi[3], gj[3];  // (DF^-1)_{alpha i}, (DF^-1)_{beta j}
     for (int i = 0; i < 3; ++i) {
-      gi[i] = (al == 2) ? (i == 2 ? 1.0 : 0.0) : (i == 2 ? 0.0 : d[al * 2 + i]);
-      gj[i] = (be == 2) ? (i == 2 ? 1.0 : 0.0) : (i == 2 ? 0.0 : d[be * 2 + i]);
+      gi[i] = d[al * 3 + i];
+      gj[i] = d[be * 3 + i];
     }
     double acc = 0.0;
     for (int i = 0; i < 3; ++i)
@@ -2566,7 +3013,7 @@ __global__ void __launch_bounds__(256) kp_bfree(BfreeArgs a) {
 #pragma unroll
     for (int k = 0; k < 36; ++k) acc[k] = 0.0;
     for (int q = 0; q < nqs; ++q) {
-      const double w = sJ[(size_t)q * 8 + 4];
+      const double w = sJ[(size_t)q * 16 + 9];
       const double Si = sS[q * nls + li], Sj = sS[q * nls + lj];
       const double Ui = sSu[q * nls + li], Uj = sSu[q * nls + lj];
       const double Vi = sSv[q * nls + li], Vj = sSv[q * nls + lj];
@@ -2795,7 +3242,8 @@ lam_status lam_assemble_standard(lam_plan* plan, double* d_values, void* stream)
   k.cfgE = D.cfgE;
   k.values = d_values;
   const size_t smem = lam::kd_smem(P);
-  LAM_CUDA(cudaFuncSetAttribute(lam::kd_standard, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LAM_CUDA(cudaFuncSetAttribute(lam::kd_standard<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LAM_CUDA(cudaFuncSetAttribute(lam::kd_standard<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int ncol = (int)P.col3_begin.size() - 1;
   cudaEvent_t ev = lam::prof_begin(P, s);
   int launched = 0;
@@ -2803,7 +3251,10 @@ lam_status lam_assemble_standard(lam_plan* plan, double* d_values, void* stream)
     const int n = P.col3_begin[c + 1] - P.col3_begin[c];
     if (n == 0) continue;
     k.elems = D.col3_elem + P.col3_begin[c];
-    lam::kd_standard<<<n, 256, smem, s>>>(k);
+    if (P.shell)
+      lam::kd_standard<true><<<n, 256, smem, s>>>(k);
+    else
+      lam::kd_standard<false><<<n, 256, smem, s>>>(k);
     LAM_CUDA(cudaGetLastError());
     ++launched;
   }
@@ -2836,6 +3287,10 @@ lam_status lam_adjoint(lam_plan* plan, const lam_cotangent* cot, double* d_dC, d
     return LAM_ERR_INVALID_ARG;
   }
   lam::Plan& P = plan->p;
+  if (P.shell) {
+    lam::set_error("lam_adjoint: general extrusion maps are not supported");
+    return LAM_ERR_UNSUPPORTED;
+  }
   if (P.adj_max_terms > lam::kAdjMaxTerms) {
     lam::set_error("lam_adjoint: a ply meets %d thickness pairs (at most %d)", P.adj_max_terms, lam::kAdjMaxTerms);
     return LAM_ERR_UNSUPPORTED;
@@ -2868,6 +3323,12 @@ lam_status lam_inplane_operators(lam_plan* plan, int32_t ply, int32_t method, do
   lam::Device& D = *P.dev;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int m = P.ply_cfg[ply];
+  if (method == LAM_P_FROM_GRAM && P.shell) {  // the 6 x 6 Gram blocks and P of every configuration
+    if ((st = lam::shell_operators(P, s)) != LAM_OK) return st;
+    LAM_CUDA(cudaMemcpyAsync(d_P, D.shellP + (size_t)m * P.nnz_s * 36, (size_t)P.nnz_s * 36 * sizeof(double),
+                             cudaMemcpyDeviceToDevice, s));
+    return LAM_OK;
+  }
   if (method == LAM_P_FROM_GRAM) {
     if ((st = lam::ensure_adjoint(P)) != LAM_OK) return st;
     if ((st = lam::inplane_gram(P, s)) != LAM_OK) return st;
@@ -2884,7 +3345,7 @@ lam_status lam_inplane_operators(lam_plan* plan, int32_t ply, int32_t method, do
   a.ip = lam::inplane_args(P);
   a.Cb = D.cfgCb + (size_t)m * 81;
   a.EP = D.bfree_EP;
-  const size_t smem = ((size_t)3 * nqs * nls + 81 * (size_t)nqs + 8 * (size_t)nqs) * sizeof(double);
+  const size_t smem = ((size_t)3 * nqs * nls + 81 * (size_t)nqs + 16 * (size_t)nqs) * sizeof(double);
   LAM_CUDA(cudaFuncSetAttribute(lam::kp_bfree, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int block = std::min(256, std::max(32, ((nls * nls + 31) / 32) * 32));
   lam::kp_bfree<<<(unsigned)nel, block, smem, s>>>(a);
@@ -3012,6 +3473,10 @@ extern "C" lam_status lam_assemble_split_noalloc(const lam_plan* plan, double* d
     return LAM_ERR_INVALID_ARG;
   }
   const lam::Plan& P = plan->p;
+  if (P.shell) {
+    lam::set_error("lam_assemble_split_noalloc: general extrusion maps are not supported");
+    return LAM_ERR_UNSUPPORTED;
+  }
   lam_status st;
   if ((st = lam::check_limits(P)) != LAM_OK) return st;
   const int ncfg = (int)P.cfg_mat.size();
@@ -3409,6 +3874,10 @@ lam_status lam_batch_create(lam_batch** out, lam_plan* const* plans, int32_t n_p
         lam::set_error("lam_batch_create: plan %d appears twice", i);
         return LAM_ERR_INVALID_ARG;
       }
+    if (plans[i]->p.shell) {
+      lam::set_error("lam_batch_create: plan %d is a general extrusion (not supported in batches)", i);
+      return LAM_ERR_UNSUPPORTED;
+    }
   }
   lam_batch* B = new (std::nothrow) lam_batch();
   if (!B) {

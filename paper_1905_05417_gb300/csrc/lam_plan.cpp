@@ -748,12 +748,40 @@ lam_status build_plan(Plan& P, const lam_inplane* inplane, const lam_basis1d* th
     set_error("n_dof %lld exceeds the int32 column index range", (long long)P.n_dof);
     return LAM_ERR_UNSUPPORTED;
   }
-  P.ctrl.assign(inplane->ctrl, inplane->ctrl + 2 * P.ns);
-  for (double x : P.ctrl)
-    if (!std::isfinite(x)) {
+  const int cdim = inplane->ctrl_dim == 0 ? 2 : inplane->ctrl_dim;
+  if (cdim != 2 && cdim != 3) {
+    set_error("ctrl_dim must be 2 or 3 (got %d)", inplane->ctrl_dim);
+    return LAM_ERR_INVALID_ARG;
+  }
+  for (int64_t k = 0; k < cdim * P.ns; ++k)
+    if (!std::isfinite(inplane->ctrl[k])) {
       set_error("non-finite control point");
       return LAM_ERR_INVALID_ARG;
     }
+  const double* ex = inplane->extrusion;
+  if (!std::isfinite(ex[0]) || !std::isfinite(ex[1]) || !std::isfinite(ex[2])) {
+    set_error("non-finite extrusion direction");
+    return LAM_ERR_INVALID_ARG;
+  }
+  const bool ez = (ex[0] == 0.0 && ex[1] == 0.0 && (ex[2] == 0.0 || ex[2] == 1.0));
+  P.shell = cdim == 3 || !ez;
+  if (ex[0] != 0.0 || ex[1] != 0.0 || ex[2] != 0.0) {
+    P.extrusion[0] = ex[0];
+    P.extrusion[1] = ex[1];
+    P.extrusion[2] = ex[2];
+  }
+  P.ctrl.resize(2 * P.ns);
+  P.ctrl3.clear();
+  if (P.shell) P.ctrl3.resize(3 * P.ns);
+  for (int64_t i = 0; i < P.ns; ++i) {
+    P.ctrl[2 * i] = inplane->ctrl[cdim * i];
+    P.ctrl[2 * i + 1] = inplane->ctrl[cdim * i + 1];
+    if (P.shell) {
+      P.ctrl3[3 * i] = inplane->ctrl[cdim * i];
+      P.ctrl3[3 * i + 1] = inplane->ctrl[cdim * i + 1];
+      P.ctrl3[3 * i + 2] = cdim == 3 ? inplane->ctrl[cdim * i + 2] : 0.0;
+    }
+  }
   P.weights.clear();
   if (inplane->weights) {
     if (P.u.kind != LAM_BSPLINE) {
@@ -911,6 +939,7 @@ lam_status lam_plan_get_info(const lam_plan* plan, lam_plan_info* info) {
   info->n_pieces = (int32_t)P.pieces.size();
   info->combine_streaming = lam::use_stream(P) ? 1 : 0;
   info->combine_chunks = (int32_t)P.ck_nslot.size();
+  info->shell = P.shell ? 1 : 0;
   return LAM_OK;
 }
 

@@ -211,3 +211,32 @@ def test_batch_rejects_invalid_arguments(lam):
     assert L.lam_batch_create(None, arr, 1) == 1
     assert L.lam_batch_assemble(None, None, None) == 1
     assert L.lam_batch_destroy(None) == 0
+
+
+def test_extrusion_maps_at_plan_creation(lam):
+    """ctrl_dim / extrusion of lam_inplane (Eq. extrusion): the general map is
+    recognised, malformed values are rejected, and the entry points that do not
+    handle it refuse it before any device work."""
+    assert lam.Plan.from_laminate(W.cross_ply_plate()).info["shell"] == 0
+    sh = W.shell_plate(n_el=3, degree=2, repeats=1)
+    p = lam.Plan.from_laminate(sh)
+    assert p.info["shell"] == 1
+    assert p.info["nnz"] == lam.Plan.from_laminate(W.curved_plate(n_el=3, degree=2, repeats=1)).info["nnz"]
+    # a planar surface with a tilted extrusion is general too; a = e_z or a = 0 is the plate
+    kw = _kw(W.cross_ply_plate())
+    assert lam.Plan(**kw, extrusion=(0.0, 0.0, 1.0)).info["shell"] == 0
+    assert lam.Plan(**kw, extrusion=(0.0, 0.0, 0.0)).info["shell"] == 0
+    assert lam.Plan(**kw, extrusion=(0.1, 0.0, 1.0)).info["shell"] == 1
+    assert lam.Plan(**dict(kw, ctrl=np.c_[kw["ctrl"], np.zeros(len(kw["ctrl"]))])).info["shell"] == 1
+    with pytest.raises(lam.LamError) as e:
+        lam.Plan(**kw, extrusion=(np.nan, 0.0, 1.0))
+    assert e.value.status == 1
+    L = lam.load()
+    c = lam._Cotangent()
+    c.kind, c.rank, c.values = 0, 1, 0x1000
+    assert L.lam_adjoint(p.handle, ctypes.byref(c), 0x2000, None, None, None) == 2
+    assert "extrusion" in lam.last_error()
+    out = ctypes.c_void_p()
+    arr = (ctypes.c_void_p * 1)(p.handle.value)
+    assert L.lam_batch_create(ctypes.byref(out), arr, 1) == 2
+    assert L.lam_assemble_split_noalloc(p.handle, 0x1000, None) == 2

@@ -74,6 +74,8 @@ struct Device {
   double* shellP = nullptr;    // n_cfg x nnz_s x 36
   size_t shellP_elems = 0;
   unsigned long long* shell_pmax = nullptr;  // 4 block maxima of |P|
+  float2* shell_Edf = nullptr;  // cfgE 2^-kE per configuration, float pairs (configuration tables)
+  int* shell_kE = nullptr;
   int n_sm = 0;
   double* q = nullptr;   // nnz_t x n_cfg x 4
   // adjoint: geometry tables and workspace (allocated by the first lam_adjoint)
@@ -241,10 +243,10 @@ static size_t kd_smem(const Plan& P) {
   if (P.shell) return (size_t)nqs * nls * 4 * sizeof(double) + (size_t)nqs * 16 * sizeof(double);
   return (size_t)nqs * nls * 3 * sizeof(double) + (size_t)nqs * 8 * sizeof(double);
 }
-// K-a of a general extrusion: FP64 point values, float pairs of u and w u, per point 16 doubles
+// K-a of a general extrusion: float pairs of u and w u, per point 16 doubles
 static size_t ka_shell_smem(const Plan& P) {
   const int nqs = P.nqu * P.nqv, nls = ka_nls(P);
-  return (size_t)nqs * nls * (4 * sizeof(double) + 24 * sizeof(float)) + (size_t)nqs * 16 * sizeof(double);
+  return (size_t)nqs * nls * 24 * sizeof(float) + (size_t)nqs * 16 * sizeof(double);
 }
 
 // ---------------------------------------------------------------------------
@@ -939,13 +941,14 @@ __global__ void __launch_bounds__(256) ka_local(KaLocalArgs a) {
 // now have three gradient components each (the planar map has (g_x, g_y, 0)
 // and (0, 0, R)), so the configuration-free Gram of a local pair has 6 x 6
 // entries: G_(alpha a)(beta b) = sum_q w|DF| u^li_(alpha a) u^lj_(beta b),
-// u_1 = g1, u_2 = R g^2. EG[(e * 36 + blk * 9 + a * 3 + b) * npl + pair],
-// blk = 2 alpha + beta, pair li <= lj (the other order is the transposed
-// block: G^ji_(alpha a)(beta b) = G^ij_(beta b)(alpha a)). Point values in
-// FP64 (shell_points); the products in double-float, with u_1, u_2 and w|DF|
-// divided by per-element powers of two (k1, k2, kq) so that the float pairs
-// keep any geometry scale; block (alpha, beta) is scaled back by
-// 2^(kq + k_alpha + k_beta).
+// u_1 = g1, u_2 = R g^2. EG[(e * npl + pair) * 36 + blk * 9 + a * 3 + b],
+// blk = 2 alpha + beta, pair li <= lj; the 36 entries of a pair are
+// contiguous, so that the per-row gather reads whole lines. The other order is
+// the transposed block: G^ji_(alpha a)(beta b) = G^ij_(beta b)(alpha a). The
+// geometry sums and DF^-1 in FP64, the point values and the products in
+// double-float, with u_1, u_2 and w|DF| divided by per-element powers of two
+// (k1, k2, kq) so that the float pairs keep any geometry scale; block
+// (alpha, beta) is scaled back by 2^(kq + k_alpha + k_beta).
 // ---------------------------------------------------------------------------
 struct KaShellArgs {
   InplaneArgs ip;
@@ -954,60 +957,176 @@ struct KaShellArgs {
 
 __device__ __forceinline__ int exp_field(double v) { return (__double2hiint(v) >> 20) & 0x7FF; }
 
+// The element's point values of a general extrusion as float pairs
+// phf / pwf ([item][12]: hi u_0..u_5, lo u_0..u_5; pwf = w|DF| phf), with
+// u = (R_,1 g^0 + R_,2 g^1, R g^2):
+//   A (FP64) per (point, sum): dS/dxi1 and dS/dxi2 (three coordinates each),
+//     or for NURBS the twelve sums W, dW/dxi_k and the same with w X, w Y, w Z,
+//     factorised over the tensor product;
+//   P (FP64) per point: the columns of DF, the dual vectors g^k, w|DF|;
+//   B (double-float) per (point, function).
+// g^0, g^1 enter divided by 2^k1, g^2 by 2^k2 and w|DF| by 2^kq (s_k[0..2]).
+__device__ __forceinline__ void ka_shell_point_values(const InplaneArgs& ip, int ex, int ey, float* phf, float* pwf,
+                                                      double* qd, int* s_k) {
+  const int nlx = ip.pu + 1, nly = ip.pv + 1, nls = nlx * nly, nqs = ip.nqu * ip.nqv;
+  const int fx = ip.firstU[ex], fy = ip.firstV[ey];
+  const bool rat = ip.weights != nullptr;
+  const int nsum = rat ? 12 : 6;
+  double* S = reinterpret_cast<double*>(phf);   // phase A results (consumed before phase B)
+  double* hc = reinterpret_cast<double*>(pwf);  // (w, w X, w Y, w Z) of a NURBS element
+  if (rat) {
+    for (int k = threadIdx.x; k < nls; k += blockDim.x) {
+      const size_t gi = (size_t)(fy + k / nlx) * ip.nx + fx + k % nlx;
+      const double w = ip.weights[gi];
+      hc[k] = w;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) hc[(1 + c) * nls + k] = w * ip.ctrl3[3 * gi + c];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < nqs * nsum; t += blockDim.x) {
+    const int q = t / nsum, sidx = t % nsum;
+    const int qu = q % ip.nqu, qv = q / ip.nqu;
+    // der: 0 value, 1 d/dxi1, 2 d/dxi2; dat: coordinate (B-spline) or w, w X, w Y, w Z (NURBS)
+    const int dat = rat ? sidx / 3 : sidx % 3, der = rat ? sidx % 3 : 1 + sidx / 3;
+    const double* tu = ip.tabU + ((size_t)ex * ip.nqu + qu) * nlx * 2 + (der == 1 ? 1 : 0);
+    const double* tv = ip.tabV + ((size_t)ey * ip.nqv + qv) * nly * 2 + (der == 2 ? 1 : 0);
+    double acc = 0.0;
+    for (int ly = 0; ly < nly; ++ly) {
+      double row = 0.0;
+      for (int lx = 0; lx < nlx; ++lx) {
+        const double c = rat ? hc[dat * nls + ly * nlx + lx]
+                             : ip.ctrl3[3 * ((size_t)(fy + ly) * ip.nx + fx + lx) + dat];
+        row = fma(tu[2 * lx], c, row);
+      }
+      acc = fma(tv[2 * ly], row, acc);
+    }
+    S[t] = acc;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < nqs; q += blockDim.x) {
+    const double* sq = S + (size_t)q * nsum;
+    double A0[3], A1[3], iw = 1.0, r1 = 0.0, r2 = 0.0;
+    if (rat) {  // d(A / W) = (dA - (A / W) dW) / W
+      iw = 1.0 / sq[0];
+      r1 = sq[1] * iw;
+      r2 = sq[2] * iw;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        A0[c] = (sq[3 * (1 + c) + 1] - sq[3 * (1 + c)] * r1) * iw;
+        A1[c] = (sq[3 * (1 + c) + 2] - sq[3 * (1 + c)] * r2) * iw;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        A0[c] = sq[c];
+        A1[c] = sq[3 + c];
+      }
+    }
+    const double A2[3] = {ip.ax, ip.ay, ip.az};
+    double g0[3], g1[3], g2[3];
+    cross3(A1, A2, g0);
+    cross3(A2, A0, g1);
+    cross3(A0, A1, g2);
+    const double det = A0[0] * g0[0] + A0[1] * g0[1] + A0[2] * g0[2], inv = 1.0 / det;
+    const int qu = q % ip.nqu, qv = q / ip.nqu;
+    double* d = qd + (size_t)q * kShellQ;
+    int e1 = 0, e2 = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      d[c] = g0[c] * inv;
+      d[3 + c] = g1[c] * inv;
+      d[6 + c] = g2[c] * inv;
+      e1 = max(e1, max(exp_field(d[c]), exp_field(d[3 + c])));
+      e2 = max(e2, exp_field(d[6 + c]));
+    }
+    d[9] = ip.wU[(size_t)ex * ip.nqu + qu] * ip.wV[(size_t)ey * ip.nqv + qv] * fabs(det);
+    d[10] = iw;
+    d[11] = r1;
+    d[12] = r2;
+    atomicMax(&s_k[0], e1);
+    atomicMax(&s_k[1], e2);
+    atomicMax(&s_k[2], exp_field(d[9]));
+  }
+  __syncthreads();
+  const int k1 = s_k[0] > 0 ? s_k[0] - 1023 : 0, k2 = s_k[1] > 0 ? s_k[1] - 1023 : 0;
+  const int kq = s_k[2] > 0 ? s_k[2] - 1023 : 0;
+  for (int t = threadIdx.x; t < nqs * nls; t += blockDim.x) {
+    const int q = t / nls, k = t % nls;
+    const int qu = q % ip.nqu, qv = q / ip.nqu, lx = k % nlx, ly = k / nlx;
+    const double* tu = ip.tabU + ((size_t)ex * ip.nqu + qu) * nlx * 2 + 2 * lx;
+    const double* tv = ip.tabV + ((size_t)ey * ip.nqv + qv) * nly * 2 + 2 * ly;
+    const double* d = qd + (size_t)q * kShellQ;
+    float u0h, u0l, u1h, u1l, v0h, v0l, v1h, v1l;
+    split_df_fast(tu[0], u0h, u0l);
+    split_df_fast(tu[1], u1h, u1l);
+    split_df_fast(tv[0], v0h, v0l);
+    split_df_fast(tv[1], v1h, v1l);
+    float Rh, Rl, R1h, R1l, R2h, R2l;
+    df_prod(u0h, u0l, v0h, v0l, Rh, Rl);
+    df_prod(u1h, u1l, v0h, v0l, R1h, R1l);
+    df_prod(u0h, u0l, v1h, v1l, R2h, R2l);
+    if (rat) {  // R = c N, R_,k = c (N_,k - N W_,k / W), c = w / W
+      float ch, cl, rh, rl, th, tl;
+      split_df_fast(ip.weights[(size_t)(fy + ly) * ip.nx + fx + lx] * d[10], ch, cl);
+      split_df_fast(d[11], rh, rl);
+      df_prod(Rh, Rl, -rh, -rl, th, tl);
+      df_add(th, tl, R1h, R1l);
+      df_norm(R1h, R1l);
+      df_prod(R1h, R1l, ch, cl, R1h, R1l);
+      split_df_fast(d[12], rh, rl);
+      df_prod(Rh, Rl, -rh, -rl, th, tl);
+      df_add(th, tl, R2h, R2l);
+      df_norm(R2h, R2l);
+      df_prod(R2h, R2l, ch, cl, R2h, R2l);
+      df_prod(Rh, Rl, ch, cl, Rh, Rl);
+    }
+    float wh, wl;
+    split_df_off(d[9], kq, wh, wl);
+    float* f = phf + (size_t)t * 12;
+    float* fw = pwf + (size_t)t * 12;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float ah, al, bh, bl, gh, gl, h, l;
+      split_df_off(d[c], k1, ah, al);
+      split_df_off(d[3 + c], k1, bh, bl);
+      df_mul(ah, al, R1h, R1l, gh, gl);  // R_,1 g^0 + R_,2 g^1
+      df_mac(bh, bl, R2h, R2l, gh, gl);
+      df_norm(gh, gl);
+      f[c] = gh;
+      f[6 + c] = gl;
+      df_prod(wh, wl, gh, gl, h, l);
+      fw[c] = h;
+      fw[6 + c] = l;
+      split_df_off(d[6 + c], k2, ah, al);  // R g^2
+      df_prod(Rh, Rl, ah, al, gh, gl);
+      f[3 + c] = gh;
+      f[9 + c] = gl;
+      df_prod(wh, wl, gh, gl, h, l);
+      fw[3 + c] = h;
+      fw[9 + c] = l;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) ka_shell(KaShellArgs a) {
   extern __shared__ double sm[];
   const InplaneArgs& ip = a.ip;
   const int nlx = ip.pu + 1, nly = ip.pv + 1, nls = nlx * nly, nqs = ip.nqu * ip.nqv;
   const int e = blockIdx.x, ex = e % ip.nel_u, ey = e / ip.nel_u;
   const int nit = nqs * nls;
-  double* ph = sm;
-  double* qs = ph + (size_t)nit * 4;
-  float* phf = reinterpret_cast<float*>(qs + (size_t)nqs * kShellQ);  // [item][12]: hi 6, lo 6
+  float* phf = reinterpret_cast<float*>(sm);  // [item][12]: hi 6, lo 6
   float* pwf = phf + (size_t)nit * 12;
+  double* qs = reinterpret_cast<double*>(pwf + (size_t)nit * 12);
   __shared__ int s_k[3];
   if (threadIdx.x < 3) s_k[threadIdx.x] = 0;
-  shell_points(ip, ex, ey, ph, qs);  // begins and ends with a barrier-separated phase
-  {
-    int e1 = 0, e2 = 0, eq = 0;
-    for (int t = threadIdx.x; t < nit; t += blockDim.x) {
-      const double* f = ph + (size_t)t * 4;
-      const double* d = qs + (size_t)(t / nls) * kShellQ;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        e1 = max(e1, exp_field(f[c]));
-        e2 = max(e2, exp_field(f[3] * d[6 + c]));
-      }
-    }
-    for (int q = threadIdx.x; q < nqs; q += blockDim.x) eq = max(eq, exp_field(qs[(size_t)q * kShellQ + 9]));
-    atomicMax(&s_k[0], e1);
-    atomicMax(&s_k[1], e2);
-    atomicMax(&s_k[2], eq);
-  }
   __syncthreads();
+  ka_shell_point_values(ip, ex, ey, phf, pwf, qs, s_k);
   const int k1 = s_k[0] > 0 ? s_k[0] - 1023 : 0, k2 = s_k[1] > 0 ? s_k[1] - 1023 : 0;
   const int kq = s_k[2] > 0 ? s_k[2] - 1023 : 0;
-  for (int t = threadIdx.x; t < nit; t += blockDim.x) {
-    const double* f = ph + (size_t)t * 4;
-    const double* d = qs + (size_t)(t / nls) * kShellQ;
-    const double w = d[9];
-    float* o = phf + (size_t)t * 12;
-    float* ow = pwf + (size_t)t * 12;
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      const double v = j < 3 ? f[j] : f[3] * d[3 + j];
-      const int kj = j < 3 ? k1 : k2;
-      float h, l;
-      split_df_off(v, kj, h, l);
-      o[j] = h;
-      o[6 + j] = l;
-      split_df_off(w * v, kj + kq, h, l);
-      ow[j] = h;
-      ow[6 + j] = l;
-    }
-  }
   __syncthreads();
   const int npl = nls * (nls + 1) / 2;
-  double* out = a.EG + (size_t)e * 36 * npl;
+  double* out = a.EG + (size_t)e * npl * 36;
   for (int t = threadIdx.x; t < 4 * npl; t += blockDim.x) {
     const int blk = t / npl, pr = t % npl, al = blk >> 1, be = blk & 1;
     int li = 0, rem = pr;
@@ -1042,7 +1161,7 @@ __global__ void __launch_bounds__(256) ka_shell(KaShellArgs a) {
       const float ls = __fsub_rn(sl[k], __fsub_rn(hs, sh[k]));
       long long b = __double_as_longlong(df_to_double(hs, ls));
       if (b & 0x7FFFFFFFFFFFFFFFll) b += (long long)sc * (1ll << 52);  // times 2^sc, exact
-      out[(size_t)(blk * 9 + k) * npl + pr] = __longlong_as_double(b);
+      out[(size_t)pr * 36 + blk * 9 + k] = __longlong_as_double(b);
     }
   }
 }
@@ -1051,19 +1170,27 @@ __global__ void __launch_bounds__(256) ka_shell(KaShellArgs a) {
 // The row's 6 x 6 Gram blocks are summed over the shared elements (fixed
 // order) into shared memory, then P_(alpha beta)[c][d] = sum_(a,b)
 // D_m[V(c,a)][V(d,b)] G_(alpha a)(beta b) (Eq. P) for every configuration m,
-// into P[(m * nnz_s + pair) * 36 + blk * 9 + c * 3 + d].
+// into P[(m * nnz_s + pair) * 36 + blk * 9 + c * 3 + d]. The 9-term sums run
+// in double-float on the FP32 pipes: each 3 x 3 Gram block is divided by a
+// power of two 2^kg (largest entry in [1, 2)) and each configuration's D by
+// 2^kE (host side), and P is scaled back by 2^(kE + kg), so any scale of
+// geometry or material stays inside float range.
 struct KpShellArgs {
   int nx, nel_u, nlx, nls, npl, ncfg;
   int64_t nnz_s;
   const int64_t* LSb;
   const int *lenX, *lenY, *loX, *loY, *eloX, *ehiX, *eloY, *ehiY, *firstU, *firstV;
   const double* EG;
-  const double* cfgE;
+  const float2* Edf;  // D_m[V(c,a)][V(d,b)] 2^-kE[m] as float pairs, [m][cd][ab]
+  const int* kE;
   double* P;
   unsigned long long* pmax;  // largest |P| per block (bit patterns; positive doubles order as integers)
 };
 
-__global__ void __launch_bounds__(256) kp_shell(KpShellArgs a) {
+// SMEM_E: the configurations' D tables staged in shared memory (few configurations).
+constexpr int kKpShellSmemCfg = 32;
+template <bool SMEM_E>
+__global__ void __launch_bounds__(1024) kp_shell(KpShellArgs a) {
   extern __shared__ double sG[];
   __shared__ unsigned long long smax[4];
   if (threadIdx.x < 4) smax[threadIdx.x] = 0ull;
@@ -1083,27 +1210,56 @@ __global__ void __launch_bounds__(256) kp_shell(KpShellArgs a) {
       for (int ex = ex0; ex <= ex1; ++ex) {
         const int fx = a.firstU[ex];
         const int li = (iy - fy) * a.nlx + (ix - fx), lj = (jy - fy) * a.nlx + (jx - fx);
-        const size_t e36 = ((size_t)ey * a.nel_u + ex) * 36;
-        if (li <= lj)
-          acc += a.EG[(e36 + k) * a.npl + upper_pair(li, lj, a.nls)];
-        else
-          acc += a.EG[(e36 + kt) * a.npl + upper_pair(lj, li, a.nls)];
+        const size_t e0 = ((size_t)ey * a.nel_u + ex) * a.npl;
+        acc += li <= lj ? a.EG[(e0 + upper_pair(li, lj, a.nls)) * 36 + k]
+                        : a.EG[(e0 + upper_pair(lj, li, a.nls)) * 36 + kt];
       }
     }
     sG[item] = acc;
   }
+  float2* sE = reinterpret_cast<float2*>(sG + (size_t)36 * ls);
+  if (SMEM_E)
+    for (int k = threadIdx.x; k < a.ncfg * 81; k += blockDim.x) sE[k] = a.Edf[k];
   __syncthreads();
-  const int per_cfg = 36 * ls;
-  for (int item = threadIdx.x; item < a.ncfg * per_cfg; item += blockDim.x) {
-    const int m = item / per_cfg, r = item % per_cfg, ks = r / 36, k = r % 36, blk = k / 9, cd = k % 9;
-    const double* E = a.cfgE + (size_t)m * 81 + cd * 9;
-    const double* g = sG + (size_t)ks * 36 + blk * 9;
-    double p = 0.0;
+  // thread per (k_s, block): the 3 x 3 Gram block as float pairs (divided by
+  // 2^kg) in registers, then its 9 entries of P for every configuration
+  unsigned long long pm = 0ull;  // this thread's largest |P| (bit pattern: integer max, off the FP64 pipe)
+  const int item = threadIdx.x;
+  const int blk = item & 3;
+  if (item < 4 * ls) {
+    const int ks = item >> 2;
+    const double* g = sG + (size_t)item * 9;  // (ks, blk)
+    int e = 0;
 #pragma unroll
-    for (int ab = 0; ab < 9; ++ab) p = fma(E[ab], g[ab], p);
-    a.P[((size_t)m * a.nnz_s + ls0 + ks) * 36 + k] = p;
-    atomicMax(&smax[blk], (unsigned long long)__double_as_longlong(fabs(p)));
+    for (int ab = 0; ab < 9; ++ab) e = max(e, exp_field(g[ab]));
+    const int kg = e > 0 ? e - 1023 : 0;
+    float gh[9], gl[9];
+#pragma unroll
+    for (int ab = 0; ab < 9; ++ab) split_df_off(g[ab], kg, gh[ab], gl[ab]);
+    for (int m = 0; m < a.ncfg; ++m) {
+      const float2* E = (SMEM_E ? sE : a.Edf) + (size_t)m * 81;
+      const int sc = a.kE[m] + kg;
+      double* out = a.P + ((size_t)m * a.nnz_s + ls0 + ks) * 36 + blk * 9;
+#pragma unroll
+      for (int cd = 0; cd < 9; ++cd) {
+        float sh = 0.0f, sl = 0.0f;
+#pragma unroll
+        for (int ab = 0; ab < 9; ++ab) {
+          const float2 ee = SMEM_E ? E[cd * 9 + ab] : __ldg(E + cd * 9 + ab);
+          df_mac(ee.x, ee.y, gh[ab], gl[ab], sh, sl);
+        }
+        const float hs = __fadd_rn(sh, sl);
+        const float lsum = __fsub_rn(sl, __fsub_rn(hs, sh));
+        long long b = __double_as_longlong(df_to_double(hs, lsum));
+        if (b & 0x7FFFFFFFFFFFFFFFll) b += (long long)sc * (1ll << 52);  // exact
+        out[cd] = __longlong_as_double(b);
+        pm = max(pm, (unsigned long long)(b & 0x7FFFFFFFFFFFFFFFll));
+      }
+    }
   }
+  // per block: the largest |P| over the CTA (lanes of one warp share blk modulo 4)
+  for (int off = 16; off >= 4; off >>= 1) pm = max(pm, __shfl_xor_sync(0xffffffffu, pm, off));
+  if ((threadIdx.x & 31) < 4) atomicMax(&smax[blk], pm);
   __syncthreads();
   if (threadIdx.x < 4) atomicMax(&a.pmax[threadIdx.x], smax[threadIdx.x]);
 }
@@ -1792,6 +1948,26 @@ static lam_status ensure_device(Plan& P) {
     float* edf_dev = nullptr;
     UP(L, edf_dev, edf);
     D->cfgEdf = reinterpret_cast<float2*>(edf_dev);
+    if (P.shell) {  // D of every configuration divided by a power of two (largest entry in [1, 2))
+      const int nc = (int)(P.cfgE.size() / 81);
+      std::vector<int> kE(nc, 0);
+      std::vector<float> sedf(P.cfgE.size() * 2);
+      for (int m = 0; m < nc; ++m) {
+        double mx = 0.0;
+        for (int k = 0; k < 81; ++k) mx = std::max(mx, std::fabs(P.cfgE[(size_t)m * 81 + k]));
+        if (mx > 0.0) kE[m] = std::ilogb(mx);
+        for (int k = 0; k < 81; ++k) {
+          const double e = std::ldexp(P.cfgE[(size_t)m * 81 + k], -kE[m]);
+          const float h = (float)e;
+          sedf[2 * ((size_t)m * 81 + k)] = h;
+          sedf[2 * ((size_t)m * 81 + k) + 1] = (float)(e - (double)h);
+        }
+      }
+      float* sedf_dev = nullptr;
+      UP(L, sedf_dev, sedf);
+      D->shell_Edf = reinterpret_cast<float2*>(sedf_dev);
+      UP(L, D->shell_kE, kE);
+    }
     UP(L, D->pair_cls, P.pair_cls);
     UP(L, D->ck_it, P.ck_it);
     UP(L, D->ck_term, P.ck_term);
@@ -1830,7 +2006,11 @@ static lam_status check_limits(const Plan& P) {
     set_error("in-plane rows with more than %d neighbours are not supported by the combine kernel", 1024 / 9);
     return LAM_ERR_UNSUPPORTED;
   }
-  if (kc_smem(P) > 200 * 1024 || ka_smem(P) > 200 * 1024 || kd_smem(P) > 200 * 1024) {
+  // the class-major combine's tables matter where it runs (a general extrusion
+  // takes the streaming form whenever that fits, and has no allocation-free path)
+  const bool class_major = !(P.shell && use_stream(P));
+  if ((class_major && kc_smem(P) > 200 * 1024) || ka_smem(P) > 200 * 1024 || kd_smem(P) > 200 * 1024 ||
+      (P.shell && ka_shell_smem(P) > 200 * 1024)) {
     set_error("plan tables exceed the shared-memory budget of this build");
     return LAM_ERR_UNSUPPORTED;
   }
@@ -2044,13 +2224,21 @@ static lam_status shell_operators(Plan& P, cudaStream_t s) {
   kp.firstU = D.firstU;
   kp.firstV = D.firstV;
   kp.EG = D.shellEG;
-  kp.cfgE = D.cfgE;
+  kp.Edf = D.shell_Edf;
+  kp.kE = D.shell_kE;
   kp.P = D.shellP;
   kp.pmax = D.shell_pmax;
   LAM_CUDA(cudaMemsetAsync(D.shell_pmax, 0, 4 * sizeof(unsigned long long), s));
-  const size_t smem_p = (size_t)36 * max_len_s(P) * sizeof(double);
-  LAM_CUDA(cudaFuncSetAttribute(kp_shell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p));
-  kp_shell<<<(unsigned)P.ns, 256, smem_p, s>>>(kp);
+  const bool smem_e = ncfg <= kKpShellSmemCfg;
+  const size_t smem_p = (size_t)max_len_s(P) * 36 * sizeof(double) + (smem_e ? (size_t)ncfg * 81 * sizeof(float2) : 0);
+  const int block_p = std::max(64, ((4 * max_len_s(P) + 31) / 32) * 32);
+  if (smem_e) {
+    LAM_CUDA(cudaFuncSetAttribute(kp_shell<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p));
+    kp_shell<true><<<(unsigned)P.ns, block_p, smem_p, s>>>(kp);
+  } else {
+    LAM_CUDA(cudaFuncSetAttribute(kp_shell<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p));
+    kp_shell<false><<<(unsigned)P.ns, block_p, smem_p, s>>>(kp);
+  }
   LAM_CUDA(cudaGetLastError());
   prof_end(P, LAM_KERNEL_INPLANE, 2, s, ev);
   return LAM_OK;

@@ -53,6 +53,9 @@ SHELLS = {
     # rows of 81 in-plane neighbours: the class-major combine
     "quartic_class_major": lambda: W.laminate("p4", W.BSPLINE, 4, 6, [0, 45], 0.02, mapping=W.bump_map(0.1),
                                               n_el_y=6, thickness_degree=1, extrusion=(0.0, 0.2, 1.0)),
+    # 40 configurations: the D tables of the P formation read from global memory
+    "many_configurations": lambda: W.laminate("many_cfg", W.BSPLINE, 2, 3, list(np.linspace(-85.0, 85.0, 40)), 0.002,
+                                              mapping=W.bump_map(0.1), extrusion=(0.1, 0.0, 1.0)),
     # uneven plies: the streaming combine in chunks
     "uneven_plies_chunked": lambda: W.laminate(
         "uneven", W.BSPLINE, 1, 3, list(np.random.default_rng(4).choice([0.0, 45.0, -45.0, 90.0], 70)),

@@ -1168,7 +1168,7 @@ __global__ void __launch_bounds__(256) ka_shell(KaShellArgs a) {
 
 // P of every configuration for a general extrusion: CTA per in-plane row i_s.
 // The row's 6 x 6 Gram blocks are summed over the shared elements (fixed
-// order) into shared memory, then P_(alpha beta)[c][d] = sum_(a,b)
+// order), then P_(alpha beta)[c][d] = sum_(a,b)
 // D_m[V(c,a)][V(d,b)] G_(alpha a)(beta b) (Eq. P) for every configuration m,
 // into P[(m * nnz_s + pair) * 36 + blk * 9 + c * 3 + d]. The 9-term sums run
 // in double-float on the FP32 pipes: each 3 x 3 Gram block is divided by a
@@ -1189,46 +1189,53 @@ struct KpShellArgs {
 
 // SMEM_E: the configurations' D tables staged in shared memory (few configurations).
 constexpr int kKpShellSmemCfg = 32;
-template <bool SMEM_E>
+// MONO: every D is monoclinic about z (D[I][J] = 0 for I < 4 <= J), so
+// D[V(c,a)][V(d,b)] vanishes unless exactly-one-index-is-z holds for both
+// (c, a) and (d, b) or for neither: 5 of the 9 terms per entry remain.
+template <bool SMEM_E, bool MONO>
 __global__ void __launch_bounds__(1024) kp_shell(KpShellArgs a) {
-  extern __shared__ double sG[];
+  extern __shared__ float2 sE[];  // the configurations' D tables (SMEM_E)
   __shared__ unsigned long long smax[4];
   if (threadIdx.x < 4) smax[threadIdx.x] = 0ull;
+  if (SMEM_E)
+    for (int k = threadIdx.x; k < a.ncfg * 81; k += blockDim.x) sE[k] = a.Edf[k];
+  __syncthreads();
   const int64_t is = blockIdx.x;
   const int ix = (int)(is % a.nx), iy = (int)(is / a.nx);
   const int lx = a.lenX[ix], ls = lx * a.lenY[iy];
   const int64_t ls0 = a.LSb[is];
-  for (int item = threadIdx.x; item < 36 * ls; item += blockDim.x) {
-    const int ks = item / 36, k = item % 36, blk = k / 9, ab = k % 9;
+  // thread per (k_s, block): the block's 9 Gram entries summed over the shared
+  // elements (row-major element order), divided by 2^kg as float pairs in
+  // registers, then its 9 entries of P for every configuration
+  unsigned long long pm = 0ull;  // this thread's largest |P| (bit pattern: integer max, off the FP64 pipe)
+  const int item = threadIdx.x;
+  const int blk = item & 3;
+  if (item < 4 * ls) {
+    const int ks = item >> 2;
     const int jx = a.loX[ix] + ks % lx, jy = a.loY[iy] + ks / lx;
     const int ex0 = max(a.eloX[ix], a.eloX[jx]), ex1 = min(a.ehiX[ix], a.ehiX[jx]);
     const int ey0 = max(a.eloY[iy], a.eloY[jy]), ey1 = min(a.ehiY[iy], a.ehiY[jy]);
-    const int kt = ((blk & 1) * 2 + (blk >> 1)) * 9 + (ab % 3) * 3 + ab / 3;  // the transposed entry
-    double acc = 0.0;
+    const int blkT = (blk & 1) * 2 + (blk >> 1);  // the transposed block (beta, alpha)
+    double g[9];
+#pragma unroll
+    for (int ab = 0; ab < 9; ++ab) g[ab] = 0.0;
     for (int ey = ey0; ey <= ey1; ++ey) {
       const int fy = a.firstV[ey];
       for (int ex = ex0; ex <= ex1; ++ex) {
         const int fx = a.firstU[ex];
         const int li = (iy - fy) * a.nlx + (ix - fx), lj = (jy - fy) * a.nlx + (jx - fx);
         const size_t e0 = ((size_t)ey * a.nel_u + ex) * a.npl;
-        acc += li <= lj ? a.EG[(e0 + upper_pair(li, lj, a.nls)) * 36 + k]
-                        : a.EG[(e0 + upper_pair(lj, li, a.nls)) * 36 + kt];
+        if (li <= lj) {
+          const double* src = a.EG + (e0 + upper_pair(li, lj, a.nls)) * 36 + blk * 9;
+#pragma unroll
+          for (int ab = 0; ab < 9; ++ab) g[ab] += src[ab];
+        } else {  // G^ji_(alpha a)(beta b) = G^ij_(beta b)(alpha a)
+          const double* src = a.EG + (e0 + upper_pair(lj, li, a.nls)) * 36 + blkT * 9;
+#pragma unroll
+          for (int ab = 0; ab < 9; ++ab) g[ab] += src[(ab % 3) * 3 + ab / 3];
+        }
       }
     }
-    sG[item] = acc;
-  }
-  float2* sE = reinterpret_cast<float2*>(sG + (size_t)36 * ls);
-  if (SMEM_E)
-    for (int k = threadIdx.x; k < a.ncfg * 81; k += blockDim.x) sE[k] = a.Edf[k];
-  __syncthreads();
-  // thread per (k_s, block): the 3 x 3 Gram block as float pairs (divided by
-  // 2^kg) in registers, then its 9 entries of P for every configuration
-  unsigned long long pm = 0ull;  // this thread's largest |P| (bit pattern: integer max, off the FP64 pipe)
-  const int item = threadIdx.x;
-  const int blk = item & 3;
-  if (item < 4 * ls) {
-    const int ks = item >> 2;
-    const double* g = sG + (size_t)item * 9;  // (ks, blk)
     int e = 0;
 #pragma unroll
     for (int ab = 0; ab < 9; ++ab) e = max(e, exp_field(g[ab]));
@@ -1245,6 +1252,8 @@ __global__ void __launch_bounds__(1024) kp_shell(KpShellArgs a) {
         float sh = 0.0f, sl = 0.0f;
 #pragma unroll
         for (int ab = 0; ab < 9; ++ab) {
+          const int c = cd / 3, d = cd % 3, aa = ab / 3, bb = ab % 3;
+          if (MONO && (((c == 2) != (aa == 2)) != ((d == 2) != (bb == 2)))) continue;
           const float2 ee = SMEM_E ? E[cd * 9 + ab] : __ldg(E + cd * 9 + ab);
           df_mac(ee.x, ee.y, gh[ab], gl[ab], sh, sl);
         }
@@ -2230,15 +2239,12 @@ static lam_status shell_operators(Plan& P, cudaStream_t s) {
   kp.pmax = D.shell_pmax;
   LAM_CUDA(cudaMemsetAsync(D.shell_pmax, 0, 4 * sizeof(unsigned long long), s));
   const bool smem_e = ncfg <= kKpShellSmemCfg;
-  const size_t smem_p = (size_t)max_len_s(P) * 36 * sizeof(double) + (smem_e ? (size_t)ncfg * 81 * sizeof(float2) : 0);
+  const size_t smem_p = smem_e ? (size_t)ncfg * 81 * sizeof(float2) : 0;
   const int block_p = std::max(64, ((4 * max_len_s(P) + 31) / 32) * 32);
-  if (smem_e) {
-    LAM_CUDA(cudaFuncSetAttribute(kp_shell<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p));
-    kp_shell<true><<<(unsigned)P.ns, block_p, smem_p, s>>>(kp);
-  } else {
-    LAM_CUDA(cudaFuncSetAttribute(kp_shell<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p));
-    kp_shell<false><<<(unsigned)P.ns, block_p, smem_p, s>>>(kp);
-  }
+  auto kern = smem_e ? (P.monoclinic ? kp_shell<true, true> : kp_shell<true, false>)
+                     : (P.monoclinic ? kp_shell<false, true> : kp_shell<false, false>);
+  LAM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p));
+  kern<<<(unsigned)P.ns, block_p, smem_p, s>>>(kp);
   LAM_CUDA(cudaGetLastError());
   prof_end(P, LAM_KERNEL_INPLANE, 2, s, ev);
   return LAM_OK;

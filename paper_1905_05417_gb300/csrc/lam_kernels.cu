@@ -74,6 +74,9 @@ struct Device {
   double* shellP = nullptr;    // n_cfg x nnz_s x 36
   size_t shellP_elems = 0;
   unsigned long long* shell_pmax = nullptr;  // 4 block maxima of |P|
+  // K-b runs on a stream of its own beside K-a, forked from and joined to the caller's stream
+  cudaStream_t kb_stream = nullptr;
+  cudaEvent_t kb_fork = nullptr, kb_join = nullptr;
   float2* shell_Edf = nullptr;  // cfgE 2^-kE per configuration, float pairs (configuration tables)
   int* shell_kE = nullptr;
   int n_sm = 0;
@@ -199,6 +202,9 @@ void free_device(Plan& P) {
     if (P.dev->ev_copied[k]) cudaEventDestroy(P.dev->ev_copied[k]);
   }
   if (P.dev->copy_stream) cudaStreamDestroy(P.dev->copy_stream);
+  if (P.dev->kb_stream) cudaStreamDestroy(P.dev->kb_stream);
+  if (P.dev->kb_fork) cudaEventDestroy(P.dev->kb_fork);
+  if (P.dev->kb_join) cudaEventDestroy(P.dev->kb_join);
   if (P.dev->shellP) cudaFree(P.dev->shellP);
   delete P.dev;
   P.dev = nullptr;
@@ -1217,23 +1223,31 @@ __global__ void __launch_bounds__(1024) kp_shell(KpShellArgs a) {
     const int ey0 = max(a.eloY[iy], a.eloY[jy]), ey1 = min(a.ehiY[iy], a.ehiY[jy]);
     const int blkT = (blk & 1) * 2 + (blk >> 1);  // the transposed block (beta, alpha)
     double g[9];
-#pragma unroll
-    for (int ab = 0; ab < 9; ++ab) g[ab] = 0.0;
+    bool first = true;  // the first element initialises the sums (one FP64 add fewer per entry)
     for (int ey = ey0; ey <= ey1; ++ey) {
       const int fy = a.firstV[ey];
       for (int ex = ex0; ex <= ex1; ++ex) {
         const int fx = a.firstU[ex];
         const int li = (iy - fy) * a.nlx + (ix - fx), lj = (jy - fy) * a.nlx + (jx - fx);
         const size_t e0 = ((size_t)ey * a.nel_u + ex) * a.npl;
+        double v[9];
         if (li <= lj) {
           const double* src = a.EG + (e0 + upper_pair(li, lj, a.nls)) * 36 + blk * 9;
 #pragma unroll
-          for (int ab = 0; ab < 9; ++ab) g[ab] += src[ab];
+          for (int ab = 0; ab < 9; ++ab) v[ab] = src[ab];
         } else {  // G^ji_(alpha a)(beta b) = G^ij_(beta b)(alpha a)
           const double* src = a.EG + (e0 + upper_pair(lj, li, a.nls)) * 36 + blkT * 9;
 #pragma unroll
-          for (int ab = 0; ab < 9; ++ab) g[ab] += src[(ab % 3) * 3 + ab / 3];
+          for (int ab = 0; ab < 9; ++ab) v[ab] = src[(ab % 3) * 3 + ab / 3];
         }
+        if (first) {
+#pragma unroll
+          for (int ab = 0; ab < 9; ++ab) g[ab] = v[ab];
+        } else {
+#pragma unroll
+          for (int ab = 0; ab < 9; ++ab) g[ab] += v[ab];
+        }
+        first = false;
       }
     }
     int e = 0;
@@ -1711,7 +1725,8 @@ __device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm,
 
 template <bool MONO, bool CHUNKED, bool DF, bool SHELL = false>
 __global__ void __maxnreg__(64) kc_stream(KcArgs a) {
-  if (!DF && a.conditional && *a.flag == 0) return;
+  // FP64 pass after a double-float one: only if a slice was not finite or no entry reached 2^-60
+  if (!DF && a.conditional && *a.flag == 0 && *a.emax >= kKcMinExp) return;
   extern __shared__ double sm[];
   int emax = 0;
   bool bad = false;
@@ -1724,11 +1739,6 @@ __global__ void __maxnreg__(64) kc_stream(KcArgs a) {
       if (any_bad) atomicOr(a.flag, 1);
     }
   }
-}
-
-// After the double-float pass: flag the FP64 pass when no entry reached 2^-60.
-__global__ void kc_check(int* flag, const int* emax) {
-  if (*emax < kKcMinExp) *flag = 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -2121,8 +2131,8 @@ static KcArgs kc_args(const Plan& P, double* values) {
   return k;
 }
 
-// Double-float pass, the exponent check, then the FP64 pass that runs only if
-// the flag is set (2 CTAs per SM, each looping over rows).
+// Double-float pass, then the FP64 pass (2 CTAs per SM, each looping over rows),
+// whose CTAs exit at once unless a slice was not finite or no entry reached 2^-60.
 template <bool MONO, bool CHUNKED, bool SHELL = false>
 static lam_status launch_kcs(const Plan& P, const KcArgs& k, cudaStream_t s) {
   const size_t smem = kcs_smem(P);
@@ -2134,14 +2144,12 @@ static lam_status launch_kcs(const Plan& P, const KcArgs& k, cudaStream_t s) {
   cudaEvent_t ev = prof_begin(const_cast<Plan&>(P), s);
   kc_stream<MONO, CHUNKED, true, SHELL><<<(unsigned)P.ns, kcs_block(P), smem, s>>>(k);
   LAM_CUDA(cudaGetLastError());
-  kc_check<<<1, 1, 0, s>>>(k.flag, k.emax);
-  LAM_CUDA(cudaGetLastError());
   KcArgs k64 = k;
   k64.conditional = 1;
   const int64_t grid64 = std::min<int64_t>(P.ns, (int64_t)kcs_ctas_per_sm(P) * std::max(1, P.dev->n_sm));
   kc_stream<MONO, CHUNKED, false, SHELL><<<(unsigned)grid64, kcs_block(P), smem, s>>>(k64);
   LAM_CUDA(cudaGetLastError());
-  prof_end(const_cast<Plan&>(P), LAM_KERNEL_COMBINE, 3, s, ev);
+  prof_end(const_cast<Plan&>(P), LAM_KERNEL_COMBINE, 2, s, ev);
   return LAM_OK;
 }
 
@@ -2269,11 +2277,23 @@ static lam_status split_integrals(Plan& P, cudaStream_t s) {
   kb.wT = D.wT;
   kb.q = D.q;
   kb.qdf = D.qdf;
-  cudaEvent_t ev = prof_begin(P, s);
-  kb_thickness<<<(unsigned)((P.nnz_t + 127) / 128), 128, 0, s>>>(kb);
+  // K-b (a few microseconds) beside K-a: forked after the work already on the
+  // caller's stream (the previous combine reads Q), joined before the combine
+  if (!D.kb_stream) {
+    LAM_CUDA(cudaStreamCreateWithFlags(&D.kb_stream, cudaStreamNonBlocking));
+    LAM_CUDA(cudaEventCreateWithFlags(&D.kb_fork, cudaEventDisableTiming));
+    LAM_CUDA(cudaEventCreateWithFlags(&D.kb_join, cudaEventDisableTiming));
+  }
+  LAM_CUDA(cudaEventRecord(D.kb_fork, s));
+  LAM_CUDA(cudaStreamWaitEvent(D.kb_stream, D.kb_fork, 0));
+  cudaEvent_t ev = prof_begin(P, D.kb_stream);
+  kb_thickness<<<(unsigned)((P.nnz_t + 127) / 128), 128, 0, D.kb_stream>>>(kb);
   LAM_CUDA(cudaGetLastError());
-  prof_end(P, LAM_KERNEL_THICKNESS, 1, s, ev);
-  return P.shell ? shell_operators(P, s) : inplane_gram(P, s);
+  prof_end(P, LAM_KERNEL_THICKNESS, 1, D.kb_stream, ev);
+  LAM_CUDA(cudaEventRecord(D.kb_join, D.kb_stream));
+  const lam_status st = P.shell ? shell_operators(P, s) : inplane_gram(P, s);
+  LAM_CUDA(cudaStreamWaitEvent(s, D.kb_join, 0));
+  return st;
 }
 
 // ---------------------------------------------------------------------------

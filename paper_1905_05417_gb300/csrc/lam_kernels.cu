@@ -1191,6 +1191,7 @@ struct KpShellArgs {
   const int* kE;
   double* P;
   unsigned long long* pmax;  // largest |P| per block (bit patterns; positive doubles order as integers)
+  int full;                  // 0: pairs with j_s >= i_s only (the combine reads the others transposed)
 };
 
 // SMEM_E: the configurations' D tables staged in shared memory (few configurations).
@@ -1214,10 +1215,12 @@ __global__ void __launch_bounds__(1024) kp_shell(KpShellArgs a) {
   // elements (row-major element order), divided by 2^kg as float pairs in
   // registers, then its 9 entries of P for every configuration
   unsigned long long pm = 0ull;  // this thread's largest |P| (bit pattern: integer max, off the FP64 pipe)
-  const int item = threadIdx.x;
-  const int blk = item & 3;
-  if (item < 4 * ls) {
-    const int ks = item >> 2;
+  // P^ji_(alpha beta)[c][d] = P^ij_(beta alpha)[d][c]: unless asked for every pair,
+  // only j_s >= i_s is formed, the neighbours from the row's own position on
+  const int ks0 = a.full ? 0 : (iy - a.loY[iy]) * lx + (ix - a.loX[ix]);
+  const int blk = threadIdx.x & 3;  // the same for every item of this thread (blockDim is a multiple of 32)
+  for (int item = threadIdx.x; item < 4 * (ls - ks0); item += blockDim.x) {
+    const int ks = ks0 + (item >> 2);
     const int jx = a.loX[ix] + ks % lx, jy = a.loY[iy] + ks / lx;
     const int ex0 = max(a.eloX[ix], a.eloX[jx]), ex1 = min(a.ehiX[ix], a.ehiX[jx]);
     const int ey0 = max(a.eloY[iy], a.eloY[jy]), ey1 = min(a.ehiY[iy], a.ehiY[jy]);
@@ -1335,6 +1338,23 @@ struct KcArgs {
 };
 
 
+// P of a general extrusion for entry (c, d) of the in-plane pair (i_s, k_s-th
+// neighbour j_s): pairs with j_s >= i_s hold it (blocks at 0, 9, 18, 27); the
+// others read the mirror pair transposed, P^ij_(alpha beta)[c][d] =
+// P^ji_(beta alpha)[d][c], so blocks 12 and 21 trade places.
+struct ShellPRef {
+  const double* p;  // entry of block 11 of configuration 0
+  int o12, o21;     // offsets of blocks 12 and 21
+};
+__device__ __forceinline__ ShellPRef shell_p_ref(const KcArgs& a, int64_t is, int ix, int iy, int lx, int64_t ls0,
+                                                 int ks, int c, int d) {
+  const int jx = a.loX[ix] + ks % lx, jy = a.loY[iy] + ks / lx;
+  const int64_t js = (int64_t)jy * a.nx + jx;
+  if (js >= is) return ShellPRef{a.shellP + (size_t)(ls0 + ks) * 36 + c * 3 + d, 9, 18};
+  const int ksT = (iy - a.loY[jy]) * a.lenX[jx] + (ix - a.loX[jx]);
+  return ShellPRef{a.shellP + (size_t)(a.LSb[js] + ksT) * 36 + d * 3 + c, 18, 9};
+}
+
 template <bool MONO, bool CHUNKED, bool GATHER, bool SHELL = false>
 __global__ void __launch_bounds__(1024, 2) kc_combine(KcArgs a) {
   static_assert(!(SHELL && MONO), "a general extrusion couples every block");
@@ -1411,12 +1431,14 @@ __global__ void __launch_bounds__(1024, 2) kc_combine(KcArgs a) {
   const int cd = c * 3 + d;
   // P for every configuration, into shared memory (indexed by the class terms)
   const bool block_type = ((c == 2) == (d == 2));
+  ShellPRef pr{nullptr, 9, 18};
+  if (SHELL) pr = shell_p_ref(a, is, ix, iy, lx, ls0, ks, c, d);
   for (int m = 0; m < a.ncfg; ++m) {
     const double* E = a.cfgE + (size_t)m * 81 + cd * 9;
-    const double* Pp = SHELL ? a.shellP + ((size_t)m * a.nnz_s + ls0 + ks) * 36 + cd : nullptr;
+    const double* Pp = SHELL ? pr.p + (size_t)m * a.nnz_s * 36 : nullptr;
     const double p11 = SHELL ? Pp[0] : E[0] * g[0] + E[1] * g[1] + E[3] * g[3] + E[4] * g[4];
-    const double p12 = SHELL ? Pp[9] : E[2] * g[2] + E[5] * g[5];
-    const double p21 = SHELL ? Pp[18] : E[6] * g[6] + E[7] * g[7];
+    const double p12 = SHELL ? Pp[pr.o12] : E[2] * g[2] + E[5] * g[5];
+    const double p21 = SHELL ? Pp[pr.o21] : E[6] * g[6] + E[7] * g[7];
     const double p22 = SHELL ? Pp[27] : E[8] * g[8];
     if (MONO) {
       Ps[(m * 2 + 0) * nthr + tid] = block_type ? p11 : p12;
@@ -1558,12 +1580,20 @@ __device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm,
   // general extrusion, double-float pass: block j of P enters divided by 2^ps[j]
   // (its largest entry in [1, 2)) and Q_j multiplied by it (exact), so that the
   // float pairs hold blocks of very different magnitude (P_22 / P_11 ~ L^2).
+  // (blocks 12 and 21 share one scale: over all pairs max |P_12| = max |P_21|,
+  // and only pairs j_s >= i_s are formed)
   int ps[4] = {0, 0, 0, 0};
-  if (SHELL && DF) {
+  ShellPRef pref{nullptr, 9, 18};
+  if (SHELL) {
+    if (active) pref = shell_p_ref(a, is, ix, iy, lx, ls0, ks, c, d);
+    if (DF) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const double mx = __longlong_as_double((long long)a.shell_pmax[j]);
-      ps[j] = mx > 0.0 ? exp_field(mx) - 1023 : 0;
+      for (int j = 0; j < 4; ++j) {
+        const int jj = (j == 1 || j == 2) ? 3 - j : j;
+        const unsigned long long bits = max(a.shell_pmax[j], a.shell_pmax[jj]);
+        const double mx = __longlong_as_double((long long)bits);
+        ps[j] = mx > 0.0 ? exp_field(mx) - 1023 : 0;
+      }
     }
   }
   const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
@@ -1607,10 +1637,10 @@ __device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm,
             cur = m;
             const float2* E = a.cfgEdf + (size_t)m * 81 + cd * 9;
             if (SHELL) {
-              const double* Pp = a.shellP + ((size_t)m * a.nnz_s + ls0 + ks) * 36 + cd;
+              const double* Pp = pref.p + (size_t)m * a.nnz_s * 36;
               split_df_off(Pp[0], ps[0], ah, al);
-              split_df_off(Pp[9], ps[1], bh, bl);
-              split_df_off(Pp[18], ps[2], ch_, cl);
+              split_df_off(Pp[pref.o12], ps[1], bh, bl);
+              split_df_off(Pp[pref.o21], ps[2], ch_, cl);
               split_df_off(Pp[27], ps[3], dh, dl);
             } else if (MONO) {
               if (block_type) {
@@ -1670,10 +1700,10 @@ __device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm,
             cur = m;
             const double* E = a.cfgE + (size_t)m * 81 + cd * 9;
             if (SHELL) {
-              const double* Pp = a.shellP + ((size_t)m * a.nnz_s + ls0 + ks) * 36 + cd;
+              const double* Pp = pref.p + (size_t)m * a.nnz_s * 36;
               p11 = Pp[0];
-              p12 = Pp[9];
-              p21 = Pp[18];
+              p12 = Pp[pref.o12];
+              p21 = Pp[pref.o21];
               p22 = Pp[27];
             } else if (MONO) {
               if (block_type) {
@@ -2192,7 +2222,7 @@ static lam_status inplane_gram(Plan& P, cudaStream_t s) {
 
 // General extrusion: the 6 x 6 element Gram blocks (ka_shell), then P of
 // every configuration per in-plane pair (kp_shell), into D.shellP.
-static lam_status shell_operators(Plan& P, cudaStream_t s) {
+static lam_status shell_operators(Plan& P, cudaStream_t s, bool full) {
   Device& D = *P.dev;
   const int nel = P.u.nel * P.v.nel, npl = ka_npl(P), ncfg = (int)P.cfg_mat.size();
   if (!D.shellEG && alloc_dev(D.allocs, &D.shellEG, (size_t)nel * 36 * npl) != LAM_OK) return LAM_ERR_OOM;
@@ -2245,10 +2275,12 @@ static lam_status shell_operators(Plan& P, cudaStream_t s) {
   kp.kE = D.shell_kE;
   kp.P = D.shellP;
   kp.pmax = D.shell_pmax;
+  kp.full = full ? 1 : 0;
   LAM_CUDA(cudaMemsetAsync(D.shell_pmax, 0, 4 * sizeof(unsigned long long), s));
   const bool smem_e = ncfg <= kKpShellSmemCfg;
   const size_t smem_p = smem_e ? (size_t)ncfg * 81 * sizeof(float2) : 0;
-  const int block_p = std::max(64, ((4 * max_len_s(P) + 31) / 32) * 32);
+  // threads for the pairs j_s >= i_s of an interior row (about half); rows with more loop
+  const int block_p = std::max(64, ((4 * (max_len_s(P) / 2 + 1) + 31) / 32) * 32);
   auto kern = smem_e ? (P.monoclinic ? kp_shell<true, true> : kp_shell<true, false>)
                      : (P.monoclinic ? kp_shell<false, true> : kp_shell<false, false>);
   LAM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p));
@@ -2291,7 +2323,7 @@ static lam_status split_integrals(Plan& P, cudaStream_t s) {
   LAM_CUDA(cudaGetLastError());
   prof_end(P, LAM_KERNEL_THICKNESS, 1, D.kb_stream, ev);
   LAM_CUDA(cudaEventRecord(D.kb_join, D.kb_stream));
-  const lam_status st = P.shell ? shell_operators(P, s) : inplane_gram(P, s);
+  const lam_status st = P.shell ? shell_operators(P, s, false) : inplane_gram(P, s);
   LAM_CUDA(cudaStreamWaitEvent(s, D.kb_join, 0));
   return st;
 }
@@ -3538,7 +3570,7 @@ lam_status lam_inplane_operators(lam_plan* plan, int32_t ply, int32_t method, do
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int m = P.ply_cfg[ply];
   if (method == LAM_P_FROM_GRAM && P.shell) {  // the 6 x 6 Gram blocks and P of every configuration
-    if ((st = lam::shell_operators(P, s)) != LAM_OK) return st;
+    if ((st = lam::shell_operators(P, s, true)) != LAM_OK) return st;
     LAM_CUDA(cudaMemcpyAsync(d_P, D.shellP + (size_t)m * P.nnz_s * 36, (size_t)P.nnz_s * 36 * sizeof(double),
                              cudaMemcpyDeviceToDevice, s));
     return LAM_OK;

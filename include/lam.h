@@ -92,9 +92,10 @@ typedef struct {
  * S = (x, y, 0) with a = e_z (ctrl_dim 2, extrusion zero) is the plate case
  * of the split kernels; any other S or a (a "shell") is a general extrusion,
  * assembled by the split and standard paths (lam_assemble_split,
- * lam_assemble_split_host, lam_assemble_standard, lam_inplane_operators) and
- * refused with LAM_ERR_UNSUPPORTED by lam_adjoint, lam_batch_create and
- * lam_assemble_split_noalloc. DF = [dS/dxi1 | dS/dxi2 | a] must be regular. */
+ * lam_assemble_split_host, lam_assemble_standard, lam_inplane_operators, and
+ * in batches, one by one), differentiated by lam_adjoint (FP64 contraction)
+ * and refused with LAM_ERR_UNSUPPORTED by lam_assemble_split_noalloc.
+ * DF = [dS/dxi1 | dS/dxi2 | a] must be regular. */
 typedef struct {
   lam_basis1d u;          /* xi^1 direction, index ix */
   lam_basis1d v;          /* xi^2 direction, index iy */
@@ -265,6 +266,10 @@ typedef struct {
  * magnitude. Entries below 2^-80 next to larger ones contribute with an
  * absolute error below 2^-100 of their own size. LAM_ADJOINT_FP64 forces the
  * FP64 evaluation.
+ * A general extrusion (lam_inplane.shell): every (a, b) of D_l meets all four
+ * thickness types through the 6 x 6 Gram blocks G_(alpha a)(beta b), and the
+ * contraction, CSR or low-rank, runs in FP64 (workspace 8 * 36 * nnz_inplane
+ * bytes more).
  * The in-plane Gram blocks depend on the plan's geometry only, which never
  * changes: the first call computes them and later calls reuse them
  * (lam_inplane_operators with LAM_P_FROM_GRAM discards the copy). Workspace: about
@@ -292,9 +297,10 @@ typedef struct lam_batch lam_batch;
 
 typedef struct {
   int32_t n_plans;
-  int32_t n_meshes;        /* distinct in-plane discretisations (K-a runs once for each) */
+  int32_t n_meshes;        /* distinct planar in-plane discretisations (K-a runs once for each) */
   int64_t nnz_total;       /* stored entries over all instances */
-  int32_t n_persistent;    /* instances combined by the persistent launch (the others: lam_assemble_split) */
+  int32_t n_persistent;    /* instances combined by the persistent launch (the others -- class-major rows,
+                              general extrusions -- by lam_assemble_split after it) */
   int32_t ctas_per_sm;     /* chosen by the autotuner, 0 before the first lam_batch_assemble */
   int32_t graph;           /* 1 once the launches are replayed from a CUDA graph */
   int32_t reserved;

@@ -74,6 +74,9 @@ struct Device {
   double* shellP = nullptr;    // n_cfg x nnz_s x 36
   size_t shellP_elems = 0;
   unsigned long long* shell_pmax = nullptr;  // 4 block maxima of |P|
+  // adjoint of a general extrusion: the assembled 6 x 6 Gram blocks, and unit scales
+  double* adj_G36 = nullptr;   // nnz_s x 36
+  double* adj_ones = nullptr;  // 9 x 1.0
   // K-b runs on a stream of its own beside K-a, forked from and joined to the caller's stream
   cudaStream_t kb_stream = nullptr;
   cudaEvent_t kb_fork = nullptr, kb_join = nullptr;
@@ -1290,6 +1293,45 @@ __global__ void __launch_bounds__(1024) kp_shell(KpShellArgs a) {
   if (threadIdx.x < 4) atomicMax(&a.pmax[threadIdx.x], smax[threadIdx.x]);
 }
 
+// The assembled 6 x 6 Gram blocks of every in-plane pair of a general extrusion
+// (the adjoint's G): CTA per in-plane row, thread per (k_s, block), the block's
+// 9 entries summed over the shared elements in row-major element order, FP64.
+__global__ void __launch_bounds__(256) kg_shell(KpShellArgs a, double* __restrict__ G36) {
+  const int64_t is = blockIdx.x;
+  const int ix = (int)(is % a.nx), iy = (int)(is / a.nx);
+  const int lx = a.lenX[ix], ls = lx * a.lenY[iy];
+  const int64_t ls0 = a.LSb[is];
+  for (int item = threadIdx.x; item < 4 * ls; item += blockDim.x) {
+    const int ks = item >> 2, blk = item & 3, blkT = (blk & 1) * 2 + (blk >> 1);
+    const int jx = a.loX[ix] + ks % lx, jy = a.loY[iy] + ks / lx;
+    const int ex0 = max(a.eloX[ix], a.eloX[jx]), ex1 = min(a.ehiX[ix], a.ehiX[jx]);
+    const int ey0 = max(a.eloY[iy], a.eloY[jy]), ey1 = min(a.ehiY[iy], a.ehiY[jy]);
+    double g[9];
+#pragma unroll
+    for (int ab = 0; ab < 9; ++ab) g[ab] = 0.0;
+    for (int ey = ey0; ey <= ey1; ++ey) {
+      const int fy = a.firstV[ey];
+      for (int ex = ex0; ex <= ex1; ++ex) {
+        const int fx = a.firstU[ex];
+        const int li = (iy - fy) * a.nlx + (ix - fx), lj = (jy - fy) * a.nlx + (jx - fx);
+        const size_t e0 = ((size_t)ey * a.nel_u + ex) * a.npl;
+        if (li <= lj) {
+          const double* src = a.EG + (e0 + upper_pair(li, lj, a.nls)) * 36 + blk * 9;
+#pragma unroll
+          for (int ab = 0; ab < 9; ++ab) g[ab] += src[ab];
+        } else {  // G^ji_(alpha a)(beta b) = G^ij_(beta b)(alpha a)
+          const double* src = a.EG + (e0 + upper_pair(lj, li, a.nls)) * 36 + blkT * 9;
+#pragma unroll
+          for (int ab = 0; ab < 9; ++ab) g[ab] += src[(ab % 3) * 3 + ab / 3];
+        }
+      }
+    }
+    double* out = G36 + (ls0 + ks) * 36 + blk * 9;
+#pragma unroll
+    for (int ab = 0; ab < 9; ++ab) out[ab] = g[ab];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // K-c: fused combine. One CTA per in-plane row i_s; thread <-> (c, k_s, d) of
 // that row. The CTA first forms the row's G blocks (gathered from the element
@@ -2222,10 +2264,49 @@ static lam_status inplane_gram(Plan& P, cudaStream_t s) {
 
 // General extrusion: the 6 x 6 element Gram blocks (ka_shell), then P of
 // every configuration per in-plane pair (kp_shell), into D.shellP.
+static KpShellArgs kp_shell_args(const Plan& P) {
+  const Device& D = *P.dev;
+  KpShellArgs kp{};
+  kp.nx = P.u.n;
+  kp.nel_u = P.u.nel;
+  kp.nlx = P.u.p + 1;
+  kp.nls = ka_nls(P);
+  kp.npl = ka_npl(P);
+  kp.ncfg = (int)P.cfg_mat.size();
+  kp.nnz_s = P.nnz_s;
+  kp.LSb = D.LSb;
+  kp.lenX = D.lenX;
+  kp.lenY = D.lenY;
+  kp.loX = D.loX;
+  kp.loY = D.loY;
+  kp.eloX = D.eloX;
+  kp.ehiX = D.ehiX;
+  kp.eloY = D.eloY;
+  kp.ehiY = D.ehiY;
+  kp.firstU = D.firstU;
+  kp.firstV = D.firstV;
+  kp.EG = D.shellEG;
+  return kp;
+}
+
+// K-a of a general extrusion: the 6 x 6 element Gram blocks into D.shellEG.
+static lam_status shell_element_gram(Plan& P, cudaStream_t s) {
+  Device& D = *P.dev;
+  const int nel = P.u.nel * P.v.nel, npl = ka_npl(P);
+  if (!D.shellEG && alloc_dev(D.allocs, &D.shellEG, (size_t)nel * 36 * npl) != LAM_OK) return LAM_ERR_OOM;
+  KaShellArgs ka{};
+  ka.ip = inplane_args(P);
+  ka.EG = D.shellEG;
+  const size_t smem = ka_shell_smem(P);
+  LAM_CUDA(cudaFuncSetAttribute(ka_shell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ka_shell<<<(unsigned)nel, 256, smem, s>>>(ka);
+  LAM_CUDA(cudaGetLastError());
+  return LAM_OK;
+}
+
 static lam_status shell_operators(Plan& P, cudaStream_t s, bool full) {
   Device& D = *P.dev;
-  const int nel = P.u.nel * P.v.nel, npl = ka_npl(P), ncfg = (int)P.cfg_mat.size();
-  if (!D.shellEG && alloc_dev(D.allocs, &D.shellEG, (size_t)nel * 36 * npl) != LAM_OK) return LAM_ERR_OOM;
+  const int ncfg = (int)P.cfg_mat.size();
   if (!D.shell_pmax) {
     double* pm = nullptr;
     if (alloc_dev(D.allocs, &pm, 4) != LAM_OK) return LAM_ERR_OOM;
@@ -2243,34 +2324,10 @@ static lam_status shell_operators(Plan& P, cudaStream_t s, bool full) {
     }
     D.shellP_elems = need;
   }
-  KaShellArgs ka{};
-  ka.ip = inplane_args(P);
-  ka.EG = D.shellEG;
-  const size_t smem = ka_shell_smem(P);
-  LAM_CUDA(cudaFuncSetAttribute(ka_shell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   cudaEvent_t ev = prof_begin(P, s);
-  ka_shell<<<(unsigned)nel, 256, smem, s>>>(ka);
-  LAM_CUDA(cudaGetLastError());
-  KpShellArgs kp{};
-  kp.nx = P.u.n;
-  kp.nel_u = P.u.nel;
-  kp.nlx = P.u.p + 1;
-  kp.nls = ka_nls(P);
-  kp.npl = npl;
-  kp.ncfg = ncfg;
-  kp.nnz_s = P.nnz_s;
-  kp.LSb = D.LSb;
-  kp.lenX = D.lenX;
-  kp.lenY = D.lenY;
-  kp.loX = D.loX;
-  kp.loY = D.loY;
-  kp.eloX = D.eloX;
-  kp.ehiX = D.ehiX;
-  kp.eloY = D.eloY;
-  kp.ehiY = D.ehiY;
-  kp.firstU = D.firstU;
-  kp.firstV = D.firstV;
-  kp.EG = D.shellEG;
+  lam_status st = shell_element_gram(P, s);
+  if (st != LAM_OK) return st;
+  KpShellArgs kp = kp_shell_args(P);
   kp.Edf = D.shell_Edf;
   kp.kE = D.shell_kE;
   kp.P = D.shellP;
@@ -2443,10 +2500,18 @@ struct AdjArgs {
   int* flag;                // set by the double-float pass on a non-finite partial
   int* emax;                // largest biased exponent of the cotangent seen by that pass
   int conditional;          // run only if the double-float result is not kept
+  // general extrusion (FP64 pass): the 6 x 6 Gram blocks G_(alpha a)(beta b) of
+  // every in-plane pair, unscaled, and the scales of the four Q types
+  const double* G36;        // nnz_s x 36, [blk * 9 + ab]
+  double qs[4];
 };
 
-template <bool LOWRANK, bool DF>
+// SHELL: a general extrusion, whose entry (c, d) of K couples every (a, b) of
+// D_l through all four thickness types: S[ab] += sum_type z_type G_(type)(ab)
+// (FP64 only).
+template <bool LOWRANK, bool DF, bool SHELL = false>
 __global__ void __launch_bounds__(1024) adj_ply(AdjArgs a) {
+  static_assert(!(SHELL && DF), "general extrusions take the FP64 pass");
   if (a.conditional && *a.flag == 0 && *a.emax >= kAdjMinExp && *a.emax <= kAdjMaxExp) return;
   extern __shared__ double sm[];
   const int l = blockIdx.y, chunk = blockIdx.x;
@@ -2568,6 +2633,11 @@ __global__ void __launch_bounds__(1024) adj_ply(AdjArgs a) {
         df_mul(zh[ty], zl[ty], gq.x, gq.y, p, e);
         df_add(p, e, Sh[ab], Sl[ab]);
       }
+    } else if (SHELL) {
+      const double* g36 = a.G36 + (ls0 + ks) * 36;
+      const double z0 = z[0] * a.qs[0], z1 = z[1] * a.qs[1], z2 = z[2] * a.qs[2], z3 = z[3] * a.qs[3];
+#pragma unroll
+      for (int ab = 0; ab < 9; ++ab) S[ab] += z0 * g36[ab] + z1 * g36[9 + ab] + z2 * g36[18 + ab] + z3 * g36[27 + ab];
     } else {
 #pragma unroll
       for (int ab = 0; ab < 9; ++ab) {
@@ -2912,12 +2982,13 @@ static lam_status ensure_adjoint(Plan& P) {
   return LAM_OK;
 }
 
-template <bool LOWRANK, bool DF>
+template <bool LOWRANK, bool DF, bool SHELL = false>
 static lam_status launch_adj_ply(const Plan& P, const AdjArgs& a, cudaStream_t s) {
   const size_t smem = adj_smem(P);
-  LAM_CUDA(cudaFuncSetAttribute(adj_ply<LOWRANK, DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LAM_CUDA(cudaFuncSetAttribute(adj_ply<LOWRANK, DF, SHELL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
   dim3 grid((unsigned)adj_nchunks(P), (unsigned)P.plies.size());
-  adj_ply<LOWRANK, DF><<<grid, adj_block(P), smem, s>>>(a);
+  adj_ply<LOWRANK, DF, SHELL><<<grid, adj_block(P), smem, s>>>(a);
   LAM_CUDA(cudaGetLastError());
   return LAM_OK;
 }
@@ -2962,8 +3033,90 @@ static lam_status gather_gram(Plan& P, cudaStream_t s) {
   return LAM_OK;
 }
 
+// General extrusion: every (a, b) of D_l meets all four thickness types, so the
+// contraction runs in FP64 on unscaled 6 x 6 Gram blocks (assembled on the
+// first call and kept) with the Q types scaled back inside the kernel.
+static lam_status adjoint_shell(Plan& P, const lam_cotangent& cot, double* dC, double* dtheta, double* dDout,
+                                cudaStream_t s) {
+  Device& D = *P.dev;
+  lam_status st;
+  if (!D.adj_ones) {
+    const std::vector<double> ones(9, 1.0);
+    if ((st = upload(P, D.allocs, &D.adj_ones, ones)) != LAM_OK) return st;
+  }
+  if (!D.adj_g_cached) {
+    if (!D.adj_G36 && (st = alloc_dev(D.allocs, &D.adj_G36, (size_t)36 * P.nnz_s)) != LAM_OK) return st;
+    if ((st = shell_element_gram(P, s)) != LAM_OK) return st;
+    cudaEvent_t ev0 = prof_begin(P, s);
+    kg_shell<<<(unsigned)P.ns, 256, 0, s>>>(kp_shell_args(P), D.adj_G36);
+    LAM_CUDA(cudaGetLastError());
+    prof_end(P, LAM_KERNEL_ADJOINT_AUX, 1, s, ev0);
+    D.adj_g_cached = true;
+  }
+  AdjArgs a{};
+  a.ns = P.ns;
+  a.n_dof = P.n_dof;
+  a.nx = P.u.n;
+  a.lsp = max_len_s(P);
+  a.nchunks = adj_nchunks(P);
+  a.mt = P.adj_max_terms;
+  a.LSb = D.LSb;
+  a.lenX = D.lenX;
+  a.lenY = D.lenY;
+  a.loX = D.loX;
+  a.loY = D.loY;
+  a.term_begin = D.adj_begin;
+  a.term_pair = D.adj_pair;
+  a.term_q = D.adj_q;
+  a.term_qdf = D.adj_qdf;
+  a.tp_A = D.tp_A;
+  a.tp_lt = D.tp_lt;
+  a.tp_k = D.tp_k;
+  a.tp_row = D.tp_row;
+  a.tp_col = D.tp_col;
+  a.gbar = cot.values;
+  a.u = cot.u;
+  a.v = cot.v;
+  a.rank = cot.rank;
+  a.G36 = D.adj_G36;
+  for (int k = 0; k < 4; ++k) a.qs[k] = P.adj_qscale[k];
+  a.partial = D.adj_partial;
+  a.flag = D.adj_flag;
+  a.emax = D.adj_flag + 1;
+  a.conditional = 0;
+  cudaEvent_t ev = prof_begin(P, s);
+  st = cot.kind == LAM_COTANGENT_LOWRANK ? launch_adj_ply<true, false, true>(P, a, s)
+                                         : launch_adj_ply<false, false, true>(P, a, s);
+  if (st != LAM_OK) return st;
+  prof_end(P, LAM_KERNEL_ADJOINT, 1, s, ev);
+  ev = prof_begin(P, s);
+  AdjReduceArgs r{};
+  r.nchunks = a.nchunks;
+  for (int k = 0; k < 4; ++k) r.qscale[k] = 1.0;
+  r.gscale = D.adj_ones;
+  r.partial = D.adj_partial;
+  r.ply_M = D.ply_M;
+  r.ply_dM = D.ply_dM;
+  r.mat_C = D.mat_C;
+  r.ply_mat = D.ply_mat;
+  r.dD = dDout;
+  r.dtheta = dtheta;
+  r.plyC = D.adj_plyC;
+  adj_reduce<<<(unsigned)P.plies.size(), 384, 0, s>>>(r);
+  LAM_CUDA(cudaGetLastError());
+  int aux = 1;
+  if (dC) {
+    adj_material<<<1, 256, 0, s>>>((int)P.plies.size(), (int)P.mats.size(), D.ply_mat, D.adj_plyC, dC);
+    LAM_CUDA(cudaGetLastError());
+    ++aux;
+  }
+  prof_end(P, LAM_KERNEL_ADJOINT_AUX, aux, s, ev);
+  return LAM_OK;
+}
+
 static lam_status adjoint(Plan& P, const lam_cotangent& cot, double* dC, double* dtheta, double* dDout,
                           cudaStream_t s) {
+  if (P.shell) return adjoint_shell(P, cot, dC, dtheta, dDout, s);
   Device& D = *P.dev;
   lam_status st;
   double* gscale = reinterpret_cast<double*>(D.adj_gmax + 9);
@@ -3533,10 +3686,6 @@ lam_status lam_adjoint(lam_plan* plan, const lam_cotangent* cot, double* d_dC, d
     return LAM_ERR_INVALID_ARG;
   }
   lam::Plan& P = plan->p;
-  if (P.shell) {
-    lam::set_error("lam_adjoint: general extrusion maps are not supported");
-    return LAM_ERR_UNSUPPORTED;
-  }
   if (P.adj_max_terms > lam::kAdjMaxTerms) {
     lam::set_error("lam_adjoint: a ply meets %d thickness pairs (at most %d)", P.adj_max_terms, lam::kAdjMaxTerms);
     return LAM_ERR_UNSUPPORTED;
@@ -4120,10 +4269,6 @@ lam_status lam_batch_create(lam_batch** out, lam_plan* const* plans, int32_t n_p
         lam::set_error("lam_batch_create: plan %d appears twice", i);
         return LAM_ERR_INVALID_ARG;
       }
-    if (plans[i]->p.shell) {
-      lam::set_error("lam_batch_create: plan %d is a general extrusion (not supported in batches)", i);
-      return LAM_ERR_UNSUPPORTED;
-    }
   }
   lam_batch* B = new (std::nothrow) lam_batch();
   if (!B) {
@@ -4157,6 +4302,7 @@ lam_status lam_batch_create(lam_batch** out, lam_plan* const* plans, int32_t n_p
   // distinct meshes and their shared Gram-block buffers
   std::vector<int> mesh_of(n_plans, -1), mesh_rep;
   for (int i = 0; i < n_plans; ++i) {
+    if (plans[i]->p.shell) continue;  // general extrusions are assembled one by one (below)
     for (size_t g = 0; g < mesh_rep.size() && mesh_of[i] < 0; ++g)
       if (lam::same_mesh(plans[mesh_rep[g]]->p, plans[i]->p)) mesh_of[i] = (int)g;
     if (mesh_of[i] < 0) {
@@ -4183,7 +4329,7 @@ lam_status lam_batch_create(lam_batch** out, lam_plan* const* plans, int32_t n_p
   // instances of the persistent combine, largest first
   B->inst_slot.assign(n_plans, -1);
   for (int i = 0; i < n_plans; ++i) {
-    if (lam::use_stream(plans[i]->p))
+    if (!plans[i]->p.shell && lam::use_stream(plans[i]->p))
       B->persistent.push_back(i);
     else
       B->fallback.push_back(i);

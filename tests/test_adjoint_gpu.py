@@ -68,6 +68,12 @@ CASES = {
     "quartic_inplane": lambda: W.laminate("p4", W.BSPLINE, 4, 5, [0, 45], 0.02, mapping=W.curved_map(),
                                           n_el_y=4, thickness_degree=1),
     "single_element_single_ply": lambda: W.laminate("min", W.BSPLINE, 1, 1, [30.0], 0.5, thickness_degree=1),
+    # general extrusions (Eq. extrusion): the FP64 contraction over the 6 x 6 Gram blocks
+    "shell_bump_p2": lambda: W.shell_plate(n_el=3, degree=2, repeats=1, extrusion=(0.3, 0.2, 0.9)),
+    "shell_triclinic": lambda: W.laminate(
+        "shtri", W.BSPLINE, 2, 3, [0, 20, -35, 90], 0.01, mapping=W.bump_map(0.15), extrusion=(0.1, -0.2, 1.0),
+        materials=np.array([W.random_C21(np.random.default_rng(11)), W.random_C21(np.random.default_rng(12))]),
+        ply_material=[0, 1, 1, 0]),
 }
 
 
@@ -93,7 +99,8 @@ def test_csr_cotangent_parity(L, name, fp64):
                                                       np.abs(ref[2]).max() * np.abs(lam.C21).max()), "dL/dtheta"
 
 
-@pytest.mark.parametrize("name", ["curved_p3_3x3_8plies", "lagrange_q2_3x3", "single_thickness_element"])
+@pytest.mark.parametrize("name", ["curved_p3_3x3_8plies", "lagrange_q2_3x3", "single_thickness_element",
+                                  "shell_bump_p2"])
 def test_lowrank_cotangent_parity(L, name):
     lam = CASES[name]()
     rp, col = O.pattern(lam)

@@ -107,3 +107,29 @@ def test_batch_of_seeded_laminates(L):
         torch.cuda.synchronize()
         assert torch.equal(v, out[k]), k
     b.close()
+
+
+def test_batch_with_general_extrusions(L):
+    """Shells (general extrusion maps) in a batch: assembled one by one after the
+    persistent launch, outside the mesh groups even when they share a plate's
+    in-plane discretisation; bit for bit against their own plans and against
+    the oracle."""
+    import torch
+    plate = W.curved_plate(n_el=3, degree=3, repeats=1)
+    shell_same_mesh = W.shell_plate(n_el=3, degree=3, repeats=1)        # the plate's knots, lifted and tilted
+    shell_other = W.laminate("sh", W.BSPLINE, 2, 4, [0, 45, 90], 0.004, mapping=W.bump_map(0.1), n_el_y=3,
+                             extrusion=(0.1, -0.2, 1.0))
+    lams = [plate, shell_same_mesh, shell_other]
+    plans = [L.Plan.from_laminate(l) for l in lams]
+    ref = [p.assemble_split().cpu().numpy() for p in plans]
+    b = L.Batch(plans)
+    info = b.info
+    assert info["n_meshes"] == 1 and info["n_persistent"] == 1
+    out = b.assemble()
+    torch.cuda.synchronize()
+    for k in range(len(plans)):
+        assert np.array_equal(out[k].cpu().numpy(), ref[k]), k
+    for k in (1, 2):
+        rp, col, val = O.assemble(lams[k])
+        assert np.abs(out[k].cpu().numpy() - val).max() <= 1e-12 * np.abs(val).max()
+    b.close()

@@ -193,3 +193,61 @@ def test_split_formula_equals_standard_on_a_shell():
     a = O.assemble(lam)[2]
     b = O.assemble_split(lam)[2]
     assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
+
+
+# ------------------------------------------------------------------ adjoint of a general extrusion
+def _cotangent(lam, seed):
+    rp, col, _ = O.assemble(lam)
+    return rp, col, np.random.default_rng(seed).standard_normal(len(col))
+
+
+def _L(lam, g):
+    return float(g @ O.assemble(lam)[2])
+
+
+def _shell_two_materials():
+    rng = np.random.default_rng(8)
+    return W.laminate("sh2", W.BSPLINE, 2, 2, [0, 35, -60, 90], 0.05, mapping=W.bump_map(0.1),
+                      materials=np.array([W.ply_C21(), W.random_C21(rng)]), ply_material=[0, 1, 1, 0],
+                      extrusion=(0.2, -0.1, 1.0))
+
+
+def test_shell_adjoint_euler_identity():
+    """K is homogeneous of degree one in the D_l: sum_l <dL/dD_l, D_l> = L."""
+    lam = W.shell_plate(n_el=2, degree=2, repeats=1, extrusion=(0.3, 0.2, 0.9))
+    lam.weights = np.random.default_rng(2).uniform(0.6, 1.7, lam.n_s)
+    rp, col, g = _cotangent(lam, 5)
+    dD = O.adjoint_D(lam, rp, col, g)
+    Ds = [O.rotated_D(lam.C21[lam.ply_material[l]], lam.ply_angle[l]) for l in range(len(lam.ply_angle))]
+    lhs = sum(float(np.sum(dD[l] * Ds[l])) for l in range(len(Ds)))
+    assert abs(lhs - _L(lam, g)) <= 1e-12 * np.abs(g).sum() * np.abs(O.assemble(lam)[2]).max()
+
+
+def test_shell_adjoint_matches_finite_differences():
+    """dL/dC by central differences (exact up to rounding: L is linear in C) and
+    dL/dtheta by central differences, on a shell with two materials."""
+    lam = _shell_two_materials()
+    rp, col, g = _cotangent(lam, 6)
+    dC, dth, _ = O.adjoint(lam, rp, col, g)
+    base = lam.C21.copy()
+    fd = np.zeros_like(dC)
+    for m in range(base.shape[0]):
+        for k in range(21):
+            h = 1e-3 * max(abs(base[m, k]), 1.0)
+            lam.C21 = base.copy(); lam.C21[m, k] += h
+            Lp = _L(lam, g)
+            lam.C21 = base.copy(); lam.C21[m, k] -= h
+            Lm = _L(lam, g)
+            fd[m, k] = (Lp - Lm) / (2 * h)
+    lam.C21 = base
+    assert np.abs(dC - fd).max() <= 1e-8 * np.abs(fd).max()
+    ang = lam.ply_angle.copy()
+    fdt = np.zeros_like(dth)
+    for l in range(len(ang)):
+        lam.ply_angle = ang.copy(); lam.ply_angle[l] += 1e-5
+        Lp = _L(lam, g)
+        lam.ply_angle = ang.copy(); lam.ply_angle[l] -= 1e-5
+        Lm = _L(lam, g)
+        fdt[l] = (Lp - Lm) / 2e-5
+    lam.ply_angle = ang
+    assert np.abs(dth - fdt).max() <= 1e-7 * np.abs(fdt).max()

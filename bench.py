@@ -335,6 +335,17 @@ def run_adjoint(args, L, dev, flush, peak, peak_kind, world):
                         "kernel": "adj_ply_df", "bytes_per_launch": k_bytes, "ms_per_launch": k_ms,
                         "peak_kind": f"{peak_kind} copy bandwidth"}}
     plan.close()
+    # the same plate as a general extrusion (lifted onto a bump, tilted a): FP64 contraction
+    shell = L.Plan.from_laminate(W.laminate("adjoint_shell", W.BSPLINE, 3, 32, [math.degrees(x) for x in lam.ply_angle],
+                                            0.0025, mapping=W.bump_map(0.05, inner=W.identity_map),
+                                            extrusion=(0.05, -0.03, 1.0)))
+    if shell.nnz == nnz:
+        plan = shell
+        ms_sh, _ = timed(lambda: shell.adjoint(values=g, want_dD=False), max(2, steps // 4))
+        out["shell"] = {"workload": "the same plate lifted onto z = 0.05 sin(pi xi) sin(pi eta), extruded along "
+                                    "a = (0.05, -0.03, 1) (general extrusion: FP64 contraction over 6x6 Gram blocks)",
+                        "ms_per_step": ms_sh, "value": aggregate_throughput(nnz, world, ms_sh / 1e3), "unit": UNIT}
+    shell.close()
     del g, vals
     torch.cuda.empty_cache()
     return out

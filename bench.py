@@ -343,7 +343,7 @@ def run_adjoint(args, L, dev, flush, peak, peak_kind, world):
         plan = shell
         ms_sh, _ = timed(lambda: shell.adjoint(values=g, want_dD=False), max(2, steps // 4))
         out["shell"] = {"workload": "the same plate lifted onto z = 0.05 sin(pi xi) sin(pi eta), extruded along "
-                                    "a = (0.05, -0.03, 1) (general extrusion: FP64 contraction over 6x6 Gram blocks)",
+                                    "a = (0.05, -0.03, 1) (general extrusion: double-float contraction over 6x6 Gram blocks)",
                         "ms_per_step": ms_sh, "value": aggregate_throughput(nnz, world, ms_sh / 1e3), "unit": UNIT}
     shell.close()
     del g, vals

@@ -93,8 +93,7 @@ typedef struct {
  * of the split kernels; any other S or a (a "shell") is a general extrusion,
  * assembled by the split and standard paths (lam_assemble_split,
  * lam_assemble_split_host, lam_assemble_standard, lam_inplane_operators, and
- * in batches, one by one), differentiated by lam_adjoint (FP64 contraction)
- * and refused with LAM_ERR_UNSUPPORTED by lam_assemble_split_noalloc.
+ * in batches, one by one), differentiated by lam_adjoint and refused with LAM_ERR_UNSUPPORTED by lam_assemble_split_noalloc.
  * DF = [dS/dxi1 | dS/dxi2 | a] must be regular. */
 typedef struct {
   lam_basis1d u;          /* xi^1 direction, index ix */
@@ -267,9 +266,10 @@ typedef struct {
  * absolute error below 2^-100 of their own size. LAM_ADJOINT_FP64 forces the
  * FP64 evaluation.
  * A general extrusion (lam_inplane.shell): every (a, b) of D_l meets all four
- * thickness types through the 6 x 6 Gram blocks G_(alpha a)(beta b), and the
- * contraction, CSR or low-rank, runs in FP64 (workspace 8 * 36 * nnz_inplane
- * bytes more).
+ * thickness types through the 6 x 6 Gram blocks G_(alpha a)(beta b); CSR
+ * cotangents take the same double-float pass (with the same FP64 re-pass
+ * rules), low-rank ones and plies meeting more than 32 thickness pairs the
+ * FP64 pass (workspace 16 * 36 * nnz_inplane bytes more).
  * The in-plane Gram blocks depend on the plan's geometry only, which never
  * changes: the first call computes them and later calls reuse them
  * (lam_inplane_operators with LAM_P_FROM_GRAM discards the copy). Workspace: about

@@ -76,7 +76,8 @@ struct Device {
   unsigned long long* shell_pmax = nullptr;  // 4 block maxima of |P|
   // adjoint of a general extrusion: the assembled 6 x 6 Gram blocks, and unit scales
   double* adj_G36 = nullptr;   // nnz_s x 36
-  double* adj_ones = nullptr;  // 9 x 1.0
+  float2* adj_G36df = nullptr;  // its scaled float pairs
+  double* adj_gscale36 = nullptr;  // the 9 scales of adj_G36df
   // K-b runs on a stream of its own beside K-a, forked from and joined to the caller's stream
   cudaStream_t kb_stream = nullptr;
   cudaEvent_t kb_fork = nullptr, kb_join = nullptr;
@@ -1332,6 +1333,51 @@ __global__ void __launch_bounds__(256) kg_shell(KpShellArgs a, double* __restric
   }
 }
 
+// The shells' adjoint Gram blocks rescaled in place: w = qs[blk] G_(blk)(ab)
+// (the Q types enter divided by qs), gscale[ab] = a power of two at least
+// max |w| over every pair and block, G = w / gscale[ab] (all exact) and its
+// float pairs Gdf; both passes then accumulate in the same units.
+__global__ void kg_shell_max(int64_t n36, const double* __restrict__ G36, double q0, double q1, double q2, double q3,
+                             unsigned long long* __restrict__ gmax) {
+  __shared__ unsigned long long smax[9];
+  if (threadIdx.x < 9) smax[threadIdx.x] = 0ull;
+  __syncthreads();
+  const double qs[4] = {q0, q1, q2, q3};
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n36; k += (int64_t)gridDim.x * blockDim.x) {
+    const int e = (int)(k % 36);
+    atomicMax(&smax[e % 9], (unsigned long long)__double_as_longlong(fabs(qs[e / 9] * G36[k])));
+  }
+  __syncthreads();
+  if (threadIdx.x < 9) atomicMax(&gmax[threadIdx.x], smax[threadIdx.x]);
+}
+
+__global__ void kg_shell_split(int64_t n36, double* __restrict__ G36, double q0, double q1, double q2,
+                               double q3, const unsigned long long* __restrict__ gmax, float2* __restrict__ Gdf,
+                               double* __restrict__ gscale) {
+  __shared__ double inv[9];
+  const double qs[4] = {q0, q1, q2, q3};
+  if (threadIdx.x < 9) {
+    const double m = __longlong_as_double((long long)gmax[threadIdx.x]);
+    double sc = 1.0;
+    if (m > 0.0 && m <= 1.7976931348623157e308) {
+      int e = 0;
+      frexp(m, &e);
+      sc = ldexp(1.0, e);
+    }
+    inv[threadIdx.x] = 1.0 / sc;
+    if (blockIdx.x == 0) gscale[threadIdx.x] = sc;
+  }
+  __syncthreads();
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n36; k += (int64_t)gridDim.x * blockDim.x) {
+    const int e = (int)(k % 36);
+    const double w = qs[e / 9] * G36[k] * inv[e % 9];
+    G36[k] = w;
+    float hi, lo;
+    split_df(w, hi, lo);
+    Gdf[k] = make_float2(hi, lo);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // K-c: fused combine. One CTA per in-plane row i_s; thread <-> (c, k_s, d) of
 // that row. The CTA first forms the row's G blocks (gathered from the element
@@ -2504,6 +2550,8 @@ struct AdjArgs {
   // every in-plane pair, unscaled, and the scales of the four Q types
   const double* G36;        // nnz_s x 36, [blk * 9 + ab]
   double qs[4];
+  // ... and for the double-float pass: qs[blk] G_(blk)(ab) / gscale[ab] as float pairs
+  const float2* G36df;
 };
 
 // SHELL: a general extrusion, whose entry (c, d) of K couples every (a, b) of
@@ -2674,7 +2722,7 @@ __global__ void __launch_bounds__(1024) adj_ply(AdjArgs a) {
 constexpr int kAdjRowTerms = 9;
 constexpr int kAdjFastTerms = 32;
 
-template <typename Idx>
+template <typename Idx, bool SHELL = false>
 __global__ void __launch_bounds__(1024) adj_ply_df(AdjArgs a) {
   extern __shared__ double sm[];
   const int l = blockIdx.y, chunk = blockIdx.x;
@@ -2755,14 +2803,27 @@ __global__ void __launch_bounds__(1024) adj_ply_df(AdjArgs a) {
       zl[k] = __fsub_rn(zl[k], __fsub_rn(hsum, zh[k]));
       zh[k] = hsum;
     }
-    const float2* gp = a.Gdf + ((int64_t)sLs0[r] + ks) * 9;
+    if (SHELL) {  // S[ab] += sum_type z_type G_(type)(ab), all four types
+      const float2* gp = a.G36df + ((int64_t)sLs0[r] + ks) * 36;
 #pragma unroll
-    for (int ab = 0; ab < 9; ++ab) {
-      const int ty = 2 * (ab / 3 == 2) + (ab % 3 == 2);
-      const float2 gq = gp[ab];
-      float p, e;
-      df_mul(zh[ty], zl[ty], gq.x, gq.y, p, e);
-      df_add(p, e, Sh[ab], Sl[ab]);
+      for (int ab = 0; ab < 9; ++ab)
+#pragma unroll
+        for (int ty = 0; ty < 4; ++ty) {
+          const float2 gq = gp[ty * 9 + ab];
+          float p, e;
+          df_mul(zh[ty], zl[ty], gq.x, gq.y, p, e);
+          df_add(p, e, Sh[ab], Sl[ab]);
+        }
+    } else {
+      const float2* gp = a.Gdf + ((int64_t)sLs0[r] + ks) * 9;
+#pragma unroll
+      for (int ab = 0; ab < 9; ++ab) {
+        const int ty = 2 * (ab / 3 == 2) + (ab % 3 == 2);
+        const float2 gq = gp[ab];
+        float p, e;
+        df_mul(zh[ty], zl[ty], gq.x, gq.y, p, e);
+        df_add(p, e, Sh[ab], Sl[ab]);
+      }
     }
   }
   emax = __reduce_max_sync(0xffffffffu, emax);
@@ -2993,12 +3054,12 @@ static lam_status launch_adj_ply(const Plan& P, const AdjArgs& a, cudaStream_t s
   return LAM_OK;
 }
 
-template <typename Idx>
+template <typename Idx, bool SHELL = false>
 static lam_status launch_adj_df(const Plan& P, const AdjArgs& a, cudaStream_t s) {
   const size_t smem = adj_df_smem(adj_block(P), sizeof(Idx));
-  LAM_CUDA(cudaFuncSetAttribute(adj_ply_df<Idx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LAM_CUDA(cudaFuncSetAttribute(adj_ply_df<Idx, SHELL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((unsigned)adj_nchunks(P), (unsigned)P.plies.size());
-  adj_ply_df<Idx><<<grid, adj_block(P), smem, s>>>(a);
+  adj_ply_df<Idx, SHELL><<<grid, adj_block(P), smem, s>>>(a);
   LAM_CUDA(cudaGetLastError());
   return LAM_OK;
 }
@@ -3033,26 +3094,40 @@ static lam_status gather_gram(Plan& P, cudaStream_t s) {
   return LAM_OK;
 }
 
-// General extrusion: every (a, b) of D_l meets all four thickness types, so the
-// contraction runs in FP64 on unscaled 6 x 6 Gram blocks (assembled on the
-// first call and kept) with the Q types scaled back inside the kernel.
+// General extrusion: every (a, b) of D_l meets all four thickness types. The
+// 6 x 6 Gram blocks (assembled on the first call and kept) are multiplied by
+// the Q types' scales and divided by one power of two per (a, b), so the
+// double-float pass (CSR cotangents) and the FP64 pass accumulate in the same
+// units and the reduce restores them with the 9 scales.
 static lam_status adjoint_shell(Plan& P, const lam_cotangent& cot, double* dC, double* dtheta, double* dDout,
                                 cudaStream_t s) {
   Device& D = *P.dev;
   lam_status st;
-  if (!D.adj_ones) {
-    const std::vector<double> ones(9, 1.0);
-    if ((st = upload(P, D.allocs, &D.adj_ones, ones)) != LAM_OK) return st;
-  }
   if (!D.adj_g_cached) {
-    if (!D.adj_G36 && (st = alloc_dev(D.allocs, &D.adj_G36, (size_t)36 * P.nnz_s)) != LAM_OK) return st;
+    const int64_t n36 = 36 * P.nnz_s;
+    if (!D.adj_G36 && (st = alloc_dev(D.allocs, &D.adj_G36, (size_t)n36)) != LAM_OK) return st;
+    if (!D.adj_G36df) {
+      double* p = nullptr;
+      if ((st = alloc_dev(D.allocs, &p, (size_t)n36)) != LAM_OK) return st;
+      D.adj_G36df = reinterpret_cast<float2*>(p);
+    }
+    if (!D.adj_gscale36 && (st = alloc_dev(D.allocs, &D.adj_gscale36, 9)) != LAM_OK) return st;
     if ((st = shell_element_gram(P, s)) != LAM_OK) return st;
     cudaEvent_t ev0 = prof_begin(P, s);
     kg_shell<<<(unsigned)P.ns, 256, 0, s>>>(kp_shell_args(P), D.adj_G36);
     LAM_CUDA(cudaGetLastError());
-    prof_end(P, LAM_KERNEL_ADJOINT_AUX, 1, s, ev0);
+    const double* q = P.adj_qscale;
+    LAM_CUDA(cudaMemsetAsync(D.adj_gmax, 0, 9 * sizeof(unsigned long long), s));
+    const unsigned grid = (unsigned)std::min<int64_t>((n36 + 255) / 256, 152 * 8);
+    kg_shell_max<<<grid, 256, 0, s>>>(n36, D.adj_G36, q[0], q[1], q[2], q[3], D.adj_gmax);
+    LAM_CUDA(cudaGetLastError());
+    kg_shell_split<<<grid, 256, 0, s>>>(n36, D.adj_G36, q[0], q[1], q[2], q[3], D.adj_gmax, D.adj_G36df,
+                                        D.adj_gscale36);
+    LAM_CUDA(cudaGetLastError());
+    prof_end(P, LAM_KERNEL_ADJOINT_AUX, 3, s, ev0);
     D.adj_g_cached = true;
   }
+  LAM_CUDA(cudaMemsetAsync(D.adj_flag, 0, 2 * sizeof(int), s));
   AdjArgs a{};
   a.ns = P.ns;
   a.n_dof = P.n_dof;
@@ -3078,22 +3153,39 @@ static lam_status adjoint_shell(Plan& P, const lam_cotangent& cot, double* dC, d
   a.u = cot.u;
   a.v = cot.v;
   a.rank = cot.rank;
-  a.G36 = D.adj_G36;
-  for (int k = 0; k < 4; ++k) a.qs[k] = P.adj_qscale[k];
+  a.G36 = D.adj_G36;      // already multiplied by qs[type] / gscale[ab]
+  for (int k = 0; k < 4; ++k) a.qs[k] = 1.0;
+  a.G36df = D.adj_G36df;
   a.partial = D.adj_partial;
   a.flag = D.adj_flag;
   a.emax = D.adj_flag + 1;
-  a.conditional = 0;
+  const bool lowrank = cot.kind == LAM_COTANGENT_LOWRANK;
+  const bool force64 = (cot.flags & LAM_ADJOINT_FP64) != 0;
+  // double-float pass for CSR cotangents whose plies meet few thickness pairs;
+  // the FP64 pass after it runs only when its result is rejected
+  const bool df = !lowrank && !force64 && P.adj_max_terms <= kAdjFastTerms;
   cudaEvent_t ev = prof_begin(P, s);
-  st = cot.kind == LAM_COTANGENT_LOWRANK ? launch_adj_ply<true, false, true>(P, a, s)
-                                         : launch_adj_ply<false, false, true>(P, a, s);
+  if (df) {
+    a.conditional = 0;
+    st = P.nnz < ((int64_t)1 << 31) ? launch_adj_df<int32_t, true>(P, a, s) : launch_adj_df<int64_t, true>(P, a, s);
+    if (st != LAM_OK) return st;
+    prof_end(P, LAM_KERNEL_ADJOINT, 1, s, ev);
+    ev = prof_begin(P, s);
+  }
+  a.conditional = df ? 1 : 0;
+  st = lowrank ? launch_adj_ply<true, false, true>(P, a, s) : launch_adj_ply<false, false, true>(P, a, s);
   if (st != LAM_OK) return st;
-  prof_end(P, LAM_KERNEL_ADJOINT, 1, s, ev);
-  ev = prof_begin(P, s);
+  int aux = 1;
+  if (df) {
+    ++aux;  // the conditional FP64 pass
+  } else {
+    prof_end(P, LAM_KERNEL_ADJOINT, 1, s, ev);
+    ev = prof_begin(P, s);
+  }
   AdjReduceArgs r{};
   r.nchunks = a.nchunks;
   for (int k = 0; k < 4; ++k) r.qscale[k] = 1.0;
-  r.gscale = D.adj_ones;
+  r.gscale = D.adj_gscale36;
   r.partial = D.adj_partial;
   r.ply_M = D.ply_M;
   r.ply_dM = D.ply_dM;
@@ -3104,7 +3196,6 @@ static lam_status adjoint_shell(Plan& P, const lam_cotangent& cot, double* dC, d
   r.plyC = D.adj_plyC;
   adj_reduce<<<(unsigned)P.plies.size(), 384, 0, s>>>(r);
   LAM_CUDA(cudaGetLastError());
-  int aux = 1;
   if (dC) {
     adj_material<<<1, 256, 0, s>>>((int)P.plies.size(), (int)P.mats.size(), D.ply_mat, D.adj_plyC, dC);
     LAM_CUDA(cudaGetLastError());

@@ -74,6 +74,10 @@ CASES = {
         "shtri", W.BSPLINE, 2, 3, [0, 20, -35, 90], 0.01, mapping=W.bump_map(0.15), extrusion=(0.1, -0.2, 1.0),
         materials=np.array([W.random_C21(np.random.default_rng(11)), W.random_C21(np.random.default_rng(12))]),
         ply_material=[0, 1, 1, 0]),
+    # one sextic element through five plies: 49 thickness pairs per ply, the FP64-only path
+    "shell_one_thickness_element": lambda: W.laminate(
+        "shss", W.BSPLINE, 2, 2, [0, 90, 0, 90, 0], [0.1, 0.1, 0.2, 0.1, 0.1], mapping=W.bump_map(0.1),
+        thickness=W.single_element_thickness(0.6, 6), extrusion=(0.2, 0.1, 1.0)),
 }
 
 

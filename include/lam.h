@@ -93,8 +93,9 @@ typedef struct {
  * of the split kernels; any other S or a (a "shell") is a general extrusion,
  * assembled by the split and standard paths (lam_assemble_split,
  * lam_assemble_split_host, lam_assemble_standard, lam_inplane_operators, and
- * in batches, one by one), differentiated by lam_adjoint and refused with LAM_ERR_UNSUPPORTED by lam_assemble_split_noalloc.
- * DF = [dS/dxi1 | dS/dxi2 | a] must be regular. */
+ * in batches, one by one), differentiated by lam_adjoint, and refused with
+ * LAM_ERR_UNSUPPORTED by lam_assemble_split_noalloc. DF = [dS/dxi1 |
+ * dS/dxi2 | a] must be regular. */
 typedef struct {
   lam_basis1d u;          /* xi^1 direction, index ix */
   lam_basis1d v;          /* xi^2 direction, index iy */

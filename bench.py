@@ -35,6 +35,7 @@ import re
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -146,7 +147,8 @@ class ClockSampler:
 
     def __enter__(self):
         try:
-            out_dir = os.path.join(ROOT, "gpurun_out") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp"
+            # the raw samples go to LAM_BENCH_OUT (default: the system temporary folder)
+            out_dir = os.environ.get("LAM_BENCH_OUT") or tempfile.gettempdir()
             self.path = os.path.join(out_dir, f"clocks_rank{dist_env()[0]}.csv")
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader",

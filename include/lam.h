@@ -65,7 +65,7 @@ extern "C" {
 typedef enum {
   LAM_OK = 0,
   LAM_ERR_INVALID_ARG = 1,  /* malformed input (degree, knots, plies, sizes) */
-  LAM_ERR_UNSUPPORTED = 2,  /* valid input outside what this build handles */
+  LAM_ERR_UNSUPPORTED = 2,  /* valid input outside what the library handles */
   LAM_ERR_OOM = 3,          /* host or device allocation failed */
   LAM_ERR_CUDA = 4,         /* a CUDA runtime call failed */
   LAM_ERR_TIMEOUT = 5       /* a bounded device wait gave up */

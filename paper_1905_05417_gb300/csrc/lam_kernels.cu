@@ -2148,7 +2148,7 @@ static lam_status check_limits(const Plan& P) {
   const bool class_major = !(P.shell && use_stream(P));
   if ((class_major && kc_smem(P) > 200 * 1024) || ka_smem(P) > 200 * 1024 || kd_smem(P) > 200 * 1024 ||
       (P.shell && ka_shell_smem(P) > 200 * 1024)) {
-    set_error("plan tables exceed the shared-memory budget of this build");
+    set_error("plan tables exceed the shared-memory budget of the kernels");
     return LAM_ERR_UNSUPPORTED;
   }
   return LAM_OK;

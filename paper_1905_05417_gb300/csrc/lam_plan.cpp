@@ -830,7 +830,7 @@ lam_status build_plan(Plan& P, const lam_inplane* inplane, const lam_basis1d* th
     return LAM_ERR_UNSUPPORTED;
   }
   if ((P.u.p + 1) * (P.v.p + 1) > 64 || P.nqu * P.nqv > 256) {
-    set_error("in-plane element too large for this build");
+    set_error("in-plane element too large for the kernels");
     return LAM_ERR_UNSUPPORTED;
   }
   P.class_tol = o.class_tol < 0.0 ? 1e-13 : o.class_tol;

@@ -287,3 +287,32 @@ def test_lagrange_plate_full_size_sampled(L):
     sampled blocks against the oracle's block integrator and symmetry; the
     pattern's construction is checked whole on the other plates."""
     _sampled_parity(L, W.lagrange_plate(), "split", n_rows=40, whole_pattern=False)
+
+
+def test_split_on_a_side_stream_and_in_a_cuda_graph(L):
+    """lam_assemble_split is stream-ordered (K-b runs on a stream forked from the
+    caller's and joined back): on a non-default stream after an angle update,
+    and captured into a CUDA graph and replayed, it gives the oracle's matrix."""
+    import torch
+    lam = W.curved_plate(n_el=4, degree=3, repeats=1)
+    p = L.Plan.from_laminate(lam)
+    side = torch.cuda.Stream()
+    out = torch.empty(p.nnz, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(side):
+        p.assemble_split(out)                       # warm: device tables, workspace
+        new = np.deg2rad(np.linspace(-60.0, 75.0, len(lam.ply_angle)))
+        p.update(ply_angle=new)
+        p.assemble_split(out)
+    side.synchronize()
+    lam.ply_angle = new
+    ref = O.assemble(lam)
+    assert np.abs(out.cpu().numpy() - ref[2]).max() <= TOL * np.abs(ref[2]).max()
+    g = torch.cuda.CUDAGraph()
+    graph_out = torch.full((p.nnz,), np.nan, dtype=torch.float64, device="cuda")
+    with torch.cuda.graph(g):
+        p.assemble_split(graph_out)
+    graph_out.fill_(np.nan)
+    g.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(graph_out.cpu().numpy(), out.cpu().numpy())
+    p.close()

@@ -3,13 +3,19 @@
 // Split path (Section 3 of Antolin 2019, Eq. Km_2):
 //   K-b  kb_thickness  Q_{m,ab}^{i_t j_t} = sum_{plies l of configuration m}
 //                      int_{ply l} tau_a^{i_t} tau_b^{j_t} dz   (Eq. Q; tau_1 = T, tau_2 = T')
-//   K-a  ka_inplane    configuration-free in-plane Gram blocks
+//   K-a  ka_local      configuration-free in-plane Gram blocks per element
 //                      G_{ab}^{i_s j_s} = int g_a^{i_s} g_b^{j_s} |DF| dxi,
 //                      g = (dS/dx, dS/dy, S)   (pull-back of Eq. gradient)
-//   K-c  kc_combine    P_{m,ab}[c][d] = sum D_m[V(c,a)][V(d,b)] G_{ab} (Eq. P with a
+//                      (ka_inplane: the same, accumulated per pair, for the
+//                      allocation-free entry point)
+//   K-c  kc_stream     P_{m,ab}[c][d] = sum D_m[V(c,a)][V(d,b)] G_{ab} (Eq. P with a
 //                      homogeneous ply), then K = sum_m sum_ab P_{m,ab} Q_{m,ab}
-//                      written straight into the CSR values.
+//                      written straight into the CSR values (kc_combine: the
+//                      class-major form for rows of many neighbours)
+// General extrusions (Eq. extrusion): ka_shell (6 x 6 Gram blocks), kp_shell (P
+// per configuration), the combine reading P.
 // Standard path (Section 2.4): K-d kd_standard, one CTA per 3D element.
+// Adjoint: adj_* (dL/dD_l, dL/dC, dL/dtheta). Batches: kb_batch, ka_batch, kc_batch.
 // Pattern: kp_row_ptr / kp_col_ind.
 #include <cuda_runtime.h>
 

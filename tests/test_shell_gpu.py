@@ -129,6 +129,32 @@ def test_shell_update_angles_then_reassemble(L):
     p.close()
 
 
+def test_shell_update_materials_then_reassemble_and_differentiate(L):
+    """New constants (a triclinic material and a scaled ply material) on a
+    shell: the configuration tables, the scaled D of the P formation and the
+    adjoint follow the update."""
+    import torch
+    lam = W.laminate("sh_m", W.BSPLINE, 2, 3, [0, 30, -45, 90], 0.01, mapping=W.bump_map(0.1),
+                     materials=np.array([W.ply_C21(), W.ply_C21()]), ply_material=[0, 1, 1, 0],
+                     extrusion=(0.15, -0.05, 1.0))
+    p = L.Plan.from_laminate(lam)
+    p.assemble_split()
+    new = np.array([W.random_C21(np.random.default_rng(31)), 3.0 * W.ply_C21()])
+    p.update(C21=new)
+    lam.C21 = new
+    vals = p.assemble_split()
+    torch.cuda.synchronize()
+    rp, col, ref = O.assemble(lam)
+    assert np.abs(vals.cpu().numpy() - ref).max() <= TOL * np.abs(ref).max()
+    g = np.random.default_rng(5).standard_normal(len(col))
+    dC, dth, dD = p.adjoint(values=torch.from_numpy(g).cuda())
+    torch.cuda.synchronize()
+    rdC, rdth, rdD = O.adjoint(lam, rp, col, g)
+    assert np.abs(dD.cpu().numpy().reshape(rdD.shape) - rdD).max() <= 1e-10 * np.abs(rdD).max()
+    assert np.abs(dC.cpu().numpy() - rdC).max() <= 1e-10 * np.abs(rdC).max()
+    p.close()
+
+
 @pytest.mark.parametrize("scale", [2.0 ** -60, 2.0 ** 60])
 def test_shell_extreme_geometry_scale(L, scale):
     """Surface and extrusion scaled by 2^+-60: the per-element powers of two of

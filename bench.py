@@ -11,14 +11,18 @@ functions); orthotropic ply E1=140, E2=E3=10, G12=G13=5, G23=3.4, nu12=nu13=0.3,
 nu23=0.49; 1,306,299 DOFs, 723,661,785 stored nonzeros.
 
 One step = one call of lam_assemble_split (thickness integrals, in-plane Gram
-blocks, fused combine into the CSR values) into a resident device buffer; the
-pattern is built once before timing. Every timed step is preceded by a 256 MiB
-device write that flushes the 129 MB L2 (outside the step's events). The line
-also reports the standard path (lam_assemble_standard) on the same plan, the
+blocks, fused combine into the CSR values) into a resident device buffer, in
+FP64 arithmetic (the plan's default LAM_ARITH_FP64); the pattern is built once
+before timing. Every timed step is preceded by a 256 MiB device write that
+flushes the 129 MB L2 (outside the step's events). The line also reports the
+opt-in double-float arithmetic (its time and its largest difference from the
+FP64 matrix), the standard path (lam_assemble_standard) on the same plan, the
 end-to-end figure through lam_assemble_split_host (ply angles in from pinned
-host memory, all values out to pinned host memory), the roofline of the
-dominant kernel from the library's own event timing, SM clocks sampled during
-the timed regions, and the CPU oracle timed on a bounded sample.
+host memory, all values out to pinned host memory) with its breakdown and the
+host link measured alone, the roofline of the dominant kernel from the
+library's own event timing, SM clocks sampled during the timed regions, and the
+CPU oracle (standard assembly with the CSR scatter, on every host core) timed
+on a bounded sample.
 
 Under torchrun (N > 1) every rank assembles its own replica of the workload
 (weak scaling, no collective on the data path); the step time is the maximum
@@ -196,6 +200,29 @@ class ClockSampler:
                 "samples": len(sm), "samples_under_load": len(loaded), "power_w_max": max(power)}
 
 
+def bind_host_to_gpu(local_rank: int) -> dict:
+    """Pin this process to the CPUs next to the GPU (its PCI device's
+    local_cpulist), so that pinned host buffers allocated afterwards sit in the
+    memory nearest to it. Best effort: returns what was done."""
+    try:
+        q = subprocess.run(["nvidia-smi", "--query-gpu=pci.bus_id", "--format=csv,noheader", "-i",
+                            str(gpu_index(local_rank))], capture_output=True, text=True, timeout=20)
+        bus = q.stdout.strip().lower()
+        dom, rest = bus.split(":", 1)
+        bus = f"{int(dom, 16) & 0xffff:04x}:{rest}"
+        base = f"/sys/bus/pci/devices/{bus}"
+        cpulist = open(f"{base}/local_cpulist").read().strip()
+        node = open(f"{base}/numa_node").read().strip()
+        cpus = set()
+        for part in cpulist.split(","):
+            lo, _, hi = part.partition("-")
+            cpus.update(range(int(lo), int(hi or lo) + 1))
+        os.sched_setaffinity(0, cpus)
+        return {"pci": bus, "numa_node": node, "cpus": cpulist}
+    except Exception as e:  # no sysfs entry, no nvidia-smi, ...
+        return {"binding": f"none ({type(e).__name__})"}
+
+
 def gpu_index(local_rank: int) -> int:
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     ids = [v.strip() for v in vis.split(",") if v.strip()]
@@ -205,37 +232,51 @@ def gpu_index(local_rank: int) -> int:
 
 
 # ----------------------------------------------------------------------------- CPU oracle legs
-def oracle_sample(lam, budget_s: float, nnz: int):
-    """Time the CPU oracle's element stiffness (Section 2.4, Eq. Km_0 per
-    element) on a bounded, evenly spread sample of the workload's 3D elements
-    and scale by the element count. Single-threaded plain C."""
+def config_dict(args, n_dof: int, nnz: int) -> dict:
+    """The workload, identical for both arms."""
+    return {"workload": workload_desc(args), "n_dof": n_dof, "nnz": nnz,
+            "l2": "256 MiB device write before every timed GPU step (L2 is 129 MB); outputs 5.8 GB per step"}
+
+
+def oracle_threaded(lam, budget_s: float, nnz: int, prepared=None, threads: int | None = None):
+    """CPU baseline: the oracle's standard assembly (element stiffness of
+    Section 2.4, Eq. Km_0, plus the scatter into its own CSR) on the host's
+    cores. Element colours (elements sharing no basis function) run one after
+    another, each split over `threads` threads (the C calls release the GIL).
+    A bounded sample of the workload -- whole colours, the last one cut short,
+    about budget_s seconds -- is timed and scaled by the element count; the
+    pattern is built once before timing. Plain C, not tuned for speed."""
+    import numpy as np
     import oracle
-    prob = oracle.Problem(lam)
-    nex = oracle.n_elements(lam.u.kind, lam.u.degree, lam.u.knots)
-    ney = oracle.n_elements(lam.v.kind, lam.v.degree, lam.v.knots)
-    net = oracle.n_elements(lam.t.kind, lam.t.degree, lam.t.knots)
-    n_el = nex * ney * net
+    from concurrent.futures import ThreadPoolExecutor
+    threads = threads or os.cpu_count() or 1
+    if prepared is None:
+        prob = oracle.Problem(lam)
+        row_ptr, col = oracle.pattern(lam)
+        prepared = (prob, row_ptr, col, np.zeros(len(col)), oracle.element_colours(lam))
+    prob, row_ptr, col, val, groups = prepared
+    n_el = sum(len(g) for g in groups)
     t0 = time.perf_counter()
-    oracle.element_stiffness(lam, 0, 0, 0, prob)
+    oracle.assemble_elements(lam, row_ptr, col, groups[0][:1], val, prob)
     one = max(time.perf_counter() - t0, 1e-6)
-    n = int(max(1, min(n_el, budget_s / one)))
-    stride = max(1, n_el // n)
-    t0 = time.perf_counter()
+    want = int(max(threads, min(n_el, budget_s * threads / one)))
     done = 0
-    for k in range(0, n_el, stride):
-        if done >= n:
-            break
-        et, rem = divmod(k, nex * ney)
-        ey, ex = divmod(rem, nex)
-        oracle.element_stiffness(lam, ex, ey, et, prob)
-        done += 1
-    dt = time.perf_counter() - t0
-    per_elem = dt / done
-    full = per_elem * n_el
-    return {"value": nnz / full, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle element stiffness of {done} of {n_el} 3D elements (every {stride}th), "
-                      f"{dt:.1f} s, scaled by the element count; CSR scatter not timed",
-            "seconds_full_estimate": full}
+    with ThreadPoolExecutor(threads) as ex:
+        t0 = time.perf_counter()
+        for g in groups:
+            g = g[:want - done]
+            if len(g) == 0:
+                break
+            list(ex.map(lambda c: oracle.assemble_elements(lam, row_ptr, col, c, val, prob),
+                        [c for c in np.array_split(g, threads) if len(c)]))
+            done += len(g)
+        dt = time.perf_counter() - t0
+    full = dt / done * n_el
+    return {"value": nnz / full, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "nproc": os.cpu_count(),
+            "sample": f"oracle standard assembly (element stiffness + CSR scatter) of {done} of {n_el} 3D elements "
+                      f"(whole element colours in order), {dt:.1f} s on {threads} threads, scaled by the element count",
+            "seconds_full_estimate": full}, prepared
 
 
 def run_reference(args):
@@ -245,18 +286,22 @@ def run_reference(args):
     import oracle
     lam = make_workload(args)
     n_dof, nnz = oracle.sizes(lam)
-    budget = max(0.2, min(2.0, 150.0 / max(1, args.steps + args.warmup)))
+    budget = max(0.5, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+    prepared = None
     for _ in range(args.warmup):
-        oracle_sample(lam, budget, nnz)
-    vals = [oracle_sample(lam, budget, nnz) for _ in range(args.steps)]
+        _, prepared = oracle_threaded(lam, budget, nnz, prepared)
+    vals = []
+    for _ in range(args.steps):
+        v, prepared = oracle_threaded(lam, budget, nnz, prepared)
+        vals.append(v)
     secs = [nnz / v["value"] for v in vals]
     value = nnz / statistics.mean(secs)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": workload_desc(args), "n_dof": n_dof, "nnz": nnz, "parallelism": "none (host)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": vals[0]["sample"] + "; one such sample per step"},
+            "config": config_dict(args, n_dof, nnz), "parallelism": f"host threads ({vals[0]['cores']})",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": vals[0]["cores"], "nproc": vals[0]["nproc"],
+                             "kind": "oracle", "sample": vals[0]["sample"] + "; one such sample per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -317,11 +362,16 @@ def run_adjoint(args, L, dev, flush, peak, peak_kind, world):
     ms_lr, _ = timed(lambda: plan.adjoint(u=u, v=u, want_dD=False), steps)
     ms, pr = timed(lambda: plan.adjoint(values=g, want_dD=False), steps)
     ms_fwd, _ = timed(lambda: plan.assemble_split(vals), steps)
-    ms64, _ = timed(lambda: plan.adjoint(values=g, want_dD=False, fp64=True), max(2, steps // 4))
+    ms_df, prd = timed(lambda: plan.adjoint(values=g, want_dD=False, double_float=True), steps)
     k = pr["adjoint"]
-    k_ms = k["ms"] / steps
+    k_ms = k["ms"] / k["launches"]
     k_bytes = 8 * nnz + 8 * 9 * nnz_s
-    achieved = k_bytes / (k_ms / 1e3) / 1e9
+    # FP64 work of the contraction: 4 fused multiply-adds per cotangent entry (the
+    # thickness sums of the four Q types, each entry counted once) and 81 per
+    # (in-plane pair entry, ply) (S += z G)
+    k_flops = 2 * (4 * nnz + 81 * nnz_s * len(lam.ply_angle))
+    kd = prd["adjoint"]
+    kd_ms = kd["ms"] / kd["launches"]
     out = {"workload": "adjoint plate: cubic B-spline 32x32 unit square, [0/90]_12 (24 plies x 0.0025), "
                        "CSR cotangent N(0,1) (torch seed 1905), outputs dL/dC (21) and dL/dtheta (24)",
            "metric": "cotangent entries contracted per second", "value": aggregate_throughput(nnz, world, ms / 1e3),
@@ -329,13 +379,22 @@ def run_adjoint(args, L, dev, flush, peak, peak_kind, world):
            "split_assembly_ms_same_plate": ms_fwd, "adjoint_over_assembly": ms / ms_fwd,
            "compliance_gradient_ms": ms_lr,
            "compliance_gradient": "L = u^T K u, u ~ N(0,1) per DOF (torch seed 1905): the low-rank cotangent u u^T",
-           "fp64_pass_ms": ms64,
+           "arith": "FP64 (default)",
            "kernels_ms_per_step": {kk: pr[kk]["ms"] / steps for kk in L.KERNEL_KINDS if pr[kk]["launches"]},
            "gpu_launches": sum(pr[kk]["launches"] for kk in L.KERNEL_KINDS) // steps,
-           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                        "traffic": recorded_traffic("adj_ply_df_adjoint_plate_p3_32x32_24plies.md", "adj_ply_df"),
-                        "kernel": "adj_ply_df", "bytes_per_launch": k_bytes, "ms_per_launch": k_ms,
-                        "peak_kind": f"{peak_kind} copy bandwidth"}}
+           "roofline": {"bound": "alu", "achieved": k_flops / (k_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                        "unit": "TFLOP/s", "frac": k_flops / (k_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                        "traffic": None, "kernel": "adj_ply (FP64 CSR contraction)", "flops_per_launch": k_flops,
+                        "ms_per_launch": k_ms, "hbm_frac": k_bytes / (k_ms / 1e3) / 1e9 / peak,
+                        "peak_kind": "nominal FP64 rate (1.20 TFLOP/s measured by a DFMA probe)"},
+           "double_float": {"ms_per_step": ms_df, "value": aggregate_throughput(nnz, world, ms_df / 1e3),
+                            "arith": "double-float products on the FP32 pipes (LAM_ADJOINT_DOUBLE_FLOAT, opt-in)",
+                            "roofline": {"bound": "hbm", "achieved": k_bytes / (kd_ms / 1e3) / 1e9, "peak": peak,
+                                         "unit": "GB/s", "frac": k_bytes / (kd_ms / 1e3) / 1e9 / peak,
+                                         "traffic": recorded_traffic("adj_ply_df_adjoint_plate_p3_32x32_24plies.md",
+                                                                     "adj_ply_df"),
+                                         "kernel": "adj_ply_df", "bytes_per_launch": k_bytes, "ms_per_launch": kd_ms,
+                                         "peak_kind": f"{peak_kind} copy bandwidth"}}}
     plan.close()
     # the same plate as a general extrusion (lifted onto a bump, tilted a): FP64 contraction
     shell = L.Plan.from_laminate(W.laminate("adjoint_shell", W.BSPLINE, 3, 32, [math.degrees(x) for x in lam.ply_angle],
@@ -345,7 +404,7 @@ def run_adjoint(args, L, dev, flush, peak, peak_kind, world):
         plan = shell
         ms_sh, _ = timed(lambda: shell.adjoint(values=g, want_dD=False), max(2, steps // 4))
         out["shell"] = {"workload": "the same plate lifted onto z = 0.05 sin(pi xi) sin(pi eta), extruded along "
-                                    "a = (0.05, -0.03, 1) (general extrusion: double-float contraction over 6x6 Gram blocks)",
+                                    "a = (0.05, -0.03, 1) (general extrusion: FP64 contraction over 6x6 Gram blocks)",
                         "ms_per_step": ms_sh, "value": aggregate_throughput(nnz, world, ms_sh / 1e3), "unit": UNIT}
     shell.close()
     del g, vals
@@ -503,7 +562,7 @@ def run_large(args, L, dev, flush, peak, peak_kind, world):
            "kernels_ms_per_step": {k: pr[k]["ms"] / steps for k in L.KERNEL_KINDS if pr[k]["launches"]},
            "standard_ms": std_ms, "speedup_split_vs_standard": std_ms / ms,
            "roofline": {"bound": "hbm", "achieved": kc_bytes / (kc_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-                        "frac": kc_bytes / (kc_ms / 1e3) / 1e9 / peak, "traffic": None, "kernel": "kc_stream",
+                        "frac": kc_bytes / (kc_ms / 1e3) / 1e9 / peak, "traffic": None, "kernel": "kc_ws",
                         "peak_kind": f"{peak_kind} copy bandwidth"}}
     plan.close()
     del values
@@ -557,7 +616,7 @@ def run_shell(args, L, dev, flush, peak, peak_kind, world):
            "kernels_ms_per_step": {k: pr[k]["ms"] / steps for k in L.KERNEL_KINDS if pr[k]["launches"]},
            "standard_ms": std_ms, "speedup_split_vs_standard": None if std_ms is None else std_ms / ms,
            "roofline": {"bound": "hbm", "achieved": kc_bytes / (kc_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-                        "frac": kc_bytes / (kc_ms / 1e3) / 1e9 / peak, "traffic": None, "kernel": "kc_stream",
+                        "frac": kc_bytes / (kc_ms / 1e3) / 1e9 / peak, "traffic": None, "kernel": "kc_ws",
                         "peak_kind": f"{peak_kind} copy bandwidth"}}
     plan.close()
     del values
@@ -572,10 +631,12 @@ def run_lam(args):
     dev = torch.device("cuda", local)
     import paper_1905_05417_gb300 as L
     lam = make_workload(args)
-    plan = L.Plan.from_laminate(lam)
+    plan = L.Plan.from_laminate(lam)  # FP64 arithmetic (LAM_ARITH_FP64, the default)
+    assert plan.info["arith"] == L.ARITH_FP64
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = oracle_sample(lam, args.cpu_budget, plan.nnz)
+        cpu, prepared = oracle_threaded(lam, args.cpu_budget, plan.nnz)
+        del prepared
     info = plan.info
     nnz, nnz_s = info["nnz"], info["nnz_inplane"]
     row_ptr, col = plan.pattern()
@@ -608,6 +669,36 @@ def run_lam(args):
         ms_local = sum(step_ms) / args.steps
         ms = max_over_ranks(ms_local, dev)
         launches = sum(prof[k]["launches"] for k in L.KERNEL_KINDS)
+
+        # ---- the double-float variant (LAM_ARITH_DOUBLE_FLOAT, opt-in), against the FP64 result
+        dfl = None
+        if args.df_steps > 0:
+            dplan = L.Plan.from_laminate(lam, arith=L.ARITH_DOUBLE_FLOAT)
+            dvals = torch.empty(nnz, dtype=torch.float64, device=dev)
+            for _ in range(args.warmup):
+                dplan.assemble_split(dvals)
+            torch.cuda.synchronize()
+            barrier()
+            dplan.profile_enable(True)
+            dev_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(args.df_steps)]
+            for k in range(args.df_steps):
+                flush.zero_()
+                dev_ev[k][0].record()
+                dplan.assemble_split(dvals)
+                dev_ev[k][1].record()
+            torch.cuda.synchronize()
+            dprof = dplan.profile()
+            dms = max_over_ranks(sum(a.elapsed_time(b) for a, b in dev_ev) / args.df_steps, dev)
+            rel = float((dvals - values).abs().max() / values.abs().max())
+            dfl = {"value": aggregate_throughput(nnz, world, dms / 1e3), "unit": UNIT, "ms_per_step": dms,
+                   "steps": args.df_steps, "arith": "double-float products and sums on the FP32 pipes (opt-in)",
+                   "max_abs_diff_over_max_abs_vs_fp64": rel,
+                   "kernels_ms_per_step": {k: dprof[k]["ms"] / args.df_steps for k in L.KERNEL_KINDS
+                                           if dprof[k]["launches"]}}
+            dplan.close()
+            del dvals
+            torch.cuda.empty_cache()
 
         # ---- standard, timed on the same plan
         std = None
@@ -653,54 +744,84 @@ def run_lam(args):
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if args.e2e_steps > 0:
+        binding = bind_host_to_gpu(local)
         host = torch.empty(nnz, dtype=torch.float64, pin_memory=True)
         angles = torch.tensor(lam.ply_angle, dtype=torch.float64).pin_memory()
         plan.update(ply_angle=angles.numpy())
         plan.assemble_split_host(host)
+        # the host link on its own: a plain copy of the same bytes into the same pinned buffer
+        link = []
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            host.copy_(values, non_blocking=True)
+            b.record()
+            torch.cuda.synchronize()
+            link.append(a.elapsed_time(b))
+        link_gbs = 8 * nnz / (statistics.median(link) / 1e3) / 1e9
         torch.cuda.synchronize()
         barrier()
         plan.profile_enable(True)
+        upd, asm = [], []
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
+            ta = time.perf_counter()
             plan.update(ply_angle=angles.numpy())
+            tb = time.perf_counter()
             plan.assemble_split_host(host)
+            tc = time.perf_counter()
+            upd.append(tb - ta)
+            asm.append(tc - tb)
         t_e2e = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, dev)
         eprof = plan.profile()
         plan.profile_enable(False)
         barrier()
+        d2h = eprof["d2h_bytes"] // args.e2e_steps
         e2e = {"value": aggregate_throughput(nnz, world, t_e2e), "unit": UNIT,
                "h2d_bytes_per_step": eprof["h2d_bytes"] // args.e2e_steps + angles.numel() * 8,
-               "d2h_bytes_per_step": eprof["d2h_bytes"] // args.e2e_steps, "ms_per_step": 1e3 * t_e2e,
+               "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * t_e2e, "steps": args.e2e_steps,
                "call": "lam_plan_update (ply angles from pinned host memory) + lam_assemble_split_host "
-                       "(values to pinned host memory)"}
+                       "(values to pinned host memory)",
+               "breakdown_ms_per_step": {
+                   "plan_update_host": 1e3 * statistics.mean(upd),
+                   "assemble_split_host": 1e3 * statistics.mean(asm),
+                   "kernels": {k: eprof[k]["ms"] / args.e2e_steps for k in L.KERNEL_KINDS if eprof[k]["launches"]}},
+               "d2h_gbs": d2h / statistics.mean(asm) / 1e9,
+               "link_gbs": link_gbs, "link_bound_ms": 8 * nnz / link_gbs / 1e6,
+               "over_link_bound": t_e2e / (8 * nnz / link_gbs / 1e9),
+               "host_binding": binding}
         del host
 
     if rank != 0:
         return 0
     kc = prof["combine"]
-    kc_ms = kc["ms"] / args.steps  # one combine call per step: the double-float pass, its check, the FP64 re-pass gate
-    kc_bytes = 8 * nnz + 72 * nnz_s
+    kc_ms = kc["ms"] / kc["launches"]  # kc_ws: one launch per step
+    kc_bytes = 8 * nnz + 72 * nnz_s     # 8 B per stored value + the row's assembled Gram blocks (9 doubles per pair)
     achieved = kc_bytes / (kc_ms / 1e3) / 1e9
-    traffic = (recorded_traffic("kc_stream_curved_p3_64x64_48plies.md", "kcs_row+kc_stream")
+    traffic = (recorded_traffic("kc_ws_curved_p3_64x64_48plies.md", "kcw_copy_pairs+kc_ws")
                if (args.n_el, args.repeats) == (64, 6) else None)
     clk = clocks.summary()
     line = {
         "metric": METRIC,
         "value": aggregate_throughput(nnz, world, ms / 1e3),
         "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_desc(args), "n_dof": info["n_dof"], "nnz": nnz, "n_configs": info["n_configs"],
-                   "n_classes": info["n_classes"], "parallelism": "replicas" if world > 1 else "single GPU",
-                   "l2": "256 MiB device write before every timed step (L2 is 129 MB); outputs 5.8 GB per step"},
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "arith": "FP64 (every product and sum an FP64 operation: LAM_ARITH_FP64)", "data": "synthetic",
+        "config": config_dict(args, info["n_dof"], nnz),
+        "parallelism": "replicas" if world > 1 else "single GPU",
+        "plan": {"n_configs": info["n_configs"], "n_classes": info["n_classes"]},
         "step_hbm_frac": 8 * nnz / (ms / 1e3) / 1e9 / peak,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": "kc_stream", "bytes_per_launch": kc_bytes,
-                     "ms_per_launch": kc_ms, "launches_per_call": kc["launches"] // args.steps, "peak_kind": f"{peak_kind} copy bandwidth"},
+                     "traffic": traffic, "kernel": "kc_ws", "bytes_per_launch": kc_bytes,
+                     "ms_per_launch": kc_ms, "launches_per_call": kc["launches"] // args.steps,
+                     "peak_kind": f"{peak_kind} copy bandwidth"},
         "kernels_ms_per_step": {k: prof[k]["ms"] / args.steps for k in L.KERNEL_KINDS if prof[k]["launches"]},
         "gpu_launches": launches,
         "wall_s_timed": wall,
         "clocks": clk,
     }
+    if dfl is not None:
+        line["double_float"] = dfl
     if std is not None:
         line["standard"] = std
         line["speedup_split_vs_standard"] = std["ms_per_step"] / ms
@@ -715,7 +836,7 @@ def run_lam(args):
     if shell is not None:
         line["shell"] = shell
     if cpu is not None:
-        line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "nproc", "kind", "sample")}
     print(json.dumps(line), flush=True)
     plan.close()
     return 0
@@ -729,7 +850,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=("lam", "reference"), default="lam")
     ap.add_argument("--standard-steps", type=int, default=2)
     ap.add_argument("--standard-warmup", type=int, default=1)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--df-steps", type=int, default=20, help="timed double-float assemblies (0 = skip)")
     ap.add_argument("--adjoint-steps", type=int, default=20, help="timed lam_adjoint calls (0 = skip)")
     ap.add_argument("--batch-steps", type=int, default=5, help="timed lam_batch_assemble calls (0 = skip)")
     ap.add_argument("--large-steps", type=int, default=5, help="timed split assemblies of the Lagrange plate (0 = skip)")

@@ -117,12 +117,32 @@ typedef struct {
   double C[21];
 } lam_material;
 
+/* Arithmetic of the split path (lam_options.arith). The paper's claim is
+ * agreement of the split and standard matrices to machine precision (Section
+ * 3, after Eq. Q), so FP64 is the default.
+ *   LAM_ARITH_FP64          every product and sum of the in-plane integrals
+ *                           (K-a, Eq. P), the thickness integrals (K-b, Eq. Q)
+ *                           and the combine (K-c, Eq. Km_2) is an IEEE FP64
+ *                           operation (DFMA / DADD);
+ *   LAM_ARITH_DOUBLE_FLOAT  opt-in: the in-plane point values and Gram products
+ *                           and the combine's slice arithmetic run in
+ *                           double-float arithmetic (pairs of floats, error-free
+ *                           products and two-sums) on the FP32 pipes, about
+ *                           2^-44 relative per term instead of 2^-53, with an
+ *                           FP64 re-pass when a value leaves float range.
+ * Sums of partial results over elements, the thickness integrals and every
+ * stored value are FP64 in both. lam_assemble_standard and
+ * lam_assemble_split_noalloc are FP64 whatever this says. */
+#define LAM_ARITH_FP64 0
+#define LAM_ARITH_DOUBLE_FLOAT 1
+
 /* Options; pass NULL for the defaults. */
 typedef struct {
   int32_t nq_u, nq_v, nq_t; /* Gauss points per element direction; 0 = degree + 1 (Section 2.4) */
   double class_tol;         /* thickness pairs whose Q vectors (Eq. Q) agree to class_tol times the
                                largest |Q| of the same (a, b) term share one combine slice; < 0 = 1e-13,
                                0 = exact equality only */
+  int32_t arith;            /* LAM_ARITH_FP64 (default) or LAM_ARITH_DOUBLE_FLOAT */
 } lam_options;
 
 /* Sizes and structure of a plan. */
@@ -141,6 +161,7 @@ typedef struct {
                                 than 56 in-plane neighbours) */
   int32_t combine_chunks;    /* streaming: chunks of thickness rows whose classes fit in shared memory */
   int32_t shell;             /* 1: a general extrusion (surface in R^3 or a != e_z), see lam_inplane */
+  int32_t arith;             /* LAM_ARITH_FP64 or LAM_ARITH_DOUBLE_FLOAT (lam_options.arith) */
 } lam_plan_info;
 
 typedef struct lam_plan lam_plan;
@@ -202,7 +223,10 @@ lam_status lam_assemble_split_host(lam_plan* plan, double* h_values, void* strea
  *     64x64 cubic 48-ply plate needs about 16 MB.
  *   - The first call on a device looks up the array's device address for that
  *     device (once per device, with that device current); make that first
- *     call before any stream capture.
+ *     call before any stream capture. The address is kept for the life of the
+ *     process: it does not survive cudaDeviceReset (or the destruction of the
+ *     device's primary context), after which this entry point must not be
+ *     called again in that process.
  *   - All calls on a device share the one array and it keeps the last call's
  *     contents: calls that overlap on the GPU (two streams, or two host
  *     threads) race and corrupt each other's results, so serialise them.
@@ -226,13 +250,14 @@ typedef enum {
   LAM_COTANGENT_LOWRANK = 1  /* L = sum_{q < rank} u_q^T K v_q */
 } lam_cotangent_kind;
 
-/* lam_cotangent.flags */
-#define LAM_ADJOINT_FP64 1   /* evaluate every product in FP64 (slower; see lam_adjoint) */
+/* lam_cotangent.flags (0 = the default FP64 evaluation; the two flags exclude each other) */
+#define LAM_ADJOINT_FP64 1          /* low-rank cotangents: the generic FP64 pass instead of the factorised one */
+#define LAM_ADJOINT_DOUBLE_FLOAT 2  /* CSR cotangents: opt in to the double-float pass (see lam_adjoint) */
 
 typedef struct {
   int32_t kind;          /* lam_cotangent_kind */
   int32_t rank;          /* LOWRANK: number of vector pairs, >= 1 */
-  int32_t flags;         /* 0 or LAM_ADJOINT_FP64 */
+  int32_t flags;         /* 0, LAM_ADJOINT_FP64 or LAM_ADJOINT_DOUBLE_FLOAT */
   int32_t reserved;      /* 0 */
   const double* values;  /* CSR: nnz doubles (device), in the order of lam_pattern */
   const double* u;       /* LOWRANK: rank x n_dof doubles (device), row-major */
@@ -256,21 +281,23 @@ typedef struct {
  *   d_dtheta  n_plies doubles, per radian;
  *   d_dD      n_plies x 36 doubles, dL/dD_l[I][J] row-major, every entry of
  *             D_l taken as independent.
+ * Arithmetic: FP64 by default (every product and sum an FP64 operation).
  * Low-rank cotangents are contracted in factorised form (G v per thickness
- * function, then u^T (G v) per thickness pair) in FP64. For CSR cotangents:
- * Arithmetic: products and sums run in double-float arithmetic on the FP32
- * pipes (about 2^-44 relative per term) with FP64 partial sums. The whole
- * gradient is recomputed in FP64 on the same stream when a partial result is
- * not finite (a cotangent entry beyond float range, an infinity or a NaN) or
- * when no cotangent entry (low-rank: product of entries) reaches 2^-60 in
- * magnitude. Entries below 2^-80 next to larger ones contribute with an
- * absolute error below 2^-100 of their own size. LAM_ADJOINT_FP64 forces the
- * FP64 evaluation.
+ * function, then u^T (G v) per thickness pair); LAM_ADJOINT_FP64 takes them
+ * through the generic pass instead. CSR cotangents take one FP64 pass over the
+ * cotangent. With LAM_ADJOINT_DOUBLE_FLOAT (opt-in, CSR only) the products
+ * and sums run in double-float arithmetic on the FP32 pipes (about 2^-44
+ * relative per term) with FP64 partial sums, and the whole gradient is
+ * recomputed in FP64 on the same stream when a partial result is not finite (a
+ * cotangent entry beyond float range, an infinity or a NaN) or when no
+ * cotangent entry reaches 2^-60 in magnitude; entries below 2^-80 next to
+ * larger ones then contribute with an absolute error below 2^-100 of their own
+ * size.
  * A general extrusion (lam_inplane.shell): every (a, b) of D_l meets all four
  * thickness types through the 6 x 6 Gram blocks G_(alpha a)(beta b); CSR
- * cotangents take the same double-float pass (with the same FP64 re-pass
- * rules), low-rank ones and plies meeting more than 32 thickness pairs the
- * FP64 pass (workspace 16 * 36 * nnz_inplane bytes more).
+ * cotangents opting in to double-float take that pass (with the same FP64
+ * re-pass rules) unless a ply meets more than 32 thickness pairs; everything
+ * else takes the FP64 pass (workspace 16 * 36 * nnz_inplane bytes more).
  * The in-plane Gram blocks depend on the plan's geometry only, which never
  * changes: the first call computes them and later calls reuse them
  * (lam_inplane_operators with LAM_P_FROM_GRAM discards the copy). Workspace: about

@@ -71,6 +71,8 @@ def configure(L):
         L.ora_block.argtypes = [ctypes.POINTER(_Problem), ctypes.c_int64, ctypes.c_int64, _D]
         L.ora_element_stiffness.argtypes = [ctypes.POINTER(_Problem), ctypes.c_int32, ctypes.c_int32,
                                             ctypes.c_int32, _D]
+        L.ora_assemble_elements.argtypes = [ctypes.POINTER(_Problem), _I64, _I32, _I32, ctypes.c_int32, _D]
+        L.ora_inplane_row_blocks.argtypes = [ctypes.POINTER(_Problem), ctypes.c_int64, _I32, _D]
     return L
 
 
@@ -138,6 +140,12 @@ def basis1d_eval(kind: int, degree: int, knots, e: int, x: float):
     if lib().ora_basis1d_eval(ctypes.byref(b), e, x, _ptr(val), _ptr(der), ctypes.byref(first)) != 0:
         raise ValueError("bad element")
     return first.value, val, der
+
+
+def n_functions(kind: int, degree: int, knots) -> int:
+    k = np.ascontiguousarray(knots, dtype=np.float64)
+    b = _Basis(kind, degree, len(k), _ptr(k))
+    return lib().ora_nfun(ctypes.byref(b))
 
 
 def n_elements(kind: int, degree: int, knots) -> int:
@@ -266,6 +274,50 @@ def element_stiffness(lam, ex: int, ey: int, et: int, problem: Problem | None = 
     if lib().ora_element_stiffness(p.ref(), ex, ey, et, _ptr(out)) < 0:
         raise ValueError("element stiffness failed")
     return out.reshape(nl, nl, 3, 3)
+
+
+def element_colours(lam):
+    """The 3D elements (ex, ey, et) grouped so that no two elements of a group
+    share a basis function: colour (ex mod (p_u + 1), ey mod (p_v + 1),
+    et mod (q + 1)), each group an int32 array of triples."""
+    nex, ney = n_elements(lam.u.kind, lam.u.degree, lam.u.knots), n_elements(lam.v.kind, lam.v.degree, lam.v.knots)
+    net = n_elements(lam.t.kind, lam.t.degree, lam.t.knots)
+    cu, cv, ct = lam.u.degree + 1, lam.v.degree + 1, lam.t.degree + 1
+    groups = []
+    for kt in range(ct):
+        for ky in range(cv):
+            for kx in range(cu):
+                ex, ey, et = np.meshgrid(np.arange(kx, nex, cu), np.arange(ky, ney, cv), np.arange(kt, net, ct),
+                                         indexing="ij")
+                g = np.stack([ex.ravel(), ey.ravel(), et.ravel()], axis=1).astype(np.int32)
+                if len(g):
+                    groups.append(np.ascontiguousarray(g))
+    return groups
+
+
+def assemble_elements(lam, row_ptr, col, elems, val, problem: Problem | None = None) -> None:
+    """Adds the element stiffness of the listed elements (int32 triples) into
+    val on the CSR pattern (row_ptr, col) of pattern(lam). The C call releases
+    the GIL, so lists of one colour may run on several threads at once."""
+    p = problem if problem is not None else Problem(lam)
+    e = np.ascontiguousarray(elems, dtype=np.int32)
+    if lib().ora_assemble_elements(p.ref(), _ptr(row_ptr, _I64), _ptr(col, _I32), _ptr(e, _I32), len(e),
+                                   _ptr(val)) != 0:
+        raise ValueError("oracle element-list assembly failed")
+
+
+def inplane_row_blocks(lam, i_s: int, problem: Problem | None = None):
+    """Every 3x3 block of the rows (i_t, i_s) for all i_t: returns (bx0, by0,
+    blocks[it, jt, jy - by0, jx - bx0, 3, 3]). The C call releases the GIL."""
+    p = problem if problem is not None else Problem(lam)
+    nt = n_functions(lam.t.kind, lam.t.degree, lam.t.knots)
+    nbmax = (2 * lam.u.degree + 1) * (2 * lam.v.degree + 1)
+    out = np.zeros(9 * nt * nt * nbmax)
+    box = np.zeros(4, np.int32)
+    if lib().ora_inplane_row_blocks(p.ref(), int(i_s), _ptr(box, _I32), _ptr(out)) != 0:
+        raise ValueError("oracle row blocks failed")
+    bx0, nbx, by0, nby = (int(x) for x in box)
+    return bx0, by0, out[:9 * nt * nt * nbx * nby].reshape(nt, nt, nby, nbx, 3, 3)
 
 
 def to_dense(row_ptr, col, val, n):

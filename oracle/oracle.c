@@ -686,6 +686,143 @@ int ora_assemble(const ora_problem* pr, int64_t* row_ptr, int32_t* col, double* 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Element-list assembly for the timed CPU baseline: the element stiffness   */
+/* of each listed 3D element added into val on a CSR pattern given by the    */
+/* caller (the oracle's own ora_pattern), entry positions found by binary     */
+/* search in the rows. No second formula: the same element integrals as      */
+/* ora_assemble, restricted to a list, so that a caller can run lists of one */
+/* element colour (elements that share no basis function) on several threads.*/
+/* ------------------------------------------------------------------------ */
+static int64_t csr_find(const int64_t* row_ptr, const int32_t* col, int64_t r, int64_t c) {
+  int64_t lo = row_ptr[r], hi = row_ptr[r + 1];
+  while (lo < hi) {
+    int64_t mid = lo + (hi - lo) / 2;
+    if (col[mid] < c) lo = mid + 1; else hi = mid;
+  }
+  return (lo < row_ptr[r + 1] && col[lo] == c) ? lo : -1;
+}
+
+int ora_assemble_elements(const ora_problem* pr, const int64_t* row_ptr, const int32_t* col, const int32_t* elems,
+                          int32_t n, double* val) {
+  if (check_problem(pr) < 0) return -1;
+  support1d su, sv, st;
+  if (support_build(&pr->u, &su) < 0 || support_build(&pr->v, &sv) < 0 || support_build(&pr->t, &st) < 0) return -1;
+  int nlx = pr->u.degree + 1, nly = pr->v.degree + 1, nlt = pr->t.degree + 1;
+  int nls = nlx * nly, nl = nls * nlt;
+  int nx = su.n;
+  int64_t ns = (int64_t)su.n * sv.n;
+  double* Ke = malloc(sizeof(double) * (size_t)nl * nl * 9);
+  int rc = Ke ? 0 : -1;
+  for (int32_t k = 0; k < n && rc == 0; ++k) {
+    int ex = elems[3 * k], ey = elems[3 * k + 1], et = elems[3 * k + 2];
+    if (ora_element_stiffness(pr, ex, ey, et, Ke) < 0) { rc = -1; break; }
+    for (int a = 0; a < nl && rc == 0; ++a)
+      for (int b = 0; b < nl; ++b) {
+        int lta = a / nls, lsa = a % nls, ltb = b / nls, lsb = b % nls;
+        int64_t i = (int64_t)(st.first[et] + lta) * ns + (int64_t)(sv.first[ey] + lsa / nlx) * nx +
+                    (su.first[ex] + lsa % nlx);
+        int64_t j = (int64_t)(st.first[et] + ltb) * ns + (int64_t)(sv.first[ey] + lsb / nlx) * nx +
+                    (su.first[ex] + lsb % nlx);
+        for (int c = 0; c < 3; ++c) {
+          int64_t q = csr_find(row_ptr, col, 3 * i + c, 3 * j);
+          if (q < 0) { rc = -1; break; }
+          for (int d = 0; d < 3; ++d) val[q + d] += Ke[((size_t)a * nl + b) * 9 + c * 3 + d];
+        }
+        if (rc) break;
+      }
+  }
+  free(Ke);
+  support_free(&su);
+  support_free(&sv);
+  support_free(&st);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Every block of the rows of one in-plane function: K^{(it, is), (jt, js)}  */
+/* for all thickness functions it, jt and every in-plane js in the box       */
+/* |jx - ix| <= p_u, |jy - iy| <= p_v, by the integrand of ora_element_       */
+/* stiffness restricted to the row functions (it, is): the 3D elements in     */
+/* the support of is, every ply piece, the tensor Gauss rule. Layout:         */
+/* out[(((it * nt + jt) * nby + (jy - by0)) * nbx + (jx - bx0)) * 9 + c*3+d], */
+/* box[0..3] = bx0, nbx, by0, nby.                                            */
+/* ------------------------------------------------------------------------ */
+int ora_inplane_row_blocks(const ora_problem* pr, int64_t is, int32_t* box, double* out) {
+  if (check_problem(pr) < 0) return -1;
+  support1d su, sv, st;
+  if (support_build(&pr->u, &su) < 0 || support_build(&pr->v, &sv) < 0 || support_build(&pr->t, &st) < 0) return -1;
+  int rc = 0;
+  const int nx = su.n, ny = sv.n, nt = st.n;
+  const int ix = (int)(is % nx), iy = (int)(is / nx);
+  const int pu = pr->u.degree, pv = pr->v.degree;
+  const int bx0 = ix - pu > 0 ? ix - pu : 0, bx1 = ix + pu + 1 < nx ? ix + pu + 1 : nx;
+  const int by0 = iy - pv > 0 ? iy - pv : 0, by1 = iy + pv + 1 < ny ? iy + pv + 1 : ny;
+  const int nbx = bx1 - bx0, nby = by1 - by0;
+  box[0] = bx0; box[1] = nbx; box[2] = by0; box[3] = nby;
+  memset(out, 0, sizeof(double) * 9 * (size_t)nt * nt * nbx * nby);
+  const int nlx = pu + 1, nly = pv + 1, nlt = pr->t.degree + 1, nls = nlx * nly;
+  int nqu = nq_or_default(pr->nq_u, pu), nqv = nq_or_default(pr->nq_v, pv), nqt = nq_or_default(pr->nq_t, pr->t.degree);
+  double xu[64], wu[64], xv[64], wv[64], xt[64], wt[64];
+  ora_gauss(nqu, xu, wu);
+  ora_gauss(nqv, xv, wv);
+  ora_gauss(nqt, xt, wt);
+  double (*B)[6][3] = malloc(sizeof(double) * 18 * nls * nlt);
+  if (!B) rc = -1;
+  inplane_point ip;
+  for (int ey = sv.elo[iy]; ey <= sv.ehi[iy] && rc == 0; ++ey)
+    for (int ex = su.elo[ix]; ex <= su.ehi[ix] && rc == 0; ++ex) {
+      double ua, ub, va, vb;
+      int f;
+      element_of(&pr->u, ex, &ua, &ub, &f);
+      element_of(&pr->v, ey, &va, &vb, &f);
+      for (int et = 0; et < st.nel && rc == 0; ++et) {
+        double z0[512], z1[512];
+        int ply[512];
+        int npieces = ply_pieces(pr, et, z0, z1, ply, 512);
+        if (npieces < 0) { rc = -1; break; }
+        for (int pc = 0; pc < npieces && rc == 0; ++pc) {
+          int l = ply[pc];
+          double D[36];
+          ora_rotated_D(pr->C21 + 21 * pr->ply_material[l], pr->ply_angle[l], D);
+          for (int a = 0; a < nqu && rc == 0; ++a)
+            for (int b = 0; b < nqv && rc == 0; ++b) {
+              double xi = ua + 0.5 * (ub - ua) * (1.0 + xu[a]);
+              double eta = va + 0.5 * (vb - va) * (1.0 + xv[b]);
+              if (eval_inplane(pr, ex, ey, xi, eta, &ip) < 0) { rc = -1; break; }
+              const int li = (iy - ip.fy) * nlx + (ix - ip.fx);
+              for (int g = 0; g < nqt; ++g) {
+                double z = z0[pc] + 0.5 * (z1[pc] - z0[pc]) * (1.0 + xt[g]);
+                double T[8], dT[8];
+                int ft;
+                if (ora_basis1d_eval(&pr->t, et, z, T, dT, &ft) < 0) { rc = -1; break; }
+                const double wq = wu[a] * 0.5 * (ub - ua) * wv[b] * 0.5 * (vb - va) * wt[g] * 0.5 * (z1[pc] - z0[pc]);
+                const double w = wq * ip.detJ;
+                for (int lt = 0; lt < nlt; ++lt)
+                  for (int ls = 0; ls < nls; ++ls) {
+                    double grad[3];
+                    grad3(&ip, ls, T[lt], dT[lt], grad);
+                    strain_matrix(grad, B[lt * nls + ls]);
+                  }
+                for (int lt = 0; lt < nlt; ++lt)
+                  for (int ltj = 0; ltj < nlt; ++ltj)
+                    for (int lsj = 0; lsj < nls; ++lsj) {
+                      const int jx = ip.fx + lsj % nlx, jy = ip.fy + lsj / nlx;
+                      const size_t o = (((size_t)(ft + lt) * nt + (ft + ltj)) * nby + (jy - by0)) * nbx + (jx - bx0);
+                      add_btdb(w, B[lt * nls + li], D, B[ltj * nls + lsj], out + o * 9);
+                    }
+              }
+            }
+        }
+      }
+    }
+  free(B);
+  support_free(&su);
+  support_free(&sv);
+  support_free(&st);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------ */
 /* One block K^{ij}: the same integrand, summed over the 3D elements (and   */
 /* their ply pieces) in the intersection of the two supports.               */
 /* ------------------------------------------------------------------------ */

@@ -86,6 +86,22 @@ int ora_assemble(const ora_problem* pr, int64_t* row_ptr, int32_t* col, double* 
 /* Full split assembly (Eq. Km_2 with Eq. P and Eq. Q, one P per ply). */
 int ora_assemble_split(const ora_problem* pr, int64_t* row_ptr, int32_t* col, double* val);
 
+/* The element stiffness of each listed 3D element (elems: n triples ex, ey,
+ * et) added into val on the CSR pattern row_ptr / col (from ora_pattern): the
+ * integrals of ora_assemble restricted to a list, for the timed CPU baseline.
+ * Calls may run concurrently on lists of elements that share no basis
+ * function (one element colour). */
+int ora_assemble_elements(const ora_problem* pr, const int64_t* row_ptr, const int32_t* col, const int32_t* elems,
+                          int32_t n, double* val);
+
+/* Every 3x3 block of the rows of in-plane function is (all thickness
+ * functions it, jt; in-plane js in the box |jx - ix| <= p_u, |jy - iy| <= p_v,
+ * clipped): out[(((it * n_t + jt) * nby + (jy - by0)) * nbx + (jx - bx0)) * 9
+ * + c * 3 + d] with box = {bx0, nbx, by0, nby}; out holds
+ * 9 n_t^2 (2 p_u + 1)(2 p_v + 1) doubles at most. The same integrand as
+ * ora_element_stiffness, restricted to the row functions (it, is). */
+int ora_inplane_row_blocks(const ora_problem* pr, int64_t is, int32_t* box, double* out);
+
 /* One 3x3 block K^{ij} (row-major, [c][d]) for 3D basis indices i, j. */
 int ora_block(const ora_problem* pr, int64_t i, int64_t j, double* out9);
 

@@ -27,11 +27,13 @@ __all__ = [
     "LamError", "Plan", "load", "plan_create", "plan_destroy", "plan_get_info", "pattern", "assemble_split",
     "assemble_standard", "assemble_split_host", "assemble_split_noalloc", "plan_update", "profile_enable", "profile_get", "last_error",
     "version", "adjoint", "inplane_operators", "StiffnessFunction", "Batch", "batch_create", "batch_assemble", "batch_get_info",
-    "batch_destroy", "SYMBOLS", "KERNEL_KINDS", "BSPLINE", "LAGRANGE",
+    "batch_destroy", "SYMBOLS", "KERNEL_KINDS", "BSPLINE", "LAGRANGE", "ARITH_FP64", "ARITH_DOUBLE_FLOAT",
 ]
 
 BSPLINE = 0
 LAGRANGE = 1
+ARITH_FP64 = 0
+ARITH_DOUBLE_FLOAT = 1
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblam.so")
 
@@ -47,6 +49,7 @@ P_VOIGT_FREE = 1
 COTANGENT_CSR = 0
 COTANGENT_LOWRANK = 1
 ADJOINT_FP64 = 1
+ADJOINT_DOUBLE_FLOAT = 2
 
 _STATUS = {0: "LAM_OK", 1: "LAM_ERR_INVALID_ARG", 2: "LAM_ERR_UNSUPPORTED", 3: "LAM_ERR_OOM", 4: "LAM_ERR_CUDA",
            5: "LAM_ERR_TIMEOUT"}
@@ -79,7 +82,7 @@ class _Material(ctypes.Structure):
 
 class _Options(ctypes.Structure):
     _fields_ = [("nq_u", ctypes.c_int32), ("nq_v", ctypes.c_int32), ("nq_t", ctypes.c_int32),
-                ("class_tol", ctypes.c_double)]
+                ("class_tol", ctypes.c_double), ("arith", ctypes.c_int32)]
 
 
 class _Profile(ctypes.Structure):
@@ -103,7 +106,8 @@ class _Info(ctypes.Structure):
     _fields_ = [("n_dof", ctypes.c_int64), ("nnz", ctypes.c_int64), ("n_s", ctypes.c_int64), ("n_t", ctypes.c_int64),
                 ("nnz_inplane", ctypes.c_int64), ("nnz_thickness", ctypes.c_int64), ("n_configs", ctypes.c_int32),
                 ("n_classes", ctypes.c_int32), ("monoclinic", ctypes.c_int32), ("n_pieces", ctypes.c_int32),
-                ("combine_streaming", ctypes.c_int32), ("combine_chunks", ctypes.c_int32), ("shell", ctypes.c_int32)]
+                ("combine_streaming", ctypes.c_int32), ("combine_chunks", ctypes.c_int32), ("shell", ctypes.c_int32),
+                ("arith", ctypes.c_int32)]
 
 
 _lib = None
@@ -186,10 +190,12 @@ def _ptr(t) -> int:
 
 
 def plan_create(u, v, ctrl, t, ply_thickness, ply_material, ply_angle, C21, weights=None,
-                nq: Sequence[int] = (0, 0, 0), class_tol: float = -1.0, extrusion=None) -> ctypes.c_void_p:
+                nq: Sequence[int] = (0, 0, 0), class_tol: float = -1.0, extrusion=None,
+                arith: int = 0) -> ctypes.c_void_p:
     """lam_plan_create. u, v, t are (kind, degree, knots); C21 is (n_materials, 21);
     ctrl is (n_s, 2) for a planar map or (n_s, 3) for a surface in R^3;
-    extrusion is the direction a of F = S + xi^3 a (None: e_z)."""
+    extrusion is the direction a of F = S + xi^3 a (None: e_z); arith is
+    ARITH_FP64 (default) or ARITH_DOUBLE_FLOAT."""
     L = load()
     keep = []
 
@@ -225,7 +231,7 @@ def plan_create(u, v, ctrl, t, ply_thickness, ply_material, ply_angle, C21, weig
     mats = (_Material * C.shape[0])()
     for k in range(C.shape[0]):
         mats[k].C[:] = C[k].tolist()
-    opt = _Options(int(nq[0]), int(nq[1]), int(nq[2]), float(class_tol))
+    opt = _Options(int(nq[0]), int(nq[1]), int(nq[2]), float(class_tol), int(arith))
     handle = ctypes.c_void_p()
     _check(L.lam_plan_create(ctypes.byref(handle), ctypes.byref(ip), ctypes.byref(tb), plies, n, mats, C.shape[0],
                              ctypes.byref(opt)), "lam_plan_create")
@@ -293,15 +299,17 @@ def plan_update(handle, ply_angle=None, C21=None) -> None:
 
 
 def adjoint(handle, d_dC=None, d_dtheta=None, d_dD=None, values=None, u=None, v=None, rank=1, fp64=False,
-            stream=None) -> None:
+            stream=None, double_float=False) -> None:
     """lam_adjoint: gradients of L = sum(values * K) (values on the pattern) or
-    of L = sum_q u_q^T K v_q (u, v: rank x n_dof) into the given device buffers."""
+    of L = sum_q u_q^T K v_q (u, v: rank x n_dof) into the given device buffers.
+    fp64: LAM_ADJOINT_FP64 (low rank through the generic pass); double_float:
+    LAM_ADJOINT_DOUBLE_FLOAT (CSR cotangents, opt-in)."""
     c = _Cotangent()
     if values is not None:
         c.kind, c.values = COTANGENT_CSR, _ptr(values)
     else:
         c.kind, c.rank, c.u, c.v = COTANGENT_LOWRANK, int(rank), _ptr(u), _ptr(v)
-    c.flags = ADJOINT_FP64 if fp64 else 0
+    c.flags = (ADJOINT_FP64 if fp64 else 0) | (ADJOINT_DOUBLE_FLOAT if double_float else 0)
     _check(load().lam_adjoint(handle, ctypes.byref(c), _ptr(d_dC), _ptr(d_dtheta), _ptr(d_dD), _stream_handle(stream)),
            "lam_adjoint")
 
@@ -358,21 +366,21 @@ class Plan:
     """Convenience owner of a lam_plan handle; outputs are torch tensors."""
 
     def __init__(self, u, v, ctrl, t, ply_thickness, ply_material, ply_angle, C21, weights=None,
-                 nq=(0, 0, 0), class_tol=-1.0, extrusion=None):
+                 nq=(0, 0, 0), class_tol=-1.0, extrusion=None, arith=0):
         self.handle = plan_create(u, v, ctrl, t, ply_thickness, ply_material, ply_angle, C21, weights=weights,
-                                  nq=nq, class_tol=class_tol, extrusion=extrusion)
+                                  nq=nq, class_tol=class_tol, extrusion=extrusion, arith=arith)
         self.info = plan_get_info(self.handle)
         self.n_plies = len(ply_thickness)
         self.n_materials = int(np.atleast_2d(np.asarray(C21)).shape[0])
 
     @classmethod
-    def from_laminate(cls, lam, class_tol=-1.0) -> "Plan":
+    def from_laminate(cls, lam, class_tol=-1.0, arith=0) -> "Plan":
         """Build from any object with the fields u, v, t (kind, degree, knots),
         ctrl, weights, ply_thickness, ply_material, ply_angle, C21, nq."""
         b = lambda x: (x.kind, x.degree, x.knots)
         return cls(b(lam.u), b(lam.v), lam.ctrl, b(lam.t), lam.ply_thickness, lam.ply_material, lam.ply_angle,
                    lam.C21, weights=lam.weights, nq=tuple(lam.nq), class_tol=class_tol,
-                   extrusion=getattr(lam, "extrusion", None))
+                   extrusion=getattr(lam, "extrusion", None), arith=arith)
 
     @property
     def nnz(self) -> int:
@@ -420,7 +428,7 @@ class Plan:
         inplane_operators(self.handle, ply, method, P, stream)
         return P
 
-    def adjoint(self, values=None, u=None, v=None, fp64=False, want_dD=True, stream=None):
+    def adjoint(self, values=None, u=None, v=None, fp64=False, want_dD=True, stream=None, double_float=False):
         """(dL/dC: n_materials x 21, dL/dtheta: n_plies, dL/dD: n_plies x 6 x 6 or None)
         for L = sum(values * K) or L = sum_q u_q^T K v_q; device tensors."""
         import torch
@@ -433,7 +441,8 @@ class Plan:
             rank = u.shape[0]
             if v.shape[0] != rank:
                 raise ValueError("u and v must have the same number of rows")
-        adjoint(self.handle, dC, dth, dD, values=values, u=u, v=v, rank=rank, fp64=fp64, stream=stream)
+        adjoint(self.handle, dC, dth, dD, values=values, u=u, v=v, rank=rank, fp64=fp64, stream=stream,
+                double_float=double_float)
         return dC, dth, dD
 
     def profile_enable(self, enable=True):

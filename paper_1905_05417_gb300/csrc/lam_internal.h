@@ -49,6 +49,7 @@ struct Plan {
   std::vector<lam_material> mats;
   int nqu = 0, nqv = 0, nqt = 0;
   double class_tol = 1e-13;
+  int arith = LAM_ARITH_FP64;    // lam_options.arith
 
   // Gauss-Legendre rules on [-1, 1]
   std::vector<double> gxu, gwu, gxv, gwv, gxt, gwt;

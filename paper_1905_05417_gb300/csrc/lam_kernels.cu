@@ -69,6 +69,7 @@ struct Device {
   float2* qdf = nullptr;  // float pairs of q
 
   double* EG = nullptr;  // element Gram blocks: n_el x 9 x pairs
+  double* Grow = nullptr;  // assembled Gram blocks of every in-plane pair: nnz_s x 9 (FP64 combine)
   int* kc_flag = nullptr;      // streaming combine: FP64 re-pass flag, then the largest exponent
   float2* cfgEdf = nullptr;    // float pairs of cfgE
   double* cfgCb = nullptr;     // Appendix A bracket tensors per configuration
@@ -90,6 +91,7 @@ struct Device {
   float2* shell_Edf = nullptr;  // cfgE 2^-kE per configuration, float pairs (configuration tables)
   int* shell_kE = nullptr;
   int n_sm = 0;
+  int smem_optin = 0;    // largest dynamic shared memory of one CTA
   double* q = nullptr;   // nnz_t x n_cfg x 4
   // adjoint: geometry tables and workspace (allocated by the first lam_adjoint)
   bool adj_ready = false;
@@ -1300,6 +1302,112 @@ __global__ void __launch_bounds__(1024) kp_shell(KpShellArgs a) {
   if (threadIdx.x < 4) atomicMax(&a.pmax[threadIdx.x], smax[threadIdx.x]);
 }
 
+// K-a of a general extrusion in FP64: the output of ka_shell, with the point
+// values of shell_points (u_1 = g1 = R_,1 g^0 + R_,2 g^1, u_2 = R g^2, w|DF|)
+// and thread <-> (block (alpha, beta), unordered local pair), 9 FP64 fused
+// multiply-adds per point: G_(alpha a)(beta b) = sum_q w|DF| u_alpha^li[a] u_beta^lj[b].
+__global__ void __launch_bounds__(256) ka_shell64(KaShellArgs a) {
+  extern __shared__ double sm[];
+  const InplaneArgs& ip = a.ip;
+  const int nlx = ip.pu + 1, nly = ip.pv + 1, nls = nlx * nly, nqs = ip.nqu * ip.nqv;
+  const int e = blockIdx.x, ex = e % ip.nel_u, ey = e / ip.nel_u;
+  double* ph = sm;                              // [q][k][4]: g1 (3), R
+  double* qs = ph + (size_t)nqs * nls * 4;      // [q][kShellQ]
+  shell_points(ip, ex, ey, ph, qs);
+  const int npl = nls * (nls + 1) / 2;
+  double* out = a.EG + (size_t)e * npl * 36;
+  for (int t = threadIdx.x; t < 4 * npl; t += blockDim.x) {
+    const int blk = t / npl, pr = t % npl, al = blk >> 1, be = blk & 1;
+    int li = 0, rem = pr;
+    while (rem >= nls - li) {
+      rem -= nls - li;
+      ++li;
+    }
+    const int lj = li + rem;
+    double acc[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[k] = 0.0;
+    for (int q = 0; q < nqs; ++q) {
+      const double* d = qs + (size_t)q * kShellQ;
+      const double* fi = ph + ((size_t)q * nls + li) * 4;
+      const double* fj = ph + ((size_t)q * nls + lj) * 4;
+      const double w = d[9];
+      double ui[3], uj[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        ui[k] = w * (al ? fi[3] * d[6 + k] : fi[k]);
+        uj[k] = be ? fj[3] * d[6 + k] : fj[k];
+      }
+#pragma unroll
+      for (int x = 0; x < 3; ++x)
+#pragma unroll
+        for (int y = 0; y < 3; ++y) acc[x * 3 + y] = fma(ui[x], uj[y], acc[x * 3 + y]);
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) out[(size_t)pr * 36 + blk * 9 + k] = acc[k];
+  }
+}
+
+// P of every configuration for a general extrusion in FP64: the output of
+// kp_shell (same layout and pair set) with P_(alpha beta)[c][d] =
+// sum_(a,b) D_m[V(c,a)][V(d,b)] G_(alpha a)(beta b) as FP64 fused multiply-adds
+// (E = the configurations' cfgE tables, staged in shared memory when few).
+template <bool SMEM_E, bool MONO>
+__global__ void __launch_bounds__(1024) kp_shell64(KpShellArgs a, const double* __restrict__ cfgE) {
+  extern __shared__ double sE64[];
+  if (SMEM_E)
+    for (int k = threadIdx.x; k < a.ncfg * 81; k += blockDim.x) sE64[k] = cfgE[k];
+  __syncthreads();
+  const int64_t is = blockIdx.x;
+  const int ix = (int)(is % a.nx), iy = (int)(is / a.nx);
+  const int lx = a.lenX[ix], ls = lx * a.lenY[iy];
+  const int64_t ls0 = a.LSb[is];
+  const int ks0 = a.full ? 0 : (iy - a.loY[iy]) * lx + (ix - a.loX[ix]);
+  const int blk = threadIdx.x & 3;
+  for (int item = threadIdx.x; item < 4 * (ls - ks0); item += blockDim.x) {
+    const int ks = ks0 + (item >> 2);
+    const int jx = a.loX[ix] + ks % lx, jy = a.loY[iy] + ks / lx;
+    const int ex0 = max(a.eloX[ix], a.eloX[jx]), ex1 = min(a.ehiX[ix], a.ehiX[jx]);
+    const int ey0 = max(a.eloY[iy], a.eloY[jy]), ey1 = min(a.ehiY[iy], a.ehiY[jy]);
+    const int blkT = (blk & 1) * 2 + (blk >> 1);
+    double g[9];
+#pragma unroll
+    for (int ab = 0; ab < 9; ++ab) g[ab] = 0.0;
+    for (int ey = ey0; ey <= ey1; ++ey) {
+      const int fy = a.firstV[ey];
+      for (int ex = ex0; ex <= ex1; ++ex) {
+        const int fx = a.firstU[ex];
+        const int li = (iy - fy) * a.nlx + (ix - fx), lj = (jy - fy) * a.nlx + (jx - fx);
+        const size_t e0 = ((size_t)ey * a.nel_u + ex) * a.npl;
+        if (li <= lj) {
+          const double* src = a.EG + (e0 + upper_pair(li, lj, a.nls)) * 36 + blk * 9;
+#pragma unroll
+          for (int ab = 0; ab < 9; ++ab) g[ab] += src[ab];
+        } else {
+          const double* src = a.EG + (e0 + upper_pair(lj, li, a.nls)) * 36 + blkT * 9;
+#pragma unroll
+          for (int ab = 0; ab < 9; ++ab) g[ab] += src[(ab % 3) * 3 + ab / 3];
+        }
+      }
+    }
+    for (int m = 0; m < a.ncfg; ++m) {
+      const double* E = (SMEM_E ? sE64 : cfgE) + (size_t)m * 81;
+      double* out = a.P + ((size_t)m * a.nnz_s + ls0 + ks) * 36 + blk * 9;
+#pragma unroll
+      for (int cd = 0; cd < 9; ++cd) {
+        double v = 0.0;
+#pragma unroll
+        for (int ab = 0; ab < 9; ++ab) {
+          const int c = cd / 3, d = cd % 3, aa = ab / 3, bb = ab % 3;
+          if (MONO && (((c == 2) != (aa == 2)) != ((d == 2) != (bb == 2)))) continue;
+          v = fma(E[cd * 9 + ab], g[ab], v);
+        }
+        out[cd] = v;
+      }
+    }
+  }
+}
+
 // The assembled 6 x 6 Gram blocks of every in-plane pair of a general extrusion
 // (the adjoint's G): CTA per in-plane row, thread per (k_s, block), the block's
 // 9 entries summed over the shared elements in row-major element order, FP64.
@@ -1799,25 +1907,34 @@ __device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm,
               p12 = Pp[pref.o12];
               p21 = Pp[pref.o21];
               p22 = Pp[27];
-            } else if (MONO) {
+            } else if (MONO) {  // the fused multiply-adds of kc_ws, in its order (bitwise equal results)
               if (block_type) {
-                pa = E[0] * g[0] + E[1] * g[1] + E[3] * g[3] + E[4] * g[4];
+                pa = fma(E[4], g[4], fma(E[3], g[3], fma(E[1], g[1], E[0] * g[0])));
                 pb = E[8] * g[8];
               } else {
-                pa = E[2] * g[2] + E[5] * g[5];
-                pb = E[6] * g[6] + E[7] * g[7];
+                pa = fma(E[5], g[5], E[2] * g[2]);
+                pb = fma(E[7], g[7], E[6] * g[6]);
               }
             } else {
-              p11 = E[0] * g[0] + E[1] * g[1] + E[3] * g[3] + E[4] * g[4];
-              p12 = E[2] * g[2] + E[5] * g[5];
-              p21 = E[6] * g[6] + E[7] * g[7];
+              p11 = fma(E[4], g[4], fma(E[3], g[3], fma(E[1], g[1], E[0] * g[0])));
+              p12 = fma(E[5], g[5], E[2] * g[2]);
+              p21 = fma(E[7], g[7], E[6] * g[6]);
               p22 = E[8] * g[8];
             }
           }
           const double* Q = sQ + 4 * (size_t)t;
-          const double v = MONO ? Q[offa] * pa + Q[offb] * pb : Q[0] * p11 + Q[1] * p12 + Q[2] * p21 + Q[3] * p22;
           double* dst = slices + (size_t)sSlot[t] * a.slice_stride + item;
-          *dst = sFirst[t] ? v : *dst + v;
+          double v = sFirst[t] ? 0.0 : *dst;
+          if (MONO) {
+            v = fma(Q[offa], pa, v);
+            v = fma(Q[offb], pb, v);
+          } else {
+            v = fma(Q[0], p11, v);
+            v = fma(Q[1], p12, v);
+            v = fma(Q[2], p21, v);
+            v = fma(Q[3], p22, v);
+          }
+          *dst = v;
         }
       }
     }
@@ -1863,6 +1980,355 @@ __global__ void __maxnreg__(64) kc_stream(KcArgs a) {
       if (any_bad) atomicOr(a.flag, 1);
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// K-c in FP64, warp-specialised streaming form. One persistent CTA per SM
+// takes the work units (in-plane row i_s, thickness chunk) of rows
+// blockIdx.x, blockIdx.x + gridDim.x, ... Its first nct threads (the compute
+// group, thread (c, k_s, d) of the row as in kcs_row) load the row's
+// assembled G (kg_rows), form P_{m,ab}[c][d] per configuration (Eq. P for a homogeneous ply) and the
+// class slices sum_m sum_ab Q_{m,ab} P_{m,ab} (Eq. Km_2) with FP64 fused
+// multiply-adds into one of two shared-memory buffers, while the other warps
+// (the copy group) write the previous unit's share of the CSR values from the
+// other buffer in address order. The FP64 pipe and the HBM writes are thus
+// busy at the same time instead of in alternating phases. Hand-offs use
+// hardware named barriers: FULL[b] (compute arrives, copy waits) when buffer b
+// holds a unit's slices, EMPTY[b] (copy arrives, compute waits) when the copy
+// group has read it; both groups walk the same unit sequence, so every
+// barrier is met exactly as often by both sides.
+// ---------------------------------------------------------------------------
+constexpr int kBarCompute = 1, kBarFull = 2, kBarEmpty = 4;
+// (the non-.aligned forms: threads of a warp may reach them after divergent code)
+__device__ __forceinline__ void named_bar_sync(int id, int n) {
+  asm volatile("barrier.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void named_bar_arrive(int id, int n) {
+  asm volatile("barrier.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// the chunk's thickness rows, clipped to the rows written (CHUNKED output); false if none
+template <bool CHUNKED>
+__device__ __forceinline__ bool kcw_chunk(const KcArgs& a, int ch, int& it0, int& it1) {
+  it0 = a.ck_it[ch];
+  it1 = a.ck_it[ch + 1];
+  if (CHUNKED) {
+    it0 = max(it0, a.it_lo);
+    it1 = min(it1, a.it_hi);
+  }
+  return it0 < it1;
+}
+
+// The assembled in-plane Gram blocks of every in-plane pair, G_ab(i_s, k_s) =
+// sum over the shared elements (fixed row-major element order) of the element
+// blocks of K-a, into G[(LSb[i_s] + k_s) * 9 + ab]: CTA per in-plane row,
+// thread per (k_s, ab). FP64 sums, the order of the combine's own gather.
+__global__ void __launch_bounds__(512) kg_rows(KcArgs a, double* __restrict__ G) {
+  const int64_t is = blockIdx.x;
+  const int ix = (int)(is % a.nx), iy = (int)(is / a.nx);
+  const int lx = a.lenX[ix], n9 = 9 * lx * a.lenY[iy];
+  const int64_t ls0 = a.LSb[is];
+  for (int it = threadIdx.x; it < n9; it += blockDim.x) {
+    const int ks = it / 9, ab = it % 9;
+    const int jx = a.loX[ix] + ks % lx, jy = a.loY[iy] + ks / lx;
+    const int ex0 = max(a.eloX[ix], a.eloX[jx]), ex1 = min(a.ehiX[ix], a.ehiX[jx]);
+    const int ey0 = max(a.eloY[iy], a.eloY[jy]), ey1 = min(a.ehiY[iy], a.ehiY[jy]);
+    const int ba = (ab % 3) * 3 + ab / 3;
+    double acc = 0.0;
+    for (int ey = ey0; ey <= ey1; ++ey) {
+      const int fy = a.firstV[ey];
+      for (int ex = ex0; ex <= ex1; ++ex) {
+        const int fx = a.firstU[ex];
+        const int li = (iy - fy) * a.nlx + (ix - fx), lj = (jy - fy) * a.nlx + (jx - fx);
+        const size_t e9 = ((size_t)ey * a.nel_u + ex) * 9;
+        if (li <= lj)
+          acc += a.EG[(e9 + ab) * a.npl + upper_pair(li, lj, a.nls)];
+        else
+          acc += a.EG[(e9 + ba) * a.npl + upper_pair(lj, li, a.nls)];
+      }
+    }
+    G[ls0 * 9 + it] = acc;
+  }
+}
+
+// Copies the thickness pairs of one unit (pairs p_begin .. p_begin + npairs - 1
+// of row i_s, slices in S) into the CSR values, one warp per pair: the pair's
+// three segments (c = 0, 1, 2) of 3 len_s values, one CSR row apart. Pairs are
+// handed out by the shared counter *next, so any number of warps can join; a
+// warp takes its next pair (and loads that pair's table entries) before it
+// copies the current one.
+__device__ __forceinline__ void kcw_copy_pairs(const KcArgs& a, const double* S, int* next, int64_t p_begin,
+                                               int npairs, int64_t ls0, int seg_len, int lane) {
+  auto take = [&]() {
+    int q = 0;
+    if (lane == 0) q = atomicAdd(next, 1);
+    return __shfl_sync(0xffffffffu, q, 0);
+  };
+  int q = take();
+  int64_t A = 0;
+  int lt = 0, kt = 0, u = 0;
+  if (q < npairs) {
+    A = __ldg(a.tp_A + p_begin + q);
+    lt = __ldg(a.tp_lt + p_begin + q);
+    kt = __ldg(a.tp_k + p_begin + q);
+    u = __ldg(a.pair_slot + p_begin + q);
+  }
+  while (q < npairs) {
+    const int qn = take();
+    int64_t An = 0;
+    int ltn = 0, ktn = 0, un = 0;
+    if (qn < npairs) {
+      An = __ldg(a.tp_A + p_begin + qn);
+      ltn = __ldg(a.tp_lt + p_begin + qn);
+      ktn = __ldg(a.tp_k + p_begin + qn);
+      un = __ldg(a.pair_slot + p_begin + qn);
+    }
+    const double* src = S + (size_t)u * a.slice_stride;
+    double* dst = a.values + (A + (int64_t)lt * 9 * ls0 + (int64_t)kt * seg_len - a.out_offset);
+    const int64_t row_step = (int64_t)lt * seg_len;
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+      double v[kSegUnroll];
+#pragma unroll
+      for (int j = 0; j < kSegUnroll; ++j) v[j] = (lane + 32 * j < seg_len) ? src[cc * seg_len + lane + 32 * j] : 0.0;
+#pragma unroll
+      for (int j = 0; j < kSegUnroll; ++j)
+        if (lane + 32 * j < seg_len) dst[cc * row_step + lane + 32 * j] = v[j];
+    }
+    q = qn;
+    A = An;
+    lt = ltn;
+    kt = ktn;
+    u = un;
+  }
+}
+
+template <bool MONO, bool CHUNKED, bool SHELL>
+__global__ void __launch_bounds__(896, 1) kc_ws(KcArgs a, int nct) {
+  static_assert(!(SHELL && MONO), "a general extrusion couples every block");
+  extern __shared__ double sm[];
+  const int tid = threadIdx.x, nall = blockDim.x;
+  const size_t buf_elems = (size_t)a.nslot_max * a.slice_stride;
+  double* sG = sm + 2 * buf_elems;                                     // the row's G blocks (9 per neighbour)
+  double* sQ = sG + a.slice_stride;                                    // chunk terms: Q
+  int2* sMeta = reinterpret_cast<int2*>(sQ + 4 * (size_t)a.max_terms);  // (2 slot + first, configuration)
+  int* sNext = reinterpret_cast<int*>(sMeta + a.max_terms);               // next pair of each buffer's unit
+  if (tid < 2) sNext[tid] = 0;
+  __syncthreads();  // the only CTA-wide barrier: the groups part here
+  int nch_eff = 0;
+  for (int ch = 0; ch < a.nchunk; ++ch) {
+    int it0, it1;
+    nch_eff += kcw_chunk<CHUNKED>(a, ch, it0, it1) ? 1 : 0;
+  }
+  const int64_t nrows = blockIdx.x < a.ns ? (a.ns - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t nunits = nrows * nch_eff;
+  if (tid < nct) {
+    // ---------------- compute group ----------------
+    int k = 0, loaded = -1;
+    double gpre = 0.0;  // this thread's G entry of the next row (prefetched)
+    const int lane = tid & 31;
+    // the previous unit, whose copy the compute warps join once their own slices are done
+    int prev_b = -1, prev_np = 0, prev_seg = 0;
+    int64_t prev_p0 = 0, prev_ls0 = 0;
+    for (int64_t is = blockIdx.x; is < a.ns; is += gridDim.x) {
+      const int ix = (int)(is % a.nx), iy = (int)(is / a.nx);
+      const int lx = a.lenX[ix];
+      const int ls = lx * a.lenY[iy];
+      const int n9 = 9 * ls;
+      const int64_t ls0 = a.LSb[is];
+      const int item = tid;
+      const bool active = item < n9;
+      int c = 0, ks = 0, d = 0;
+      if (active) {
+        c = item / (3 * ls);
+        const int rem = item % (3 * ls);
+        ks = rem / 3;
+        d = rem % 3;
+      }
+      const int cd = c * 3 + d;
+      const bool block_type = ((c == 2) == (d == 2));
+      const int offa = block_type ? 0 : 1, offb = block_type ? 3 : 2;
+      ShellPRef pref{nullptr, 9, 18};
+      if (SHELL && active) pref = shell_p_ref(a, is, ix, iy, lx, ls0, ks, c, d);
+      bool first_unit_of_row = true;
+      for (int ch = 0; ch < a.nchunk; ++ch) {
+        int it0, it1;
+        if (!kcw_chunk<CHUNKED>(a, ch, it0, it1)) continue;
+        const int b = k & 1;
+        double* S = sm + (size_t)b * buf_elems;
+        if (k >= 2) named_bar_sync(kBarEmpty + b, nall);  // the copy group has read buffer b
+        if (!SHELL && first_unit_of_row) {
+          // phase 0: the row's assembled G blocks (kg_rows) into sG, after every
+          // thread has formed its last P from the previous row's; the entry of
+          // this thread was loaded during the previous row (one load per thread,
+          // n9 <= nct), and the next row's entry is requested right after
+          if (k > 0) named_bar_sync(kBarCompute, nct);
+          if (k == 0 && tid < n9) gpre = a.G[ls0 * 9 + tid];
+          if (tid < n9) sG[tid] = gpre;
+          named_bar_sync(kBarCompute, nct);
+          const int64_t nx_is = is + gridDim.x;
+          if (nx_is < a.ns) {
+            const int nix = (int)(nx_is % a.nx), niy = (int)(nx_is / a.nx);
+            if (tid < 9 * a.lenX[nix] * a.lenY[niy]) gpre = a.G[a.LSb[nx_is] * 9 + tid];
+          }
+        }
+        first_unit_of_row = false;
+        // the chunk's terms (loaded once when the plan has one chunk)
+        const int tb = a.ck_term[ch], nterm = a.ck_term[ch + 1] - tb;
+        if (loaded != ch) {
+          if (loaded >= 0) named_bar_sync(kBarCompute, nct);  // nobody still reads the previous chunk's terms
+          for (int q = tid; q < nterm; q += nct) {
+            const int t = tb + q, m = a.ckt_cfg[t];
+            const size_t qi = ((size_t)a.ckt_rep[t] * a.ncfg + m) * 4;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) sQ[4 * (size_t)q + j] = a.q[qi + j];
+            sMeta[q] = make_int2(2 * a.ckt_slot[t] + (a.ckt_first[t] ? 1 : 0), m);
+          }
+          named_bar_sync(kBarCompute, nct);
+          loaded = ch;
+        }
+        // phase 1: the slice of every class of the chunk, FP64
+        if (active) {
+          const double* g = sG + ks * 9;
+          int cur = -1;
+          double pa = 0.0, pb = 0.0, p11 = 0.0, p12 = 0.0, p21 = 0.0, p22 = 0.0;
+          for (int t = 0; t < nterm; ++t) {
+            const int2 meta = sMeta[t];
+            const int m = meta.y;
+            if (m != cur) {
+              cur = m;
+              if (SHELL) {
+                const double* Pp = pref.p + (size_t)m * a.nnz_s * 36;
+                p11 = Pp[0];
+                p12 = Pp[pref.o12];
+                p21 = Pp[pref.o21];
+                p22 = Pp[27];
+              } else {
+                const double* E = a.cfgE + (size_t)m * 81 + cd * 9;
+                if (MONO) {
+                  if (block_type) {
+                    pa = fma(E[4], g[4], fma(E[3], g[3], fma(E[1], g[1], E[0] * g[0])));
+                    pb = E[8] * g[8];
+                  } else {
+                    pa = fma(E[5], g[5], E[2] * g[2]);
+                    pb = fma(E[7], g[7], E[6] * g[6]);
+                  }
+                } else {
+                  p11 = fma(E[4], g[4], fma(E[3], g[3], fma(E[1], g[1], E[0] * g[0])));
+                  p12 = fma(E[5], g[5], E[2] * g[2]);
+                  p21 = fma(E[7], g[7], E[6] * g[6]);
+                  p22 = E[8] * g[8];
+                }
+              }
+            }
+            const double* Q = sQ + 4 * (size_t)t;
+            double* dst = S + (size_t)(meta.x >> 1) * a.slice_stride + item;
+            double v = (meta.x & 1) ? 0.0 : *dst;
+            if (MONO) {
+              v = fma(Q[offa], pa, v);
+              v = fma(Q[offb], pb, v);
+            } else {
+              v = fma(Q[0], p11, v);
+              v = fma(Q[1], p12, v);
+              v = fma(Q[2], p21, v);
+              v = fma(Q[3], p22, v);
+            }
+            *dst = v;
+          }
+        }
+        if (tid == 0) sNext[b] = 0;  // nobody takes pairs of buffer b until FULL[b] completes
+        __threadfence_block();
+        named_bar_arrive(kBarFull + b, nall);  // buffer b holds the unit's slices
+        // join the copy of the previous unit, whose buffer the next unit reuses
+        if (prev_b >= 0)
+          kcw_copy_pairs(a, sm + (size_t)prev_b * buf_elems, sNext + prev_b, prev_p0, prev_np, prev_ls0, prev_seg, lane);
+        prev_b = b;
+        prev_p0 = a.LTb[it0];
+        prev_np = (int)(a.LTb[it1] - a.LTb[it0]);
+        prev_ls0 = ls0;
+        prev_seg = 3 * ls;
+        ++k;
+      }
+    }
+    if (prev_b >= 0) {  // the last unit: every compute thread's slices are visible after the barrier
+      named_bar_sync(kBarCompute, nct);
+      kcw_copy_pairs(a, sm + (size_t)prev_b * buf_elems, sNext + prev_b, prev_p0, prev_np, prev_ls0, prev_seg, lane);
+    }
+  } else {
+    // ---------------- copy group ----------------
+    const int lane = tid & 31;
+    int64_t k = 0;
+    for (int64_t is = blockIdx.x; is < a.ns; is += gridDim.x) {
+      const int ix = (int)(is % a.nx), iy = (int)(is / a.nx);
+      const int ls = a.lenX[ix] * a.lenY[iy];
+      const int seg_len = 3 * ls;
+      const int64_t ls0 = a.LSb[is];
+      for (int ch = 0; ch < a.nchunk; ++ch) {
+        int it0, it1;
+        if (!kcw_chunk<CHUNKED>(a, ch, it0, it1)) continue;
+        const int b = (int)(k & 1);
+        const double* S = sm + (size_t)b * buf_elems;
+        named_bar_sync(kBarFull + b, nall);
+        kcw_copy_pairs(a, S, sNext + b, a.LTb[it0], (int)(a.LTb[it1] - a.LTb[it0]), ls0, seg_len, lane);
+        if (k + 2 < nunits) {
+          __threadfence_block();
+          named_bar_arrive(kBarEmpty + b, nall);  // buffer b may be overwritten
+        }
+        ++k;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K-a in FP64 (single launch): one CTA per in-plane element, the same output
+// as ka_local. Point values (Eq. gradient: g = (dR/dx, dR/dy, R) and w|DF| g
+// at every Gauss point) by inplane_points, then thread <-> unordered local
+// pair (li <= lj): G_ab = sum_q (w|DF| g_a^li)(q) g_b^lj(q), 9 FP64 fused
+// multiply-adds per point, into EG[(e * 9 + ab) * npl + pair].
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void ka_elem64(const KaLocalArgs& a, int e, double* sm) {
+  const InplaneArgs& ip = a.ip;
+  const int nlx = ip.pu + 1, nly = ip.pv + 1, nls = nlx * nly, nqs = ip.nqu * ip.nqv;
+  double* phi = sm;
+  double* phiw = phi + (size_t)nqs * nls * 3;
+  double* qd = phiw + (size_t)nqs * nls * 3;
+  const int ex = e % ip.nel_u, ey = e / ip.nel_u;
+  inplane_points(ip, ex, ey, phi, phiw, qd);
+  const int npl = nls * (nls + 1) / 2;
+  double* out = a.EG + (size_t)e * 9 * npl;
+  for (int t = threadIdx.x; t < npl; t += blockDim.x) {
+    int li = 0, rem = t;
+    while (rem >= nls - li) {
+      rem -= nls - li;
+      ++li;
+    }
+    const int lj = li + rem;
+    double acc[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) acc[q] = 0.0;
+    for (int q = 0; q < nqs; ++q) {
+      const double* A = phiw + ((size_t)q * nls + li) * 3;
+      const double* B = phi + ((size_t)q * nls + lj) * 3;
+      const double a0 = A[0], a1 = A[1], a2 = A[2], b0 = B[0], b1 = B[1], b2 = B[2];
+      acc[0] = fma(a0, b0, acc[0]);
+      acc[1] = fma(a0, b1, acc[1]);
+      acc[2] = fma(a0, b2, acc[2]);
+      acc[3] = fma(a1, b0, acc[3]);
+      acc[4] = fma(a1, b1, acc[4]);
+      acc[5] = fma(a1, b2, acc[5]);
+      acc[6] = fma(a2, b0, acc[6]);
+      acc[7] = fma(a2, b1, acc[7]);
+      acc[8] = fma(a2, b2, acc[8]);
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q) out[(size_t)q * npl + t] = acc[q];
+  }
+}
+
+__global__ void __launch_bounds__(256) ka_local64(KaLocalArgs a) {
+  extern __shared__ double sm[];
+  ka_elem64(a, blockIdx.x, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -2053,6 +2519,10 @@ static lam_status ensure_device(Plan& P) {
       free_device(P);
       return st;
     }
+    if ((st = alloc_dev(L, &D->Grow, (size_t)P.nnz_s * 9)) != LAM_OK) {
+      free_device(P);
+      return st;
+    }
     double* fl = nullptr;
     if ((st = alloc_dev(L, &fl, 1)) != LAM_OK) {
       free_device(P);
@@ -2060,6 +2530,7 @@ static lam_status ensure_device(Plan& P) {
     }
     D->kc_flag = reinterpret_cast<int*>(fl);
     LAM_CUDA(cudaDeviceGetAttribute(&D->n_sm, cudaDevAttrMultiProcessorCount, cur));
+    LAM_CUDA(cudaDeviceGetAttribute(&D->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, cur));
   }
   if (P.cfg_dirty) {
     Device* D = P.dev;
@@ -2289,12 +2760,64 @@ static lam_status launch_kc(const Plan& P, const KcArgs& k, cudaStream_t s) {
   return LAM_OK;
 }
 
-// Combine into `values`: streaming form when a row's slices fit, class-major form otherwise.
+// FP64 streaming combine. The warp-specialised form (kc_ws: one CTA per SM,
+// compute threads (c, k_s, d) plus kcw_copy_threads copy threads, two slice
+// buffers) when both buffers fit in shared memory; otherwise kc_stream in FP64
+// (two CTAs per SM alternating their compute and copy phases).
+static int kcw_copy_threads(const Plan& P) { return std::min(512, 896 - kcs_block(P)); }
+static size_t kcw_smem(const Plan& P) {
+  int slots = 1;
+  for (int v : P.ck_nslot) slots = std::max(slots, v);
+  return (2 * (size_t)slots + 1) * kcs_stride(P) * sizeof(double) + (size_t)kcs_max_terms(P) * (32 + 8) + 16 + 16;
+}
+static bool kcw_fits(const Plan& P) {
+  return kcs_block(P) + 64 <= 896 && kcw_smem(P) <= (size_t)P.dev->smem_optin;
+}
+template <bool MONO, bool CHUNKED, bool SHELL = false>
+static lam_status launch_kc64(const Plan& P, const KcArgs& k, cudaStream_t s) {
+  if (kcw_fits(P) && !SHELL && (!CHUNKED || k.it_lo == 0)) {
+    // the rows' assembled Gram blocks, read by kc_ws in one coalesced load per
+    // row (once per assembly: the host-output path's slabs follow on the same
+    // stream); profiled with the in-plane kernels
+    cudaEvent_t eg = prof_begin(const_cast<Plan&>(P), s);
+    kg_rows<<<(unsigned)P.ns, std::min(512, std::max(64, ((9 * max_len_s(P) + 31) / 32) * 32)), 0, s>>>(k, P.dev->Grow);
+    LAM_CUDA(cudaGetLastError());
+    prof_end(const_cast<Plan&>(P), LAM_KERNEL_INPLANE, 1, s, eg);
+  }
+  cudaEvent_t ev = prof_begin(const_cast<Plan&>(P), s);
+  if (kcw_fits(P)) {
+    KcArgs kw = k;
+    if (!SHELL) kw.G = P.dev->Grow;
+    const size_t smem = kcw_smem(P);
+    LAM_CUDA(cudaFuncSetAttribute(kc_ws<MONO, CHUNKED, SHELL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int nct = kcs_block(P), block = nct + kcw_copy_threads(P);
+    const int64_t grid = std::min<int64_t>(P.ns, std::max(1, P.dev->n_sm));
+    kc_ws<MONO, CHUNKED, SHELL><<<(unsigned)grid, block, smem, s>>>(kw, nct);
+  } else {
+    const size_t smem = kcs_smem(P);
+    LAM_CUDA(cudaFuncSetAttribute(kc_stream<MONO, CHUNKED, false, SHELL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    const int64_t grid = std::min<int64_t>(P.ns, (int64_t)kcs_ctas_per_sm(P) * std::max(1, P.dev->n_sm));
+    kc_stream<MONO, CHUNKED, false, SHELL><<<(unsigned)grid, kcs_block(P), smem, s>>>(k);
+  }
+  LAM_CUDA(cudaGetLastError());
+  prof_end(const_cast<Plan&>(P), LAM_KERNEL_COMBINE, 1, s, ev);
+  return LAM_OK;
+}
+
+// Combine into `values`: streaming form when a row's slices fit, class-major
+// form (FP64) otherwise; the streaming form in the plan's arithmetic.
 template <bool CHUNKED>
 static lam_status launch_combine(const Plan& P, const KcArgs& k, cudaStream_t s) {
-  if (P.shell) return use_stream(P) ? launch_kcs<false, CHUNKED, true>(P, k, s) : launch_kc<false, CHUNKED, true>(P, k, s);
-  if (use_stream(P))
-    return P.monoclinic ? launch_kcs<true, CHUNKED>(P, k, s) : launch_kcs<false, CHUNKED>(P, k, s);
+  const bool df = P.arith == LAM_ARITH_DOUBLE_FLOAT;
+  if (P.shell) {
+    if (!use_stream(P)) return launch_kc<false, CHUNKED, true>(P, k, s);
+    return df ? launch_kcs<false, CHUNKED, true>(P, k, s) : launch_kc64<false, CHUNKED, true>(P, k, s);
+  }
+  if (use_stream(P)) {
+    if (df) return P.monoclinic ? launch_kcs<true, CHUNKED>(P, k, s) : launch_kcs<false, CHUNKED>(P, k, s);
+    return P.monoclinic ? launch_kc64<true, CHUNKED>(P, k, s) : launch_kc64<false, CHUNKED>(P, k, s);
+  }
   return P.monoclinic ? launch_kc<true, CHUNKED>(P, k, s) : launch_kc<false, CHUNKED>(P, k, s);
 }
 
@@ -2306,9 +2829,13 @@ static lam_status inplane_gram(Plan& P, cudaStream_t s) {
   ka.nel = P.u.nel * P.v.nel;
   ka.EG = D.EG;
   const size_t smem = ka_smem(P);
-  LAM_CUDA(cudaFuncSetAttribute(ka_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const bool df = P.arith == LAM_ARITH_DOUBLE_FLOAT;
+  LAM_CUDA(cudaFuncSetAttribute(df ? ka_local : ka_local64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   cudaEvent_t ev = prof_begin(P, s);
-  ka_local<<<ka.nel, ka_block(P), smem, s>>>(ka);
+  if (df)
+    ka_local<<<ka.nel, ka_block(P), smem, s>>>(ka);
+  else
+    ka_local64<<<ka.nel, ka_block(P), smem, s>>>(ka);
   LAM_CUDA(cudaGetLastError());
   prof_end(P, LAM_KERNEL_INPLANE, 1, s, ev);
   return LAM_OK;
@@ -2349,9 +2876,15 @@ static lam_status shell_element_gram(Plan& P, cudaStream_t s) {
   KaShellArgs ka{};
   ka.ip = inplane_args(P);
   ka.EG = D.shellEG;
-  const size_t smem = ka_shell_smem(P);
-  LAM_CUDA(cudaFuncSetAttribute(ka_shell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  ka_shell<<<(unsigned)nel, 256, smem, s>>>(ka);
+  if (P.arith == LAM_ARITH_DOUBLE_FLOAT) {
+    const size_t smem = ka_shell_smem(P);
+    LAM_CUDA(cudaFuncSetAttribute(ka_shell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ka_shell<<<(unsigned)nel, 256, smem, s>>>(ka);
+  } else {
+    const size_t smem = kd_smem(P);  // shell_points: nqs x nls x 4 + nqs x 16 doubles
+    LAM_CUDA(cudaFuncSetAttribute(ka_shell64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ka_shell64<<<(unsigned)nel, 256, smem, s>>>(ka);
+  }
   LAM_CUDA(cudaGetLastError());
   return LAM_OK;
 }
@@ -2387,13 +2920,21 @@ static lam_status shell_operators(Plan& P, cudaStream_t s, bool full) {
   kp.full = full ? 1 : 0;
   LAM_CUDA(cudaMemsetAsync(D.shell_pmax, 0, 4 * sizeof(unsigned long long), s));
   const bool smem_e = ncfg <= kKpShellSmemCfg;
-  const size_t smem_p = smem_e ? (size_t)ncfg * 81 * sizeof(float2) : 0;
   // threads for the pairs j_s >= i_s of an interior row (about half); rows with more loop
   const int block_p = std::max(64, ((4 * (max_len_s(P) / 2 + 1) + 31) / 32) * 32);
-  auto kern = smem_e ? (P.monoclinic ? kp_shell<true, true> : kp_shell<true, false>)
-                     : (P.monoclinic ? kp_shell<false, true> : kp_shell<false, false>);
-  LAM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p));
-  kern<<<(unsigned)P.ns, block_p, smem_p, s>>>(kp);
+  if (P.arith == LAM_ARITH_DOUBLE_FLOAT) {
+    const size_t smem_p = smem_e ? (size_t)ncfg * 81 * sizeof(float2) : 0;
+    auto kern = smem_e ? (P.monoclinic ? kp_shell<true, true> : kp_shell<true, false>)
+                       : (P.monoclinic ? kp_shell<false, true> : kp_shell<false, false>);
+    LAM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p));
+    kern<<<(unsigned)P.ns, block_p, smem_p, s>>>(kp);
+  } else {
+    const size_t smem_p = smem_e ? (size_t)ncfg * 81 * sizeof(double) : 0;
+    auto kern = smem_e ? (P.monoclinic ? kp_shell64<true, true> : kp_shell64<true, false>)
+                       : (P.monoclinic ? kp_shell64<false, true> : kp_shell64<false, false>);
+    LAM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p));
+    kern<<<(unsigned)P.ns, block_p, smem_p, s>>>(kp, D.cfgE);
+  }
   LAM_CUDA(cudaGetLastError());
   prof_end(P, LAM_KERNEL_INPLANE, 2, s, ev);
   return LAM_OK;
@@ -3166,10 +3707,10 @@ static lam_status adjoint_shell(Plan& P, const lam_cotangent& cot, double* dC, d
   a.flag = D.adj_flag;
   a.emax = D.adj_flag + 1;
   const bool lowrank = cot.kind == LAM_COTANGENT_LOWRANK;
-  const bool force64 = (cot.flags & LAM_ADJOINT_FP64) != 0;
-  // double-float pass for CSR cotangents whose plies meet few thickness pairs;
-  // the FP64 pass after it runs only when its result is rejected
-  const bool df = !lowrank && !force64 && P.adj_max_terms <= kAdjFastTerms;
+  const bool want_df = (cot.flags & LAM_ADJOINT_DOUBLE_FLOAT) != 0;
+  // double-float pass (opt-in) for CSR cotangents whose plies meet few
+  // thickness pairs; the FP64 pass after it runs only when its result is rejected
+  const bool df = !lowrank && want_df && P.adj_max_terms <= kAdjFastTerms;
   cudaEvent_t ev = prof_begin(P, s);
   if (df) {
     a.conditional = 0;
@@ -3263,7 +3804,11 @@ static lam_status adjoint(Plan& P, const lam_cotangent& cot, double* dC, double*
   a.flag = D.adj_flag;
   a.emax = D.adj_flag + 1;
   const bool lowrank = cot.kind == LAM_COTANGENT_LOWRANK;
+  // LAM_ADJOINT_FP64 sends a low-rank cotangent through the generic FP64 pass
+  // (a cross-check of the factorised one); LAM_ADJOINT_DOUBLE_FLOAT opts a CSR
+  // cotangent into the double-float pass
   const bool force64 = (cot.flags & LAM_ADJOINT_FP64) != 0;
+  const bool df = !lowrank && (cot.flags & LAM_ADJOINT_DOUBLE_FLOAT) != 0;
   int nchunks_out = a.nchunks;
   ev = prof_begin(P, s);
   if (lowrank && !force64) {
@@ -3299,11 +3844,9 @@ static lam_status adjoint(Plan& P, const lam_cotangent& cot, double* dC, double*
     prof_end(P, LAM_KERNEL_ADJOINT, 2 * cot.rank + 1, s, ev);
     ev = prof_begin(P, s);
     nchunks_out = 1;
-  } else if (!force64) {
+  } else if (df) {
     a.conditional = 0;
-    if (lowrank)
-      st = launch_adj_ply<true, true>(P, a, s);
-    else if (P.adj_max_terms > kAdjFastTerms)
+    if (P.adj_max_terms > kAdjFastTerms)
       st = launch_adj_ply<false, true>(P, a, s);
     else if (P.nnz < ((int64_t)1 << 31))
       st = launch_adj_df<int32_t>(P, a, s);
@@ -3315,10 +3858,10 @@ static lam_status adjoint(Plan& P, const lam_cotangent& cot, double* dC, double*
   }
   int aux = 1;  // the reduce
   if (!(lowrank && !force64)) {
-    a.conditional = force64 ? 0 : 1;  // otherwise it runs only when the double-float result is rejected
+    a.conditional = df ? 1 : 0;  // after a double-float pass it runs only when that result is rejected
     st = lowrank ? launch_adj_ply<true, false>(P, a, s) : launch_adj_ply<false, false>(P, a, s);
     if (st != LAM_OK) return st;
-    if (force64) {
+    if (!df) {
       prof_end(P, LAM_KERNEL_ADJOINT, 1, s, ev);
       ev = prof_begin(P, s);
     } else {
@@ -3778,8 +4321,9 @@ lam_status lam_adjoint(lam_plan* plan, const lam_cotangent* cot, double* d_dC, d
     lam::set_error("lam_adjoint: unknown cotangent kind %d", (int)cot->kind);
     return LAM_ERR_INVALID_ARG;
   }
-  if ((cot->flags & ~LAM_ADJOINT_FP64) != 0) {
-    lam::set_error("lam_adjoint: unknown flags 0x%x", (unsigned)cot->flags);
+  if ((cot->flags & ~(LAM_ADJOINT_FP64 | LAM_ADJOINT_DOUBLE_FLOAT)) != 0 ||
+      (cot->flags & (LAM_ADJOINT_FP64 | LAM_ADJOINT_DOUBLE_FLOAT)) == (LAM_ADJOINT_FP64 | LAM_ADJOINT_DOUBLE_FLOAT)) {
+    lam::set_error("lam_adjoint: unknown or conflicting flags 0x%x", (unsigned)cot->flags);
     return LAM_ERR_INVALID_ARG;
   }
   lam::Plan& P = plan->p;
@@ -4185,12 +4729,17 @@ __global__ void kb_batch(const KbArgs* __restrict__ args, const int64_t* __restr
   kb_pair(args[i], g - prefix[i]);
 }
 
-// In-plane Gram blocks of every element of every distinct mesh.
+// In-plane Gram blocks of every element of every distinct mesh (DF: the
+// double-float K-a, otherwise FP64).
+template <bool DF>
 __global__ void __launch_bounds__(256) ka_batch(const KaLocalArgs* __restrict__ args, const int64_t* __restrict__ prefix,
                                                 int n) {
   extern __shared__ double sm[];
   const int i = find_slot(prefix, n, blockIdx.x);
-  ka_elem(args[i], (int)(blockIdx.x - prefix[i]), sm);
+  if (DF)
+    ka_elem(args[i], (int)(blockIdx.x - prefix[i]), sm);
+  else
+    ka_elem64(args[i], (int)(blockIdx.x - prefix[i]), sm);
 }
 
 struct BatchKcArgs {
@@ -4204,10 +4753,11 @@ struct BatchKcArgs {
 };
 
 // Persistent combine: CTAs take (instance, in-plane row) items from an atomic
-// counter until none are left. DF = false re-runs only the flagged instances.
-// MONO = true when every instance is monoclinic (the general form is exact for
-// the others too).
-template <bool MONO, bool DF>
+// counter until none are left. DF = true: double-float slices; DF = false and
+// COND = true: the FP64 re-pass of the flagged instances only; DF = false and
+// COND = false: FP64 for every instance. MONO = true when every instance is
+// monoclinic (the general form is exact for the others too).
+template <bool MONO, bool DF, bool COND = true>
 __global__ void __maxnreg__(64) kc_batch(BatchKcArgs b) {
   extern __shared__ double sm[];
   __shared__ unsigned long long s_item;
@@ -4220,7 +4770,7 @@ __global__ void __maxnreg__(64) kc_batch(BatchKcArgs b) {
     if (g >= total) break;
     const int k = find_slot(b.row_prefix, b.n, g);
     const int inst = b.order[k];
-    if (!DF && b.flags[2 * inst] == 0) continue;
+    if (!DF && COND && b.flags[2 * inst] == 0) continue;
     int emax = 0;
     bool bad = false;
     kcs_row<MONO, false, DF>(b.kc[inst], g - b.row_prefix[k], sm, emax, bad);
@@ -4268,6 +4818,7 @@ struct lam_batch {
   unsigned long long* d_counter = nullptr;
   int ka_block = 32, kc_block = 128;
   bool all_mono = true;
+  bool df = true;                 // double-float only when every plan opted in (LAM_ARITH_DOUBLE_FLOAT)
   size_t ka_smem = 0, kc_smem = 0;
   int n_sm = 1, max_ctas = 1;
   // tuning and graph
@@ -4305,7 +4856,10 @@ static lam_status batch_launch(lam_batch& B, int ctas_per_sm, cudaStream_t s) {
   LAM_CUDA(cudaMemsetAsync(B.d_counter, 0, 2 * sizeof(unsigned long long), s));
   kb_batch<<<(unsigned)((B.total_pairs + 127) / 128), 128, 0, s>>>(B.d_kb, B.d_pair_prefix, n);
   LAM_CUDA(cudaGetLastError());
-  ka_batch<<<(unsigned)B.total_elems, B.ka_block, B.ka_smem, s>>>(B.d_ka, B.d_elem_prefix, B.n_meshes);
+  if (B.df)
+    ka_batch<true><<<(unsigned)B.total_elems, B.ka_block, B.ka_smem, s>>>(B.d_ka, B.d_elem_prefix, B.n_meshes);
+  else
+    ka_batch<false><<<(unsigned)B.total_elems, B.ka_block, B.ka_smem, s>>>(B.d_ka, B.d_elem_prefix, B.n_meshes);
   LAM_CUDA(cudaGetLastError());
   BatchKcArgs b{};
   b.kc = B.d_kc;
@@ -4316,6 +4870,14 @@ static lam_status batch_launch(lam_batch& B, int ctas_per_sm, cudaStream_t s) {
   b.counter = B.d_counter;
   b.flags = B.d_flags;
   const unsigned grid = (unsigned)(ctas_per_sm * B.n_sm);
+  if (!B.df) {  // FP64 for every instance
+    if (B.all_mono)
+      kc_batch<true, false, false><<<grid, B.kc_block, B.kc_smem, s>>>(b);
+    else
+      kc_batch<false, false, false><<<grid, B.kc_block, B.kc_smem, s>>>(b);
+    LAM_CUDA(cudaGetLastError());
+    return LAM_OK;
+  }
   if (B.all_mono)
     kc_batch<true, true><<<grid, B.kc_block, B.kc_smem, s>>>(b);
   else
@@ -4392,6 +4954,7 @@ lam_status lam_batch_create(lam_batch** out, lam_plan* const* plans, int32_t n_p
     lam::Plan& P = plans[i]->p;
     BCHECK(lam::check_limits(P));
     BCHECK(lam::ensure_device(P));
+    B->df = B->df && P.arith == LAM_ARITH_DOUBLE_FLOAT;
     B->versions.push_back(P.cfg_version);
     B->nnz_total += P.nnz;
   }
@@ -4495,7 +5058,10 @@ lam_status lam_batch_create(lam_batch** out, lam_plan* const* plans, int32_t n_p
   int by_smem = (int)(233472 / (B->kc_smem + 1024 + 16));
   B->max_ctas = std::max(1, std::min(4, std::min(by_regs, by_smem)));
   if (B->ka_smem > 48 * 1024) {
-    if (cudaFuncSetAttribute(lam::ka_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->ka_smem) != cudaSuccess) {
+    if (cudaFuncSetAttribute(lam::ka_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->ka_smem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(lam::ka_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->ka_smem) !=
+            cudaSuccess) {
       lam::set_error("lam_batch_create: K-a shared memory");
       lam::batch_free(B);
       return LAM_ERR_UNSUPPORTED;
@@ -4505,7 +5071,11 @@ lam_status lam_batch_create(lam_batch** out, lam_plan* const* plans, int32_t n_p
   if (cudaFuncSetAttribute(lam::kc_batch<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ks) != cudaSuccess ||
       cudaFuncSetAttribute(lam::kc_batch<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ks) != cudaSuccess ||
       cudaFuncSetAttribute(lam::kc_batch<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ks) != cudaSuccess ||
-      cudaFuncSetAttribute(lam::kc_batch<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ks) != cudaSuccess) {
+      cudaFuncSetAttribute(lam::kc_batch<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ks) != cudaSuccess ||
+      cudaFuncSetAttribute(lam::kc_batch<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ks) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(lam::kc_batch<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ks) !=
+          cudaSuccess) {
     lam::set_error("lam_batch_create: combine shared memory (%zu bytes)", B->kc_smem);
     lam::batch_free(B);
     return LAM_ERR_UNSUPPORTED;

@@ -820,8 +820,13 @@ lam_status build_plan(Plan& P, const lam_inplane* inplane, const lam_basis1d* th
         set_error("material %d: non-finite constant", m);
         return LAM_ERR_INVALID_ARG;
       }
-  lam_options o{0, 0, 0, -1.0};
+  lam_options o{0, 0, 0, -1.0, LAM_ARITH_FP64};
   if (opt) o = *opt;
+  if (o.arith != LAM_ARITH_FP64 && o.arith != LAM_ARITH_DOUBLE_FLOAT) {
+    set_error("unknown arithmetic %d (LAM_ARITH_FP64 or LAM_ARITH_DOUBLE_FLOAT)", (int)o.arith);
+    return LAM_ERR_INVALID_ARG;
+  }
+  P.arith = o.arith;
   P.nqu = o.nq_u > 0 ? o.nq_u : P.u.p + 1;
   P.nqv = o.nq_v > 0 ? o.nq_v : P.v.p + 1;
   P.nqt = o.nq_t > 0 ? o.nq_t : P.t.p + 1;
@@ -940,6 +945,7 @@ lam_status lam_plan_get_info(const lam_plan* plan, lam_plan_info* info) {
   info->combine_streaming = lam::use_stream(P) ? 1 : 0;
   info->combine_chunks = (int32_t)P.ck_nslot.size();
   info->shell = P.shell ? 1 : 0;
+  info->arith = P.arith;
   return LAM_OK;
 }
 

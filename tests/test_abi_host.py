@@ -232,5 +232,13 @@ def test_extrusion_maps_at_plan_creation(lam):
         lam.Plan(**kw, extrusion=(np.nan, 0.0, 1.0))
     assert e.value.status == 1
     L = lam.load()
-    assert L.lam_assemble_split_noalloc(p.handle, 0x1000, None) == 2
+    # the refusal comes before any device work; where a GPU is present the call
+    # still gets a real buffer of the plan's size, so a regression could not
+    # write through a made-up address
+    import torch
+    if torch.cuda.is_available():
+        buf = torch.empty(p.info["nnz"], dtype=torch.float64, device="cuda")
+        assert L.lam_assemble_split_noalloc(p.handle, buf.data_ptr(), None) == 2
+    else:
+        assert L.lam_assemble_split_noalloc(p.handle, 0x1000, None) == 2
     assert "extrusion" in lam.last_error()

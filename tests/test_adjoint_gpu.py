@@ -1,10 +1,10 @@
 """Parity of lam_adjoint (GPU) with the oracle's adjoint, and its properties
 at full size (GPU required).
 
-Bar: dL/dD, dL/dC and dL/dtheta within 1e-10 of the largest oracle entry (the
-double-float pass carries about 2^-44 per term; sums of up to 10^5 signed
-terms of similar size stay three orders of magnitude inside), 1e-12 for the
-FP64 pass. At the full 32 x 32 cubic 24-ply size the oracle is too slow, so
+Bar: dL/dD, dL/dC and dL/dtheta within 1e-12 of the largest oracle entry for
+the default FP64 evaluation; 1e-10 for the opt-in double-float pass (about
+2^-44 per term; sums of up to 10^5 signed terms of similar size stay three
+orders of magnitude inside). At the full 32 x 32 cubic 24-ply size the oracle is too slow, so
 the checks are properties that hold at any size: Euler's identity against the
 split assembly, central finite differences of the split assembly in the
 angles and constants (step 1e-6, agreement 1e-6), and the double-float pass
@@ -36,16 +36,18 @@ def rel(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
-def gpu_adjoint(L, lam, g=None, u=None, v=None, fp64=False):
+def gpu_adjoint(L, lam, g=None, u=None, v=None, fp64=False, double_float=False):
+    """double_float: the whole double-float pipeline (plan arithmetic and the
+    adjoint's flag); fp64: LAM_ADJOINT_FP64 (low rank through the generic pass)."""
     import torch
-    p = L.Plan.from_laminate(lam)
+    p = L.Plan.from_laminate(lam, arith=L.ARITH_DOUBLE_FLOAT if double_float else L.ARITH_FP64)
     kw = {}
     if g is not None:
         kw["values"] = torch.from_numpy(g).cuda()
     else:
         kw["u"] = torch.from_numpy(np.atleast_2d(u)).cuda()
         kw["v"] = torch.from_numpy(np.atleast_2d(v)).cuda()
-    dC, dth, dD = p.adjoint(fp64=fp64, **kw)
+    dC, dth, dD = p.adjoint(fp64=fp64, double_float=double_float, **kw)
     torch.cuda.synchronize()
     out = dC.cpu().numpy(), dth.cpu().numpy(), dD.cpu().numpy()
     p.close()
@@ -88,14 +90,14 @@ def _nurbs():
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
-@pytest.mark.parametrize("fp64", [False, True])
-def test_csr_cotangent_parity(L, name, fp64):
+@pytest.mark.parametrize("double_float", [False, True])
+def test_csr_cotangent_parity(L, name, double_float):
     lam = CASES[name]()
     rp, col = O.pattern(lam)
     g = np.random.default_rng(1905).standard_normal(len(col))
     ref = O.adjoint(lam, rp, col, g)
-    got = gpu_adjoint(L, lam, g=g, fp64=fp64)
-    tol = 1e-12 if fp64 else 1e-10
+    got = gpu_adjoint(L, lam, g=g, double_float=double_float)
+    tol = 1e-10 if double_float else 1e-12
     assert rel(got[2], ref[2]) <= tol, "dL/dD"
     assert rel(got[0], ref[0]) <= tol, "dL/dC"
     # dtheta = <dL/dD, dD/dtheta>: its error scales with |dL/dD| |C|
@@ -105,29 +107,36 @@ def test_csr_cotangent_parity(L, name, fp64):
 
 @pytest.mark.parametrize("name", ["curved_p3_3x3_8plies", "lagrange_q2_3x3", "single_thickness_element",
                                   "shell_bump_p2"])
-def test_lowrank_cotangent_parity(L, name):
+@pytest.mark.parametrize("generic", [False, True])
+def test_lowrank_cotangent_parity(L, name, generic):
+    """The factorised FP64 contraction (default) and the generic FP64 pass
+    (LAM_ADJOINT_FP64) of a rank-2 cotangent."""
     lam = CASES[name]()
     rp, col = O.pattern(lam)
     rng = np.random.default_rng(3)
     u, v = rng.standard_normal((2, lam.n_dof)), rng.standard_normal((2, lam.n_dof))
     ref = O.adjoint(lam, rp, col, O.lowrank_cotangent(rp, col, u, v))
-    got = gpu_adjoint(L, lam, u=u, v=v)
-    assert rel(got[2], ref[2]) <= 1e-10
-    assert rel(got[0], ref[0]) <= 1e-10
+    got = gpu_adjoint(L, lam, u=u, v=v, fp64=generic)
+    assert rel(got[2], ref[2]) <= 1e-12
+    assert rel(got[0], ref[0]) <= 1e-12
 
 
-def test_nonfinite_and_out_of_range_cotangents_take_the_fp64_pass(L):
+@pytest.mark.parametrize("double_float", [False, True])
+def test_nonfinite_and_out_of_range_cotangents(L, double_float):
+    """Cotangents scaled by 2^+-200 give the exactly scaled gradient (the
+    double-float pass rejects them and the FP64 pass recomputes); an infinite
+    entry gives a non-finite gradient."""
     lam = W.curved_plate(n_el=3, degree=3, repeats=1)
     rp, col = O.pattern(lam)
     g = np.random.default_rng(5).standard_normal(len(col))
     ref = O.adjoint(lam, rp, col, g)
     for scale in (2.0 ** 200, 2.0 ** -200):   # beyond float range either way: exact scaling of the result
-        got = gpu_adjoint(L, lam, g=g * scale)
+        got = gpu_adjoint(L, lam, g=g * scale, double_float=double_float)
         assert rel(got[2], ref[2] * scale) <= 1e-12
         assert rel(got[0], ref[0] * scale) <= 1e-12
     g2 = g.copy()
     g2[len(g2) // 2] = np.inf
-    got = gpu_adjoint(L, lam, g=g2)
+    got = gpu_adjoint(L, lam, g=g2, double_float=double_float)
     assert not np.all(np.isfinite(got[2]))
 
 
@@ -150,11 +159,13 @@ def full(L):
 
 def test_full_size_double_float_matches_fp64(L, full):
     lam, p, g = full
-    a = [x.cpu().numpy() for x in p.adjoint(values=g)]
-    b = [x.cpu().numpy() for x in p.adjoint(values=g, fp64=True)]
+    a = [x.cpu().numpy() for x in p.adjoint(values=g, double_float=True)]
+    b = [x.cpu().numpy() for x in p.adjoint(values=g)]
     assert rel(a[2], b[2]) <= 1e-10 and rel(a[0], b[0]) <= 1e-10
-    c = [x.cpu().numpy() for x in p.adjoint(values=g)]
-    assert all(np.array_equal(x, y) for x, y in zip(a, c))  # bitwise repeatable
+    for kw in ({}, {"double_float": True}):
+        c = [x.cpu().numpy() for x in p.adjoint(values=g, **kw)]
+        ref = b if not kw else a
+        assert all(np.array_equal(x, y) for x, y in zip(ref, c))  # bitwise repeatable
 
 
 def test_full_size_euler_identity(L, full):

@@ -398,3 +398,45 @@ def test_config_sizes_match_published_counts():
     """DOF and nnz of the cross-ply plate (2700 DOFs, 574,992 nonzeros)."""
     lam = W.cross_ply_plate()
     assert O.sizes(lam) == (2700, 574992)
+
+
+# ---------------------------------------------------------------- helpers of the timed baseline and the row checks
+def test_element_colour_lists_on_threads_equal_the_assembly():
+    """ora_assemble_elements over every element colour, each colour split over
+    four threads, reproduces ora_assemble; the colours cover every element once."""
+    from concurrent.futures import ThreadPoolExecutor
+    lam = W.curved_plate(n_el=4, degree=3, repeats=1)
+    rp, col, ref = O.assemble(lam)
+    groups = O.element_colours(lam)
+    seen = np.concatenate(groups)
+    assert len(seen) == len(np.unique(seen, axis=0)) == 4 * 4 * 8
+    val = np.zeros_like(ref)
+    prob = O.Problem(lam)
+    with ThreadPoolExecutor(4) as ex:
+        for g in groups:
+            list(ex.map(lambda c: O.assemble_elements(lam, rp, col, c, val, prob), np.array_split(g, 4)))
+    assert np.abs(val - ref).max() <= 1e-14 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("make", [lambda: W.curved_plate(n_el=4, degree=3, repeats=1),
+                                  lambda: W.lagrange_plate(n_el=3, n_plies=4),
+                                  lambda: W.shell_plate(n_el=3, degree=2, repeats=1)])
+def test_inplane_row_blocks_equal_the_assembled_rows(make):
+    """ora_inplane_row_blocks gives every stored entry of the rows (i_t, i_s, c)
+    of ora_assemble, and zero for every block the pattern does not store."""
+    lam = make()
+    rp, col, val = O.assemble(lam)
+    ns, nt = lam.n_s, lam.n_t
+    nx = O.n_functions(lam.u.kind, lam.u.degree, lam.u.knots)
+    for i_s in (0, ns // 2, ns - 1):
+        bx0, by0, B = O.inplane_row_blocks(lam, i_s)
+        for it in range(nt):
+            for c in range(3):
+                r = 3 * (it * ns + i_s) + c
+                for k in range(rp[r], rp[r + 1]):
+                    j, d = divmod(int(col[k]), 3)
+                    jt, js = divmod(j, ns)
+                    jy, jx = divmod(js, nx)
+                    assert abs(val[k] - B[it, jt, jy - by0, jx - bx0, c, d]) <= 1e-14 * np.abs(val).max()
+                    B[it, jt, jy - by0, jx - bx0, c, d] = 0.0
+        assert np.abs(B).max() <= 1e-14 * np.abs(val).max()

@@ -1,13 +1,19 @@
 """Parity of the CUDA assembly paths with the CPU oracle (GPU required).
 
-Bar (FP64 throughout): the sparsity pattern is bit-exact, and the values agree
-to max|K_gpu - K_oracle| <= 1e-12 * max|K_oracle| (the paper states that the
+Bar: the sparsity pattern is bit-exact, and the values agree to
+max|K_gpu - K_oracle| <= 1e-12 * max|K_oracle| (the paper states that the
 split and the standard matrices agree to machine precision, Section 3 after
-Eq. Q and Section 4). Small cases are compared element by element over the
-whole matrix; the full-size workloads, in the launch configuration bench.py
-times, are compared on the whole pattern and on sampled blocks that the
-oracle integrates one by one, plus symmetry.
+Eq. Q and Section 4). The split path runs in both arithmetics of
+lam_options.arith: FP64 (the default: every product and sum an FP64
+operation) and the opt-in double-float form; on the GPU the FP64 split and the
+FP64 standard matrices agree to 1e-14 of max|K|. Small cases are compared
+element by element over the whole matrix; the full-size workloads, in the
+launch configuration bench.py times, are compared on the whole pattern, on
+sampled blocks that the oracle integrates one by one, and on every entry of
+whole in-plane rows (all thickness rows and chunks), plus symmetry.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -16,6 +22,7 @@ import workloads as W
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
+ARITH = {"fp64": 0, "double_float": 1}
 
 
 @pytest.fixture(scope="module")
@@ -30,9 +37,10 @@ def L():
     return lam
 
 
-def gpu_matrix(L, lam, path="split", class_tol=-1.0):
+def gpu_matrix(L, lam, path="split", class_tol=-1.0, arith="fp64"):
     import torch
-    p = L.Plan.from_laminate(lam, class_tol=class_tol)
+    p = L.Plan.from_laminate(lam, class_tol=class_tol, arith=ARITH[arith])
+    assert p.info["arith"] == ARITH[arith]
     row_ptr, col = p.pattern()
     vals = p.assemble_split() if path == "split" else p.assemble_standard()
     torch.cuda.synchronize()
@@ -81,18 +89,18 @@ SMALL = {
 
 
 @pytest.mark.parametrize("name", sorted(SMALL))
-@pytest.mark.parametrize("path", ["split", "standard"])
-def test_small_full_parity(L, name, path):
+@pytest.mark.parametrize("path,arith", [("split", "fp64"), ("split", "double_float"), ("standard", "fp64")])
+def test_small_full_parity(L, name, path, arith):
     lam = SMALL[name]()
-    assert_parity(gpu_matrix(L, lam, path), O.assemble(lam))
+    assert_parity(gpu_matrix(L, lam, path, arith=arith), O.assemble(lam))
 
 
 def test_nurbs_parity(L):
     lam = W.curved_plate(n_el=4, degree=2, repeats=1)
     lam.weights = np.random.default_rng(7).uniform(0.5, 2.0, lam.n_s)
     ref = O.assemble(lam)
-    for path in ("split", "standard"):
-        assert_parity(gpu_matrix(L, lam, path), ref)
+    for path, arith in (("split", "fp64"), ("split", "double_float"), ("standard", "fp64")):
+        assert_parity(gpu_matrix(L, lam, path, arith=arith), ref)
 
 
 def test_fully_anisotropic_materials(L):
@@ -103,8 +111,8 @@ def test_fully_anisotropic_materials(L):
     p = L.Plan.from_laminate(lam)
     assert p.info["monoclinic"] == 0
     ref = O.assemble(lam)
-    for path in ("split", "standard"):
-        assert_parity(gpu_matrix(L, lam, path), ref)
+    for path, arith in (("split", "fp64"), ("split", "double_float"), ("standard", "fp64")):
+        assert_parity(gpu_matrix(L, lam, path, arith=arith), ref)
 
 
 def test_exact_classes_and_merged_classes_agree(L):
@@ -114,21 +122,24 @@ def test_exact_classes_and_merged_classes_agree(L):
     assert np.abs(a[2] - b[2]).max() <= 1e-14 * np.abs(a[2]).max()
 
 
-def test_split_equals_standard_on_gpu(L):
-    """The split path forms its in-plane Gram blocks in double-float arithmetic
-    on the FP32 pipes (about 2^-47 per term); against the all-FP64 standard
-    path it stays two orders of magnitude inside the parity bar."""
+@pytest.mark.parametrize("arith,bar", [("fp64", 1e-14), ("double_float", 2e-13)])
+def test_split_equals_standard_on_gpu(L, arith, bar):
+    """Both matrices of the GPU, FP64 split against FP64 standard: they sum the
+    same integrals in different orders and agree to 1e-14 of max|K| (machine
+    precision, Section 3 after Eq. Q). The opt-in double-float split (about
+    2^-44 per term) stays within 2e-13."""
     lam = W.curved_plate(n_el=6, degree=3, repeats=2)
-    s = gpu_matrix(L, lam, "split")
+    s = gpu_matrix(L, lam, "split", arith=arith)
     t = gpu_matrix(L, lam, "standard")
     assert np.array_equal(s[1], t[1])
-    assert np.abs(s[2] - t[2]).max() <= 1e-14 * 20 * np.abs(t[2]).max()
+    assert np.abs(s[2] - t[2]).max() <= bar * np.abs(t[2]).max()
 
 
-def test_host_output_path_matches_device_path(L):
+@pytest.mark.parametrize("arith", ["fp64", "double_float"])
+def test_host_output_path_matches_device_path(L, arith):
     import torch
     lam = W.curved_plate(n_el=8, degree=3, repeats=1)
-    p = L.Plan.from_laminate(lam)
+    p = L.Plan.from_laminate(lam, arith=ARITH[arith])
     d = p.assemble_split()
     torch.cuda.synchronize()
     h = np.empty(p.nnz)
@@ -140,10 +151,11 @@ def test_host_output_path_matches_device_path(L):
     p.close()
 
 
-def test_repeated_calls_are_bitwise_stable(L):
+@pytest.mark.parametrize("arith", ["fp64", "double_float"])
+def test_repeated_calls_are_bitwise_stable(L, arith):
     import torch
     lam = W.curved_plate(n_el=5, degree=3, repeats=1)
-    p = L.Plan.from_laminate(lam)
+    p = L.Plan.from_laminate(lam, arith=ARITH[arith])
     a = p.assemble_split().cpu().numpy()
     b = p.assemble_split().cpu().numpy()
     c = p.assemble_standard().cpu().numpy()
@@ -247,9 +259,10 @@ def test_uneven_plies_triclinic(L):
     assert_parity(gpu_matrix(L, lam, "split"), O.assemble(lam))
 
 
-def test_chunked_host_output_uneven_plies(L):
+@pytest.mark.parametrize("arith", ["fp64", "double_float"])
+def test_chunked_host_output_uneven_plies(L, arith):
     lam = _uneven(np.array([W.ply_C21()]), 23)
-    p = L.Plan.from_laminate(lam)
+    p = L.Plan.from_laminate(lam, arith=ARITH[arith])
     import torch
     d = p.assemble_split()
     torch.cuda.synchronize()
@@ -259,26 +272,28 @@ def test_chunked_host_output_uneven_plies(L):
     p.close()
 
 
-# ---------------------------------------------------------------- scale robustness of the double-float steps
+# ---------------------------------------------------------------- scale robustness (the double-float steps above all)
+@pytest.mark.parametrize("arith", ["fp64", "double_float"])
 @pytest.mark.parametrize("scale", [2.0 ** -90, 2.0 ** 90])
-def test_extreme_geometry_scale(L, scale):
-    """In-plane coordinates scaled by 2^+-90: K-a's per-element power-of-two
-    scaling keeps its float pairs in range; entries of K then span ~2^360, the
-    largest ones overflow float in the combine's double-float pass (2^90) and
-    the FP64 pass recomputes."""
+def test_extreme_geometry_scale(L, scale, arith):
+    """In-plane coordinates scaled by 2^+-90: entries of K then span ~2^360.
+    Double-float: K-a's per-element power-of-two scaling keeps its float pairs
+    in range, the largest entries overflow float in the combine (2^90) and the
+    FP64 pass recomputes. FP64: nothing to rescale."""
     curved = W.curved_map(0.04)
     lam = W.laminate("geom", W.BSPLINE, 2, 3, [0, 45, 90], 0.01,
                      mapping=lambda xi, eta: tuple(scale * c for c in curved(xi, eta)))
-    assert_parity(gpu_matrix(L, lam, "split"), O.assemble(lam))
+    assert_parity(gpu_matrix(L, lam, "split", arith=arith), O.assemble(lam))
 
 
+@pytest.mark.parametrize("arith", ["fp64", "double_float"])
 @pytest.mark.parametrize("scale", [2.0 ** -200, 2.0 ** 200])
-def test_extreme_material_scale(L, scale):
-    """Constants scaled by 2^+-200: every entry of K is beyond float range, the
-    combine's double-float pass flags it and the FP64 pass recomputes."""
+def test_extreme_material_scale(L, scale, arith):
+    """Constants scaled by 2^+-200: every entry of K is beyond float range (the
+    double-float combine flags it and the FP64 pass recomputes)."""
     lam = W.curved_plate(n_el=3, degree=3, repeats=1)
     lam.C21 = lam.C21 * scale
-    got = gpu_matrix(L, lam, "split")
+    got = gpu_matrix(L, lam, "split", arith=arith)
     assert_parity(got, O.assemble(lam))
 
 
@@ -316,3 +331,174 @@ def test_split_on_a_side_stream_and_in_a_cuda_graph(L):
     torch.cuda.synchronize()
     assert np.array_equal(graph_out.cpu().numpy(), out.cpu().numpy())
     p.close()
+
+
+# ---------------------------------------------------------------- the paper's own discretisation (Section 4)
+# One element of degree p through the whole thickness, cut into m layers (the
+# paper's experiment: Pagano material, p = 1..4, 0/90/... and 0/45/-45/90/...
+# stacks), 3 x 3 in-plane elements; p = 4 at m = 64 on one in-plane element (its
+# oracle is the slowest: 64 pieces of 125 Gauss points per element) and on
+# 4 x 4 elements, whose rows of 64 in-plane neighbours take the class-major combine.
+SWEEP = ([(p, m, 3, "cross") for p in (1, 2, 3) for m in (1, 2, 8, 64)] + [(4, m, 3, "cross") for m in (1, 2, 8)]
+         + [(4, 64, 1, "cross"), (4, 2, 4, "cross"), (2, 8, 3, "quasi"), (3, 64, 3, "quasi")])
+
+
+def _sweep_reference(case):
+    """The oracle's matrix of one sweep point (runs in a spawned worker)."""
+    import oracle as O_
+    import workloads as W_
+    p, m, n, stack = case
+    return O_.assemble(W_.pagano_sweep_plate(p, n, m, stack))
+
+
+@pytest.fixture(scope="module")
+def sweep_references():
+    """Every sweep point's oracle matrix, computed by a pool of spawned
+    processes (no fork after the CUDA context exists) while the GPU tests run."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    ex = ProcessPoolExecutor(max_workers=max(1, min(len(SWEEP), os.cpu_count() or 1)),
+                             mp_context=mp.get_context("spawn"))
+    futures = {case: ex.submit(_sweep_reference, case) for case in SWEEP}
+    yield futures
+    ex.shutdown(cancel_futures=True)
+
+
+@pytest.mark.parametrize("case", SWEEP, ids=[f"p{p}_m{m}_{n}x{n}_{s}" for p, m, n, s in SWEEP])
+def test_pagano_sweep_parity(L, sweep_references, case):
+    p, m, n, stack = case
+    lam = W.pagano_sweep_plate(p, n, m, stack)
+    plan = L.Plan.from_laminate(lam)
+    assert plan.info["n_pieces"] == m  # one thickness element cut into m pieces
+    if n >= 4 and p == 4:
+        assert plan.info["combine_streaming"] == 0
+    plan.close()
+    ref = sweep_references[case].result()
+    for path, arith in (("split", "fp64"), ("split", "double_float"), ("standard", "fp64")):
+        assert_parity(gpu_matrix(L, lam, path, arith=arith), ref)
+
+
+# ---------------------------------------------------------------- whole in-plane rows at full size
+def _rows_to_check(lam, extra_seed=0):
+    """Eight or more in-plane rows: the four corners, edge midpoints, the centre
+    and two seeded interior rows."""
+    nx = O.n_functions(lam.u.kind, lam.u.degree, lam.u.knots)
+    ny = O.n_functions(lam.v.kind, lam.v.degree, lam.v.knots)
+    ns = nx * ny
+    rng = np.random.default_rng(100 + extra_seed)
+    rows = {0, nx - 1, ns - nx, ns - 1, nx // 2, (ny // 2) * nx, (ny // 2) * nx + nx // 2, (ny - 1) * nx + nx // 3}
+    rows.update(int(r) for r in rng.integers(0, ns, 2))
+    return sorted(rows)
+
+
+def _row_references(lam, rows):
+    """The oracle's blocks of each row, on host threads (the C call releases the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+    prob = O.Problem(lam)
+    ex = ThreadPoolExecutor(max(1, min(len(rows), os.cpu_count() or 1)))
+    return ex, {i_s: ex.submit(O.inplane_row_blocks, lam, i_s, prob) for i_s in rows}
+
+
+def _check_rows(lam, row_ptr, col, vals, refs):
+    """Every stored entry of the CSR rows (i_t, i_s, c), all i_t and c, of each
+    row i_s against the oracle's blocks, and every oracle block of those rows
+    that the pattern does not store is zero (the pattern misses nothing)."""
+    import torch
+    nx = O.n_functions(lam.u.kind, lam.u.degree, lam.u.knots)
+    ny = O.n_functions(lam.v.kind, lam.v.degree, lam.v.knots)
+    nt = O.n_functions(lam.t.kind, lam.t.degree, lam.t.knots)
+    ns = nx * ny
+    rp = row_ptr.cpu().numpy()
+    scale = float(vals.abs().max())
+    assert np.isfinite(scale) and scale > 0
+    worst = 0.0
+    for i_s, fut in refs.items():
+        bx0, by0, B = fut.result()
+        B = B.copy()
+        rows = (3 * (np.arange(nt)[:, None] * ns + i_s) + np.arange(3)[None, :]).ravel()
+        lens = rp[rows + 1] - rp[rows]
+        idx = np.concatenate([np.arange(rp[r], rp[r + 1]) for r in rows])
+        it_c = np.repeat(np.arange(len(rows)), lens)
+        it, c = it_c // 3, it_c % 3
+        t_idx = torch.from_numpy(idx).to(vals.device)
+        v = vals[t_idx].cpu().numpy()
+        cc = col[t_idx].cpu().numpy().astype(np.int64)
+        j, d = cc // 3, cc % 3
+        jt, js = j // ns, j % ns
+        jy, jx = js // nx, js % nx
+        assert np.all((jx - bx0 >= 0) & (jx - bx0 < B.shape[3]) & (jy - by0 >= 0) & (jy - by0 < B.shape[2]))
+        ref = B[it, jt, jy - by0, jx - bx0, c, d]
+        worst = max(worst, float(np.abs(v - ref).max()))
+        B[it, jt, jy - by0, jx - bx0, c, d] = 0.0
+        assert np.abs(B).max() <= 1e-14 * scale, f"row {i_s}: an oracle block outside the pattern"
+    assert worst <= TOL * scale, worst / scale
+    return worst / scale
+
+
+@pytest.mark.parametrize("arith", ["fp64", "double_float"])
+def test_curved_plate_full_size_whole_rows(L, arith):
+    """The benchmark workload (cubic, 64x64 curved, 48 plies) as bench.py
+    launches it: every entry of ten in-plane rows, all 97 thickness rows."""
+    import torch
+    lam = W.curved_plate()
+    ex, refs = _row_references(lam, _rows_to_check(lam))
+    p = L.Plan.from_laminate(lam, arith=ARITH[arith])
+    row_ptr, col = p.pattern()
+    vals = p.assemble_split()
+    torch.cuda.synchronize()
+    _check_rows(lam, row_ptr, col, vals, refs)
+    ex.shutdown()
+    p.close()
+
+
+def test_lagrange_plate_full_size_whole_rows(L):
+    """Lagrange Q2 96x96, 64 plies (2.73e9 entries, int64 row pointers): every
+    entry of ten in-plane rows, all 129 thickness rows."""
+    import torch
+    lam = W.lagrange_plate()
+    ex, refs = _row_references(lam, _rows_to_check(lam, 1))
+    p = L.Plan.from_laminate(lam)
+    row_ptr, col = p.pattern()
+    vals = p.assemble_split()
+    torch.cuda.synchronize()
+    _check_rows(lam, row_ptr, col, vals, refs)
+    ex.shutdown()
+    p.close()
+    del vals, col, row_ptr
+    torch.cuda.empty_cache()
+
+
+def test_curved_shell_full_size_whole_rows(L):
+    """The curved shell (general extrusion) at the benchmark's size."""
+    import torch
+    lam = W.shell_plate()
+    ex, refs = _row_references(lam, _rows_to_check(lam, 2))
+    p = L.Plan.from_laminate(lam)
+    row_ptr, col = p.pattern()
+    vals = p.assemble_split()
+    torch.cuda.synchronize()
+    _check_rows(lam, row_ptr, col, vals, refs)
+    ex.shutdown()
+    p.close()
+
+
+def test_batch_uneven_instances_whole_rows(L):
+    """Three uneven-ply instances of the 256-laminate batch recipe (12, 8 and 3
+    thickness chunks) assembled by one lam_batch_assemble: whole rows of each."""
+    import torch
+    lams = [W.batch_laminates()[k] for k in (0, 2, 3)]
+    plans = [L.Plan.from_laminate(x) for x in lams]
+    assert [p.info["combine_chunks"] for p in plans] == [12, 8, 3]
+    refs = [_row_references(x, _rows_to_check(x, 3 + k)) for k, x in enumerate(lams)]
+    values = [torch.empty(p.nnz, dtype=torch.float64, device="cuda") for p in plans]
+    b = L.Batch(plans)
+    b.assemble(values)
+    b.assemble(values)  # the replayed graph
+    torch.cuda.synchronize()
+    for x, p, v, (ex, r) in zip(lams, plans, values, refs):
+        row_ptr, col = p.pattern()
+        _check_rows(x, row_ptr, col, v, r)
+        ex.shutdown()
+    b.close()
+    for p in plans:
+        p.close()

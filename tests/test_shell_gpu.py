@@ -64,9 +64,9 @@ SHELLS = {
 }
 
 
-@pytest.mark.parametrize("path", ["split", "standard"])
+@pytest.mark.parametrize("path,arith", [("split", "fp64"), ("split", "double_float"), ("standard", "fp64")])
 @pytest.mark.parametrize("name", sorted(SHELLS))
-def test_shell_parity(L, name, path):
+def test_shell_parity(L, name, path, arith):
     lam = SHELLS[name]()
     p = L.Plan.from_laminate(lam)
     assert p.info["shell"] == 1
@@ -75,7 +75,7 @@ def test_shell_parity(L, name, path):
     if name == "uneven_plies_chunked":
         assert p.info["combine_streaming"] == 1 and p.info["combine_chunks"] >= 2
     p.close()
-    assert_parity(gpu_matrix(L, lam, path), O.assemble(lam))
+    assert_parity(gpu_matrix(L, lam, path, arith=arith), O.assemble(lam))
 
 
 def test_planar_surface_through_the_shell_path(L):
@@ -155,15 +155,16 @@ def test_shell_update_materials_then_reassemble_and_differentiate(L):
     p.close()
 
 
+@pytest.mark.parametrize("arith", ["fp64", "double_float"])
 @pytest.mark.parametrize("scale", [2.0 ** -60, 2.0 ** 60])
-def test_shell_extreme_geometry_scale(L, scale):
-    """Surface and extrusion scaled by 2^+-60: the per-element powers of two of
-    the shell K-a keep its float pairs in range."""
+def test_shell_extreme_geometry_scale(L, scale, arith):
+    """Surface and extrusion scaled by 2^+-60 (double-float: the per-element
+    powers of two of the shell K-a keep its float pairs in range)."""
     bump = W.bump_map(0.1)
     lam = W.laminate("geom", W.BSPLINE, 2, 3, [0, 45, 90], 0.01 * scale,
                      mapping=lambda xi, eta: tuple(scale * c for c in bump(xi, eta)),
                      extrusion=(0.1, -0.1, 1.0))
-    assert_parity(gpu_matrix(L, lam, "split"), O.assemble(lam))
+    assert_parity(gpu_matrix(L, lam, "split", arith=arith), O.assemble(lam))
 
 
 def test_shell_inplane_operators_match_the_oracle(L):

@@ -84,9 +84,20 @@ def test_noalloc_on_the_benchmark_plate(lib):
 
 
 def test_noalloc_rejects_plans_beyond_the_array(lib):
+    """A plan whose workspace exceeds the static array (a quadratic 140x140
+    in-plane mesh: about 35 MB of assembled in-plane Gram blocks) but whose
+    matrix is small (one linear ply, 17.6 M entries): the call is refused with
+    LAM_ERR_UNSUPPORTED before any device work, and the caller's full-size
+    buffer is left untouched."""
+    import re
     import torch
-    plan = lib.Plan.from_laminate(W.lagrange_plate())   # about 43 MB of in-plane workspace
-    dummy = torch.empty(1, dtype=torch.float64, device="cuda")
-    assert _noalloc(lib, plan, dummy) == 2              # LAM_ERR_UNSUPPORTED, nothing launched
-    assert "static array holds" in lib.last_error()
+    lam = W.laminate("wide", W.BSPLINE, 2, 140, [0.0], 0.01, thickness_degree=1)
+    plan = lib.Plan.from_laminate(lam)
+    out = torch.full((plan.nnz,), float("nan"), dtype=torch.float64, device="cuda")
+    assert _noalloc(lib, plan, out) == 2              # LAM_ERR_UNSUPPORTED
+    msg = lib.last_error()
+    m = re.search(r"needs (\d+) bytes of scratch, the static array holds (\d+)", msg)
+    assert m and int(m.group(1)) > int(m.group(2)) == 32 << 20, msg
+    torch.cuda.synchronize()
+    assert torch.isnan(out).all()                     # nothing was written
     plan.close()

@@ -21,8 +21,11 @@
  *   - In-plane: tensor-product B-spline (optionally NURBS) or Lagrange Q_p basis
  *     on [knots], with n_x * n_y functions, i_s = iy * n_x + ix; the in-plane
  *     map is x(xi) = sum_i S^i(xi) X_i from the control points X_i.
- *   - Thickness: B-spline or Lagrange basis in PHYSICAL z (the extrusion of
- *     Eq. extrusion with a = e_z; Assumption 2 holds by construction).
+ *   - Thickness: B-spline or Lagrange basis in the extrusion coordinate xi^3
+ *     of Eq. extrusion, F = S(xi^1, xi^2) + xi^3 a (physical z for the plate,
+ *     a = e_z; any constant direction a for a general extrusion, see
+ *     lam_inplane). DF does not depend on xi^3, so Assumption 2 holds by
+ *     construction.
  *   - 3D function index i = i_t * n_s + i_s (0-based form of Assumption 1);
  *     DOF index 3*i + c, c in {x, y, z}.
  * Plies (Eq. C_layers, Assumption 3): ply 0 starts at the first thickness
@@ -50,7 +53,12 @@
  *     call is stream-ordered and asynchronous unless stated otherwise. A plan
  *     must not be used on two streams at the same time.
  *   - The plan owns its device workspace (allocated with cudaMalloc on the
- *     first device call, on the device current at that time).
+ *     first device call, on the device current at that time). A failed
+ *     allocation returns LAM_ERR_OOM and releases what the call had allocated;
+ *     the plan stays usable. For tests of these paths, LAM_FAIL_ALLOC=n in the
+ *     environment makes the n-th device allocation counted from the moment the
+ *     variable took its value fail as out of memory (host side; no device
+ *     fault is involved).
  */
 #ifndef LAM_H
 #define LAM_H
@@ -68,7 +76,7 @@ typedef enum {
   LAM_ERR_UNSUPPORTED = 2,  /* valid input outside what the library handles */
   LAM_ERR_OOM = 3,          /* host or device allocation failed */
   LAM_ERR_CUDA = 4,         /* a CUDA runtime call failed */
-  LAM_ERR_TIMEOUT = 5       /* a bounded device wait gave up */
+  LAM_ERR_TIMEOUT = 5       /* reserved: no call waits on the device with a bound, none returns it */
 } lam_status;
 
 typedef enum { LAM_BSPLINE = 0, LAM_LAGRANGE = 1 } lam_basis_kind;
@@ -190,8 +198,10 @@ lam_status lam_pattern(lam_plan* plan, int64_t* nnz_out, int64_t* d_row_ptr, int
 
 /* Split assembly (Section 3, Eq. Km_2 with Eq. P and Eq. Q): writes all nnz
  * FP64 values of K, in the order of lam_pattern, to the device buffer
- * d_values (nnz doubles). Recomputes the in-plane and thickness integrals on
- * every call. Asynchronous on `stream`. */
+ * d_values (nnz doubles), in the plan's arithmetic (lam_options.arith).
+ * Recomputes the in-plane integrals on every call; the thickness integrals
+ * (Eq. Q) depend on the plies only and are computed by the first call and by
+ * the first call after each lam_plan_update. Asynchronous on `stream`. */
 lam_status lam_assemble_split(lam_plan* plan, double* d_values, void* stream);
 
 /* Standard assembly (Section 2.4, Eq. Km_0): the same matrix by

@@ -3,21 +3,25 @@
 // Split path (Section 3 of Antolin 2019, Eq. Km_2):
 //   K-b  kb_thickness  Q_{m,ab}^{i_t j_t} = sum_{plies l of configuration m}
 //                      int_{ply l} tau_a^{i_t} tau_b^{j_t} dz   (Eq. Q; tau_1 = T, tau_2 = T')
-//   K-a  ka_local      configuration-free in-plane Gram blocks per element
+//   K-a  ka_local64    configuration-free in-plane Gram blocks per element
 //                      G_{ab}^{i_s j_s} = int g_a^{i_s} g_b^{j_s} |DF| dxi,
-//                      g = (dS/dx, dS/dy, S)   (pull-back of Eq. gradient)
-//                      (ka_inplane: the same, accumulated per pair, for the
-//                      allocation-free entry point)
-//   K-c  kc_stream     P_{m,ab}[c][d] = sum D_m[V(c,a)][V(d,b)] G_{ab} (Eq. P with a
+//                      g = (dS/dx, dS/dy, S)   (pull-back of Eq. gradient), FP64
+//                      (ka_local: double-float; ka_inplane: accumulated per pair,
+//                      for the allocation-free entry point); kg_rows sums them
+//                      per in-plane pair
+//   K-c  kc_ws         P_{m,ab}[c][d] = sum D_m[V(c,a)][V(d,b)] G_{ab} (Eq. P with a
 //                      homogeneous ply), then K = sum_m sum_ab P_{m,ab} Q_{m,ab}
-//                      written straight into the CSR values (kc_combine: the
-//                      class-major form for rows of many neighbours)
-// General extrusions (Eq. extrusion): ka_shell (6 x 6 Gram blocks), kp_shell (P
-// per configuration), the combine reading P.
+//                      written straight into the CSR values, FP64, warp-specialised
+//                      (kc_stream: the double-float pass and the fallback;
+//                      kc_combine: the class-major form for rows of many neighbours)
+// General extrusions (Eq. extrusion): ka_shell64 / ka_shell (6 x 6 Gram blocks),
+// kp_shell64 / kp_shell (P per configuration), the combine reading P.
 // Standard path (Section 2.4): K-d kd_standard, one CTA per 3D element.
 // Adjoint: adj_* (dL/dD_l, dL/dC, dL/dtheta). Batches: kb_batch, ka_batch, kc_batch.
 // Pattern: kp_row_ptr / kp_col_ind.
 #include <cuda_runtime.h>
+#include <mutex>
+#include <string>
 
 #include <algorithm>
 #include <cstdio>
@@ -93,6 +97,7 @@ struct Device {
   int n_sm = 0;
   int smem_optin = 0;    // largest dynamic shared memory of one CTA
   double* q = nullptr;   // nnz_t x n_cfg x 4
+  bool q_valid = false;  // q holds Eq. Q of the current configurations (recomputed after lam_plan_update)
   // adjoint: geometry tables and workspace (allocated by the first lam_adjoint)
   bool adj_ready = false;
   bool adj_g_cached = false;       // adj_G / adj_Gdf / scales hold this plan's scaled Gram blocks
@@ -119,12 +124,40 @@ struct Device {
   std::vector<void*> cfg_allocs;  // configuration tables (replaced after lam_plan_update)
 };
 
+// Every device allocation of the library goes through here. Fault injection
+// for tests of the error paths (host side only, no device fault): with
+// LAM_FAIL_ALLOC=n in the environment, the n-th allocation counted from the
+// moment the variable took its current value fails as an out-of-memory
+// cudaMalloc would, and the caller's usual clean-up runs.
+static cudaError_t device_alloc(void** p, size_t bytes) {
+  static std::mutex mu;
+  static std::string armed;
+  static long count = 0;
+  const char* env = getenv("LAM_FAIL_ALLOC");
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    const std::string v = env ? env : "";
+    if (v != armed) {
+      armed = v;
+      count = 0;
+    }
+    if (!v.empty()) {
+      const long n = atol(v.c_str());
+      if (n > 0 && ++count == n) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+      }
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
+
 template <typename T>
 static lam_status upload(Plan& P, std::vector<void*>& list, T** dst, const std::vector<T>& src) {
   *dst = nullptr;
   size_t bytes = std::max<size_t>(src.size(), 1) * sizeof(T);
   void* p = nullptr;
-  cudaError_t e = cudaMalloc(&p, bytes);
+  cudaError_t e = device_alloc(&p, bytes);
   if (e != cudaSuccess) {
     set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? LAM_ERR_OOM : LAM_ERR_CUDA;
@@ -140,7 +173,7 @@ static lam_status upload(Plan& P, std::vector<void*>& list, T** dst, const std::
 
 static lam_status alloc_dev(std::vector<void*>& list, double** dst, size_t n) {
   void* p = nullptr;
-  cudaError_t e = cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(double));
+  cudaError_t e = device_alloc(&p, std::max<size_t>(n, 1) * sizeof(double));
   if (e != cudaSuccess) {
     set_error("cudaMalloc(%zu doubles) failed: %s", n, cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? LAM_ERR_OOM : LAM_ERR_CUDA;
@@ -1678,7 +1711,10 @@ __global__ void __launch_bounds__(1024, 2) kc_combine(KcArgs a) {
 
 // ---------------------------------------------------------------------------
 // K-c, streaming form (used when a row's class slices fit in shared memory):
-// one 512-thread CTA per in-plane row i_s, two CTAs per SM. Phase 1 forms the
+// one CTA per in-plane row i_s (threads = 9 max len_s rounded up to warps: 448
+// for cubic rows), as many CTAs per SM as 64 registers per thread allow (two
+// for cubic rows). The double-float pass of the plan's opt-in arithmetic, the
+// FP64 fallback when kc_ws's two buffers do not fit, and the batches' rows. Phase 1 forms the
 // row's G blocks (gathered from the element blocks); each thread (c, k_s, d)
 // forms the P_{m,ab}[c][d] it needs per configuration and accumulates
 // slice_u = sum Q P for every class u in shared memory. Phase 2 writes the
@@ -2023,6 +2059,7 @@ __device__ __forceinline__ bool kcw_chunk(const KcArgs& a, int ch, int& it0, int
 // sum over the shared elements (fixed row-major element order) of the element
 // blocks of K-a, into G[(LSb[i_s] + k_s) * 9 + ab]: CTA per in-plane row,
 // thread per (k_s, ab). FP64 sums, the order of the combine's own gather.
+constexpr int kRowLoads = 16;  // (p + 1)^2 shared elements of a cubic pair
 __global__ void __launch_bounds__(512) kg_rows(KcArgs a, double* __restrict__ G) {
   const int64_t is = blockIdx.x;
   const int ix = (int)(is % a.nx), iy = (int)(is / a.nx);
@@ -2034,19 +2071,25 @@ __global__ void __launch_bounds__(512) kg_rows(KcArgs a, double* __restrict__ G)
     const int ex0 = max(a.eloX[ix], a.eloX[jx]), ex1 = min(a.ehiX[ix], a.ehiX[jx]);
     const int ey0 = max(a.eloY[iy], a.eloY[jy]), ey1 = min(a.ehiY[iy], a.ehiY[jy]);
     const int ba = (ab % 3) * 3 + ab / 3;
+    const int nex = ex1 - ex0 + 1, ne = nex * (ey1 - ey0 + 1);
+    // the shared elements' entries, row-major in (ey, ex); up to kRowLoads are
+    // loaded before the first add (one memory latency instead of one per element)
+    auto entry = [&](int q) {
+      const int ey = ey0 + q / nex, ex = ex0 + q % nex;
+      const int fy = a.firstV[ey], fx = a.firstU[ex];
+      const int li = (iy - fy) * a.nlx + (ix - fx), lj = (jy - fy) * a.nlx + (jx - fx);
+      const size_t e9 = ((size_t)ey * a.nel_u + ex) * 9;
+      return li <= lj ? a.EG[(e9 + ab) * a.npl + upper_pair(li, lj, a.nls)]
+                      : a.EG[(e9 + ba) * a.npl + upper_pair(lj, li, a.nls)];
+    };
+    double v[kRowLoads];
+#pragma unroll
+    for (int q = 0; q < kRowLoads; ++q) v[q] = q < ne ? entry(q) : 0.0;
     double acc = 0.0;
-    for (int ey = ey0; ey <= ey1; ++ey) {
-      const int fy = a.firstV[ey];
-      for (int ex = ex0; ex <= ex1; ++ex) {
-        const int fx = a.firstU[ex];
-        const int li = (iy - fy) * a.nlx + (ix - fx), lj = (jy - fy) * a.nlx + (jx - fx);
-        const size_t e9 = ((size_t)ey * a.nel_u + ex) * 9;
-        if (li <= lj)
-          acc += a.EG[(e9 + ab) * a.npl + upper_pair(li, lj, a.nls)];
-        else
-          acc += a.EG[(e9 + ba) * a.npl + upper_pair(lj, li, a.nls)];
-      }
-    }
+#pragma unroll
+    for (int q = 0; q < kRowLoads; ++q)
+      if (q < ne) acc += v[q];
+    for (int q = kRowLoads; q < ne; ++q) acc += entry(q);
     G[ls0 * 9 + it] = acc;
   }
 }
@@ -2605,6 +2648,7 @@ static lam_status ensure_device(Plan& P) {
       return st;
     }
     D->qdf = reinterpret_cast<float2*>(qdf);
+    D->q_valid = false;
     P.cfg_dirty = false;
   }
 #undef UP
@@ -2902,7 +2946,7 @@ static lam_status shell_operators(Plan& P, cudaStream_t s, bool full) {
     if (D.shellP) cudaFree(D.shellP);
     D.shellP = nullptr;
     D.shellP_elems = 0;
-    cudaError_t e = cudaMalloc(&D.shellP, need * sizeof(double));
+    cudaError_t e = device_alloc(reinterpret_cast<void**>(&D.shellP), need * sizeof(double));
     if (e != cudaSuccess) {
       set_error("cudaMalloc(P of the general extrusion, %zu doubles) failed: %s", need, cudaGetErrorString(e));
       return LAM_ERR_OOM;
@@ -2959,22 +3003,28 @@ static lam_status split_integrals(Plan& P, cudaStream_t s) {
   kb.wT = D.wT;
   kb.q = D.q;
   kb.qdf = D.qdf;
-  // K-b (a few microseconds) beside K-a: forked after the work already on the
-  // caller's stream (the previous combine reads Q), joined before the combine
-  if (!D.kb_stream) {
-    LAM_CUDA(cudaStreamCreateWithFlags(&D.kb_stream, cudaStreamNonBlocking));
-    LAM_CUDA(cudaEventCreateWithFlags(&D.kb_fork, cudaEventDisableTiming));
-    LAM_CUDA(cudaEventCreateWithFlags(&D.kb_join, cudaEventDisableTiming));
+  // Eq. Q depends on the plies only: computed on the first call and after every
+  // lam_plan_update (which replaces the configuration tables), kept otherwise.
+  // K-b (a few microseconds) runs beside K-a: forked after the work already on
+  // the caller's stream, joined before the combine.
+  const bool run_kb = !D.q_valid;
+  if (run_kb) {
+    if (!D.kb_stream) {
+      LAM_CUDA(cudaStreamCreateWithFlags(&D.kb_stream, cudaStreamNonBlocking));
+      LAM_CUDA(cudaEventCreateWithFlags(&D.kb_fork, cudaEventDisableTiming));
+      LAM_CUDA(cudaEventCreateWithFlags(&D.kb_join, cudaEventDisableTiming));
+    }
+    LAM_CUDA(cudaEventRecord(D.kb_fork, s));
+    LAM_CUDA(cudaStreamWaitEvent(D.kb_stream, D.kb_fork, 0));
+    cudaEvent_t ev = prof_begin(P, D.kb_stream);
+    kb_thickness<<<(unsigned)((P.nnz_t + 127) / 128), 128, 0, D.kb_stream>>>(kb);
+    LAM_CUDA(cudaGetLastError());
+    prof_end(P, LAM_KERNEL_THICKNESS, 1, D.kb_stream, ev);
+    LAM_CUDA(cudaEventRecord(D.kb_join, D.kb_stream));
+    D.q_valid = true;
   }
-  LAM_CUDA(cudaEventRecord(D.kb_fork, s));
-  LAM_CUDA(cudaStreamWaitEvent(D.kb_stream, D.kb_fork, 0));
-  cudaEvent_t ev = prof_begin(P, D.kb_stream);
-  kb_thickness<<<(unsigned)((P.nnz_t + 127) / 128), 128, 0, D.kb_stream>>>(kb);
-  LAM_CUDA(cudaGetLastError());
-  prof_end(P, LAM_KERNEL_THICKNESS, 1, D.kb_stream, ev);
-  LAM_CUDA(cudaEventRecord(D.kb_join, D.kb_stream));
   const lam_status st = P.shell ? shell_operators(P, s, false) : inplane_gram(P, s);
-  LAM_CUDA(cudaStreamWaitEvent(s, D.kb_join, 0));
+  if (run_kb) LAM_CUDA(cudaStreamWaitEvent(s, D.kb_join, 0));
   return st;
 }
 
@@ -3565,9 +3615,21 @@ static size_t adj_smem(const Plan& P) {
   return (size_t)P.adj_max_terms * (8 + 32 + 16) + 16 + (size_t)9 * adj_block(P) * sizeof(double);
 }
 
+static lam_status ensure_adjoint_alloc(Plan& P);
+// The adjoint's workspace; a failed allocation releases what this call allocated.
 static lam_status ensure_adjoint(Plan& P) {
   Device& D = *P.dev;
   if (D.adj_ready) return LAM_OK;
+  const size_t mark = D.allocs.size();
+  const lam_status st = ensure_adjoint_alloc(P);
+  if (st != LAM_OK) {
+    for (size_t k = mark; k < D.allocs.size(); ++k) cudaFree(D.allocs[k]);
+    D.allocs.resize(mark);
+  }
+  return st;
+}
+static lam_status ensure_adjoint_alloc(Plan& P) {
+  Device& D = *P.dev;
   lam_status st;
   auto& L = D.allocs;
   if ((st = upload(P, L, &D.adj_begin, P.adj_begin)) != LAM_OK) return st;
@@ -4192,9 +4254,13 @@ lam_status lam_assemble_split_host(lam_plan* plan, double* h_values, void* strea
   if ((st = lam::ensure_device(P)) != LAM_OK) return st;
   lam::Device& D = *P.dev;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // slabs of thickness rows: about 256 MB of values each
+  // slabs of thickness rows: at least about 256 MB of values each and at most
+  // about twelve slabs (every slab's combine forms the slices of all of its
+  // rows' classes, so fewer slabs cost less arithmetic; the first slab's
+  // kernels and the last slab's copy are not overlapped)
   const int64_t per_row = 9 * P.nnz_s * 4;  // upper bound of one thickness row's share (len_t <= 4 avg)
   int64_t rows_per_slab = std::max<int64_t>(1, (int64_t)(32 << 20) / std::max<int64_t>(1, per_row));
+  rows_per_slab = std::max<int64_t>(rows_per_slab, (P.nt + 11) / 12);
   rows_per_slab = std::min<int64_t>(rows_per_slab, P.nt);
   size_t need = 0;
   for (int64_t r0 = 0; r0 < P.nt; r0 += rows_per_slab) {
@@ -4205,7 +4271,7 @@ lam_status lam_assemble_split_host(lam_plan* plan, double* h_values, void* strea
     for (int k = 0; k < 2; ++k) {
       if (D.stage[k]) cudaFree(D.stage[k]);
       D.stage[k] = nullptr;
-      cudaError_t e = cudaMalloc(&D.stage[k], need * sizeof(double));
+      cudaError_t e = lam::device_alloc(reinterpret_cast<void**>(&D.stage[k]), need * sizeof(double));
       if (e != cudaSuccess) {
         lam::set_error("cudaMalloc(staging) failed: %s", cudaGetErrorString(e));
         D.stage_elems = 0;
@@ -4834,7 +4900,11 @@ namespace lam {
 template <typename T>
 static lam_status batch_upload(lam_batch& B, T** dst, const T* src, size_t n) {
   void* p = nullptr;
-  LAM_CUDA(cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)));
+  const cudaError_t e = device_alloc(&p, std::max<size_t>(n, 1) * sizeof(T));
+  if (e != cudaSuccess) {
+    set_error("cudaMalloc(%zu) failed: %s", std::max<size_t>(n, 1) * sizeof(T), cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? LAM_ERR_OOM : LAM_ERR_CUDA;
+  }
   B.allocs.push_back(p);
   if (n) LAM_CUDA(cudaMemcpy(p, src, n * sizeof(T), cudaMemcpyHostToDevice));
   *dst = static_cast<T*>(p);

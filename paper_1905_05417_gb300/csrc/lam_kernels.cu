@@ -294,6 +294,11 @@ static size_t kd_smem(const Plan& P) {
   if (P.shell) return (size_t)nqs * nls * 4 * sizeof(double) + (size_t)nqs * 16 * sizeof(double);
   return (size_t)nqs * nls * 3 * sizeof(double) + (size_t)nqs * 8 * sizeof(double);
 }
+// K-a of a general extrusion in FP64: shell_points plus the gradient parts u and w u
+static size_t ka_shell64_smem(const Plan& P) {
+  const int nqs = P.nqu * P.nqv, nls = ka_nls(P);
+  return (size_t)nqs * nls * 16 * sizeof(double) + (size_t)nqs * 16 * sizeof(double);
+}
 // K-a of a general extrusion: float pairs of u and w u, per point 16 doubles
 static size_t ka_shell_smem(const Plan& P) {
   const int nqs = P.nqu * P.nqv, nls = ka_nls(P);
@@ -1346,7 +1351,23 @@ __global__ void __launch_bounds__(256) ka_shell64(KaShellArgs a) {
   const int e = blockIdx.x, ex = e % ip.nel_u, ey = e / ip.nel_u;
   double* ph = sm;                              // [q][k][4]: g1 (3), R
   double* qs = ph + (size_t)nqs * nls * 4;      // [q][kShellQ]
+  double* uu = qs + (size_t)nqs * kShellQ;      // [q][k][12]: u (6), w|DF| u (6)
   shell_points(ip, ex, ey, ph, qs);
+  // u = (g1, R g^2) and its weighted copy, once per (point, function)
+  for (int t = threadIdx.x; t < nqs * nls; t += blockDim.x) {
+    const int q = t / nls;
+    const double* d = qs + (size_t)q * kShellQ;
+    const double* f = ph + (size_t)t * 4;
+    double* o = uu + (size_t)t * 12;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      o[k] = f[k];
+      o[3 + k] = f[3] * d[6 + k];
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) o[6 + k] = d[9] * o[k];
+  }
+  __syncthreads();
   const int npl = nls * (nls + 1) / 2;
   double* out = a.EG + (size_t)e * npl * 36;
   for (int t = threadIdx.x; t < 4 * npl; t += blockDim.x) {
@@ -1361,20 +1382,18 @@ __global__ void __launch_bounds__(256) ka_shell64(KaShellArgs a) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) acc[k] = 0.0;
     for (int q = 0; q < nqs; ++q) {
-      const double* d = qs + (size_t)q * kShellQ;
-      const double* fi = ph + ((size_t)q * nls + li) * 4;
-      const double* fj = ph + ((size_t)q * nls + lj) * 4;
-      const double w = d[9];
-      double ui[3], uj[3];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        ui[k] = w * (al ? fi[3] * d[6 + k] : fi[k]);
-        uj[k] = be ? fj[3] * d[6 + k] : fj[k];
-      }
-#pragma unroll
-      for (int x = 0; x < 3; ++x)
-#pragma unroll
-        for (int y = 0; y < 3; ++y) acc[x * 3 + y] = fma(ui[x], uj[y], acc[x * 3 + y]);
+      const double* ui = uu + ((size_t)q * nls + li) * 12 + 6 + 3 * al;  // w|DF| u_alpha^li
+      const double* uj = uu + ((size_t)q * nls + lj) * 12 + 3 * be;      // u_beta^lj
+      const double a0 = ui[0], a1 = ui[1], a2 = ui[2], b0 = uj[0], b1 = uj[1], b2 = uj[2];
+      acc[0] = fma(a0, b0, acc[0]);
+      acc[1] = fma(a0, b1, acc[1]);
+      acc[2] = fma(a0, b2, acc[2]);
+      acc[3] = fma(a1, b0, acc[3]);
+      acc[4] = fma(a1, b1, acc[4]);
+      acc[5] = fma(a1, b2, acc[5]);
+      acc[6] = fma(a2, b0, acc[6]);
+      acc[7] = fma(a2, b1, acc[7]);
+      acc[8] = fma(a2, b2, acc[8]);
     }
 #pragma unroll
     for (int k = 0; k < 9; ++k) out[(size_t)pr * 36 + blk * 9 + k] = acc[k];
@@ -1572,6 +1591,39 @@ struct KcArgs {
   const unsigned long long* shell_pmax;
 };
 
+
+// G_ab of the in-plane pair (i_s, k_s-th neighbour j_s): the sum over the shared
+// elements, row-major in (ey, ex), of the element blocks of K-a. Loads go out
+// four at a time before their adds; missing entries of a group add an exact
+// zero. The same order everywhere it is formed (kg_rows, kcs_row), so every
+// path that assembles a row's G gets the same bits.
+__device__ __forceinline__ double gram_pair_sum(const KcArgs& a, int ix, int iy, int lx, int ks, int ab) {
+  const int jx = a.loX[ix] + ks % lx, jy = a.loY[iy] + ks / lx;
+  const int ex0 = max(a.eloX[ix], a.eloX[jx]), ex1 = min(a.ehiX[ix], a.ehiX[jx]);
+  const int ey0 = max(a.eloY[iy], a.eloY[jy]), ey1 = min(a.ehiY[iy], a.ehiY[jy]);
+  const int ba = (ab % 3) * 3 + ab / 3;
+  const int nex = ex1 - ex0 + 1, ne = nex * (ey1 - ey0 + 1);
+  double acc = 0.0;
+  for (int q0 = 0; q0 < ne; q0 += 4) {
+    double v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int q = q0 + j;
+      v[j] = 0.0;
+      if (q < ne) {
+        const int ey = ey0 + q / nex, ex = ex0 + q % nex;
+        const int fy = a.firstV[ey], fx = a.firstU[ex];
+        const int li = (iy - fy) * a.nlx + (ix - fx), lj = (jy - fy) * a.nlx + (jx - fx);
+        const size_t e9 = ((size_t)ey * a.nel_u + ex) * 9;
+        v[j] = li <= lj ? a.EG[(e9 + ab) * a.npl + upper_pair(li, lj, a.nls)]
+                        : a.EG[(e9 + ba) * a.npl + upper_pair(lj, li, a.nls)];
+      }
+    }
+    acc = ((acc + v[0]) + v[1]) + v[2];
+    acc = acc + v[3];
+  }
+  return acc;
+}
 
 // P of a general extrusion for entry (c, d) of the in-plane pair (i_s, k_s-th
 // neighbour j_s): pairs with j_s >= i_s hold it (blocks at 0, 9, 18, 27); the
@@ -1772,27 +1824,7 @@ __device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm,
   const int n9 = 9 * ls;
   const int64_t ls0 = a.LSb[is];
   // phase 0: the row's G blocks into slices[0 .. 9 ls) (a general extrusion reads P instead)
-  for (int item = tid; item < (SHELL ? 0 : n9); item += nthr) {
-    const int ks = item / 9, ab = item % 9;
-    const int jx = a.loX[ix] + ks % lx, jy = a.loY[iy] + ks / lx;
-    const int ex0 = max(a.eloX[ix], a.eloX[jx]), ex1 = min(a.ehiX[ix], a.ehiX[jx]);
-    const int ey0 = max(a.eloY[iy], a.eloY[jy]), ey1 = min(a.ehiY[iy], a.ehiY[jy]);
-    const int ba = (ab % 3) * 3 + ab / 3;
-    double acc = 0.0;
-    for (int ey = ey0; ey <= ey1; ++ey) {
-      const int fy = a.firstV[ey];
-      for (int ex = ex0; ex <= ex1; ++ex) {
-        const int fx = a.firstU[ex];
-        const int li = (iy - fy) * a.nlx + (ix - fx), lj = (jy - fy) * a.nlx + (jx - fx);
-        const size_t e9 = ((size_t)ey * a.nel_u + ex) * 9;
-        if (li <= lj)
-          acc += a.EG[(e9 + ab) * a.npl + upper_pair(li, lj, a.nls)];
-        else
-          acc += a.EG[(e9 + ba) * a.npl + upper_pair(lj, li, a.nls)];
-      }
-    }
-    slices[item] = acc;
-  }
+  for (int item = tid; item < (SHELL ? 0 : n9); item += nthr) slices[item] = gram_pair_sum(a, ix, iy, lx, item / 9, item % 9);
   __syncthreads();
   const int item = tid;
   const bool active = item < n9;
@@ -2059,37 +2091,13 @@ __device__ __forceinline__ bool kcw_chunk(const KcArgs& a, int ch, int& it0, int
 // sum over the shared elements (fixed row-major element order) of the element
 // blocks of K-a, into G[(LSb[i_s] + k_s) * 9 + ab]: CTA per in-plane row,
 // thread per (k_s, ab). FP64 sums, the order of the combine's own gather.
-constexpr int kRowLoads = 16;  // (p + 1)^2 shared elements of a cubic pair
-__global__ void __launch_bounds__(512) kg_rows(KcArgs a, double* __restrict__ G) {
+__global__ void __launch_bounds__(512, 4) kg_rows(KcArgs a, double* __restrict__ G) {
   const int64_t is = blockIdx.x;
   const int ix = (int)(is % a.nx), iy = (int)(is / a.nx);
   const int lx = a.lenX[ix], n9 = 9 * lx * a.lenY[iy];
   const int64_t ls0 = a.LSb[is];
   for (int it = threadIdx.x; it < n9; it += blockDim.x) {
-    const int ks = it / 9, ab = it % 9;
-    const int jx = a.loX[ix] + ks % lx, jy = a.loY[iy] + ks / lx;
-    const int ex0 = max(a.eloX[ix], a.eloX[jx]), ex1 = min(a.ehiX[ix], a.ehiX[jx]);
-    const int ey0 = max(a.eloY[iy], a.eloY[jy]), ey1 = min(a.ehiY[iy], a.ehiY[jy]);
-    const int ba = (ab % 3) * 3 + ab / 3;
-    const int nex = ex1 - ex0 + 1, ne = nex * (ey1 - ey0 + 1);
-    // the shared elements' entries, row-major in (ey, ex); up to kRowLoads are
-    // loaded before the first add (one memory latency instead of one per element)
-    auto entry = [&](int q) {
-      const int ey = ey0 + q / nex, ex = ex0 + q % nex;
-      const int fy = a.firstV[ey], fx = a.firstU[ex];
-      const int li = (iy - fy) * a.nlx + (ix - fx), lj = (jy - fy) * a.nlx + (jx - fx);
-      const size_t e9 = ((size_t)ey * a.nel_u + ex) * 9;
-      return li <= lj ? a.EG[(e9 + ab) * a.npl + upper_pair(li, lj, a.nls)]
-                      : a.EG[(e9 + ba) * a.npl + upper_pair(lj, li, a.nls)];
-    };
-    double v[kRowLoads];
-#pragma unroll
-    for (int q = 0; q < kRowLoads; ++q) v[q] = q < ne ? entry(q) : 0.0;
-    double acc = 0.0;
-#pragma unroll
-    for (int q = 0; q < kRowLoads; ++q)
-      if (q < ne) acc += v[q];
-    for (int q = kRowLoads; q < ne; ++q) acc += entry(q);
+    const double acc = gram_pair_sum(a, ix, iy, lx, it / 9, it % 9);
     G[ls0 * 9 + it] = acc;
   }
 }
@@ -2100,6 +2108,7 @@ __global__ void __launch_bounds__(512) kg_rows(KcArgs a, double* __restrict__ G)
 // handed out by the shared counter *next, so any number of warps can join; a
 // warp takes its next pair (and loads that pair's table entries) before it
 // copies the current one.
+template <int U>
 __device__ __forceinline__ void kcw_copy_pairs(const KcArgs& a, const double* S, int* next, int64_t p_begin,
                                                int npairs, int64_t ls0, int seg_len, int lane) {
   auto take = [&]() {
@@ -2131,11 +2140,11 @@ __device__ __forceinline__ void kcw_copy_pairs(const KcArgs& a, const double* S,
     const int64_t row_step = (int64_t)lt * seg_len;
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) {
-      double v[kSegUnroll];
+      double v[U];  // U * 32 >= 3 len_s of the plan's longest row
 #pragma unroll
-      for (int j = 0; j < kSegUnroll; ++j) v[j] = (lane + 32 * j < seg_len) ? src[cc * seg_len + lane + 32 * j] : 0.0;
+      for (int j = 0; j < U; ++j) v[j] = (lane + 32 * j < seg_len) ? src[cc * seg_len + lane + 32 * j] : 0.0;
 #pragma unroll
-      for (int j = 0; j < kSegUnroll; ++j)
+      for (int j = 0; j < U; ++j)
         if (lane + 32 * j < seg_len) dst[cc * row_step + lane + 32 * j] = v[j];
     }
     q = qn;
@@ -2146,7 +2155,7 @@ __device__ __forceinline__ void kcw_copy_pairs(const KcArgs& a, const double* S,
   }
 }
 
-template <bool MONO, bool CHUNKED, bool SHELL>
+template <bool MONO, bool CHUNKED, bool SHELL, int U>
 __global__ void __launch_bounds__(896, 1) kc_ws(KcArgs a, int nct) {
   static_assert(!(SHELL && MONO), "a general extrusion couples every block");
   extern __shared__ double sm[];
@@ -2284,7 +2293,7 @@ __global__ void __launch_bounds__(896, 1) kc_ws(KcArgs a, int nct) {
         named_bar_arrive(kBarFull + b, nall);  // buffer b holds the unit's slices
         // join the copy of the previous unit, whose buffer the next unit reuses
         if (prev_b >= 0)
-          kcw_copy_pairs(a, sm + (size_t)prev_b * buf_elems, sNext + prev_b, prev_p0, prev_np, prev_ls0, prev_seg, lane);
+          kcw_copy_pairs<U>(a, sm + (size_t)prev_b * buf_elems, sNext + prev_b, prev_p0, prev_np, prev_ls0, prev_seg, lane);
         prev_b = b;
         prev_p0 = a.LTb[it0];
         prev_np = (int)(a.LTb[it1] - a.LTb[it0]);
@@ -2295,7 +2304,7 @@ __global__ void __launch_bounds__(896, 1) kc_ws(KcArgs a, int nct) {
     }
     if (prev_b >= 0) {  // the last unit: every compute thread's slices are visible after the barrier
       named_bar_sync(kBarCompute, nct);
-      kcw_copy_pairs(a, sm + (size_t)prev_b * buf_elems, sNext + prev_b, prev_p0, prev_np, prev_ls0, prev_seg, lane);
+      kcw_copy_pairs<U>(a, sm + (size_t)prev_b * buf_elems, sNext + prev_b, prev_p0, prev_np, prev_ls0, prev_seg, lane);
     }
   } else {
     // ---------------- copy group ----------------
@@ -2312,7 +2321,7 @@ __global__ void __launch_bounds__(896, 1) kc_ws(KcArgs a, int nct) {
         const int b = (int)(k & 1);
         const double* S = sm + (size_t)b * buf_elems;
         named_bar_sync(kBarFull + b, nall);
-        kcw_copy_pairs(a, S, sNext + b, a.LTb[it0], (int)(a.LTb[it1] - a.LTb[it0]), ls0, seg_len, lane);
+        kcw_copy_pairs<U>(a, S, sNext + b, a.LTb[it0], (int)(a.LTb[it1] - a.LTb[it0]), ls0, seg_len, lane);
         if (k + 2 < nunits) {
           __threadfence_block();
           named_bar_arrive(kBarEmpty + b, nall);  // buffer b may be overwritten
@@ -2668,7 +2677,8 @@ static lam_status check_limits(const Plan& P) {
   // takes the streaming form whenever that fits, and has no allocation-free path)
   const bool class_major = !(P.shell && use_stream(P));
   if ((class_major && kc_smem(P) > 200 * 1024) || ka_smem(P) > 200 * 1024 || kd_smem(P) > 200 * 1024 ||
-      (P.shell && ka_shell_smem(P) > 200 * 1024)) {
+      (P.shell && ka_shell_smem(P) > 200 * 1024) ||
+      (P.shell && P.arith == LAM_ARITH_FP64 && ka_shell64_smem(P) > 200 * 1024)) {
     set_error("plan tables exceed the shared-memory budget of the kernels");
     return LAM_ERR_UNSUPPORTED;
   }
@@ -2808,7 +2818,7 @@ static lam_status launch_kc(const Plan& P, const KcArgs& k, cudaStream_t s) {
 // compute threads (c, k_s, d) plus kcw_copy_threads copy threads, two slice
 // buffers) when both buffers fit in shared memory; otherwise kc_stream in FP64
 // (two CTAs per SM alternating their compute and copy phases).
-static int kcw_copy_threads(const Plan& P) { return std::min(512, 896 - kcs_block(P)); }
+static int kcw_copy_threads(const Plan& P) { return 896 - kcs_block(P); }
 static size_t kcw_smem(const Plan& P) {
   int slots = 1;
   for (int v : P.ck_nslot) slots = std::max(slots, v);
@@ -2833,10 +2843,14 @@ static lam_status launch_kc64(const Plan& P, const KcArgs& k, cudaStream_t s) {
     KcArgs kw = k;
     if (!SHELL) kw.G = P.dev->Grow;
     const size_t smem = kcw_smem(P);
-    LAM_CUDA(cudaFuncSetAttribute(kc_ws<MONO, CHUNKED, SHELL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int nct = kcs_block(P), block = nct + kcw_copy_threads(P);
     const int64_t grid = std::min<int64_t>(P.ns, std::max(1, P.dev->n_sm));
-    kc_ws<MONO, CHUNKED, SHELL><<<(unsigned)grid, block, smem, s>>>(kw, nct);
+    // copy steps of 32 values per segment: the fewest that cover 3 len_s
+    const int need = (3 * max_len_s(P) + 31) / 32;
+    auto kern = need <= 3 ? kc_ws<MONO, CHUNKED, SHELL, 3> : need <= 5 ? kc_ws<MONO, CHUNKED, SHELL, 5>
+                                                                        : kc_ws<MONO, CHUNKED, SHELL, 6>;
+    LAM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(unsigned)grid, block, smem, s>>>(kw, nct);
   } else {
     const size_t smem = kcs_smem(P);
     LAM_CUDA(cudaFuncSetAttribute(kc_stream<MONO, CHUNKED, false, SHELL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2925,7 +2939,7 @@ static lam_status shell_element_gram(Plan& P, cudaStream_t s) {
     LAM_CUDA(cudaFuncSetAttribute(ka_shell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ka_shell<<<(unsigned)nel, 256, smem, s>>>(ka);
   } else {
-    const size_t smem = kd_smem(P);  // shell_points: nqs x nls x 4 + nqs x 16 doubles
+    const size_t smem = ka_shell64_smem(P);
     LAM_CUDA(cudaFuncSetAttribute(ka_shell64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ka_shell64<<<(unsigned)nel, 256, smem, s>>>(ka);
   }

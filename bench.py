@@ -453,8 +453,13 @@ def run_batch(args, L, dev, flush, peak, peak_kind, world):
                        "unit square, 8..64 plies of thickness U[0.0005, 0.002], angles {0, +-45, 90}, 1..4 materials",
            "metric": "stored entries assembled per second", "value": aggregate_throughput(nnz, world, ms / 1e3),
            "unit": UNIT, "ms_per_step": ms, "steps": steps, "nnz_total": nnz, "n_plans": len(plans),
-           "n_meshes": info["n_meshes"], "n_persistent": info["n_persistent"], "ctas_per_sm": info["ctas_per_sm"],
-           "autotuner_ms": [round(x, 3) for x in info["tuned_ms"] if x > 0], "cuda_graph": bool(info["graph"]),
+           "n_meshes": info["n_meshes"], "n_persistent": info["n_persistent"],
+           "autotuner": {"axes": {"ctas_per_sm": [1, 2, 3, 4], "rows_per_item": [1, 2, 4]},
+                         "chosen": {"ctas_per_sm": info["ctas_per_sm"], "rows_per_item": info["rows_per_item"]},
+                         "ms": {f"{c}x{r}": round(info["tuned_ms"][ri * 4 + c - 1], 3)
+                                for ri, r in enumerate((1, 2, 4)) for c in (1, 2, 3, 4)
+                                if info["tuned_ms"][ri * 4 + c - 1] > 0}},
+           "cuda_graph": bool(info["graph"]),
            "one_plan_at_a_time_ms": seq_ms, "speedup_vs_one_at_a_time": seq_ms / ms,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "traffic": None, "kernel": "whole batch (8 B per stored entry)",
@@ -503,10 +508,10 @@ def run_sweep(args):
                 plan = L.Plan.from_laminate(lam)
                 v = torch.empty(plan.nnz, dtype=torch.float64, device="cuda")
                 split_ms = timed(lambda: plan.assemble_split(v), 10)
-                std_ms = timed(lambda: plan.assemble_standard(v), 3 if p < 4 else 1)
+                std_ms = timed(lambda: plan.assemble_standard(v), 3 if p < 4 else 1) if args.sweep_standard else None
                 points.append({"p": p, "stack": stack, "layers": m, "nnz": plan.nnz,
                                "configs": plan.info["n_configs"], "split_ms": split_ms, "standard_ms": std_ms,
-                               "speedup": std_ms / split_ms})
+                               "speedup": None if std_ms is None else std_ms / split_ms})
                 plan.close()
                 del v
     shape = {}
@@ -514,7 +519,8 @@ def run_sweep(args):
         for stack in ("cross", "quasi"):
             sel = {q["layers"]: q for q in points if q["p"] == p and q["stack"] == stack}
             shape[f"p{p}_{stack}"] = {"split_t64_over_t8": sel[64]["split_ms"] / sel[8]["split_ms"],
-                                      "standard_t64_over_t8": sel[64]["standard_ms"] / sel[8]["standard_ms"],
+                                      "standard_t64_over_t8": (None if sel[8]["standard_ms"] is None else
+                                                               sel[64]["standard_ms"] / sel[8]["standard_ms"]),
                                       "speedup_at_64": sel[64]["speedup"]}
     print(json.dumps({"sweep": "pagano_one_element_through_thickness", "n_el": args.sweep_n, "dtype": "f64",
                       "data": "synthetic", "points": points, "shape": shape}), flush=True)
@@ -858,6 +864,8 @@ def main(argv=None):
     ap.add_argument("--shell-steps", type=int, default=5, help="timed split assemblies of the curved shell (0 = skip)")
     ap.add_argument("--sweep", action="store_true", help="the paper's layer sweep (one element through the thickness)")
     ap.add_argument("--sweep-n", type=int, default=16, help="in-plane elements per direction in the sweep")
+    ap.add_argument("--sweep-no-standard", dest="sweep_standard", action="store_false",
+                    help="time only the split path in the sweep")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--n-el", type=int, default=64, help="in-plane elements per direction (64 = the benchmark)")

@@ -170,6 +170,11 @@ typedef struct {
   int32_t combine_chunks;    /* streaming: chunks of thickness rows whose classes fit in shared memory */
   int32_t shell;             /* 1: a general extrusion (surface in R^3 or a != e_z), see lam_inplane */
   int32_t arith;             /* LAM_ARITH_FP64 or LAM_ARITH_DOUBLE_FLOAT (lam_options.arith) */
+  int32_t combine_terms;     /* streaming: (slot, configuration) terms over all chunks */
+  int32_t combine_source_terms; /* ... of them evaluated by the FP64 combine of a monoclinic plate: a slot
+                                   whose classes agree on the Q terms of an entry kind (Q_11, Q_22 or
+                                   Q_12, Q_21) with an earlier slot of its chunk is copied from it, counted
+                                   once per kind (so up to 2 combine_terms) */
 } lam_plan_info;
 
 typedef struct lam_plan lam_plan;
@@ -328,8 +333,9 @@ lam_status lam_adjoint(lam_plan* plan, const lam_cotangent* cotangent, double* d
  * instance, one launch the Gram blocks of every mesh, and one persistent
  * launch combines every in-plane row of every instance from an atomic work
  * queue (largest instances first). The first lam_batch_assemble times the
- * persistent launch at 1..4 CTAs per SM, keeps the fastest, and captures the
- * whole sequence in a CUDA graph that later calls replay.
+ * whole sequence for every pair (CTAs per SM 1..4, in-plane rows per work item
+ * 1, 2 or 4), keeps the fastest, and captures it in a CUDA graph that later
+ * calls replay.
  * ------------------------------------------------------------------------- */
 typedef struct lam_batch lam_batch;
 
@@ -341,8 +347,9 @@ typedef struct {
                               general extrusions -- by lam_assemble_split after it) */
   int32_t ctas_per_sm;     /* chosen by the autotuner, 0 before the first lam_batch_assemble */
   int32_t graph;           /* 1 once the launches are replayed from a CUDA graph */
-  int32_t reserved;
-  double tuned_ms[4];      /* autotuner: one assembly with 1..4 CTAs per SM (0 = not tried) */
+  int32_t rows_per_item;   /* chosen by the autotuner: in-plane rows of one instance per work item */
+  double tuned_ms[12];     /* autotuner: one assembly per candidate, [r * 4 + c - 1] for c CTAs per SM and
+                              1, 2, 4 rows per item (r = 0, 1, 2); 0 = not tried */
 } lam_batch_info;
 
 /* Batch of n_plans plans (borrowed: they must outlive the batch, all on the

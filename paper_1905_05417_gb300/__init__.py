@@ -99,7 +99,7 @@ class _Cotangent(ctypes.Structure):
 class _BatchInfo(ctypes.Structure):
     _fields_ = [("n_plans", ctypes.c_int32), ("n_meshes", ctypes.c_int32), ("nnz_total", ctypes.c_int64),
                 ("n_persistent", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("graph", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("tuned_ms", ctypes.c_double * 4)]
+                ("rows_per_item", ctypes.c_int32), ("tuned_ms", ctypes.c_double * 12)]
 
 
 class _Info(ctypes.Structure):
@@ -107,7 +107,8 @@ class _Info(ctypes.Structure):
                 ("nnz_inplane", ctypes.c_int64), ("nnz_thickness", ctypes.c_int64), ("n_configs", ctypes.c_int32),
                 ("n_classes", ctypes.c_int32), ("monoclinic", ctypes.c_int32), ("n_pieces", ctypes.c_int32),
                 ("combine_streaming", ctypes.c_int32), ("combine_chunks", ctypes.c_int32), ("shell", ctypes.c_int32),
-                ("arith", ctypes.c_int32)]
+                ("arith", ctypes.c_int32), ("combine_terms", ctypes.c_int32),
+                ("combine_source_terms", ctypes.c_int32)]
 
 
 _lib = None
@@ -338,7 +339,7 @@ def batch_assemble(handle, d_values, stream=None) -> None:
 def batch_get_info(handle) -> dict:
     info = _BatchInfo()
     _check(load().lam_batch_get_info(handle, ctypes.byref(info)), "lam_batch_get_info")
-    out = {name: getattr(info, name) for name, _ in _BatchInfo._fields_ if name not in ("reserved", "tuned_ms")}
+    out = {name: getattr(info, name) for name, _ in _BatchInfo._fields_ if name != "tuned_ms"}
     out["tuned_ms"] = list(info.tuned_ms)
     return out
 

@@ -96,6 +96,16 @@ struct Plan {
   std::vector<int> ck_it, ck_term, ck_nslot;
   std::vector<int> ckt_slot, ckt_cfg, ckt_rep, ckt_first;
   std::vector<int> pair_slot;            // slot of every thickness pair within its chunk
+  // ... and for monoclinic plates, per chunk, the terms of the slots that are
+  // computed for each entry kind (block: Q_11, Q_22; off: Q_12, Q_21): terms
+  // ck_sterm[ch] .. + ck_nblk[ch] - 1 for the block kind, then the off kind's up
+  // to ck_sterm[ch + 1] - 1 (sorted by configuration, cks_first marking the
+  // first term of a slot); slots that share a kind's Q terms with an earlier slot
+  // are copied from it: ck_copy[ch] .. ck_copy[ch + 1] - 1, ckc_dst = 2 slot +
+  // kind, ckc_src = the source slot
+  std::vector<int> ck_sterm, ck_nblk, cks_slot, cks_cfg, cks_rep, cks_first;
+  std::vector<int> ck_copy, ckc_dst, ckc_src;
+  double q_scale[4] = {0.0, 0.0, 0.0, 0.0};  // largest |Q_ab| over every pair and configuration
   std::vector<int> cls_term_begin;       // size ncls + 1
   std::vector<int> cls_terms;            // configuration ids with nonzero Q
   std::vector<int> cls_occ_begin;        // size ncls + 1
@@ -170,13 +180,22 @@ inline int kcs_stride(const Plan& P) { return 9 * max_len_s(P); }
 inline int kcs_max_terms(const Plan& P) {
   int mt = 1;
   for (size_t ch = 0; ch + 1 < P.ck_term.size(); ++ch) mt = mt > P.ck_term[ch + 1] - P.ck_term[ch] ? mt : P.ck_term[ch + 1] - P.ck_term[ch];
+  for (size_t ch = 0; ch + 1 < P.ck_sterm.size(); ++ch)
+    mt = mt > P.ck_sterm[ch + 1] - P.ck_sterm[ch] ? mt : P.ck_sterm[ch + 1] - P.ck_sterm[ch];
   return mt;
+}
+// largest copy list of a chunk (entries of slots taken from a source slot)
+inline int kcs_max_copies(const Plan& P) {
+  int mc = 1;
+  for (size_t ch = 0; ch + 1 < P.ck_copy.size(); ++ch) mc = mc > P.ck_copy[ch + 1] - P.ck_copy[ch] ? mc : P.ck_copy[ch + 1] - P.ck_copy[ch];
+  return mc;
 }
 inline size_t kcs_smem(const Plan& P) {
   int slots = 1;
   for (int v : P.ck_nslot) slots = slots > v ? slots : v;
   // slices, then per term of a chunk: Q (4 float pairs or 4 doubles), slot, first flag, configuration
-  return (size_t)slots * kcs_stride(P) * sizeof(double) + (size_t)kcs_max_terms(P) * (32 + 12) + 16;
+  return (size_t)slots * kcs_stride(P) * sizeof(double) + (size_t)kcs_max_terms(P) * (32 + 12) +
+         (size_t)kcs_max_copies(P) * 8 + 16;
 }
 inline bool use_stream(const Plan& P) { return 9 * max_len_s(P) <= 512 && !P.ck_nslot.empty(); }
 

@@ -70,6 +70,8 @@ struct Device {
   int* pair_cls = nullptr;
   int *ck_it = nullptr, *ck_term = nullptr, *ck_nslot = nullptr, *pair_slot = nullptr;
   int *ckt_slot = nullptr, *ckt_cfg = nullptr, *ckt_rep = nullptr, *ckt_first = nullptr;
+  int *ck_sterm = nullptr, *ck_nblk = nullptr, *cks_slot = nullptr, *cks_cfg = nullptr, *cks_rep = nullptr,
+      *cks_first = nullptr, *ck_copy = nullptr, *ckc_dst = nullptr, *ckc_src = nullptr;
   float2* qdf = nullptr;  // float pairs of q
 
   double* EG = nullptr;  // element Gram blocks: n_el x 9 x pairs
@@ -1589,7 +1591,18 @@ struct KcArgs {
   // largest |P| of each block (11, 12, 21, 22) as bit patterns
   const double* shellP;
   const unsigned long long* shell_pmax;
+  // monoclinic plates: per-kind source terms and the copies of the other slots
+  const int *ck_sterm, *ck_nblk, *cks_slot, *cks_cfg, *cks_rep, *cks_first;
+  const int *ck_copy, *ckc_dst, *ckc_src;
+  int max_copies;
 };
+
+// Entries (c, d) of a monoclinic 3 x 3 block by kind: block (c and d both
+// in-plane or both z: Q_11, Q_22) first, then off (Q_12, Q_21). A thread of the
+// combine's slice arithmetic takes entry kBlkC/D[g] (g < 5) or kOffC/D[g - 5]
+// for in-plane neighbour k_s, so that most warps hold one kind.
+__constant__ int kKindC[9] = {0, 0, 1, 1, 2, 0, 1, 2, 2};
+__constant__ int kKindD[9] = {0, 1, 0, 1, 2, 2, 2, 0, 1};
 
 
 // G_ab of the in-plane pair (i_s, k_s-th neighbour j_s): the sum over the shared
@@ -1818,6 +1831,10 @@ __device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm,
   int* sSlot = reinterpret_cast<int*>(sQ + 4 * (size_t)a.max_terms);       // slot
   int* sFirst = sSlot + a.max_terms;                                       // first term of its slot
   int* sCfg = sFirst + a.max_terms;                                        // configuration
+  int* sCopyDst = sCfg + a.max_terms;                                      // FP64, monoclinic: copied slots
+  int* sCopySrc = sCopyDst + a.max_copies;                                 // ... and their source slots
+  // FP64 on a monoclinic plate: the per-kind source terms and slot copies of kc_ws
+  constexpr bool SPLIT = MONO && !DF && !SHELL;
   const int ix = (int)(is % a.nx), iy = (int)(is / a.nx);
   const int lx = a.lenX[ix];
   const int ls = lx * a.lenY[iy];
@@ -1826,16 +1843,22 @@ __device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm,
   // phase 0: the row's G blocks into slices[0 .. 9 ls) (a general extrusion reads P instead)
   for (int item = tid; item < (SHELL ? 0 : n9); item += nthr) slices[item] = gram_pair_sum(a, ix, iy, lx, item / 9, item % 9);
   __syncthreads();
-  const int item = tid;
-  const bool active = item < n9;
+  const bool active = tid < n9;
   int c = 0, ks = 0, d = 0;
   double g[9];
   float gh[9], gl[9];
   if (active) {
-    c = item / (3 * ls);
-    const int rem = item % (3 * ls);
-    ks = rem / 3;
-    d = rem % 3;
+    if (SPLIT) {  // entries grouped by kind, as in kc_ws
+      const int gk = tid / ls;
+      ks = tid - gk * ls;
+      c = kKindC[gk];
+      d = kKindD[gk];
+    } else {
+      c = tid / (3 * ls);
+      const int rem = tid % (3 * ls);
+      ks = rem / 3;
+      d = rem % 3;
+    }
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       g[k] = SHELL ? 0.0 : slices[ks * 9 + k];
@@ -1843,6 +1866,7 @@ __device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm,
     }
   }
   __syncthreads();  // the G row is in registers; its space is reused by the slices
+  const int item = active ? c * 3 * ls + 3 * ks + d : tid;  // the entry's place in a slice (output order)
   const int cd = c * 3 + d;
   const bool block_type = ((c == 2) == (d == 2));
   const int offa = block_type ? 0 : 1, offb = block_type ? 3 : 2;
@@ -1875,10 +1899,17 @@ __device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm,
       if (it0 >= it1) continue;  // the same for every thread
     }
     // the chunk's terms into shared memory
-    const int tb = a.ck_term[ch], nterm = a.ck_term[ch + 1] - tb;
+    const int tb = SPLIT ? a.ck_sterm[ch] : a.ck_term[ch];
+    const int nterm = (SPLIT ? a.ck_sterm[ch + 1] : a.ck_term[ch + 1]) - tb;
+    const int nblk = SPLIT ? a.ck_nblk[ch] : 0;
+    const int cb = SPLIT ? a.ck_copy[ch] : 0, ncopy = SPLIT ? a.ck_copy[ch + 1] - cb : 0;
+    for (int k = tid; k < ncopy; k += nthr) {
+      sCopyDst[k] = a.ckc_dst[cb + k];
+      sCopySrc[k] = a.ckc_src[cb + k];
+    }
     for (int k = tid; k < nterm; k += nthr) {
-      const int t = tb + k, m = a.ckt_cfg[t];
-      const size_t qi = ((size_t)a.ckt_rep[t] * a.ncfg + m) * 4;
+      const int t = tb + k, m = SPLIT ? a.cks_cfg[t] : a.ckt_cfg[t];
+      const size_t qi = ((size_t)(SPLIT ? a.cks_rep[t] : a.ckt_rep[t]) * a.ncfg + m) * 4;
       if (DF) {
         float2* q2 = reinterpret_cast<float2*>(sQ + 4 * (size_t)k);
 #pragma unroll
@@ -1890,8 +1921,8 @@ __device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm,
 #pragma unroll
         for (int j = 0; j < 4; ++j) sQ[4 * (size_t)k + j] = a.q[qi + j];
       }
-      sSlot[k] = a.ckt_slot[t];
-      sFirst[k] = a.ckt_first[t];
+      sSlot[k] = SPLIT ? a.cks_slot[t] : a.ckt_slot[t];
+      sFirst[k] = SPLIT ? a.cks_first[t] : a.ckt_first[t];
       sCfg[k] = m;
     }
     __syncthreads();
@@ -1964,7 +1995,9 @@ __device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm,
         }
       } else {
         double pa = 0.0, pb = 0.0, p11 = 0.0, p12 = 0.0, p21 = 0.0, p22 = 0.0;
-        for (int t = 0; t < t1; ++t) {
+        const int t_begin = (SPLIT && !block_type) ? nblk : 0;
+        const int t_end = (SPLIT && block_type) ? nblk : t1;
+        for (int t = t_begin; t < t_end; ++t) {
           const int m = sCfg[t];
           if (m != cur) {
             cur = m;
@@ -2003,6 +2036,14 @@ __device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm,
             v = fma(Q[3], p22, v);
           }
           *dst = v;
+        }
+        if (SPLIT) {  // slots that share this kind's Q terms with a source slot
+          const int kind = block_type ? 0 : 1;
+          for (int q = 0; q < ncopy; ++q) {
+            const int dk = sCopyDst[q];
+            if ((dk & 1) == kind)
+              slices[(size_t)(dk >> 1) * a.slice_stride + item] = slices[(size_t)sCopySrc[q] * a.slice_stride + item];
+          }
         }
       }
     }
@@ -2164,7 +2205,9 @@ __global__ void __launch_bounds__(896, 1) kc_ws(KcArgs a, int nct) {
   double* sG = sm + 2 * buf_elems;                                     // the row's G blocks (9 per neighbour)
   double* sQ = sG + a.slice_stride;                                    // chunk terms: Q
   int2* sMeta = reinterpret_cast<int2*>(sQ + 4 * (size_t)a.max_terms);  // (2 slot + first, configuration)
-  int* sNext = reinterpret_cast<int*>(sMeta + a.max_terms);               // next pair of each buffer's unit
+  int* sCopyDst = reinterpret_cast<int*>(sMeta + a.max_terms);           // monoclinic: copied slots (2 slot + kind)
+  int* sCopySrc = sCopyDst + a.max_copies;                               // ... and their source slots
+  int* sNext = sCopySrc + a.max_copies;                                  // next pair of each buffer's unit
   if (tid < 2) sNext[tid] = 0;
   __syncthreads();  // the only CTA-wide barrier: the groups part here
   int nch_eff = 0;
@@ -2176,7 +2219,7 @@ __global__ void __launch_bounds__(896, 1) kc_ws(KcArgs a, int nct) {
   const int64_t nunits = nrows * nch_eff;
   if (tid < nct) {
     // ---------------- compute group ----------------
-    int k = 0, loaded = -1;
+    int k = 0, loaded = -1, nblk = 0, ncopy = 0;
     double gpre = 0.0;  // this thread's G entry of the next row (prefetched)
     const int lane = tid & 31;
     // the previous unit, whose copy the compute warps join once their own slices are done
@@ -2188,15 +2231,20 @@ __global__ void __launch_bounds__(896, 1) kc_ws(KcArgs a, int nct) {
       const int ls = lx * a.lenY[iy];
       const int n9 = 9 * ls;
       const int64_t ls0 = a.LSb[is];
-      const int item = tid;
-      const bool active = item < n9;
+      const bool active = tid < n9;
       int c = 0, ks = 0, d = 0;
-      if (active) {
-        c = item / (3 * ls);
-        const int rem = item % (3 * ls);
+      if (active && MONO) {  // entries grouped by kind: block first, then off
+        const int g = tid / ls;
+        ks = tid - g * ls;
+        c = kKindC[g];
+        d = kKindD[g];
+      } else if (active) {
+        c = tid / (3 * ls);
+        const int rem = tid % (3 * ls);
         ks = rem / 3;
         d = rem % 3;
       }
+      const int item = active ? c * 3 * ls + 3 * ks + d : tid;  // the entry's place in a slice (output order)
       const int cd = c * 3 + d;
       const bool block_type = ((c == 2) == (d == 2));
       const int offa = block_type ? 0 : 1, offb = block_type ? 3 : 2;
@@ -2225,16 +2273,28 @@ __global__ void __launch_bounds__(896, 1) kc_ws(KcArgs a, int nct) {
           }
         }
         first_unit_of_row = false;
-        // the chunk's terms (loaded once when the plan has one chunk)
-        const int tb = a.ck_term[ch], nterm = a.ck_term[ch + 1] - tb;
+        // the chunk's terms (loaded once when the plan has one chunk); monoclinic
+        // plates: the block kind's source terms, the off kind's, and the copies
+        const int tb = MONO ? a.ck_sterm[ch] : a.ck_term[ch];
+        const int nterm = (MONO ? a.ck_sterm[ch + 1] : a.ck_term[ch + 1]) - tb;
         if (loaded != ch) {
           if (loaded >= 0) named_bar_sync(kBarCompute, nct);  // nobody still reads the previous chunk's terms
           for (int q = tid; q < nterm; q += nct) {
-            const int t = tb + q, m = a.ckt_cfg[t];
-            const size_t qi = ((size_t)a.ckt_rep[t] * a.ncfg + m) * 4;
+            const int t = tb + q, m = MONO ? a.cks_cfg[t] : a.ckt_cfg[t];
+            const size_t qi = ((size_t)(MONO ? a.cks_rep[t] : a.ckt_rep[t]) * a.ncfg + m) * 4;
 #pragma unroll
             for (int j = 0; j < 4; ++j) sQ[4 * (size_t)q + j] = a.q[qi + j];
-            sMeta[q] = make_int2(2 * a.ckt_slot[t] + (a.ckt_first[t] ? 1 : 0), m);
+            sMeta[q] = MONO ? make_int2(2 * a.cks_slot[t] + (a.cks_first[t] ? 1 : 0), m)
+                            : make_int2(2 * a.ckt_slot[t] + (a.ckt_first[t] ? 1 : 0), m);
+          }
+          if (MONO) {
+            nblk = a.ck_nblk[ch];
+            const int cb = a.ck_copy[ch];
+            ncopy = a.ck_copy[ch + 1] - cb;
+            for (int q = tid; q < ncopy; q += nct) {
+              sCopyDst[q] = a.ckc_dst[cb + q];
+              sCopySrc[q] = a.ckc_src[cb + q];
+            }
           }
           named_bar_sync(kBarCompute, nct);
           loaded = ch;
@@ -2244,7 +2304,9 @@ __global__ void __launch_bounds__(896, 1) kc_ws(KcArgs a, int nct) {
           const double* g = sG + ks * 9;
           int cur = -1;
           double pa = 0.0, pb = 0.0, p11 = 0.0, p12 = 0.0, p21 = 0.0, p22 = 0.0;
-          for (int t = 0; t < nterm; ++t) {
+          const int t_begin = (MONO && !block_type) ? nblk : 0;
+          const int t_end = (MONO && block_type) ? nblk : nterm;
+          for (int t = t_begin; t < t_end; ++t) {
             const int2 meta = sMeta[t];
             const int m = meta.y;
             if (m != cur) {
@@ -2286,6 +2348,13 @@ __global__ void __launch_bounds__(896, 1) kc_ws(KcArgs a, int nct) {
               v = fma(Q[3], p22, v);
             }
             *dst = v;
+          }
+          if (MONO) {  // slots that share this kind's Q terms with a source slot
+            const int kind = block_type ? 0 : 1;
+            for (int q = 0; q < ncopy; ++q) {
+              const int dk = sCopyDst[q];
+              if ((dk & 1) == kind) S[(size_t)(dk >> 1) * a.slice_stride + item] = S[(size_t)sCopySrc[q] * a.slice_stride + item];
+            }
           }
         }
         if (tid == 0) sNext[b] = 0;  // nobody takes pairs of buffer b until FULL[b] completes
@@ -2643,6 +2712,15 @@ static lam_status ensure_device(Plan& P) {
     UP(L, D->ckt_cfg, P.ckt_cfg);
     UP(L, D->ckt_rep, P.ckt_rep);
     UP(L, D->ckt_first, P.ckt_first);
+    UP(L, D->ck_sterm, P.ck_sterm);
+    UP(L, D->ck_nblk, P.ck_nblk);
+    UP(L, D->cks_slot, P.cks_slot);
+    UP(L, D->cks_cfg, P.cks_cfg);
+    UP(L, D->cks_rep, P.cks_rep);
+    UP(L, D->cks_first, P.cks_first);
+    UP(L, D->ck_copy, P.ck_copy);
+    UP(L, D->ckc_dst, P.ckc_dst);
+    UP(L, D->ckc_src, P.ckc_src);
     UP(L, D->ply_M, P.ply_M);
     UP(L, D->ply_dM, P.ply_dM);
     UP(L, D->mat_C, P.mat_C);
@@ -2777,6 +2855,16 @@ static KcArgs kc_args(const Plan& P, double* values) {
   k.conditional = 0;
   k.shellP = D.shellP;
   k.shell_pmax = D.shell_pmax;
+  k.ck_sterm = D.ck_sterm;
+  k.ck_nblk = D.ck_nblk;
+  k.cks_slot = D.cks_slot;
+  k.cks_cfg = D.cks_cfg;
+  k.cks_rep = D.cks_rep;
+  k.cks_first = D.cks_first;
+  k.ck_copy = D.ck_copy;
+  k.ckc_dst = D.ckc_dst;
+  k.ckc_src = D.ckc_src;
+  k.max_copies = kcs_max_copies(P);
   return k;
 }
 
@@ -2822,7 +2910,8 @@ static int kcw_copy_threads(const Plan& P) { return 896 - kcs_block(P); }
 static size_t kcw_smem(const Plan& P) {
   int slots = 1;
   for (int v : P.ck_nslot) slots = std::max(slots, v);
-  return (2 * (size_t)slots + 1) * kcs_stride(P) * sizeof(double) + (size_t)kcs_max_terms(P) * (32 + 8) + 16 + 16;
+  return (2 * (size_t)slots + 1) * kcs_stride(P) * sizeof(double) + (size_t)kcs_max_terms(P) * (32 + 8) +
+         (size_t)kcs_max_copies(P) * 8 + 16 + 16;
 }
 static bool kcw_fits(const Plan& P) {
   return kcs_block(P) + 64 <= 896 && kcw_smem(P) <= (size_t)P.dev->smem_optin;
@@ -4824,7 +4913,8 @@ __global__ void __launch_bounds__(256) ka_batch(const KaLocalArgs* __restrict__ 
 
 struct BatchKcArgs {
   const KcArgs* kc;           // per instance
-  const int64_t* row_prefix;  // rows of the instances in work order, n + 1
+  const int64_t* row_prefix;  // work items (blocks of rows_per_item rows) of the instances in work order, n + 1
+  int rows_per_item;          // consecutive in-plane rows of one instance per work item
   const int* order;           // work order -> instance
   const int* mono;            // per instance: monoclinic
   int n;
@@ -4836,7 +4926,7 @@ struct BatchKcArgs {
 // counter until none are left. DF = true: double-float slices; DF = false and
 // COND = true: the FP64 re-pass of the flagged instances only; DF = false and
 // COND = false: FP64 for every instance. MONO = true when every instance is
-// monoclinic (the general form is exact for the others too).
+// monoclinic; otherwise each row takes its instance's form.
 template <bool MONO, bool DF, bool COND = true>
 __global__ void __maxnreg__(64) kc_batch(BatchKcArgs b) {
   extern __shared__ double sm[];
@@ -4850,10 +4940,18 @@ __global__ void __maxnreg__(64) kc_batch(BatchKcArgs b) {
     if (g >= total) break;
     const int k = find_slot(b.row_prefix, b.n, g);
     const int inst = b.order[k];
+    const int64_t r0 = (g - b.row_prefix[k]) * b.rows_per_item;
+    const int64_t r1 = min(r0 + b.rows_per_item, b.kc[inst].ns);
     if (!DF && COND && b.flags[2 * inst] == 0) continue;
     int emax = 0;
     bool bad = false;
-    kcs_row<MONO, false, DF>(b.kc[inst], g - b.row_prefix[k], sm, emax, bad);
+    // each instance in the form its single-plan assembly takes (bitwise equal results)
+    for (int64_t r = r0; r < r1; ++r) {
+      if (MONO || b.mono[inst])
+        kcs_row<true, false, DF>(b.kc[inst], r, sm, emax, bad);
+      else
+        kcs_row<false, false, DF>(b.kc[inst], r, sm, emax, bad);
+    }
     if (DF) {
       emax = __reduce_max_sync(0xffffffffu, emax);
       const bool any_bad = __any_sync(0xffffffffu, bad);
@@ -4891,7 +4989,7 @@ struct lam_batch {
   int64_t total_elems = 0;
   lam::KcArgs* d_kc = nullptr;
   lam::KcArgs* h_kc = nullptr;    // pinned host copy (value pointers change per call)
-  int64_t* d_row_prefix = nullptr;
+  int64_t* d_row_prefix[3] = {nullptr, nullptr, nullptr};  // work items of 1, 2 and 4 rows
   int* d_order = nullptr;
   int* d_mono = nullptr;
   int* d_flags = nullptr;
@@ -4903,7 +5001,8 @@ struct lam_batch {
   int n_sm = 1, max_ctas = 1;
   // tuning and graph
   int ctas_per_sm = 0;
-  double tuned_ms[4] = {0, 0, 0, 0};
+  int rows_per_item = 0;
+  double tuned_ms[12] = {};
   cudaStream_t capture_stream = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<double*> last_values;
@@ -4933,7 +5032,8 @@ static bool same_mesh(const Plan& a, const Plan& b) {
 
 // The persistent sequence: memsets, Eq. Q, Gram blocks, double-float combine,
 // exponent check, conditional FP64 combine.
-static lam_status batch_launch(lam_batch& B, int ctas_per_sm, cudaStream_t s) {
+constexpr int kBatchRows[3] = {1, 2, 4};  // rows per work item tried by the autotuner
+static lam_status batch_launch(lam_batch& B, int ctas_per_sm, int rows_index, cudaStream_t s) {
   const int n = (int)B.persistent.size();
   if (n == 0) return LAM_OK;
   LAM_CUDA(cudaMemsetAsync(B.d_flags, 0, 2 * n * sizeof(int), s));
@@ -4947,7 +5047,8 @@ static lam_status batch_launch(lam_batch& B, int ctas_per_sm, cudaStream_t s) {
   LAM_CUDA(cudaGetLastError());
   BatchKcArgs b{};
   b.kc = B.d_kc;
-  b.row_prefix = B.d_row_prefix;
+  b.row_prefix = B.d_row_prefix[rows_index];
+  b.rows_per_item = kBatchRows[rows_index];
   b.order = B.d_order;
   b.mono = B.d_mono;
   b.n = n;
@@ -5083,7 +5184,8 @@ lam_status lam_batch_create(lam_batch** out, lam_plan* const* plans, int32_t n_p
   const int n = (int)B->persistent.size();
   std::vector<lam::KbArgs> kb(n);
   std::vector<lam::KcArgs> kc(n);
-  std::vector<int64_t> pair_prefix(n + 1, 0), row_prefix(n + 1, 0);
+  std::vector<int64_t> pair_prefix(n + 1, 0);
+  std::vector<std::vector<int64_t>> row_prefix(3, std::vector<int64_t>(n + 1, 0));
   std::vector<int> order(n), mono(n);
   for (int k = 0; k < n; ++k) {
     const int i = B->persistent[k];
@@ -5113,7 +5215,8 @@ lam_status lam_batch_create(lam_batch** out, lam_plan* const* plans, int32_t n_p
     order[k] = k;
     mono[k] = P.monoclinic ? 1 : 0;
     B->all_mono = B->all_mono && P.monoclinic;
-    row_prefix[k + 1] = row_prefix[k] + P.ns;
+    for (int r = 0; r < 3; ++r)
+      row_prefix[r][k + 1] = row_prefix[r][k] + (P.ns + lam::kBatchRows[r] - 1) / lam::kBatchRows[r];
     B->kc_block = std::max(B->kc_block, lam::kcs_block(P));
     B->kc_smem = std::max(B->kc_smem, lam::kcs_smem(P));
   }
@@ -5123,7 +5226,7 @@ lam_status lam_batch_create(lam_batch** out, lam_plan* const* plans, int32_t n_p
   BCHECK(lam::batch_upload(*B, &B->d_ka, ka.data(), ka.size()));
   BCHECK(lam::batch_upload(*B, &B->d_elem_prefix, elem_prefix.data(), elem_prefix.size()));
   BCHECK(lam::batch_upload(*B, &B->d_kc, kc.data(), kc.size()));
-  BCHECK(lam::batch_upload(*B, &B->d_row_prefix, row_prefix.data(), row_prefix.size()));
+  for (int r = 0; r < 3; ++r) BCHECK(lam::batch_upload(*B, &B->d_row_prefix[r], row_prefix[r].data(), row_prefix[r].size()));
   BCHECK(lam::batch_upload(*B, &B->d_order, order.data(), order.size()));
   BCHECK(lam::batch_upload(*B, &B->d_mono, mono.data(), mono.size()));
   std::vector<int> zeros(2 * std::max(n, 1), 0);
@@ -5210,32 +5313,37 @@ lam_status lam_batch_assemble(lam_batch* B, double* const* d_values, void* strea
     LAM_CUDA(cudaMemcpyAsync(B->d_kc, B->h_kc, n * sizeof(lam::KcArgs), cudaMemcpyHostToDevice, s));
   }
   if (n > 0 && B->ctas_per_sm == 0) {
-    // autotune: one full sequence per candidate, after a warm-up
-    if ((st = lam::batch_launch(*B, 1, s)) != LAM_OK) return st;
+    // autotune: one full sequence per candidate (CTAs per SM x rows per work
+    // item), after a warm-up
+    if ((st = lam::batch_launch(*B, 1, 0, s)) != LAM_OK) return st;
     cudaEvent_t e0, e1;
     LAM_CUDA(cudaEventCreate(&e0));
     LAM_CUDA(cudaEventCreate(&e1));
     double best = 1e300;
-    for (int c = 1; c <= B->max_ctas; ++c) {
-      LAM_CUDA(cudaEventRecord(e0, s));
-      if ((st = lam::batch_launch(*B, c, s)) != LAM_OK) return st;
-      LAM_CUDA(cudaEventRecord(e1, s));
-      LAM_CUDA(cudaEventSynchronize(e1));
-      float ms = 0.0f;
-      LAM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-      B->tuned_ms[c - 1] = ms;
-      if (ms < best) {
-        best = ms;
-        B->ctas_per_sm = c;
+    int best_r = 0;
+    for (int r = 0; r < 3; ++r)
+      for (int c = 1; c <= B->max_ctas; ++c) {
+        LAM_CUDA(cudaEventRecord(e0, s));
+        if ((st = lam::batch_launch(*B, c, r, s)) != LAM_OK) return st;
+        LAM_CUDA(cudaEventRecord(e1, s));
+        LAM_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        LAM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        B->tuned_ms[r * 4 + c - 1] = ms;
+        if (ms < best) {
+          best = ms;
+          B->ctas_per_sm = c;
+          best_r = r;
+        }
       }
-    }
+    B->rows_per_item = lam::kBatchRows[best_r];
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     // capture the tuned sequence on a stream of the batch's own
     LAM_CUDA(cudaStreamCreateWithFlags(&B->capture_stream, cudaStreamNonBlocking));
     cudaGraph_t graph = nullptr;
     LAM_CUDA(cudaStreamBeginCapture(B->capture_stream, cudaStreamCaptureModeThreadLocal));
-    st = lam::batch_launch(*B, B->ctas_per_sm, B->capture_stream);
+    st = lam::batch_launch(*B, B->ctas_per_sm, best_r, B->capture_stream);
     cudaError_t ce = cudaStreamEndCapture(B->capture_stream, &graph);
     if (st != LAM_OK) return st;
     if (ce != cudaSuccess) {
@@ -5269,7 +5377,8 @@ lam_status lam_batch_get_info(const lam_batch* B, lam_batch_info* info) {
   info->n_persistent = (int32_t)B->persistent.size();
   info->ctas_per_sm = B->ctas_per_sm;
   info->graph = B->exec ? 1 : 0;
-  for (int k = 0; k < 4; ++k) info->tuned_ms[k] = B->tuned_ms[k];
+  info->rows_per_item = B->rows_per_item;
+  for (int k = 0; k < 12; ++k) info->tuned_ms[k] = B->tuned_ms[k];
   return LAM_OK;
 }
 

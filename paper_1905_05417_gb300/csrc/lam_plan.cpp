@@ -544,6 +544,7 @@ static lam_status build_classes(Plan& P) {
   }
   double scale[4] = {0, 0, 0, 0};
   for (size_t k = 0; k < P.host_q.size(); ++k) scale[k % 4] = std::max(scale[k % 4], std::fabs(P.host_q[k]));
+  for (int ab = 0; ab < 4; ++ab) P.q_scale[ab] = scale[ab];
   const double tol = P.class_tol;
   std::vector<int> cls_of(npairs, -1);
   std::vector<int> reps;
@@ -606,6 +607,21 @@ static lam_status build_classes(Plan& P) {
 // that fit in shared memory). A uniform stack is one chunk; uneven plies, where
 // almost every pair is its own class, give chunks of a few plies.
 // ---------------------------------------------------------------------------
+// Two classes agree on the Q terms (a, b) of one kind: the same configurations,
+// and those Q values equal (to class_tol of the largest |Q| of the same term).
+static bool same_q_kind(const Plan& P, int cu, int cv, int a, int b) {
+  if (P.cls_cfgs[cu] != P.cls_cfgs[cv]) return false;
+  const int nc = (int)P.cfg_mat.size();
+  const double* qu = &P.host_q[(size_t)P.cls_rep[cu] * nc * 4];
+  const double* qv = &P.host_q[(size_t)P.cls_rep[cv] * nc * 4];
+  for (int m : P.cls_cfgs[cu])
+    for (int ab : {a, b}) {
+      const double x = qu[m * 4 + ab], y = qv[m * 4 + ab];
+      if (P.class_tol == 0.0 ? x != y : std::fabs(x - y) > P.class_tol * P.q_scale[ab]) return false;
+    }
+  return true;
+}
+
 static void build_chunks_with(Plan& P, int slots) {
   P.ck_it.clear();
   P.ck_term.clear();
@@ -614,6 +630,15 @@ static void build_chunks_with(Plan& P, int slots) {
   P.ckt_cfg.clear();
   P.ckt_rep.clear();
   P.ckt_first.clear();
+  P.ck_sterm.clear();
+  P.ck_nblk.clear();
+  P.cks_slot.clear();
+  P.cks_cfg.clear();
+  P.cks_rep.clear();
+  P.cks_first.clear();
+  P.ck_copy.clear();
+  P.ckc_dst.clear();
+  P.ckc_src.clear();
   P.pair_slot.assign(P.nnz_t, 0);
   P.kc_slots = slots;
   std::vector<int> slot_of(P.ncls, -1), members;
@@ -636,6 +661,45 @@ static void build_chunks_with(Plan& P, int slots) {
     }
     P.ck_term.push_back(t0);
     P.ck_nslot.push_back((int)members.size());
+    // Monoclinic plates: an entry (c, d) with c, d both in-plane or both z meets
+    // Q_11 and Q_22 only (its "block" kind), the others Q_12 and Q_21 only ("off"
+    // kind). Slots whose classes agree on a kind's Q terms have equal slices for
+    // that kind's entries: only the first of them (its source) is computed, the
+    // others are copied from it. (Q_11, Q_22 are symmetric in the thickness pair,
+    // so mirror pairs share their block slices; Q_12, Q_21 of a pair inside one
+    // element do not depend on the element's thickness, so same-type pairs of
+    // plies of one configuration share their off slices.)
+    const int ns_ = (int)members.size();
+    std::vector<int> src_b(ns_), src_o(ns_);
+    for (int u = 0; u < ns_; ++u) {
+      src_b[u] = src_o[u] = u;
+      for (int v = 0; v < u && src_b[u] == u; ++v)
+        if (src_b[v] == v && same_q_kind(P, members[v], members[u], 0, 3)) src_b[u] = v;
+      for (int v = 0; v < u && src_o[u] == u; ++v)
+        if (src_o[v] == v && same_q_kind(P, members[v], members[u], 1, 2)) src_o[u] = v;
+    }
+    P.ck_sterm.push_back((int)P.cks_slot.size());
+    P.ck_copy.push_back((int)P.ckc_dst.size());
+    for (int kind = 0; kind < 2; ++kind) {
+      const std::vector<int>& src = kind == 0 ? src_b : src_o;
+      std::vector<char> seen2(ns_, 0);
+      int n = 0;
+      for (auto& t : tm)  // already sorted by configuration
+        if (src[t[1]] == t[1]) {
+          P.cks_cfg.push_back(t[0]);
+          P.cks_slot.push_back(t[1]);
+          P.cks_rep.push_back(P.cls_rep[t[2]]);
+          P.cks_first.push_back(seen2[t[1]] ? 0 : 1);
+          seen2[t[1]] = 1;
+          ++n;
+        }
+      if (kind == 0) P.ck_nblk.push_back(n);
+      for (int u = 0; u < ns_; ++u)
+        if (src[u] != u) {
+          P.ckc_dst.push_back(2 * u + kind);
+          P.ckc_src.push_back(src[u]);
+        }
+    }
     (void)it1;
     for (int u : members) slot_of[u] = -1;
     members.clear();
@@ -667,6 +731,8 @@ static void build_chunks_with(Plan& P, int slots) {
   close((int)P.nt);
   P.ck_it.push_back((int)P.nt);
   P.ck_term.push_back((int)P.ckt_slot.size());
+  P.ck_sterm.push_back((int)P.cks_slot.size());
+  P.ck_copy.push_back((int)P.ckc_dst.size());
 }
 
 void build_chunks(Plan& P) {
@@ -694,6 +760,15 @@ void build_chunks(Plan& P) {
   P.ckt_cfg.clear();
   P.ckt_rep.clear();
   P.ckt_first.clear();
+  P.ck_sterm.clear();
+  P.ck_nblk.clear();
+  P.cks_slot.clear();
+  P.cks_cfg.clear();
+  P.cks_rep.clear();
+  P.cks_first.clear();
+  P.ck_copy.clear();
+  P.ckc_dst.clear();
+  P.ckc_src.clear();
   P.pair_slot.assign(P.nnz_t, 0);
 }
 
@@ -946,6 +1021,8 @@ lam_status lam_plan_get_info(const lam_plan* plan, lam_plan_info* info) {
   info->combine_chunks = (int32_t)P.ck_nslot.size();
   info->shell = P.shell ? 1 : 0;
   info->arith = P.arith;
+  info->combine_terms = (int32_t)P.ckt_slot.size();
+  info->combine_source_terms = (int32_t)P.cks_slot.size();
   return LAM_OK;
 }
 

@@ -291,10 +291,17 @@ static size_t ka_smem(const Plan& P) {
   b += (size_t)(nls * (nls + 1) / 2) * 2;
   return (b + 15) & ~(size_t)15;
 }
+// K-d: point values of the in-plane element, and the element's weighted
+// thickness values (most pieces of a thickness element x points x functions x 2)
+static size_t kd_tw(const Plan& P) {
+  int mp = 1;
+  for (size_t e = 0; e + 1 < P.piece_begin.size(); ++e) mp = std::max(mp, P.piece_begin[e + 1] - P.piece_begin[e]);
+  return (size_t)mp * P.nqt * (P.t.p + 1) * 2 * sizeof(double);
+}
 static size_t kd_smem(const Plan& P) {
   const int nqs = P.nqu * P.nqv, nls = ka_nls(P);
-  if (P.shell) return (size_t)nqs * nls * 4 * sizeof(double) + (size_t)nqs * 16 * sizeof(double);
-  return (size_t)nqs * nls * 3 * sizeof(double) + (size_t)nqs * 8 * sizeof(double);
+  if (P.shell) return (size_t)nqs * nls * 4 * sizeof(double) + (size_t)nqs * 16 * sizeof(double) + kd_tw(P);
+  return (size_t)nqs * nls * 3 * sizeof(double) + (size_t)nqs * 8 * sizeof(double) + kd_tw(P);
 }
 // K-a of a general extrusion in FP64: shell_points plus the gradient parts u and w u
 static size_t ka_shell64_smem(const Plan& P) {
@@ -2501,6 +2508,19 @@ __global__ void __launch_bounds__(256) kd_standard(KdArgs a) {
   const int npairs = nl * (nl + 1) / 2;
   const int fx = ip.firstU[ex], fy = ip.firstV[ey], ft = a.firstT[et];
   const int pc0 = a.piece_begin[et], pc1 = a.piece_begin[et + 1];
+  // the element's thickness values weighted by their Gauss weights, per
+  // (piece, point, function): w_t T and w_t T' (one product fewer per 3D point
+  // and pair side than weighting inside the point loop)
+  double* tw = qd + (size_t)nqs * NQ;
+  const int ntw = (pc1 - pc0) * a.nqt * a.q1;
+  for (int k = threadIdx.x; k < ntw; k += blockDim.x) {
+    const int pcg = k / a.q1;  // (pc - pc0) * nqt + g
+    const double w = a.wT[(size_t)pc0 * a.nqt + pcg];
+    const double* tb = a.tabT + ((size_t)pc0 * a.nqt * a.q1 + k) * 2;
+    tw[2 * k] = w * tb[0];
+    tw[2 * k + 1] = w * tb[1];
+  }
+  __syncthreads();
   for (int t = threadIdx.x; t < npairs; t += blockDim.x) {
     int li = 0, rem = t;
     while (rem >= nl - li) {
@@ -2521,23 +2541,24 @@ __global__ void __launch_bounds__(256) kd_standard(KdArgs a) {
         const double* B = phi + ((size_t)qs * nls + lsj) * NV;
         const double* dq = qd + (size_t)qs * NQ;
         const double ws = dq[WQ];
+        const double wa0 = ws * A[0], wa1 = ws * A[1], wa2 = ws * A[2];  // the in-plane weight, once per point
         for (int g = 0; g < a.nqt; ++g) {
+          const double* tt = tw + ((size_t)(pc - pc0) * a.nqt + g) * a.q1 * 2;  // weighted thickness values
           const double* tb = a.tabT + ((size_t)pc * a.nqt + g) * a.q1 * 2;
-          const double w = ws * a.wT[(size_t)pc * a.nqt + g];
-          const double Ti = tb[2 * lti], dTi = tb[2 * lti + 1], Tj = tb[2 * ltj], dTj = tb[2 * ltj + 1];
+          const double Ti = tt[2 * lti], dTi = tt[2 * lti + 1], Tj = tb[2 * ltj], dTj = tb[2 * ltj + 1];
           double a0, a1, a2, b0, b1, b2;
           if (SHELL) {
             const double si = dTi * A[3], sj = dTj * B[3];
-            a0 = w * (Ti * A[0] + si * dq[6]);
-            a1 = w * (Ti * A[1] + si * dq[7]);
-            a2 = w * (Ti * A[2] + si * dq[8]);
-            b0 = Tj * B[0] + sj * dq[6];
-            b1 = Tj * B[1] + sj * dq[7];
-            b2 = Tj * B[2] + sj * dq[8];
+            a0 = ws * fma(Ti, A[0], si * dq[6]);
+            a1 = ws * fma(Ti, A[1], si * dq[7]);
+            a2 = ws * fma(Ti, A[2], si * dq[8]);
+            b0 = fma(Tj, B[0], sj * dq[6]);
+            b1 = fma(Tj, B[1], sj * dq[7]);
+            b2 = fma(Tj, B[2], sj * dq[8]);
           } else {
-            a0 = w * A[0] * Ti;
-            a1 = w * A[1] * Ti;
-            a2 = w * A[2] * dTi;
+            a0 = wa0 * Ti;
+            a1 = wa1 * Ti;
+            a2 = wa2 * dTi;
             b0 = B[0] * Tj;
             b1 = B[1] * Tj;
             b2 = B[2] * dTj;

@@ -1830,7 +1830,12 @@ __device__ __forceinline__ void df_dot(const float2* __restrict__ E, const float
 // chunk of thickness rows). `sm` is the CTA's dynamic shared memory; emax and
 // bad accumulate the double-float pass's range checks.
 template <bool MONO, bool CHUNKED, bool DF, bool SHELL = false>
-__device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm, int& emax, bool& bad) {
+// pcache (FP64 monoclinic rows only, may be NULL): 2 * n_cfg * blockDim.x doubles
+// of this CTA's own, which receive the thread's P (p_a, p_b) of every
+// configuration once per row; the chunks read them back instead of forming P
+// again (a row of an uneven stack meets all configurations in each of its chunks).
+__device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm, int& emax, bool& bad,
+                                        double* pcache = nullptr) {
   static_assert(!(SHELL && MONO), "a general extrusion couples every block");
   const int nthr = blockDim.x, tid = threadIdx.x;
   double* slices = sm;  // slots x stride (the G row first)
@@ -1898,6 +1903,22 @@ __device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm,
     }
   }
   const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
+  const bool use_pcache = SPLIT && pcache != nullptr;
+  if (use_pcache && active) {
+    for (int m = 0; m < a.ncfg; ++m) {  // the same fused multiply-adds as below, stored once
+      const double* E = a.cfgE + (size_t)m * 81 + cd * 9;
+      double pa, pb;
+      if (block_type) {
+        pa = fma(E[4], g[4], fma(E[3], g[3], fma(E[1], g[1], E[0] * g[0])));
+        pb = E[8] * g[8];
+      } else {
+        pa = fma(E[5], g[5], E[2] * g[2]);
+        pb = fma(E[7], g[7], E[6] * g[6]);
+      }
+      pcache[(size_t)(2 * m) * nthr + tid] = pa;
+      pcache[(size_t)(2 * m + 1) * nthr + tid] = pb;
+    }
+  }
   for (int ch = 0; ch < a.nchunk; ++ch) {
     int it0 = a.ck_it[ch], it1 = a.ck_it[ch + 1];
     if (CHUNKED) {
@@ -2015,6 +2036,9 @@ __device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm,
               p12 = Pp[pref.o12];
               p21 = Pp[pref.o21];
               p22 = Pp[27];
+            } else if (use_pcache) {
+              pa = pcache[(size_t)(2 * m) * nthr + tid];
+              pb = pcache[(size_t)(2 * m + 1) * nthr + tid];
             } else if (MONO) {  // the fused multiply-adds of kc_ws, in its order (bitwise equal results)
               if (block_type) {
                 pa = fma(E[4], g[4], fma(E[3], g[3], fma(E[1], g[1], E[0] * g[0])));
@@ -4941,6 +4965,8 @@ struct BatchKcArgs {
   int n;
   unsigned long long* counter;
   int* flags;                 // per instance: FP64 re-pass flag, largest exponent
+  double* pcache;             // per CTA: 2 * pcache_cfg * blockDim.x doubles (kcs_row's P of a row)
+  int pcache_cfg;             // most configurations of an instance
 };
 
 // Persistent combine: CTAs take (instance, in-plane row) items from an atomic
@@ -4967,11 +4993,12 @@ __global__ void __maxnreg__(64) kc_batch(BatchKcArgs b) {
     int emax = 0;
     bool bad = false;
     // each instance in the form its single-plan assembly takes (bitwise equal results)
+    double* pc = b.pcache + (size_t)blockIdx.x * 2 * b.pcache_cfg * blockDim.x;
     for (int64_t r = r0; r < r1; ++r) {
       if (MONO || b.mono[inst])
-        kcs_row<true, false, DF>(b.kc[inst], r, sm, emax, bad);
+        kcs_row<true, false, DF>(b.kc[inst], r, sm, emax, bad, pc);
       else
-        kcs_row<false, false, DF>(b.kc[inst], r, sm, emax, bad);
+        kcs_row<false, false, DF>(b.kc[inst], r, sm, emax, bad, pc);
     }
     if (DF) {
       emax = __reduce_max_sync(0xffffffffu, emax);
@@ -5015,6 +5042,8 @@ struct lam_batch {
   int* d_mono = nullptr;
   int* d_flags = nullptr;
   unsigned long long* d_counter = nullptr;
+  double* d_pcache = nullptr;     // kcs_row's P per (CTA, configuration, thread), L2-resident
+  int pcache_cfg = 1;
   int ka_block = 32, kc_block = 128;
   bool all_mono = true;
   bool df = true;                 // double-float only when every plan opted in (LAM_ARITH_DOUBLE_FLOAT)
@@ -5075,6 +5104,8 @@ static lam_status batch_launch(lam_batch& B, int ctas_per_sm, int rows_index, cu
   b.n = n;
   b.counter = B.d_counter;
   b.flags = B.d_flags;
+  b.pcache = B.d_pcache;
+  b.pcache_cfg = B.pcache_cfg;
   const unsigned grid = (unsigned)(ctas_per_sm * B.n_sm);
   if (!B.df) {  // FP64 for every instance
     if (B.all_mono)
@@ -5260,11 +5291,14 @@ lam_status lam_batch_create(lam_batch** out, lam_plan* const* plans, int32_t n_p
     return LAM_ERR_OOM;
   }
   std::copy(kc.begin(), kc.end(), B->h_kc);
+  for (int k = 0; k < n; ++k) B->pcache_cfg = std::max(B->pcache_cfg, kc[k].ncfg);
   B->last_values.assign(n_plans, nullptr);
   // resident CTAs per SM by registers (64 per thread) and by shared memory
   int by_regs = std::max(1, 65536 / (64 * B->kc_block));
   int by_smem = (int)(233472 / (B->kc_smem + 1024 + 16));
   B->max_ctas = std::max(1, std::min(4, std::min(by_regs, by_smem)));
+  BCHECK(lam::alloc_dev(B->allocs, &B->d_pcache,
+                        (size_t)B->max_ctas * B->n_sm * 2 * B->pcache_cfg * B->kc_block));
   if (B->ka_smem > 48 * 1024) {
     if (cudaFuncSetAttribute(lam::ka_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->ka_smem) !=
             cudaSuccess ||

@@ -530,10 +530,11 @@ def run_sweep(args):
 def run_large(args, L, dev, flush, peak, peak_kind, world):
     """The Lagrange Q2 96 x 96 plate with 64 plies [0/90]_32 (14.4 M DOFs,
     2.73e9 stored entries, 21.8 GB of values, int64 row pointers): split and
-    standard assembly."""
+    standard assembly (--large-n-el sets the in-plane elements per direction)."""
     import torch
     import workloads as W
-    lam = W.lagrange_plate()
+    n_el = args.large_n_el
+    lam = W.lagrange_plate(n_el=n_el)
     plan = L.Plan.from_laminate(lam)
     nnz = plan.nnz
     values = torch.empty(nnz, dtype=torch.float64, device=dev)
@@ -562,14 +563,16 @@ def run_large(args, L, dev, flush, peak, peak_kind, world):
     std_ms = a.elapsed_time(b)
     kc_ms = pr["combine"]["ms"] / steps
     kc_bytes = 8 * nnz + 72 * plan.info["nnz_inplane"]
-    out = {"workload": "Lagrange Q2 96x96 unit square, [0/90]_32 (64 plies), Lagrange thickness",
+    traffic = (recorded_traffic("kc_ws_lagrange_q2_96x96_64plies.md", "kcw_copy_pairs+kc_ws")
+               if n_el == 96 else None)
+    out = {"workload": f"Lagrange Q2 {n_el}x{n_el} unit square, [0/90]_32 (64 plies), Lagrange thickness",
            "value": aggregate_throughput(nnz, world, ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
            "nnz": nnz, "step_hbm_frac": 8 * nnz / (ms / 1e3) / 1e9 / peak,
            "kernels_ms_per_step": {k: pr[k]["ms"] / steps for k in L.KERNEL_KINDS if pr[k]["launches"]},
            "standard_ms": std_ms, "speedup_split_vs_standard": std_ms / ms,
            "roofline": {"bound": "hbm", "achieved": kc_bytes / (kc_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-                        "frac": kc_bytes / (kc_ms / 1e3) / 1e9 / peak, "traffic": None, "kernel": "kc_ws",
-                        "peak_kind": f"{peak_kind} copy bandwidth"}}
+                        "frac": kc_bytes / (kc_ms / 1e3) / 1e9 / peak, "traffic": traffic, "kernel": "kc_ws",
+                        "bytes_per_launch": kc_bytes, "peak_kind": f"{peak_kind} copy bandwidth"}}
     plan.close()
     del values
     torch.cuda.empty_cache()
@@ -622,8 +625,8 @@ def run_shell(args, L, dev, flush, peak, peak_kind, world):
            "kernels_ms_per_step": {k: pr[k]["ms"] / steps for k in L.KERNEL_KINDS if pr[k]["launches"]},
            "standard_ms": std_ms, "speedup_split_vs_standard": None if std_ms is None else std_ms / ms,
            "roofline": {"bound": "hbm", "achieved": kc_bytes / (kc_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-                        "frac": kc_bytes / (kc_ms / 1e3) / 1e9 / peak, "traffic": None, "kernel": "kc_ws",
-                        "peak_kind": f"{peak_kind} copy bandwidth"}}
+                        "frac": kc_bytes / (kc_ms / 1e3) / 1e9 / peak, "traffic": traffic, "kernel": "kc_ws",
+                        "bytes_per_launch": kc_bytes, "peak_kind": f"{peak_kind} copy bandwidth"}}
     plan.close()
     del values
     torch.cuda.empty_cache()
@@ -861,6 +864,7 @@ def main(argv=None):
     ap.add_argument("--adjoint-steps", type=int, default=20, help="timed lam_adjoint calls (0 = skip)")
     ap.add_argument("--batch-steps", type=int, default=5, help="timed lam_batch_assemble calls (0 = skip)")
     ap.add_argument("--large-steps", type=int, default=5, help="timed split assemblies of the Lagrange plate (0 = skip)")
+    ap.add_argument("--large-n-el", type=int, default=96, help="in-plane elements per direction of the Lagrange plate")
     ap.add_argument("--shell-steps", type=int, default=5, help="timed split assemblies of the curved shell (0 = skip)")
     ap.add_argument("--sweep", action="store_true", help="the paper's layer sweep (one element through the thickness)")
     ap.add_argument("--sweep-n", type=int, default=16, help="in-plane elements per direction in the sweep")

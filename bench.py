@@ -97,6 +97,9 @@ def aggregate_throughput(units_per_rank: int, world: int, seconds_max: float) ->
 
 
 # ----------------------------------------------------------------------------- peaks and profiles
+NOMINAL_HBM_GBS = 8000.0  # GB300 HBM3e, nominal (~8 TB/s)
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -820,6 +823,7 @@ def run_lam(args):
         "parallelism": "replicas" if world > 1 else "single GPU",
         "plan": {"n_configs": info["n_configs"], "n_classes": info["n_classes"]},
         "step_hbm_frac": 8 * nnz / (ms / 1e3) / 1e9 / peak,
+        "step_hbm_frac_of_nominal": {"peak_gbs": NOMINAL_HBM_GBS, "frac": 8 * nnz / (ms / 1e3) / 1e9 / NOMINAL_HBM_GBS},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "kernel": "kc_ws", "bytes_per_launch": kc_bytes,
                      "ms_per_launch": kc_ms, "launches_per_call": kc["launches"] // args.steps,

@@ -74,7 +74,7 @@ struct Device {
       *cks_first = nullptr, *ck_copy = nullptr, *ckc_dst = nullptr, *ckc_src = nullptr;
   float2* qdf = nullptr;  // float pairs of q
 
-  double* EG = nullptr;  // element Gram blocks: n_el x 9 x pairs
+  double* EG = nullptr;  // element Gram blocks: n_el x pairs x 9
   double* Grow = nullptr;  // assembled Gram blocks of every in-plane pair: nnz_s x 9 (FP64 combine)
   int* kc_flag = nullptr;      // streaming combine: FP64 re-pass flag, then the largest exponent
   float2* cfgEdf = nullptr;    // float pairs of cfgE
@@ -767,8 +767,9 @@ __global__ void __launch_bounds__(256) ka_inplane(KaArgs a) {
 
 // ---------------------------------------------------------------------------
 // K-a (single launch): one CTA per in-plane element; the Gram blocks of its
-// unordered local pairs (li <= lj) go to EG[(e * 9 + ab) * npl + pair], pair
-// numbered row-major over the upper triangle. The combine gathers them per row
+// unordered local pairs (li <= lj) go to EG[(e * npl + pair) * 9 + ab], pair
+// numbered row-major over the upper triangle (a pair's 9 entries contiguous,
+// so a row's gather reads them in whole sectors). The combine gathers them per row
 // in a fixed element order, so the sums are deterministic without colouring.
 // ---------------------------------------------------------------------------
 struct KaLocalArgs {
@@ -957,7 +958,7 @@ __device__ __forceinline__ void ka_elem(const KaLocalArgs& a, int e, double* sm)
   const float* phf = reinterpret_cast<const float*>(phi);
   const float* pwf = reinterpret_cast<const float*>(phiw);
   const int npl = nls * (nls + 1) / 2;
-  double* out = a.EG + (size_t)e * 9 * npl;
+  double* out = a.EG + (size_t)e * npl * 9;
   for (int t = threadIdx.x; t < npl; t += blockDim.x) {
     int li = 0, rem = t;
     while (rem >= nls - li) {
@@ -991,7 +992,7 @@ __device__ __forceinline__ void ka_elem(const KaLocalArgs& a, int e, double* sm)
       long long b = __double_as_longlong(df_to_double(hs, ls));
       const int sc = kq + kd * ((k / 3 < 2 ? 1 : 0) + (k % 3 < 2 ? 1 : 0));
       if (b & 0x7FFFFFFFFFFFFFFFll) b += (long long)sc * (1ll << 52);  // times 2^sc, exact
-      out[(size_t)k * npl + t] = __longlong_as_double(b);
+      out[(size_t)t * 9 + k] = __longlong_as_double(b);
     }
   }
 }
@@ -1634,9 +1635,9 @@ __device__ __forceinline__ double gram_pair_sum(const KcArgs& a, int ix, int iy,
         const int ey = ey0 + q / nex, ex = ex0 + q % nex;
         const int fy = a.firstV[ey], fx = a.firstU[ex];
         const int li = (iy - fy) * a.nlx + (ix - fx), lj = (jy - fy) * a.nlx + (jx - fx);
-        const size_t e9 = ((size_t)ey * a.nel_u + ex) * 9;
-        v[j] = li <= lj ? a.EG[(e9 + ab) * a.npl + upper_pair(li, lj, a.nls)]
-                        : a.EG[(e9 + ba) * a.npl + upper_pair(lj, li, a.nls)];
+        const size_t ep = ((size_t)ey * a.nel_u + ex) * a.npl;
+        v[j] = li <= lj ? a.EG[(ep + upper_pair(li, lj, a.nls)) * 9 + ab]
+                        : a.EG[(ep + upper_pair(lj, li, a.nls)) * 9 + ba];
       }
     }
     acc = ((acc + v[0]) + v[1]) + v[2];
@@ -1695,11 +1696,11 @@ __global__ void __launch_bounds__(1024, 2) kc_combine(KcArgs a) {
         for (int ex = ex0; ex <= ex1; ++ex) {
           const int fx = a.firstU[ex];
           const int li = (iy - fy) * a.nlx + (ix - fx), lj = (jy - fy) * a.nlx + (jx - fx);
-          const size_t e9 = ((size_t)ey * a.nel_u + ex) * 9;
+          const size_t ep = ((size_t)ey * a.nel_u + ex) * a.npl;
           if (li <= lj)
-            acc += a.EG[(e9 + ab) * a.npl + upper_pair(li, lj, a.nls)];
+            acc += a.EG[(ep + upper_pair(li, lj, a.nls)) * 9 + ab];
           else
-            acc += a.EG[(e9 + ba) * a.npl + upper_pair(lj, li, a.nls)];
+            acc += a.EG[(ep + upper_pair(lj, li, a.nls)) * 9 + ba];
         }
       }
       Gs[item] = acc;
@@ -2437,7 +2438,7 @@ __global__ void __launch_bounds__(896, 1) kc_ws(KcArgs a, int nct) {
 // as ka_local. Point values (Eq. gradient: g = (dR/dx, dR/dy, R) and w|DF| g
 // at every Gauss point) by inplane_points, then thread <-> unordered local
 // pair (li <= lj): G_ab = sum_q (w|DF| g_a^li)(q) g_b^lj(q), 9 FP64 fused
-// multiply-adds per point, into EG[(e * 9 + ab) * npl + pair].
+// multiply-adds per point, into EG[(e * npl + pair) * 9 + ab].
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void ka_elem64(const KaLocalArgs& a, int e, double* sm) {
   const InplaneArgs& ip = a.ip;
@@ -2448,7 +2449,7 @@ __device__ __forceinline__ void ka_elem64(const KaLocalArgs& a, int e, double* s
   const int ex = e % ip.nel_u, ey = e / ip.nel_u;
   inplane_points(ip, ex, ey, phi, phiw, qd);
   const int npl = nls * (nls + 1) / 2;
-  double* out = a.EG + (size_t)e * 9 * npl;
+  double* out = a.EG + (size_t)e * npl * 9;
   for (int t = threadIdx.x; t < npl; t += blockDim.x) {
     int li = 0, rem = t;
     while (rem >= nls - li) {
@@ -2474,7 +2475,7 @@ __device__ __forceinline__ void ka_elem64(const KaLocalArgs& a, int e, double* s
       acc[8] = fma(a2, b2, acc[8]);
     }
 #pragma unroll
-    for (int q = 0; q < 9; ++q) out[(size_t)q * npl + t] = acc[q];
+    for (int q = 0; q < 9; ++q) out[(size_t)t * 9 + q] = acc[q];
   }
 }
 
@@ -3232,11 +3233,11 @@ __global__ void __launch_bounds__(1024) adj_gather(AdjGatherArgs a) {
       for (int ex = ex0; ex <= ex1; ++ex) {
         const int fx = a.firstU[ex];
         const int li = (iy - fy) * a.nlx + (ix - fx), lj = (jy - fy) * a.nlx + (jx - fx);
-        const size_t e9 = ((size_t)ey * a.nel_u + ex) * 9;
+        const size_t ep = ((size_t)ey * a.nel_u + ex) * a.npl;
         if (li <= lj)
-          acc += a.EG[(e9 + ab) * a.npl + upper_pair(li, lj, a.nls)];
+          acc += a.EG[(ep + upper_pair(li, lj, a.nls)) * 9 + ab];
         else
-          acc += a.EG[(e9 + ba) * a.npl + upper_pair(lj, li, a.nls)];
+          acc += a.EG[(ep + upper_pair(lj, li, a.nls)) * 9 + ba];
       }
     }
     a.G[(ls0 + ks) * 9 + ab] = acc;

@@ -124,15 +124,15 @@ def kernel_source_sha(kernel: str) -> str:
     return h.hexdigest()
 
 
-def recorded_traffic(summary: str, kernel: str):
-    """DRAM bytes per launch recorded by an ncu capture of `kernel`, if that
-    kernel's source has not changed since; else None."""
+def recorded_traffic(summary: str, kernel: str, key: str = "traffic_bytes_per_launch"):
+    """DRAM bytes per launch recorded (under `key`) by an ncu capture of
+    `kernel`, if that kernel's source has not changed since; else None."""
     path = os.path.join(ROOT, "profiles", summary)
     try:
         text = open(path).read()
     except OSError:
         return None
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m = re.search(r"(?m)^" + key + r":\s*([0-9.eE+]+)", text)
     s = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
     if not m or not s or s.group(1) != kernel_source_sha(kernel):
         return None
@@ -422,7 +422,7 @@ def run_batch(args, L, dev, flush, peak, peak_kind, world):
     with lam_assemble_split for comparison."""
     import torch
     import workloads as W
-    lams = W.batch_laminates()
+    lams = W.batch_laminates(count=args.batch_n)
     plans = [L.Plan.from_laminate(l) for l in lams]
     nnz = sum(p.nnz for p in plans)
     values = [torch.empty(p.nnz, dtype=torch.float64, device=dev) for p in plans]
@@ -452,8 +452,9 @@ def run_batch(args, L, dev, flush, peak, peak_kind, world):
     seq_ms = a.elapsed_time(b)
     info = batch.info
     achieved = 8 * nnz / (ms / 1e3) / 1e9
-    out = {"workload": "256 laminates from default_rng(517): quadratic B-spline meshes {16,24,32,48}^2 on the "
-                       "unit square, 8..64 plies of thickness U[0.0005, 0.002], angles {0, +-45, 90}, 1..4 materials",
+    out = {"workload": f"{args.batch_n} laminates from default_rng(517): quadratic B-spline meshes {{16,24,32,48}}^2 "
+                       "on the unit square, 8..64 plies of thickness U[0.0005, 0.002], angles {0, +-45, 90}, "
+                       "1..4 materials",
            "metric": "stored entries assembled per second", "value": aggregate_throughput(nnz, world, ms / 1e3),
            "unit": UNIT, "ms_per_step": ms, "steps": steps, "nnz_total": nnz, "n_plans": len(plans),
            "n_meshes": info["n_meshes"], "n_persistent": info["n_persistent"],
@@ -589,7 +590,7 @@ def run_shell(args, L, dev, flush, peak, peak_kind, world):
     per configuration, the combine) and one standard assembly."""
     import torch
     import workloads as W
-    lam = W.shell_plate()
+    lam = W.shell_plate(n_el=args.shell_n_el)
     plan = L.Plan.from_laminate(lam)
     nnz = plan.nnz
     values = torch.empty(nnz, dtype=torch.float64, device=dev)
@@ -621,8 +622,11 @@ def run_shell(args, L, dev, flush, peak, peak_kind, world):
     kc_ms = pr["combine"]["ms"] / steps
     # the combine writes K and reads P of every configuration (36 doubles per pair and configuration)
     kc_bytes = 8 * nnz + 8 * 36 * plan.info["nnz_inplane"] * plan.info["n_configs"]
+    traffic = (recorded_traffic("kc_ws_curved_p3_64x64_48plies.md", "kcw_copy_pairs+kc_ws",
+                                "shell_traffic_bytes_per_launch") if args.shell_n_el == 64 else None)
     out = {"workload": "curved shell: the curved plate's map on the surface z = 0.05 sin(pi xi) sin(pi eta), "
-                       "extruded along a = (0.05, -0.03, 1), cubic B-spline 64x64, 48 plies [0/45/-45/90]_6s",
+                       f"extruded along a = (0.05, -0.03, 1), cubic B-spline {args.shell_n_el}x{args.shell_n_el}, "
+                       "48 plies [0/45/-45/90]_6s",
            "value": aggregate_throughput(nnz, world, ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
            "nnz": nnz, "step_hbm_frac": 8 * nnz / (ms / 1e3) / 1e9 / peak,
            "kernels_ms_per_step": {k: pr[k]["ms"] / steps for k in L.KERNEL_KINDS if pr[k]["launches"]},
@@ -869,6 +873,8 @@ def main(argv=None):
     ap.add_argument("--batch-steps", type=int, default=5, help="timed lam_batch_assemble calls (0 = skip)")
     ap.add_argument("--large-steps", type=int, default=5, help="timed split assemblies of the Lagrange plate (0 = skip)")
     ap.add_argument("--large-n-el", type=int, default=96, help="in-plane elements per direction of the Lagrange plate")
+    ap.add_argument("--batch-n", type=int, default=256, help="laminates in the batch (the first n of the seeded 256)")
+    ap.add_argument("--shell-n-el", type=int, default=64, help="in-plane elements per direction of the curved shell")
     ap.add_argument("--shell-steps", type=int, default=5, help="timed split assemblies of the curved shell (0 = skip)")
     ap.add_argument("--sweep", action="store_true", help="the paper's layer sweep (one element through the thickness)")
     ap.add_argument("--sweep-n", type=int, default=16, help="in-plane elements per direction in the sweep")

@@ -76,6 +76,10 @@ struct Device {
 
   double* EG = nullptr;  // element Gram blocks: n_el x pairs x 9
   double* Grow = nullptr;  // assembled Gram blocks of every in-plane pair: nnz_s x 9 (FP64 combine)
+  // per in-plane pair, the element blocks its G sums (kg_rows): gsum_off[gsum_begin[pr] ..
+  // gsum_begin[pr + 1]) = 2 x (EG position of the block) + 1 if read transposed; null if not built
+  int* gsum_begin = nullptr;
+  int* gsum_off = nullptr;
   int* kc_flag = nullptr;      // streaming combine: FP64 re-pass flag, then the largest exponent
   float2* cfgEdf = nullptr;    // float pairs of cfgE
   double* cfgCb = nullptr;     // Appendix A bracket tensors per configuration
@@ -1646,6 +1650,29 @@ __device__ __forceinline__ double gram_pair_sum(const KcArgs& a, int ix, int iy,
   return acc;
 }
 
+// gram_pair_sum from the pair's precomputed list of element-block positions
+// (same blocks, same order, same grouping of the adds: the same bits).
+__device__ __forceinline__ double gram_pair_sum_tab(const double* __restrict__ EG, const int* __restrict__ gb,
+                                                    const int* __restrict__ go, int64_t pr, int ab) {
+  const int ba = (ab % 3) * 3 + ab / 3;
+  const int b0 = __ldg(gb + pr), b1 = __ldg(gb + pr + 1);
+  double acc = 0.0;
+  for (int q0 = b0; q0 < b1; q0 += 4) {
+    double v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      v[j] = 0.0;
+      if (q0 + j < b1) {
+        const int o = __ldg(go + q0 + j);
+        v[j] = EG[(o >> 1) + ((o & 1) ? ba : ab)];
+      }
+    }
+    acc = ((acc + v[0]) + v[1]) + v[2];
+    acc = acc + v[3];
+  }
+  return acc;
+}
+
 // P of a general extrusion for entry (c, d) of the in-plane pair (i_s, k_s-th
 // neighbour j_s): pairs with j_s >= i_s hold it (blocks at 0, 9, 18, 27); the
 // others read the mirror pair transposed, P^ij_(alpha beta)[c][d] =
@@ -2163,14 +2190,18 @@ __device__ __forceinline__ bool kcw_chunk(const KcArgs& a, int ch, int& it0, int
 // The assembled in-plane Gram blocks of every in-plane pair, G_ab(i_s, k_s) =
 // sum over the shared elements (fixed row-major element order) of the element
 // blocks of K-a, into G[(LSb[i_s] + k_s) * 9 + ab]: CTA per in-plane row,
-// thread per (k_s, ab). FP64 sums, the order of the combine's own gather.
-__global__ void __launch_bounds__(512, 4) kg_rows(KcArgs a, double* __restrict__ G) {
+// thread per (k_s, ab). FP64 sums, the order of the combine's own gather; the
+// blocks' positions come from the plan's per-pair table (gb, go) when it was
+// built, else from the index arithmetic of gram_pair_sum.
+__global__ void __launch_bounds__(512, 4) kg_rows(KcArgs a, double* __restrict__ G, const int* __restrict__ gb,
+                                                  const int* __restrict__ go) {
   const int64_t is = blockIdx.x;
   const int ix = (int)(is % a.nx), iy = (int)(is / a.nx);
   const int lx = a.lenX[ix], n9 = 9 * lx * a.lenY[iy];
   const int64_t ls0 = a.LSb[is];
   for (int it = threadIdx.x; it < n9; it += blockDim.x) {
-    const double acc = gram_pair_sum(a, ix, iy, lx, it / 9, it % 9);
+    const double acc = go ? gram_pair_sum_tab(a.EG, gb, go, ls0 + it / 9, it % 9)
+                          : gram_pair_sum(a, ix, iy, lx, it / 9, it % 9);
     G[ls0 * 9 + it] = acc;
   }
 }
@@ -2627,6 +2658,39 @@ __global__ void __launch_bounds__(256) kd_standard(KdArgs a) {
 // ---------------------------------------------------------------------------
 // Device set-up
 // ---------------------------------------------------------------------------
+
+// The element blocks each in-plane pair's G sums, in the order of the row
+// gathers (shared elements row-major in (ey, ex)): per pair, 2 x (position of
+// the block in EG) + 1 when the pair is read transposed (li > lj). False when
+// a position or the table length would not fit an int (kg_rows then finds the
+// blocks itself).
+static bool pair_sum_table(const Plan& P, std::vector<int>& gb, std::vector<int>& go) {
+  const int nlx = P.u.p + 1, nls = ka_nls(P), npl = ka_npl(P);
+  if ((int64_t)P.u.nel * P.v.nel * npl * 9 * 2 >= (int64_t)INT32_MAX) return false;
+  auto upper = [](int a, int b, int n) { return a * n - a * (a - 1) / 2 + (b - a); };
+  gb.assign((size_t)P.nnz_s + 1, 0);
+  go.clear();
+  for (int64_t is = 0; is < P.ns; ++is) {
+    const int ix = (int)(is % P.u.n), iy = (int)(is / P.u.n);
+    const int lx = P.u.len[ix], ly = P.v.len[iy];
+    for (int ks = 0; ks < lx * ly; ++ks) {
+      const int jx = P.u.lo[ix] + ks % lx, jy = P.v.lo[iy] + ks / lx;
+      const int ex0 = std::max(P.u.elo[ix], P.u.elo[jx]), ex1 = std::min(P.u.ehi[ix], P.u.ehi[jx]);
+      const int ey0 = std::max(P.v.elo[iy], P.v.elo[jy]), ey1 = std::min(P.v.ehi[iy], P.v.ehi[jy]);
+      for (int ey = ey0; ey <= ey1; ++ey)
+        for (int ex = ex0; ex <= ex1; ++ex) {
+          const int fy = P.v.first[ey], fx = P.u.first[ex];
+          const int li = (iy - fy) * nlx + (ix - fx), lj = (jy - fy) * nlx + (jx - fx);
+          const int64_t e = (int64_t)ey * P.u.nel + ex;
+          const int64_t pos = (e * npl + (li <= lj ? upper(li, lj, nls) : upper(lj, li, nls))) * 9;
+          go.push_back((int)(2 * pos + (li <= lj ? 0 : 1)));
+        }
+      if (go.size() >= (size_t)INT32_MAX) return false;
+      gb[(size_t)(P.LSb[is] + ks) + 1] = (int)go.size();
+    }
+  }
+  return true;
+}
 static lam_status ensure_device(Plan& P) {
   int cur = 0;
   LAM_CUDA(cudaGetDevice(&cur));
@@ -2689,6 +2753,13 @@ static lam_status ensure_device(Plan& P) {
     if ((st = alloc_dev(L, &D->Grow, (size_t)P.nnz_s * 9)) != LAM_OK) {
       free_device(P);
       return st;
+    }
+    if (!P.shell) {
+      std::vector<int> gb, go;
+      if (pair_sum_table(P, gb, go)) {
+        UP(L, D->gsum_begin, gb);
+        UP(L, D->gsum_off, go);
+      }
     }
     double* fl = nullptr;
     if ((st = alloc_dev(L, &fl, 1)) != LAM_OK) {
@@ -2969,7 +3040,8 @@ static lam_status launch_kc64(const Plan& P, const KcArgs& k, cudaStream_t s) {
     // row (once per assembly: the host-output path's slabs follow on the same
     // stream); profiled with the in-plane kernels
     cudaEvent_t eg = prof_begin(const_cast<Plan&>(P), s);
-    kg_rows<<<(unsigned)P.ns, std::min(512, std::max(64, ((9 * max_len_s(P) + 31) / 32) * 32)), 0, s>>>(k, P.dev->Grow);
+    kg_rows<<<(unsigned)P.ns, std::min(512, std::max(64, ((9 * max_len_s(P) + 31) / 32) * 32)), 0, s>>>(
+        k, P.dev->Grow, P.dev->gsum_begin, P.dev->gsum_off);
     LAM_CUDA(cudaGetLastError());
     prof_end(const_cast<Plan&>(P), LAM_KERNEL_INPLANE, 1, s, eg);
   }

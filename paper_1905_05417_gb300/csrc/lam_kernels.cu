@@ -5051,6 +5051,12 @@ template <bool MONO, bool DF, bool COND = true>
 __global__ void __maxnreg__(64) kc_batch(BatchKcArgs b) {
   extern __shared__ double sm[];
   __shared__ unsigned long long s_item;
+  // MONO: the current instance's arguments, in shared memory: the rows' CSR stores
+  // cannot alias them there, so they need no reloading and no registers across the
+  // stores (mixed batches read them from global memory, as their larger kernel
+  // spills more with the copy)
+  __shared__ KcArgs s_kc;
+  int cur = -1;
   const int64_t total = b.row_prefix[b.n];
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(b.counter, 1ull);
@@ -5060,15 +5066,24 @@ __global__ void __maxnreg__(64) kc_batch(BatchKcArgs b) {
     if (g >= total) break;
     const int k = find_slot(b.row_prefix, b.n, g);
     const int inst = b.order[k];
+    if (MONO && inst != cur) {  // every thread has left the previous item (the barriers above)
+      const int* src = reinterpret_cast<const int*>(b.kc + inst);
+      int* dst = reinterpret_cast<int*>(&s_kc);
+      for (int w = threadIdx.x; w < (int)(sizeof(KcArgs) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+      __syncthreads();
+      cur = inst;
+    }
     const int64_t r0 = (g - b.row_prefix[k]) * b.rows_per_item;
-    const int64_t r1 = min(r0 + b.rows_per_item, b.kc[inst].ns);
+    const int64_t r1 = min(r0 + b.rows_per_item, MONO ? s_kc.ns : b.kc[inst].ns);
     if (!DF && COND && b.flags[2 * inst] == 0) continue;
     int emax = 0;
     bool bad = false;
     // each instance in the form its single-plan assembly takes (bitwise equal results)
     double* pc = b.pcache + (size_t)blockIdx.x * 2 * b.pcache_cfg * blockDim.x;
     for (int64_t r = r0; r < r1; ++r) {
-      if (MONO || b.mono[inst])
+      if (MONO)
+        kcs_row<true, false, DF>(s_kc, r, sm, emax, bad, pc);
+      else if (b.mono[inst])
         kcs_row<true, false, DF>(b.kc[inst], r, sm, emax, bad, pc);
       else
         kcs_row<false, false, DF>(b.kc[inst], r, sm, emax, bad, pc);

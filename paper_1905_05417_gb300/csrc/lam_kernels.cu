@@ -1607,6 +1607,8 @@ struct KcArgs {
   const int *ck_sterm, *ck_nblk, *cks_slot, *cks_cfg, *cks_rep, *cks_first;
   const int *ck_copy, *ckc_dst, *ckc_src;
   int max_copies;
+  // per in-plane pair, the element blocks its G sums (the plan's pair-sum table; null if not built)
+  const int *gsum_begin, *gsum_off;
 };
 
 // Entries (c, d) of a monoclinic 3 x 3 block by kind: block (c and d both
@@ -1881,7 +1883,9 @@ __device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm,
   const int n9 = 9 * ls;
   const int64_t ls0 = a.LSb[is];
   // phase 0: the row's G blocks into slices[0 .. 9 ls) (a general extrusion reads P instead)
-  for (int item = tid; item < (SHELL ? 0 : n9); item += nthr) slices[item] = gram_pair_sum(a, ix, iy, lx, item / 9, item % 9);
+  for (int item = tid; item < (SHELL ? 0 : n9); item += nthr)
+    slices[item] = a.gsum_off ? gram_pair_sum_tab(a.EG, a.gsum_begin, a.gsum_off, ls0 + item / 9, item % 9)
+                              : gram_pair_sum(a, ix, iy, lx, item / 9, item % 9);
   __syncthreads();
   const bool active = tid < n9;
   int c = 0, ks = 0, d = 0;
@@ -2982,6 +2986,8 @@ static KcArgs kc_args(const Plan& P, double* values) {
   k.ckc_dst = D.ckc_dst;
   k.ckc_src = D.ckc_src;
   k.max_copies = kcs_max_copies(P);
+  k.gsum_begin = D.gsum_begin;
+  k.gsum_off = D.gsum_off;
   return k;
 }
 

@@ -1882,10 +1882,12 @@ __device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm,
   const int ls = lx * a.lenY[iy];
   const int n9 = 9 * ls;
   const int64_t ls0 = a.LSb[is];
-  // phase 0: the row's G blocks into slices[0 .. 9 ls) (a general extrusion reads P instead)
+  // phase 0: the row's G blocks into slices[0 .. 9 ls) (a general extrusion reads P instead);
+  // the double-float pass reads the pair-sum table (the FP64 form, register-bound in
+  // batches, keeps the index arithmetic: fewer registers live)
   for (int item = tid; item < (SHELL ? 0 : n9); item += nthr)
-    slices[item] = a.gsum_off ? gram_pair_sum_tab(a.EG, a.gsum_begin, a.gsum_off, ls0 + item / 9, item % 9)
-                              : gram_pair_sum(a, ix, iy, lx, item / 9, item % 9);
+    slices[item] = (DF && a.gsum_off) ? gram_pair_sum_tab(a.EG, a.gsum_begin, a.gsum_off, ls0 + item / 9, item % 9)
+                                      : gram_pair_sum(a, ix, iy, lx, item / 9, item % 9);
   __syncthreads();
   const bool active = tid < n9;
   int c = 0, ks = 0, d = 0;

@@ -458,11 +458,12 @@ def run_batch(args, L, dev, flush, peak, peak_kind, world):
            "metric": "stored entries assembled per second", "value": aggregate_throughput(nnz, world, ms / 1e3),
            "unit": UNIT, "ms_per_step": ms, "steps": steps, "nnz_total": nnz, "n_plans": len(plans),
            "n_meshes": info["n_meshes"], "n_persistent": info["n_persistent"],
-           "autotuner": {"axes": {"ctas_per_sm": [1, 2, 3, 4], "rows_per_item": [1, 2, 4]},
-                         "chosen": {"ctas_per_sm": info["ctas_per_sm"], "rows_per_item": info["rows_per_item"]},
-                         "ms": {f"{c}x{r}": round(info["tuned_ms"][ri * 4 + c - 1], 3)
-                                for ri, r in enumerate((1, 2, 4)) for c in (1, 2, 3, 4)
-                                if info["tuned_ms"][ri * 4 + c - 1] > 0}},
+           "autotuner": {"axes": {"chunk_ctas": [4, 3, 2], "rows_per_item": [1, 2, 4], "ctas_per_sm": [1, 2, 3, 4]},
+                         "chosen": {"chunk_ctas": info["chunk_ctas"], "rows_per_item": info["rows_per_item"],
+                                    "ctas_per_sm": info["ctas_per_sm"]},
+                         "ms": {f"h{h}/r{r}/c{c}": round(info["tuned_ms"][(hi * 3 + ri) * 4 + c - 1], 3)
+                                for hi, h in enumerate((4, 3, 2)) for ri, r in enumerate((1, 2, 4))
+                                for c in range(1, 5) if info["tuned_ms"][(hi * 3 + ri) * 4 + c - 1] > 0}},
            "cuda_graph": bool(info["graph"]),
            "one_plan_at_a_time_ms": seq_ms, "speedup_vs_one_at_a_time": seq_ms / ms,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

@@ -332,9 +332,14 @@ lam_status lam_adjoint(lam_plan* plan, const lam_cotangent* cotangent, double* d
  * instance, one launch the Gram blocks of every mesh, and one persistent
  * launch combines every in-plane row of every instance from an atomic work
  * queue (largest instances first). The first lam_batch_assemble times the
- * whole sequence for every pair (CTAs per SM 1..4, in-plane rows per work item
- * 1, 2 or 4), keeps the fastest, and captures it in a CUDA graph that later
- * calls replay.
+ * whole sequence for every triple (thickness-chunk depth: chunks sized for 4,
+ * 3 or 2 CTAs per SM; CTAs per SM 1..4 that the chunks leave room for;
+ * in-plane rows per work item 1, 2 or 4), keeps the fastest, and captures it in
+ * a CUDA graph that later calls replay. The chunk depth is applied to the
+ * plans themselves (their thickness rows are regrouped), so their own
+ * lam_assemble_split uses it too and gives the batch's values bit for bit;
+ * against the default grouping the values move by rounding only (a chunk
+ * shares a slice between thickness pairs whose Q agree up to rounding).
  * ------------------------------------------------------------------------- */
 typedef struct lam_batch lam_batch;
 
@@ -347,8 +352,10 @@ typedef struct {
   int32_t ctas_per_sm;     /* chosen by the autotuner, 0 before the first lam_batch_assemble */
   int32_t graph;           /* 1 once the launches are replayed from a CUDA graph */
   int32_t rows_per_item;   /* chosen by the autotuner: in-plane rows of one instance per work item */
-  double tuned_ms[12];     /* autotuner: one assembly per candidate, [r * 4 + c - 1] for c CTAs per SM and
-                              1, 2, 4 rows per item (r = 0, 1, 2); 0 = not tried */
+  int32_t chunk_ctas;      /* chosen by the autotuner: the CTAs per SM the thickness chunks are sized for */
+  double tuned_ms[36];     /* autotuner: one assembly per candidate, [(h * 3 + r) * 4 + c - 1] for chunks
+                              sized for 4, 3, 2 CTAs per SM (h = 0, 1, 2), 1, 2, 4 rows per item (r = 0, 1, 2)
+                              and c CTAs per SM; 0 = not tried */
 } lam_batch_info;
 
 /* Batch of n_plans plans (borrowed: they must outlive the batch, all on the
@@ -360,8 +367,9 @@ lam_status lam_batch_create(lam_batch** out, lam_plan* const* plans, int32_t n_p
 
 /* Assembles every instance: d_values is a HOST array of n_plans device
  * pointers, entry k receiving plan k's nnz values (the order of lam_pattern).
- * Asynchronous on `stream`, except the first call, which tunes and captures
- * the graph and returns after the device has finished. */
+ * Asynchronous on `stream`. The first call tunes and captures the graph with
+ * the device synchronised, then replays the graph on `stream` like every later
+ * call (so its values come from the configuration chosen). */
 lam_status lam_batch_assemble(lam_batch* batch, double* const* d_values, void* stream);
 
 lam_status lam_batch_get_info(const lam_batch* batch, lam_batch_info* info);

@@ -99,7 +99,7 @@ class _Cotangent(ctypes.Structure):
 class _BatchInfo(ctypes.Structure):
     _fields_ = [("n_plans", ctypes.c_int32), ("n_meshes", ctypes.c_int32), ("nnz_total", ctypes.c_int64),
                 ("n_persistent", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("graph", ctypes.c_int32),
-                ("rows_per_item", ctypes.c_int32), ("tuned_ms", ctypes.c_double * 12)]
+                ("rows_per_item", ctypes.c_int32), ("chunk_ctas", ctypes.c_int32), ("tuned_ms", ctypes.c_double * 36)]
 
 
 class _Info(ctypes.Structure):

@@ -137,6 +137,7 @@ struct Plan {
   int device_id = -1;
   bool cfg_dirty = true;         // configuration tables must be (re)uploaded
   int cfg_version = 0;           // incremented by lam_plan_update (batches check it)
+  int chunk_ctas = 0;            // CTAs per SM the thickness chunks are sized for (0: by registers)
 
   // profiler (lam_profile_*): events are cudaEvent_t, kept opaque here
   struct Pending {
@@ -175,7 +176,11 @@ inline int kcs_ctas_per_sm(const Plan& P) {
   if (n > 2048 / kcs_block(P)) n = 2048 / kcs_block(P);
   return n < 1 ? 1 : (n > 8 ? 8 : n);
 }
-inline size_t kcs_budget(const Plan& P) { return (size_t)(233472 / kcs_ctas_per_sm(P)) - 1024; }
+// shared memory a thickness chunk may use: the SM's share of the CTAs it is sized for
+inline size_t kcs_budget(const Plan& P) {
+  const int n = P.chunk_ctas > 0 ? P.chunk_ctas : kcs_ctas_per_sm(P);
+  return (size_t)(233472 / n) - 1024;
+}
 inline int kcs_stride(const Plan& P) { return 9 * max_len_s(P); }
 inline int kcs_max_terms(const Plan& P) {
   int mt = 1;

@@ -494,10 +494,13 @@ __device__ __forceinline__ void kb_pair(const KbArgs& a, int64_t pr) {
         const double* tb = a.tabT + ((size_t)pc * a.nqt + g) * a.q1 * 2;
         const double w = a.wT[(size_t)pc * a.nqt + g];
         const double Ti = tb[2 * ia], dTi = tb[2 * ia + 1], Tj = tb[2 * jb], dTj = tb[2 * jb + 1];
-        q11 += w * Ti * Tj;
-        q12 += w * Ti * dTj;
-        q21 += w * dTi * Tj;
-        q22 += w * dTi * dTj;
+        // explicit fused multiply-adds: every kernel that inlines this (the plan's
+        // K-b, the batch's) rounds alike, whatever the compiler would contract
+        const double wTi = w * Ti, wdTi = w * dTi;
+        q11 = fma(wTi, Tj, q11);
+        q12 = fma(wTi, dTj, q12);
+        q21 = fma(wdTi, Tj, q21);
+        q22 = fma(wdTi, dTj, q22);
       }
       double* o = out + a.piece_cfg[pc] * 4;
       o[0] += q11;
@@ -562,9 +565,10 @@ __device__ void shell_points(const InplaneArgs& a, int ex, int ey, double* ph, d
       for (int ly = 0; ly < nly; ++ly)
         for (int lx = 0; lx < nlx; ++lx) {
           const double w = a.weights[(size_t)(fy + ly) * a.nx + fx + lx];
-          W += w * tu[2 * lx] * tv[2 * ly];
-          W1 += w * tu[2 * lx + 1] * tv[2 * ly];
-          W2 += w * tu[2 * lx] * tv[2 * ly + 1];
+          const double wu = w * tu[2 * lx], wdu = w * tu[2 * lx + 1];  // explicit FMAs: same rounding in every kernel
+          W = fma(wu, tv[2 * ly], W);
+          W1 = fma(wdu, tv[2 * ly], W1);
+          W2 = fma(wu, tv[2 * ly + 1], W2);
         }
     }
     double A0[3] = {0.0, 0.0, 0.0}, A1[3] = {0.0, 0.0, 0.0};
@@ -640,9 +644,10 @@ __device__ void inplane_points(const InplaneArgs& a, int ex, int ey, double* phi
       for (int ly = 0; ly < nly; ++ly)
         for (int lx = 0; lx < nlx; ++lx) {
           const double w = a.weights[(size_t)(fy + ly) * a.nx + fx + lx];
-          W += w * tu[2 * lx] * tv[2 * ly];
-          W1 += w * tu[2 * lx + 1] * tv[2 * ly];
-          W2 += w * tu[2 * lx] * tv[2 * ly + 1];
+          const double wu = w * tu[2 * lx], wdu = w * tu[2 * lx + 1];  // explicit FMAs: same rounding in every kernel
+          W = fma(wu, tv[2 * ly], W);
+          W1 = fma(wdu, tv[2 * ly], W1);
+          W2 = fma(wu, tv[2 * ly + 1], W2);
         }
     }
     double J00 = 0.0, J01 = 0.0, J10 = 0.0, J11 = 0.0;
@@ -4236,9 +4241,10 @@ __global__ void __launch_bounds__(256) kp_bfree(BfreeArgs a) {
       for (int ly = 0; ly < nly; ++ly)
         for (int lx = 0; lx < nlx; ++lx) {
           const double w = ip.weights[(size_t)(fy + ly) * ip.nx + fx + lx];
-          W += w * tu[2 * lx] * tv[2 * ly];
-          W1 += w * tu[2 * lx + 1] * tv[2 * ly];
-          W2 += w * tu[2 * lx] * tv[2 * ly + 1];
+          const double wu = w * tu[2 * lx], wdu = w * tu[2 * lx + 1];  // explicit FMAs: same rounding in every kernel
+          W = fma(wu, tv[2 * ly], W);
+          W1 = fma(wdu, tv[2 * ly], W1);
+          W2 = fma(wu, tv[2 * ly + 1], W2);
         }
     }
     // DF = [dS/dxi1 | dS/dxi2 | a] (columns A0, A1, a); planar: S = (x, y, 0), a = e_z
@@ -5148,7 +5154,9 @@ struct lam_batch {
   // tuning and graph
   int ctas_per_sm = 0;
   int rows_per_item = 0;
-  double tuned_ms[12] = {};
+  int chunk_ctas = 0;             // CTAs per SM the instances' thickness chunks are sized for
+  double tuned_ms[36] = {};
+  std::vector<double*> inst_EG;   // per persistent instance: its mesh's Gram blocks
   cudaStream_t capture_stream = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<double*> last_values;
@@ -5176,9 +5184,32 @@ static bool same_mesh(const Plan& a, const Plan& b) {
          a.nqu == b.nqu && a.nqv == b.nqv;
 }
 
+// Eq. Q arguments of one instance (pointers into the plan's device tables).
+static KbArgs batch_kb_args(const Plan& P) {
+  const Device& D = *P.dev;
+  KbArgs a{};
+  a.npairs = P.nnz_t;
+  a.ncfg = (int)P.cfg_mat.size();
+  a.nqt = P.nqt;
+  a.q1 = P.t.p + 1;
+  a.tp_row = D.tp_row;
+  a.tp_col = D.tp_col;
+  a.tp_e0 = D.tp_e0;
+  a.tp_e1 = D.tp_e1;
+  a.firstT = D.firstT;
+  a.piece_begin = D.piece_begin;
+  a.piece_cfg = D.piece_cfg;
+  a.tabT = D.tabT;
+  a.wT = D.wT;
+  a.q = D.q;
+  a.qdf = D.qdf;
+  return a;
+}
+
 // The persistent sequence: memsets, Eq. Q, Gram blocks, double-float combine,
 // exponent check, conditional FP64 combine.
 constexpr int kBatchRows[3] = {1, 2, 4};  // rows per work item tried by the autotuner
+constexpr int kBatchChunkCtas[3] = {4, 3, 2};  // CTAs per SM the thickness chunks are sized for (autotuner)
 static lam_status batch_launch(lam_batch& B, int ctas_per_sm, int rows_index, cudaStream_t s) {
   const int n = (int)B.persistent.size();
   if (n == 0) return LAM_OK;
@@ -5225,6 +5256,78 @@ static lam_status batch_launch(lam_batch& B, int ctas_per_sm, int rows_index, cu
     kc_batch<false, false><<<grid, B.kc_block, B.kc_smem, s>>>(b);
   LAM_CUDA(cudaGetLastError());
   return LAM_OK;
+}
+
+// Resident combine CTAs per SM by registers (64 per thread) and by shared
+// memory (dynamic + the kernel's static variables + 1 KB reserved per CTA).
+static void batch_max_ctas(lam_batch& B) {
+  size_t stat = 0;
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, kc_batch<true, false, false>) == cudaSuccess) stat = std::max(stat, fa.sharedSizeBytes);
+  if (cudaFuncGetAttributes(&fa, kc_batch<false, false, false>) == cudaSuccess) stat = std::max(stat, fa.sharedSizeBytes);
+  if (cudaFuncGetAttributes(&fa, kc_batch<true, true>) == cudaSuccess) stat = std::max(stat, fa.sharedSizeBytes);
+  cudaGetLastError();
+  const int by_regs = std::max(1, 65536 / (64 * B.kc_block));
+  const int by_smem = (int)(233472 / (B.kc_smem + stat + 1024));
+  B.max_ctas = std::max(1, std::min(4, std::min(by_regs, by_smem)));
+}
+
+// The combine's dynamic shared memory, for every instantiation the batch may launch.
+static lam_status batch_combine_smem(lam_batch& B) {
+  const int ks = (int)B.kc_smem;
+  if (cudaFuncSetAttribute(kc_batch<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ks) != cudaSuccess ||
+      cudaFuncSetAttribute(kc_batch<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ks) != cudaSuccess ||
+      cudaFuncSetAttribute(kc_batch<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ks) != cudaSuccess ||
+      cudaFuncSetAttribute(kc_batch<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ks) != cudaSuccess ||
+      cudaFuncSetAttribute(kc_batch<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ks) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(kc_batch<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ks) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    set_error("lam_batch: combine shared memory (%zu bytes)", B.kc_smem);
+    return LAM_ERR_UNSUPPORTED;
+  }
+  return LAM_OK;
+}
+
+// Thickness chunks of every persistent instance sized for `ctas` CTAs per SM:
+// the plans' chunks are rebuilt where their budget changes and their
+// configuration tables re-uploaded (which also moves their Q buffers), then
+// the instances' arguments, the combine's shared memory and its CTA limit are
+// refreshed. The values move by rounding only: a chunk shares a slice between
+// pairs whose Q agree up to rounding, using the Q of its first such pair.
+static lam_status batch_rechunk(lam_batch& B, int ctas) {
+  const int n = (int)B.persistent.size();
+  std::vector<KbArgs> kb(n);
+  size_t smem = 0;
+  for (int k = 0; k < n; ++k) {
+    Plan& P = B.plans[B.persistent[k]]->p;
+    const size_t before = kcs_budget(P);
+    const int old = P.chunk_ctas;
+    P.chunk_ctas = ctas;
+    if (kcs_budget(P) != before) {
+      build_chunks(P);
+      if (!use_stream(P)) {  // not expected for a larger budget: keep the previous chunks
+        P.chunk_ctas = old;
+        build_chunks(P);
+      }
+      P.cfg_dirty = true;
+      const lam_status st = ensure_device(P);
+      if (st != LAM_OK) return st;
+    }
+    kb[k] = batch_kb_args(P);
+    KcArgs kc = kc_args(P, nullptr);
+    kc.EG = B.inst_EG[k];
+    kc.values = B.h_kc[k].values;
+    B.h_kc[k] = kc;
+    smem = std::max(smem, kcs_smem(P));
+  }
+  LAM_CUDA(cudaMemcpy(B.d_kb, kb.data(), n * sizeof(KbArgs), cudaMemcpyHostToDevice));
+  LAM_CUDA(cudaMemcpy(B.d_kc, B.h_kc, n * sizeof(KcArgs), cudaMemcpyHostToDevice));
+  B.kc_smem = smem;
+  batch_max_ctas(B);
+  B.chunk_ctas = ctas;
+  return batch_combine_smem(B);
 }
 
 static void batch_free(lam_batch* B) {
@@ -5339,27 +5442,11 @@ lam_status lam_batch_create(lam_batch** out, lam_plan* const* plans, int32_t n_p
     const int i = B->persistent[k];
     B->inst_slot[i] = k;
     lam::Plan& P = plans[i]->p;
-    const lam::Device& D = *P.dev;
-    lam::KbArgs& a = kb[k];
-    a = lam::KbArgs{};
-    a.npairs = P.nnz_t;
-    a.ncfg = (int)P.cfg_mat.size();
-    a.nqt = P.nqt;
-    a.q1 = P.t.p + 1;
-    a.tp_row = D.tp_row;
-    a.tp_col = D.tp_col;
-    a.tp_e0 = D.tp_e0;
-    a.tp_e1 = D.tp_e1;
-    a.firstT = D.firstT;
-    a.piece_begin = D.piece_begin;
-    a.piece_cfg = D.piece_cfg;
-    a.tabT = D.tabT;
-    a.wT = D.wT;
-    a.q = D.q;
-    a.qdf = D.qdf;
+    kb[k] = lam::batch_kb_args(P);
     pair_prefix[k + 1] = pair_prefix[k] + P.nnz_t;
     kc[k] = lam::kc_args(P, nullptr);
     kc[k].EG = mesh_EG[mesh_of[i]];
+    B->inst_EG.push_back(mesh_EG[mesh_of[i]]);
     order[k] = k;
     mono[k] = P.monoclinic ? 1 : 0;
     B->all_mono = B->all_mono && P.monoclinic;
@@ -5389,12 +5476,10 @@ lam_status lam_batch_create(lam_batch** out, lam_plan* const* plans, int32_t n_p
   std::copy(kc.begin(), kc.end(), B->h_kc);
   for (int k = 0; k < n; ++k) B->pcache_cfg = std::max(B->pcache_cfg, kc[k].ncfg);
   B->last_values.assign(n_plans, nullptr);
-  // resident CTAs per SM by registers (64 per thread) and by shared memory
-  int by_regs = std::max(1, 65536 / (64 * B->kc_block));
-  int by_smem = (int)(233472 / (B->kc_smem + 1024 + 16));
-  B->max_ctas = std::max(1, std::min(4, std::min(by_regs, by_smem)));
-  BCHECK(lam::alloc_dev(B->allocs, &B->d_pcache,
-                        (size_t)B->max_ctas * B->n_sm * 2 * B->pcache_cfg * B->kc_block));
+  lam::batch_max_ctas(*B);
+  // the P cache of every CTA the combine can ever run per SM (registers bound it, whatever the chunking)
+  const int pcache_ctas = std::max(1, std::min(4, 65536 / (64 * B->kc_block)));
+  BCHECK(lam::alloc_dev(B->allocs, &B->d_pcache, (size_t)pcache_ctas * B->n_sm * 2 * B->pcache_cfg * B->kc_block));
   if (B->ka_smem > 48 * 1024) {
     if (cudaFuncSetAttribute(lam::ka_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->ka_smem) !=
             cudaSuccess ||
@@ -5405,19 +5490,7 @@ lam_status lam_batch_create(lam_batch** out, lam_plan* const* plans, int32_t n_p
       return LAM_ERR_UNSUPPORTED;
     }
   }
-  const int ks = (int)B->kc_smem;
-  if (cudaFuncSetAttribute(lam::kc_batch<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ks) != cudaSuccess ||
-      cudaFuncSetAttribute(lam::kc_batch<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ks) != cudaSuccess ||
-      cudaFuncSetAttribute(lam::kc_batch<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ks) != cudaSuccess ||
-      cudaFuncSetAttribute(lam::kc_batch<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ks) != cudaSuccess ||
-      cudaFuncSetAttribute(lam::kc_batch<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ks) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(lam::kc_batch<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ks) !=
-          cudaSuccess) {
-    lam::set_error("lam_batch_create: combine shared memory (%zu bytes)", B->kc_smem);
-    lam::batch_free(B);
-    return LAM_ERR_UNSUPPORTED;
-  }
+  BCHECK(lam::batch_combine_smem(*B));
 #undef BCHECK
   lam::set_error("");
   *out = B;
@@ -5464,32 +5537,41 @@ lam_status lam_batch_assemble(lam_batch* B, double* const* d_values, void* strea
     LAM_CUDA(cudaMemcpyAsync(B->d_kc, B->h_kc, n * sizeof(lam::KcArgs), cudaMemcpyHostToDevice, s));
   }
   if (n > 0 && B->ctas_per_sm == 0) {
-    // autotune: one full sequence per candidate (CTAs per SM x rows per work
-    // item), after a warm-up
-    if ((st = lam::batch_launch(*B, 1, 0, s)) != LAM_OK) return st;
+    // autotune: one full sequence per candidate (thickness-chunk depth x rows
+    // per work item x CTAs per SM that the chunks leave room for), after a
+    // warm-up per chunk depth
     cudaEvent_t e0, e1;
     LAM_CUDA(cudaEventCreate(&e0));
     LAM_CUDA(cudaEventCreate(&e1));
     double best = 1e300;
-    int best_r = 0;
-    for (int r = 0; r < 3; ++r)
-      for (int c = 1; c <= B->max_ctas; ++c) {
-        LAM_CUDA(cudaEventRecord(e0, s));
-        if ((st = lam::batch_launch(*B, c, r, s)) != LAM_OK) return st;
-        LAM_CUDA(cudaEventRecord(e1, s));
-        LAM_CUDA(cudaEventSynchronize(e1));
-        float ms = 0.0f;
-        LAM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        B->tuned_ms[r * 4 + c - 1] = ms;
-        if (ms < best) {
-          best = ms;
-          B->ctas_per_sm = c;
-          best_r = r;
+    int best_h = 0, best_r = 0, best_c = 1;
+    for (int h = 0; h < 3; ++h) {
+      if ((st = lam::batch_rechunk(*B, lam::kBatchChunkCtas[h])) != LAM_OK) return st;
+      if ((st = lam::batch_launch(*B, B->max_ctas, 0, s)) != LAM_OK) return st;
+      for (int r = 0; r < 3; ++r)
+        for (int c = 1; c <= B->max_ctas; ++c) {
+          LAM_CUDA(cudaEventRecord(e0, s));
+          if ((st = lam::batch_launch(*B, c, r, s)) != LAM_OK) return st;
+          LAM_CUDA(cudaEventRecord(e1, s));
+          LAM_CUDA(cudaEventSynchronize(e1));
+          float ms = 0.0f;
+          LAM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          B->tuned_ms[(h * 3 + r) * 4 + c - 1] = ms;
+          if (ms < best) {
+            best = ms;
+            best_h = h;
+            best_r = r;
+            best_c = c;
+          }
         }
-      }
-    B->rows_per_item = lam::kBatchRows[best_r];
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (lam::kBatchChunkCtas[best_h] != B->chunk_ctas &&
+        (st = lam::batch_rechunk(*B, lam::kBatchChunkCtas[best_h])) != LAM_OK)
+      return st;
+    B->ctas_per_sm = best_c;
+    B->rows_per_item = lam::kBatchRows[best_r];
     // capture the tuned sequence on a stream of the batch's own
     LAM_CUDA(cudaStreamCreateWithFlags(&B->capture_stream, cudaStreamNonBlocking));
     cudaGraph_t graph = nullptr;
@@ -5508,9 +5590,10 @@ lam_status lam_batch_assemble(lam_batch* B, double* const* d_values, void* strea
       lam::set_error("lam_batch_assemble: graph instantiation failed: %s", cudaGetErrorString(ce));
       return LAM_ERR_CUDA;
     }
-  } else if (n > 0) {
-    LAM_CUDA(cudaGraphLaunch(B->exec, s));
   }
+  // the values of this call come from the tuned sequence (the last candidate the
+  // autotuner timed may have used another chunk depth, which moves their rounding)
+  if (n > 0) LAM_CUDA(cudaGraphLaunch(B->exec, s));
   for (int i : B->fallback)
     if ((st = lam_assemble_split(B->plans[i], d_values[i], stream)) != LAM_OK) return st;
   return LAM_OK;
@@ -5529,7 +5612,8 @@ lam_status lam_batch_get_info(const lam_batch* B, lam_batch_info* info) {
   info->ctas_per_sm = B->ctas_per_sm;
   info->graph = B->exec ? 1 : 0;
   info->rows_per_item = B->rows_per_item;
-  for (int k = 0; k < 12; ++k) info->tuned_ms[k] = B->tuned_ms[k];
+  info->chunk_ctas = B->chunk_ctas;
+  for (int k = 0; k < 36; ++k) info->tuned_ms[k] = B->tuned_ms[k];
   return LAM_OK;
 }
 

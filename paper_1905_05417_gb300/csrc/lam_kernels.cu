@@ -5155,6 +5155,7 @@ struct lam_batch {
   int ctas_per_sm = 0;
   int rows_per_item = 0;
   int chunk_ctas = 0;             // CTAs per SM the instances' thickness chunks are sized for
+  bool broken = false;            // tuning failed part-way: the launch tables may point at freed plan tables
   double tuned_ms[36] = {};
   std::vector<double*> inst_EG;   // per persistent instance: its mesh's Gram blocks
   cudaStream_t capture_stream = nullptr;
@@ -5502,6 +5503,10 @@ lam_status lam_batch_assemble(lam_batch* B, double* const* d_values, void* strea
     lam::set_error("lam_batch_assemble: NULL argument");
     return LAM_ERR_INVALID_ARG;
   }
+  if (B->broken) {
+    lam::set_error("lam_batch_assemble: an earlier call failed while tuning the batch; recreate the batch");
+    return LAM_ERR_INVALID_ARG;
+  }
   const int np = (int)B->plans.size();
   for (int i = 0; i < np; ++i) {
     if (!d_values[i]) {
@@ -5546,7 +5551,10 @@ lam_status lam_batch_assemble(lam_batch* B, double* const* d_values, void* strea
     double best = 1e300;
     int best_h = 0, best_r = 0, best_c = 1;
     for (int h = 0; h < 3; ++h) {
-      if ((st = lam::batch_rechunk(*B, lam::kBatchChunkCtas[h])) != LAM_OK) return st;
+      if ((st = lam::batch_rechunk(*B, lam::kBatchChunkCtas[h])) != LAM_OK) {
+        B->broken = true;
+        return st;
+      }
       if ((st = lam::batch_launch(*B, B->max_ctas, 0, s)) != LAM_OK) return st;
       for (int r = 0; r < 3; ++r)
         for (int c = 1; c <= B->max_ctas; ++c) {
@@ -5568,8 +5576,10 @@ lam_status lam_batch_assemble(lam_batch* B, double* const* d_values, void* strea
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (lam::kBatchChunkCtas[best_h] != B->chunk_ctas &&
-        (st = lam::batch_rechunk(*B, lam::kBatchChunkCtas[best_h])) != LAM_OK)
+        (st = lam::batch_rechunk(*B, lam::kBatchChunkCtas[best_h])) != LAM_OK) {
+      B->broken = true;
       return st;
+    }
     B->ctas_per_sm = best_c;
     B->rows_per_item = lam::kBatchRows[best_r];
     // capture the tuned sequence on a stream of the batch's own

@@ -15,6 +15,7 @@ import pytest
 import workloads as W
 
 pytestmark = pytest.mark.gpu
+LAM_ERR_INVALID_ARG = 1
 LAM_ERR_OOM = 3
 
 
@@ -106,9 +107,49 @@ def test_batch_creation_allocation_failure(L):
         vals = [torch.empty(p.nnz, dtype=torch.float64, device="cuda") for p in plans]
         b.assemble(vals)
         torch.cuda.synchronize()
-        assert all(np.array_equal(v.cpu().numpy(), r) for v, r in zip(vals, refs))
+        # the plans carry the chunk depth the batch chose: bit for bit against their own assembly,
+        # and within rounding of the matrices they gave before
+        for p, v, r in zip(plans, vals, refs):
+            own = p.assemble_split().cpu().numpy()
+            assert np.array_equal(v.cpu().numpy(), own)
+            assert np.abs(own - r).max() <= 1e-13 * np.abs(r).max()
         b.close()
         break
     assert failures >= 1
+    for p in plans:
+        p.close()
+
+
+def test_batch_tuning_allocation_failure(L):
+    """A failed allocation while the first lam_batch_assemble tunes (the plans'
+    tables are re-uploaded per chunk depth) returns LAM_ERR_OOM; the batch then
+    refuses every call (its launch tables may point at released plan tables),
+    and a batch created anew from the same plans matches them."""
+    import torch
+    rng = np.random.default_rng(5)
+    lams = [W.laminate("uneven", W.BSPLINE, 2, 4, list(rng.choice([0.0, 45.0, 90.0], 9)),
+                       rng.uniform(0.0005, 0.002, 9)),
+            W.cross_ply_plate(n_el=4, n_plies=3)]
+    plans = [L.Plan.from_laminate(x) for x in lams]
+    vals = [torch.empty(p.nnz, dtype=torch.float64, device="cuda") for p in plans]
+    b = L.Batch(plans)
+    os.environ["LAM_FAIL_ALLOC"] = "1"
+    try:
+        with pytest.raises(L.LamError) as e:
+            b.assemble(vals)
+        assert e.value.status == LAM_ERR_OOM, str(e.value)
+    finally:
+        del os.environ["LAM_FAIL_ALLOC"]
+    torch.cuda.synchronize()
+    with pytest.raises(L.LamError) as e:
+        b.assemble(vals)
+    assert e.value.status == LAM_ERR_INVALID_ARG and "recreate" in str(e.value)
+    b.close()
+    b = L.Batch(plans)
+    b.assemble(vals)
+    torch.cuda.synchronize()
+    for p, v in zip(plans, vals):
+        assert np.array_equal(v.cpu().numpy(), p.assemble_split().cpu().numpy())
+    b.close()
     for p in plans:
         p.close()

@@ -369,7 +369,10 @@ lam_status lam_batch_create(lam_batch** out, lam_plan* const* plans, int32_t n_p
  * pointers, entry k receiving plan k's nnz values (the order of lam_pattern).
  * Asynchronous on `stream`. The first call tunes and captures the graph with
  * the device synchronised, then replays the graph on `stream` like every later
- * call (so its values come from the configuration chosen). */
+ * call (so its values come from the configuration chosen). If the first call
+ * fails while tuning (e.g. LAM_ERR_OOM when re-uploading a plan's tables), the
+ * batch refuses every later call with LAM_ERR_INVALID_ARG: destroy it and
+ * create a new one (the plans stay usable). */
 lam_status lam_batch_assemble(lam_batch* batch, double* const* d_values, void* stream);
 
 lam_status lam_batch_get_info(const lam_batch* batch, lam_batch_info* info);

@@ -827,6 +827,8 @@ def run_lam(args):
         "config": config_dict(args, info["n_dof"], nnz),
         "parallelism": "replicas" if world > 1 else "single GPU",
         "plan": {"n_configs": info["n_configs"], "n_classes": info["n_classes"]},
+        "step_ms_stats": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms),
+                          "note": "this rank's timed steps; ms_per_step is their mean (max over ranks)"},
         "step_hbm_frac": 8 * nnz / (ms / 1e3) / 1e9 / peak,
         "step_hbm_frac_of_nominal": {"peak_gbs": NOMINAL_HBM_GBS, "frac": 8 * nnz / (ms / 1e3) / 1e9 / NOMINAL_HBM_GBS},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

@@ -237,10 +237,11 @@ lam_status lam_assemble_split_host(lam_plan* plan, double* h_values, void* strea
  *     rejected with LAM_ERR_UNSUPPORTED (the message gives both sizes); the
  *     64x64 cubic 48-ply plate needs about 16 MB.
  *   - The first call on a device looks up the array's device address for that
- *     device (once per device, with that device current). The address is kept
- *     for the life of the process: it does not survive cudaDeviceReset (or the
- *     destruction of the device's primary context), after which this entry
- *     point must not be called again in that process.
+ *     device (once per device, with that device current); make that first
+ *     call before any stream capture. The address is kept for the life of the
+ *     process: it does not survive cudaDeviceReset (or the destruction of the
+ *     device's primary context), after which this entry point must not be
+ *     called again in that process.
  *   - All calls on a device share the one array and it keeps the last call's
  *     contents: calls that overlap on the GPU (two streams, or two host
  *     threads) race and corrupt each other's results, so serialise them.

@@ -175,6 +175,8 @@ typedef struct {
                                    whose classes agree on the Q terms of an entry kind (Q_11, Q_22 or
                                    Q_12, Q_21) with an earlier slot of its chunk is copied from it, counted
                                    once per kind (so up to 2 combine_terms) */
+  int32_t combine_block_terms; /* ... of the source terms, those of the block kind (Q_11, Q_22: entries
+                                  (c, d) with c and d both in-plane or both z); the rest are off kind */
 } lam_plan_info;
 
 typedef struct lam_plan lam_plan;

@@ -108,7 +108,7 @@ class _Info(ctypes.Structure):
                 ("n_classes", ctypes.c_int32), ("monoclinic", ctypes.c_int32), ("n_pieces", ctypes.c_int32),
                 ("combine_streaming", ctypes.c_int32), ("combine_chunks", ctypes.c_int32), ("shell", ctypes.c_int32),
                 ("arith", ctypes.c_int32), ("combine_terms", ctypes.c_int32),
-                ("combine_source_terms", ctypes.c_int32)]
+                ("combine_source_terms", ctypes.c_int32), ("combine_block_terms", ctypes.c_int32)]
 
 
 _lib = None

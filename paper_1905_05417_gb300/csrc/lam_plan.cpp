@@ -1023,6 +1023,9 @@ lam_status lam_plan_get_info(const lam_plan* plan, lam_plan_info* info) {
   info->arith = P.arith;
   info->combine_terms = (int32_t)P.ckt_slot.size();
   info->combine_source_terms = (int32_t)P.cks_slot.size();
+  int64_t nblk = 0;
+  for (int v : P.ck_nblk) nblk += v;
+  info->combine_block_terms = (int32_t)nblk;
   return LAM_OK;
 }
 

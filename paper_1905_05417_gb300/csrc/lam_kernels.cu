@@ -1894,14 +1894,25 @@ __device__ __forceinline__ void kcs_row(const KcArgs& a, int64_t is, double* sm,
     slices[item] = (DF && a.gsum_off) ? gram_pair_sum_tab(a.EG, a.gsum_begin, a.gsum_off, ls0 + item / 9, item % 9)
                                       : gram_pair_sum(a, ix, iy, lx, item / 9, item % 9);
   __syncthreads();
-  const bool active = tid < n9;
+  // entries grouped by kind (SPLIT): block kind (5 ls entries) first, then off
+  // kind (4 ls); where the CTA has room the block kind is padded to whole warps,
+  // so that no warp runs both kinds' term loops (entry e of thread tid)
+  bool active = tid < n9;
+  int e = tid;
+  if (SPLIT) {
+    const int nb = 5 * ls, pb = (nb + 31) & ~31;
+    if (pb + 4 * ls <= nthr) {
+      active = tid < pb ? tid < nb : tid - pb < 4 * ls;
+      e = tid < pb ? tid : nb + (tid - pb);
+    }
+  }
   int c = 0, ks = 0, d = 0;
   double g[9];
   float gh[9], gl[9];
   if (active) {
-    if (SPLIT) {  // entries grouped by kind, as in kc_ws
-      const int gk = tid / ls;
-      ks = tid - gk * ls;
+    if (SPLIT) {
+      const int gk = e / ls;
+      ks = e - gk * ls;
       c = kKindC[gk];
       d = kKindD[gk];
     } else {
